@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Power-flow throughput benchmark of libgbpf on GB300.
+
+Metric: power-flow solves per second at max |mismatch| <= 1e-8 p.u.  A step is
+one pass of the whole hot path over one batch: admittance assembly, B'/B''
+assembly, level-scheduled LDL^T factorisation, and the fast-decoupled
+iteration (nodal mismatch + level-scheduled substitutions) to tolerance, all
+through the C ABI ``pf_run_to_tol``.  The symbolic analysis (ordering,
+elimination tree, levels) runs once per topology before timing and is
+reported separately.
+
+Workloads (seeded synthetic grids, see paper_1811_02512_gb300/gridgen.py):
+  plain10k   one 10,000-bus pruned-Delaunay grid, FP64 (default)
+  batch10k   the same topology with 1,024 cases (512 load scenarios, 512
+             single-branch outages) in one launch
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbpf|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "power-flow solves/s at 1e-8 pu mismatch"
+UNIT = "PF/s"
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbpf", choices=["gbpf", "reference"])
+    ap.add_argument("--workload", default="plain10k", choices=["plain10k", "batch10k"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ workloads
+
+def make_workload(name):
+    from paper_1811_02512_gb300 import gridgen
+    base = gridgen.config(1)
+    if name == "plain10k":
+        return base, 1, None, None
+    sc = gridgen.scenarios(base, n_load=512, n_outage=512)
+    return base, sc.ncase, sc.load_scale, sc.outage
+
+
+def workload_precision(name, override):
+    if override:
+        return override
+    return "fp64" if name == "plain10k" else "fp32"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline model
+
+def algorithmic_bytes_per_half_iteration(info, nbus, nnz_y, prec_bytes):
+    """Streaming bytes of one fast-decoupled half-iteration of one case:
+    mismatch (V, theta read, Y values + pattern read, rhs written) plus one
+    LDL^T solve pair (forward + backward: L values read twice, row/column
+    indices read once each, D read once, vector read and written)."""
+    n_mean = 0.5 * (info.n[0] + info.n[1])
+    nnzl_mean = 0.5 * (info.nnz_l[0] + info.nnz_l[1])
+    mismatch = 16 * nbus + nnz_y * (8 + 8 + 4) + 4 * (nbus + 1) + 16 * nbus
+    solve = 2 * nnzl_mean * prec_bytes + nnzl_mean * (4 + 4 + 4) + n_mean * prec_bytes \
+        + 16 * n_mean
+    return mismatch + solve
+
+
+# ------------------------------------------------------------------ oracle baseline
+
+def _oracle_job(args):
+    import numpy as np  # noqa: F401
+    from oracle import oracle as O
+    from paper_1811_02512_gb300 import gridgen
+    case_ids, deadline = args
+    base = gridgen.config(1)
+    sc = None
+    if case_ids is not None and any(c is not None for c in case_ids):
+        sc = gridgen.scenarios(base, n_load=512, n_outage=512)
+    done = 0
+    t0 = time.perf_counter()
+    for cid in case_ids:
+        c = base if cid is None else gridgen.apply_scenario(base, sc, cid)
+        rc, *_ = O.power_flow(c, O.FDPF, tol=TOL)
+        done += 1 if rc == O.OK else 0
+        if time.perf_counter() > deadline:
+            break
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline(workload, sample_s, ncase):
+    """The oracle as it stands on the host cores: one process per core (spawn),
+    each solving cases of the workload (ordering + factor + FDPF, FP64) until
+    the sample budget is used."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    per = max(1, int(sample_s / 0.06 / 2))
+    jobs = []
+    for w in range(cores):
+        if workload == "plain10k":
+            ids = [None] * per
+        else:
+            ids = [(w + cores * k) % ncase for k in range(per)]
+        jobs.append(ids)
+    t0 = time.perf_counter()
+    deadline = time.perf_counter() + sample_s
+    with ctx.Pool(cores) as pool:
+        out = pool.map(_oracle_job, [(j, deadline) for j in jobs])
+    wall = time.perf_counter() - t0
+    solved = sum(o[0] for o in out)
+    return {"value": solved / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{solved} {'10k-bus' if workload == 'plain10k' else 'batch10k'} cases "
+                      f"(FP64 FDPF incl. ordering/symbolic/factor) across {cores} processes "
+                      f"in {wall:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores as the reference arm."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1811_02512_gb300 import gridgen  # noqa: F401
+    base, ncase, _, _ = make_workload(args.workload)
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, 1.0, ncase)
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(args.workload, max(2.0, 60.0 / max(1, args.steps)), ncase)
+        vals.append(last["value"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"kind": "oracle", "cores": last["cores"], "sample": last["sample"],
+                             "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1811_02512_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1811_02512_gb300 import gbpf
+
+    base, ncase, load_scale, outage = make_workload(args.workload)
+    prec_name = workload_precision(args.workload, args.precision)
+    prec = gbpf.PF_FP64 if prec_name == "fp64" else gbpf.PF_FP32
+    t0 = time.perf_counter()
+    g = gbpf.Grid(base)
+    analyze_ms = (time.perf_counter() - t0) * 1e3
+    g.set_cases(ncase, load_scale, outage)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=TOL, max_iter=200)
+    vm = torch.zeros((ncase, base.n), dtype=torch.float64, device=dev)
+    va = torch.zeros_like(vm)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(int(2.5 * 129e6) // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        st, res = step()
+    torch.cuda.synchronize()
+    converged = int(np.sum(res["status"] == gbpf.PF_OK))
+    iters = res["iters"].astype(np.int64)
+    gbpf.pf_set_profiling(g.ctx, True)
+    for k in range(gbpf.PF_K_COUNT if hasattr(gbpf, "PF_K_COUNT") else 7):
+        gbpf.pf_get_profile(g.ctx, k, reset=True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between timed steps (buffer > 2 x L2)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, res = step()
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = {}
+    launches = 0
+    for k, nm in enumerate(gbpf.KERNEL_KINDS):
+        n, ms = gbpf.pf_get_profile(g.ctx, k, reset=True)
+        prof[nm] = (n, ms)
+        launches += n
+    gbpf.pf_set_profiling(g.ctx, False)
+
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    solves = converged * args.steps * world
+    value = solves / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: per step copy the case
+    # inputs (load scales, outages) from pinned host memory, run, copy V back
+    ls_host = None if load_scale is None else torch.from_numpy(load_scale).pin_memory()
+    out_host = torch.empty((2, ncase, base.n), dtype=torch.float64).pin_memory()
+    h2d = (0 if load_scale is None else load_scale.nbytes) + (0 if outage is None else outage.nbytes)
+    d2h = out_host.numel() * 8 + ncase * 24
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.set_cases(ncase, None if ls_host is None else ls_host.numpy(), outage)
+        st, res_e = step()
+        out_host[0].copy_(vm, non_blocking=True)
+        out_host[1].copy_(va, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te0
+    e2e_val = int(np.sum(res_e["status"] == gbpf.PF_OK)) * e2e_steps / e2e_s
+
+    # roofline of the dominant kernel (the power-flow iteration kernel)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    run_n, run_ms = prof["run"]
+    prec_bytes = 8 if prec == gbpf.PF_FP64 else 4
+    per_half = algorithmic_bytes_per_half_iteration(g.info, base.n, g.info.nnz_ybus, prec_bytes)
+    half_iters = float(np.sum(res["iters"])) + float(np.sum(res["status"] == gbpf.PF_OK))
+    alg_bytes = per_half * half_iters  # per launch (one launch per step)
+    achieved = alg_bytes / (run_ms / max(run_n, 1) / 1e3) / 1e9 if run_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "k_fdpf", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_ms_per_launch": run_ms / max(run_n, 1)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == gbpf.PF_FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "nbus": base.n, "nbranch": base.m,
+                       "ncase": ncase, "precision": prec_name, "tol_pu": TOL,
+                       "l2": "flushed between timed steps (2.5x L2 buffer write)",
+                       "loading_factor": base.lam, "analyze_ms": analyze_ms,
+                       "parallelism": "replicas" if ncase == 1 else "cases-in-blocks"},
+            "converged": converged, "ncase": ncase,
+            "iters_mean": float(np.mean(iters)), "gpu_launches": launches,
+            "kernel_ms": {k: v[1] for k, v in prof.items()},
+            "kernel_launches": {k: v[0] for k, v in prof.items()},
+            "roofline": roofline, "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_s, ncase)
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * gbpf.h -- C ABI of the GB300 graph-based power-flow library (libgbpf.so).
+ *
+ * The library implements the hot path of Section III of "Graph Based Power
+ * Flow Calculation for Energy Management System" (arxiv 1811.02512): nodal-
+ * parallel formation of the bus admittance matrix (Section III.A, FormMatrixA)
+ * and of the P/Q mismatch (Section II.A), hierarchical-parallel sparse LDU
+ * factorisation over the levels of the elimination tree (Sections II.B and
+ * III.B, Eqs. 1-3), and level-scheduled forward substitution, normalisation
+ * (Eq. 4) and back substitution (Section III.C), driven by the fast-decoupled
+ * and Newton-Raphson power-flow iterations (Section III).
+ *
+ * Conventions for every entry point:
+ *  - All quantities are per unit; angles in radians.
+ *  - Buses are numbered 0..nbus-1 in the order given to pf_create.  The
+ *    unknowns of a matrix are its buses in ascending bus order ("local"
+ *    order): B' and the Newton-Raphson Jacobian use every non-slack bus, B''
+ *    every PQ bus.
+ *  - Pointers named *_dev are device memory owned by the caller (for example
+ *    torch.Tensor.data_ptr()); other pointers are host memory owned by the
+ *    caller.  pf_create copies its inputs; the library never keeps a caller
+ *    pointer beyond the call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls marked
+ *    "asynchronous" only enqueue work on it; the others return after their
+ *    work is complete.
+ *  - Batched vectors are case-major: element (c, i) of a [ncase][len] array
+ *    is at c * len + i.
+ *  - Every call returns a pf_status and never aborts, traps or exits; a
+ *    failing call leaves a message for pf_last_error.  Device-side failures
+ *    (singular pivot, non-finite value, exhausted wait) are reported per case
+ *    through status words, never through a device trap.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef GBPF_H
+#define GBPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_ctx pf_ctx;
+
+typedef enum {
+    PF_OK = 0,
+    PF_ERR_ARG = 1,           /* invalid argument or input table */
+    PF_ERR_ISLAND = 2,        /* a bus is not connected to the slack bus */
+    PF_ERR_SINGULAR = 3,      /* pivot |d_j| <= 1e-14 max |a_jj| during the factor */
+    PF_ERR_NONFINITE = 4,     /* NaN or Inf reached a pivot, mismatch or state */
+    PF_ERR_NOT_CONVERGED = 5, /* iteration limit reached above the tolerance */
+    PF_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    PF_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+    PF_ERR_OOM = 8,           /* host or device allocation failed */
+    PF_ERR_STATE = 9          /* call out of order (e.g. pf_solve before pf_factor) */
+} pf_status;
+
+enum { PF_BUS_PQ = 1, PF_BUS_PV = 2, PF_BUS_SLACK = 3 };
+enum { PF_MAT_BP = 0, PF_MAT_BPP = 1 }; /* B' (non-slack buses), B'' (PQ buses) */
+enum { PF_FDPF = 1, PF_NR = 2 };
+enum { PF_FP64 = 0, PF_FP32 = 1 };
+
+/* One bus.  type: PF_BUS_PQ / PF_BUS_PV / PF_BUS_SLACK (exactly one slack).
+ * Specified injection: P = pg - pd (non-slack), Q = -qd (PQ).  Shunt gs + j bs.
+ * vset: voltage magnitude of PV and slack buses; va: slack angle. */
+typedef struct {
+    int32_t id, type;
+    double pd, qd, gs, bs, pg, vset, va;
+} pf_bus;
+
+/* One branch (pi model).  Series r + jx, total line charging b (b/2 at each
+ * end), off-nominal tap ratio on the from side (0 or 1 = none, no phase
+ * shift), status 1 = in service, 0 = out (it keeps its matrix slot). */
+typedef struct {
+    int32_t from, to;
+    double r, x, b, tap;
+    int32_t status;
+} pf_branch;
+
+/* Sizes produced by pf_analyze, index [PF_MAT_BP] and [PF_MAT_BPP]. */
+typedef struct {
+    int32_t n[2];        /* matrix dimension (buses) */
+    int64_t nnz_l[2];    /* strict-lower nonzeros of L (fill included) */
+    int32_t nlevels[2];  /* levels of the elimination tree (leaves = 1) */
+    int32_t max_col[2];  /* largest column count of L (diagonal excluded) */
+    int64_t nupdates[2]; /* scalar update operations of one numeric factor */
+    int32_t nnz_ybus;    /* nonzeros of the bus admittance pattern */
+    double analyze_ms;   /* host wall time of the analysis */
+} pf_symbolic_info;
+
+/* Options of pf_run_to_tol. */
+typedef struct {
+    int32_t method;     /* PF_FDPF (XB fast decoupled) or PF_NR */
+    int32_t precision;  /* PF_FP64, or PF_FP32 factor/substitution with FP64
+                           mismatch, residual and refinement */
+    double tol;         /* converged when max(|dP| non-slack, |dQ| PQ) <= tol */
+    int32_t max_iter;   /* NR steps or FDPF half-iteration pairs */
+    int32_t ir_max;     /* PF_FP32: refinement corrections per linear solve */
+    double ir_tol;      /* PF_FP32: stop refining at ||r||inf <= ir_tol ||rhs||inf */
+    int32_t flat_start; /* 1: theta = slack angle / 0, V = 1 (PQ) or vset; 0: use vm/va */
+    int32_t spin_limit; /* bound on every device-side wait (0 = library default) */
+} pf_run_opts;
+
+/* Per-case outcome of pf_run_to_tol. */
+typedef struct {
+    int32_t status;      /* pf_status of this case */
+    int32_t iters;       /* NR steps, or FDPF half-iterations */
+    int32_t ir_steps;    /* refinement corrections taken (PF_FP32) */
+    int32_t pad;
+    double max_mismatch; /* last max |mismatch| evaluated */
+} pf_case_result;
+
+/* Builds a context from bus and branch tables (copied).  Checks indices,
+ * impedances (finite, x != 0 or r != 0), exactly one slack bus and
+ * connectivity to the slack bus (PF_ERR_ISLAND).  Synchronous. */
+pf_status pf_create(const pf_bus *bus, int32_t nbus, const pf_branch *branch, int32_t nbranch,
+                    pf_ctx **out);
+
+/* Host symbolic analysis of B' and B'' (the Newton-Raphson Jacobian reuses
+ * B''s): exact minimum-degree ordering (ties to the smallest bus), fill
+ * pattern of L (Section II.B.1), elimination tree (Section II.B.2), level
+ * sets (Section II.B, Table I: leaves are level 1), the level schedules and
+ * the update lists of the left-looking factor; uploads them to the current
+ * device.  info may be NULL.  Synchronous. */
+pf_status pf_analyze(pf_ctx *ctx, pf_symbolic_info *info);
+
+/* Copies the symbolic result of matrix `which` to caller arrays sized from
+ * pf_symbolic_info: perm[n] (elimination step -> local index), parent[n]
+ * (step -> parent step, -1 = root), level[n] (1 = leaf), Lp[n+1], Li[nnz_l]
+ * (strict lower pattern of L by column, rows ascending, in step numbering).
+ * Any pointer may be NULL.  Synchronous. */
+pf_status pf_get_symbolic(const pf_ctx *ctx, int32_t which, int32_t *perm, int32_t *parent,
+                          int32_t *level, int64_t *Lp, int32_t *Li);
+
+/* Defines a batch of ncase >= 1 cases sharing the topology.  load_scale
+ * [ncase][nbus] (host, NULL = all 1) multiplies pd and qd of every PQ bus of
+ * a case; outage[ncase] (host, NULL = none) names a branch taken out of
+ * service in that case (-1 = none).  Outages keep the symbolic pattern.
+ * Replaces any previous batch.  Synchronous. */
+pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
+                       const int32_t *outage);
+
+/* Assembles the bus admittance matrix (Section III.A) and the values of B'
+ * or B'' for every case and factorises them level by level (Section III.B):
+ * A = L D L^T with unit L.  precision selects FP64 or FP32 factor storage.
+ * Asynchronous; a singular or non-finite pivot is recorded in the per-case
+ * status read by pf_get_factor / pf_case_status. */
+pf_status pf_factor(pf_ctx *ctx, int32_t which, int32_t precision, void *stream);
+
+/* Copies case c's factor of matrix `which` to the host: D[n] and Lx[nnz_l]
+ * in step numbering, as doubles whatever the storage precision, and its
+ * factor status (PF_OK, PF_ERR_SINGULAR or PF_ERR_NONFINITE).  Synchronous. */
+pf_status pf_get_factor(pf_ctx *ctx, int32_t which, int32_t precision, int32_t c, double *D,
+                        double *Lx, int32_t *status);
+
+/* Solves A x = rhs in place for the first ncase cases with the factor of the
+ * given precision (forward substitution, normalisation y = z / d (Eq. 4),
+ * back substitution, Section III.C).  rhs_inout_dev is [ncase][n] double in
+ * local order.  transpose is accepted for symmetry (B' and B'' are
+ * symmetric).  Asynchronous. */
+pf_status pf_solve(pf_ctx *ctx, int32_t which, int32_t precision, int32_t transpose,
+                   double *rhs_inout_dev, int32_t ncase, void *stream);
+
+/* Nodal P/Q mismatch (Section II.A) of the first ncase cases at the states
+ * vm_dev/va_dev [ncase][nbus]: dp_dev/dq_dev [ncase][nbus] receive
+ * Psp - P (non-slack, else 0) and Qsp - Q (PQ, else 0); maxmis_dev[ncase]
+ * receives max |.|.  Uses each case's outage and load scale.  Asynchronous. */
+pf_status pf_mismatch(pf_ctx *ctx, const double *vm_dev, const double *va_dev, double *dp_dev,
+                      double *dq_dev, double *maxmis_dev, int32_t ncase, void *stream);
+
+/* Runs the power flow of every case of the batch to opts->tol on the device
+ * and returns per-case results in res_host[ncase].  vm_dev/va_dev
+ * [ncase][nbus] hold the start (unless flat_start) and receive the final
+ * state.  Assembly, factor, substitutions, mismatch and convergence checks
+ * all run in device kernels; the call returns after the device is done.
+ * Returns PF_OK when every case converged, else the first failing status. */
+pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                        pf_case_result *res_host, void *stream);
+
+/* Kernel kinds counted by the profiling hooks. */
+enum {
+    PF_K_YBUS = 0,     /* admittance matrix and XB B' assembly (Section III.A) */
+    PF_K_SPEC = 1,     /* specified injections of every case */
+    PF_K_ASSEMBLE = 2, /* B' / B'' values of every factor instance */
+    PF_K_FACTOR = 3,   /* level-scheduled LDL^T (Section III.B) */
+    PF_K_SOLVE = 4,    /* level-scheduled substitutions (Section III.C) */
+    PF_K_MISMATCH = 5, /* nodal injections and mismatch (Section II.A) */
+    PF_K_RUN = 6,      /* the power-flow iteration kernel of pf_run_to_tol */
+    PF_K_COUNT = 7
+};
+
+/* Turns per-launch CUDA-event timing of this context's kernels on (1) or off
+ * (0).  Launch counts are always kept.  Synchronous. */
+pf_status pf_set_profiling(pf_ctx *ctx, int32_t on);
+
+/* Launch count and summed device time (ms, 0 unless profiling was on) of one
+ * kernel kind since the last reset; reset = 1 clears both afterwards.
+ * Synchronises with the recorded events. */
+pf_status pf_get_profile(pf_ctx *ctx, int32_t kind, int64_t *launches, double *total_ms,
+                         int32_t reset);
+
+/* Message of the last failing call on this context (never NULL). */
+const char *pf_last_error(const pf_ctx *ctx);
+
+/* Copies the base-case admittance matrix: rowptr[nbus+1], col[nnz], G[nnz],
+ * B[nnz] (CSR, columns ascending, diagonal present).  Synchronous. */
+pf_status pf_get_ybus(pf_ctx *ctx, int32_t *rowptr, int32_t *col, double *G, double *B);
+
+/* Releases the context and all its device memory.  NULL is accepted. */
+void pf_destroy(pf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBPF_H */

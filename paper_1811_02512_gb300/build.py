@@ -1,0 +1,91 @@
+"""Builds libgbpf.so in-tree for sm_103a (GB300) with nvcc and the host C++ compiler.
+
+Two translation units compile in parallel (the CUDA kernels with nvcc, the
+host analysis with g++) and are linked against the CUDA runtime.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INC = os.path.join(ROOT, "include")
+OUT = os.path.join(PKG, "_build")
+LIB = os.path.join(PKG, "libgbpf.so")
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+
+def cuda_home() -> str:
+    for c in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if c and os.path.exists(os.path.join(c, "bin", "nvcc")):
+            return c
+    nv = shutil.which("nvcc")
+    if nv:
+        return os.path.dirname(os.path.dirname(nv))
+    raise RuntimeError("nvcc not found")
+
+
+def sources():
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                  if f.endswith((".cu", ".cpp", ".h")))
+
+
+def up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    deps = sources() + [os.path.join(INC, "gbpf.h"), __file__]
+    return all(os.path.getmtime(d) <= t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and up_to_date():
+        return LIB
+    cuda = cuda_home()
+    nvcc = os.path.join(cuda, "bin", "nvcc")
+    os.makedirs(OUT, exist_ok=True)
+    cu = [f for f in sources() if f.endswith(".cu")]
+    cpp = [f for f in sources() if f.endswith(".cpp")]
+    objs, procs = [], []
+    for f in cu:
+        o = os.path.join(OUT, os.path.basename(f) + ".o")
+        cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+               "-Xptxas", "-v" if verbose else "-O3", "-I", INC, "-I", CSRC, "-c", f, "-o", o]
+        objs.append(o)
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    for f in cpp:
+        o = os.path.join(OUT, os.path.basename(f) + ".o")
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", INC, "-I", CSRC,
+               "-I", os.path.join(cuda, "include"), "-c", f, "-o", o]
+        objs.append(o)
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    failed = False
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        text = out.decode(errors="replace")
+        if p.returncode != 0:
+            failed = True
+            sys.stderr.write(" ".join(cmd) + "\n" + text)
+        elif verbose and text:
+            sys.stderr.write(text)
+    if failed:
+        raise RuntimeError("libgbpf build failed")
+    libdirs = [os.path.join(cuda, d) for d in ("lib64", "lib", "targets/sbsa-linux/lib",
+                                               "targets/x86_64-linux/lib")]
+    link = ["g++", "-shared", "-o", LIB + ".tmp"] + objs
+    for d in libdirs:
+        if os.path.isdir(d):
+            link += ["-L", d]
+    link += ["-lcudart", "-Wl,-rpath," + os.path.join(cuda, "lib64")]
+    subprocess.check_call(link)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
+    print(LIB)

@@ -1,0 +1,825 @@
+// gbpf_host.cpp -- host side of libgbpf: input checks, the bus admittance
+// pattern, the symbolic analysis (ordering, fill, elimination tree, levels,
+// schedules) and the C ABI entry points that enqueue the device kernels.
+//
+// Symbolic analysis (Section II.B of arxiv 1811.02512):
+//   ordering   exact minimum degree on the elimination graph, ties to the
+//              smallest bus (the paper leaves the ordering open);
+//   fill       struct(L) from row subtrees of the elimination tree -- the
+//              same filled graph G+(A) that FormFilledGraph produces
+//              (Section II.B.1);
+//   etree      parent[i] = min { j > i : l_ji != 0 } (Section II.B.2),
+//              computed with path-compressed ancestor links;
+//   levels     level = 1 for leaves, 1 + max over children otherwise, which is
+//              exactly the repeated leaf peeling of FormHierarchicalPartition
+//              (Section II.B, Table I).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <set>
+#include <utility>
+
+#include "gbpf_internal.h"
+
+using namespace gbpf;
+
+namespace {
+
+pf_status fail(pf_ctx *ctx, pf_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return st;
+}
+
+pf_status cuda_fail(pf_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+template <class T>
+pf_status upload(pf_ctx *ctx, T **dst, const T *src, size_t count) {
+    *dst = nullptr;
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMalloc((void **)dst, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    ctx->allocations.push_back(*dst);
+    if (count) {
+        e = cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy H2D");
+    }
+    return PF_OK;
+}
+
+template <class T>
+pf_status dalloc(pf_ctx *ctx, T **dst, size_t count) {
+    *dst = nullptr;
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * (count ? count : 1));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    ctx->allocations.push_back(*dst);
+    return PF_OK;
+}
+
+void dfree(pf_ctx *ctx, void *p) {
+    if (!p) return;
+    auto it = std::find(ctx->allocations.begin(), ctx->allocations.end(), p);
+    if (it != ctx->allocations.end()) ctx->allocations.erase(it);
+    cudaFree(p);
+}
+
+#define TRY(x)                              \
+    do {                                    \
+        pf_status _st = (x);                \
+        if (_st != PF_OK) return _st;       \
+    } while (0)
+
+// Enqueues `launch` (which returns the cudaError_t of its launches) on stream
+// s, counting `nlaunch` kernel launches of kind `kind`; with profiling on the
+// launch is bracketed by CUDA events on the same stream.
+template <class F>
+cudaError_t counted(pf_ctx *ctx, int kind, int nlaunch, cudaStream_t s, F launch) {
+    KernelStat &k = ctx->kstat[kind];
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ctx->profiling) {
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+            return cudaErrorMemoryAllocation;
+        cudaEventRecord(a, s);
+    }
+    cudaError_t e = launch();
+    if (ctx->profiling) {
+        cudaEventRecord(b, s);
+        k.pending.push_back({a, b});
+    }
+    if (e == cudaSuccess) k.launches += nlaunch;
+    return e;
+}
+
+void drain_events(pf_ctx *ctx, KernelStat &k) {
+    for (auto &pr : k.pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(pr.second) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+            k.ms += ms;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    k.pending.clear();
+}
+
+int ypos(const pf_ctx *ctx, int i, int j) {
+    const int *b = ctx->col.data() + ctx->rowptr[i];
+    const int *e = ctx->col.data() + ctx->rowptr[i + 1];
+    const int *p = std::lower_bound(b, e, j);
+    return (p != e && *p == j) ? int(p - ctx->col.data()) : -1;
+}
+
+// ---------------------------------------------------------------- ordering
+
+// Exact minimum degree: an ordered set of (degree, vertex) picks the vertex
+// with the fewest remaining neighbours, ties to the smallest index; the
+// neighbourhood of the eliminated vertex becomes a clique.
+std::vector<int> min_degree_order(int n, std::vector<std::vector<int>> adj) {
+    std::set<std::pair<int, int>> ready;
+    for (int v = 0; v < n; v++) ready.insert({int(adj[v].size()), v});
+    std::vector<int> order;
+    order.reserve(n);
+    std::vector<int> merged;
+    while (!ready.empty()) {
+        int v = ready.begin()->second;
+        ready.erase(ready.begin());
+        order.push_back(v);
+        const std::vector<int> nb = std::move(adj[v]);
+        adj[v].clear();
+        for (int u : nb) {
+            ready.erase({int(adj[u].size()), u});
+            merged.clear();
+            std::set_union(adj[u].begin(), adj[u].end(), nb.begin(), nb.end(),
+                           std::back_inserter(merged));
+            merged.erase(std::remove_if(merged.begin(), merged.end(),
+                                        [&](int w) { return w == u || w == v; }),
+                         merged.end());
+            adj[u].swap(merged);
+            ready.insert({int(adj[u].size()), u});
+        }
+    }
+    return order;
+}
+
+// ---------------------------------------------------------------- analysis
+
+pf_status analyze_matrix(pf_ctx *ctx, int which, HostMat &H) {
+    const int nbus = ctx->nbus;
+    H = HostMat();
+    for (int i = 0; i < nbus; i++) {
+        int t = ctx->bus[i].type;
+        bool in = (which == PF_MAT_BP) ? (t != PF_BUS_SLACK) : (t == PF_BUS_PQ);
+        if (in) H.bus.push_back(i);
+    }
+    const int n = int(H.bus.size());
+    H.n = n;
+    std::vector<int> loc(nbus, -1);
+    for (int a = 0; a < n; a++) loc[H.bus[a]] = a;
+    std::vector<std::vector<int>> g(n);
+    for (int a = 0; a < n; a++) {
+        int i = H.bus[a];
+        for (int p = ctx->rowptr[i]; p < ctx->rowptr[i + 1]; p++) {
+            int j = ctx->col[p];
+            if (j != i && loc[j] >= 0) g[a].push_back(loc[j]);
+        }
+    }
+    H.perm = min_degree_order(n, g);
+    H.iperm.assign(n, 0);
+    for (int k = 0; k < n; k++) H.iperm[H.perm[k]] = k;
+    // permuted graph
+    std::vector<std::vector<int>> pg(n);
+    for (int k = 0; k < n; k++) {
+        for (int a : g[H.perm[k]]) pg[k].push_back(H.iperm[a]);
+        std::sort(pg[k].begin(), pg[k].end());
+    }
+    // elimination tree with path-compressed ancestors
+    H.parent.assign(n, -1);
+    std::vector<int> anc(n, -1);
+    for (int i = 0; i < n; i++)
+        for (int k : pg[i]) {
+            if (k >= i) break;
+            int r = k;
+            while (r != -1 && r != i) {
+                int nx = anc[r];
+                anc[r] = i;
+                if (nx == -1) H.parent[r] = i;
+                r = nx;
+            }
+        }
+    // row patterns of L: union of etree paths from struct(A_i, < i) up to i
+    std::vector<std::vector<int>> rows(n);
+    std::vector<int> mark(n, -1);
+    for (int i = 0; i < n; i++) {
+        mark[i] = i;
+        for (int k : pg[i]) {
+            if (k >= i) break;
+            for (int r = k; mark[r] != i; r = H.parent[r]) {
+                rows[i].push_back(r);
+                mark[r] = i;
+            }
+        }
+        std::sort(rows[i].begin(), rows[i].end());
+    }
+    // columns of L (rows ascending because i is visited ascending)
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int i = 0; i < n; i++)
+        for (int k : rows[i]) cnt[k + 1]++;
+    H.Lp.assign(n + 1, 0);
+    for (int k = 0; k < n; k++) H.Lp[k + 1] = H.Lp[k] + cnt[k + 1];
+    const int64_t nnz_l = H.Lp[n];
+    if (nnz_l > INT32_MAX / 2) return fail(ctx, PF_ERR_OOM, "factor too large (%lld)", (long long)nnz_l);
+    H.Li.assign(nnz_l, 0);
+    std::vector<int64_t> fill(H.Lp.begin(), H.Lp.end() - 1);
+    H.Rp.assign(n + 1, 0);
+    H.Rk.assign(nnz_l, 0);
+    H.Rpos.assign(nnz_l, 0);
+    for (int i = 0; i < n; i++) {
+        H.Rp[i + 1] = H.Rp[i] + int(rows[i].size());
+        for (size_t q = 0; q < rows[i].size(); q++) {
+            int k = rows[i][q];
+            int64_t p = fill[k]++;
+            H.Li[p] = i;
+            H.Rk[H.Rp[i] + q] = k;
+            H.Rpos[H.Rp[i] + q] = int(p);
+        }
+    }
+    H.max_col = 0;
+    for (int k = 0; k < n; k++) H.max_col = std::max<int>(H.max_col, int(H.Lp[k + 1] - H.Lp[k]));
+    // levels: leaves 1, parents 1 + max over children
+    H.level.assign(n, 1);
+    for (int j = 0; j < n; j++)
+        if (H.parent[j] >= 0) H.level[H.parent[j]] = std::max(H.level[H.parent[j]], H.level[j] + 1);
+    H.nlev = 0;
+    for (int j = 0; j < n; j++) H.nlev = std::max(H.nlev, H.level[j]);
+    H.lvl_ptr.assign(H.nlev + 1, 0);
+    for (int j = 0; j < n; j++) H.lvl_ptr[H.level[j]]++;
+    for (int l = 0; l < H.nlev; l++) H.lvl_ptr[l + 1] += H.lvl_ptr[l];
+    H.lvl_cols.assign(n, 0);
+    {
+        std::vector<int> f(H.lvl_ptr.begin(), H.lvl_ptr.end() - 1);
+        for (int j = 0; j < n; j++) H.lvl_cols[f[H.level[j] - 1]++] = j;
+    }
+    // update maps of the left-looking factor: row-list entry (j, k) updates
+    // column j from the entries of column k at rows >= j
+    H.uoff.assign(nnz_l + 1, 0);
+    for (int j = 0; j < n; j++)
+        for (int q = H.Rp[j]; q < H.Rp[j + 1]; q++) {
+            int k = H.Rk[q];
+            H.uoff[q + 1] = H.uoff[q] + int(H.Lp[k + 1] - H.Rpos[q]);
+        }
+    H.umap.assign(std::max(1, H.uoff[nnz_l]), 0);
+    for (int j = 0; j < n; j++) {
+        const int *cb = H.Li.data() + H.Lp[j];
+        const int *ce = H.Li.data() + H.Lp[j + 1];
+        for (int q = H.Rp[j]; q < H.Rp[j + 1]; q++) {
+            int k = H.Rk[q];
+            int o = H.uoff[q];
+            for (int64_t p = H.Rpos[q]; p < H.Lp[k + 1]; p++) {
+                int i = H.Li[p];
+                int tgt;
+                if (i == j) {
+                    tgt = 0;
+                } else {
+                    const int *f = std::lower_bound(cb, ce, i);
+                    if (f == ce || *f != i)
+                        return fail(ctx, PF_ERR_ARG, "internal: fill pattern not closed");
+                    tgt = 1 + int(f - cb);
+                }
+                H.umap[o++] = tgt;
+            }
+        }
+    }
+    // slot sources: diagonal slots then L slots, from the Ybus pattern
+    H.src.assign(n + nnz_l, -1);
+    for (int k = 0; k < n; k++) H.src[k] = ypos(ctx, H.bus[H.perm[k]], H.bus[H.perm[k]]);
+    for (int k = 0; k < n; k++)
+        for (int64_t p = H.Lp[k]; p < H.Lp[k + 1]; p++)
+            H.src[n + p] = ypos(ctx, H.bus[H.perm[H.Li[p]]], H.bus[H.perm[k]]);
+    H.step_of_bus.assign(nbus, -1);
+    for (int k = 0; k < n; k++) H.step_of_bus[H.bus[H.perm[k]]] = k;
+    H.br_slot.assign(3 * size_t(ctx->nbr), -1);
+    for (int e = 0; e < ctx->nbr; e++) {
+        int sf = H.step_of_bus[ctx->branch[e].from], st = H.step_of_bus[ctx->branch[e].to];
+        H.br_slot[3 * e + 0] = sf;
+        H.br_slot[3 * e + 1] = st;
+        if (sf >= 0 && st >= 0) {
+            int lo = std::min(sf, st), hi = std::max(sf, st);
+            const int *cb = H.Li.data() + H.Lp[lo];
+            const int *ce = H.Li.data() + H.Lp[lo + 1];
+            const int *f = std::lower_bound(cb, ce, hi);
+            H.br_slot[3 * e + 2] = n + int(f - H.Li.data());
+        }
+    }
+    return PF_OK;
+}
+
+pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
+    D.n = H.n;
+    D.nnz_l = int(H.Lp[H.n]);
+    D.nlev = H.nlev;
+    D.max_col = H.max_col;
+    D.nupd = H.uoff.empty() ? 0 : H.uoff.back();
+    D.stride = ((H.n + D.nnz_l + 31) / 32) * 32;
+    std::vector<int> busstep(H.n), Lp32(H.n + 1);
+    for (int k = 0; k < H.n; k++) busstep[k] = H.bus[H.perm[k]];
+    for (int k = 0; k <= H.n; k++) Lp32[k] = int(H.Lp[k]);
+    TRY(upload(ctx, &D.bus, busstep.data(), busstep.size()));
+    TRY(upload(ctx, &D.perm, H.perm.data(), H.perm.size()));
+    TRY(upload(ctx, &D.Lp, Lp32.data(), Lp32.size()));
+    TRY(upload(ctx, &D.Li, H.Li.data(), H.Li.size()));
+    TRY(upload(ctx, &D.Rp, H.Rp.data(), H.Rp.size()));
+    TRY(upload(ctx, &D.Rk, H.Rk.data(), H.Rk.size()));
+    TRY(upload(ctx, &D.Rpos, H.Rpos.data(), H.Rpos.size()));
+    TRY(upload(ctx, &D.lvl_ptr, H.lvl_ptr.data(), H.lvl_ptr.size()));
+    TRY(upload(ctx, &D.lvl_cols, H.lvl_cols.data(), H.lvl_cols.size()));
+    TRY(upload(ctx, &D.uoff, H.uoff.data(), H.uoff.size()));
+    TRY(upload(ctx, &D.umap, H.umap.data(), H.umap.size()));
+    TRY(upload(ctx, &D.src, H.src.data(), H.src.size()));
+    TRY(upload(ctx, &D.step_of_bus, H.step_of_bus.data(), H.step_of_bus.size()));
+    TRY(upload(ctx, &D.br_slot, H.br_slot.data(), H.br_slot.size()));
+    return PF_OK;
+}
+
+pf_status ensure_device(pf_ctx *ctx) {
+    const int nbus = ctx->nbus, nbranch = ctx->nbr;
+    const pf_bus *bus = ctx->bus.data();
+    const pf_branch *branch = ctx->branch.data();
+    if (ctx->on_device) return PF_OK;
+    cudaError_t ce = cudaGetDevice(&ctx->device);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "no CUDA device");
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    ctx->smem_optin = size_t(optin);
+
+    // device network tables
+    DevNet &dn = ctx->dn;
+    dn.nbus = nbus;
+    dn.nbr = nbranch;
+    dn.nnz = ctx->rowptr[nbus];
+    std::vector<int> btype(nbus), bf(nbranch), bt(nbranch), bst(nbranch);
+    std::vector<double> pd(nbus), qd(nbus), gs(nbus), bs(nbus), pg(nbus), vs(nbus), va(nbus);
+    std::vector<double> rr(nbranch), xx(nbranch), bb(nbranch), tp(nbranch);
+    for (int i = 0; i < nbus; i++) {
+        btype[i] = bus[i].type; pd[i] = bus[i].pd; qd[i] = bus[i].qd; gs[i] = bus[i].gs;
+        bs[i] = bus[i].bs; pg[i] = bus[i].pg; vs[i] = bus[i].vset; va[i] = bus[i].va;
+    }
+    for (int e = 0; e < nbranch; e++) {
+        bf[e] = branch[e].from; bt[e] = branch[e].to; bst[e] = branch[e].status;
+        rr[e] = branch[e].r; xx[e] = branch[e].x; bb[e] = branch[e].b;
+        tp[e] = branch[e].tap == 0.0 ? 1.0 : branch[e].tap;
+    }
+    const std::vector<int> &ydiag = ctx->ydiag, &inc_ptr = ctx->inc_ptr, &inc_br = ctx->inc_br,
+                           &inc_side = ctx->inc_side, &inc_pos = ctx->inc_pos, &br_pos = ctx->br_pos;
+    pf_status st = PF_OK;
+    do {
+        if ((st = upload(ctx, &dn.btype, btype.data(), nbus))) break;
+        if ((st = upload(ctx, &dn.pd, pd.data(), nbus))) break;
+        if ((st = upload(ctx, &dn.qd, qd.data(), nbus))) break;
+        if ((st = upload(ctx, &dn.gs, gs.data(), nbus))) break;
+        if ((st = upload(ctx, &dn.bs, bs.data(), nbus))) break;
+        if ((st = upload(ctx, &dn.pg, pg.data(), nbus))) break;
+        if ((st = upload(ctx, &dn.vset, vs.data(), nbus))) break;
+        if ((st = upload(ctx, &dn.va0, va.data(), nbus))) break;
+        if ((st = upload(ctx, &dn.bf, bf.data(), nbranch))) break;
+        if ((st = upload(ctx, &dn.bt, bt.data(), nbranch))) break;
+        if ((st = upload(ctx, &dn.bstatus, bst.data(), nbranch))) break;
+        if ((st = upload(ctx, &dn.br, rr.data(), nbranch))) break;
+        if ((st = upload(ctx, &dn.bx, xx.data(), nbranch))) break;
+        if ((st = upload(ctx, &dn.bb, bb.data(), nbranch))) break;
+        if ((st = upload(ctx, &dn.btap, tp.data(), nbranch))) break;
+        if ((st = upload(ctx, &dn.rowptr, ctx->rowptr.data(), ctx->rowptr.size()))) break;
+        if ((st = upload(ctx, &dn.col, ctx->col.data(), ctx->col.size()))) break;
+        if ((st = upload(ctx, &dn.ydiag, ydiag.data(), ydiag.size()))) break;
+        if ((st = upload(ctx, &dn.inc_ptr, inc_ptr.data(), inc_ptr.size()))) break;
+        if ((st = upload(ctx, &dn.inc_br, inc_br.data(), inc_br.size()))) break;
+        if ((st = upload(ctx, &dn.inc_side, inc_side.data(), inc_side.size()))) break;
+        if ((st = upload(ctx, &dn.inc_pos, inc_pos.data(), inc_pos.size()))) break;
+        if ((st = upload(ctx, &dn.br_pos, br_pos.data(), br_pos.size()))) break;
+        if ((st = dalloc(ctx, &dn.G, dn.nnz))) break;
+        if ((st = dalloc(ctx, &dn.B, dn.nnz))) break;
+        if ((st = dalloc(ctx, &dn.Bp, dn.nnz))) break;
+    } while (0);
+    if (st != PF_OK) return st;
+    if (ctx->analyzed)
+        for (int w = 0; w < 2; w++) TRY(upload_matrix(ctx, ctx->hm[w], ctx->dm[w]));
+    ctx->on_device = true;
+    return PF_OK;
+}
+
+pf_status ensure_cases(pf_ctx *ctx) {
+    if (ctx->dc.ncase > 0) return PF_OK;
+    return pf_set_cases(ctx, 1, nullptr, nullptr);
+}
+
+pf_status ensure_factor_storage(pf_ctx *ctx, int which, int prec) {
+    Workspace &w = ctx->ws;
+    const DevMat &m = ctx->dm[which];
+    size_t sz = size_t(ctx->dc.ninst) * size_t(m.stride);
+    if (!w.A[which]) TRY(dalloc(ctx, &w.A[which], sz));
+    if (prec == PF_FP64 && !w.F64[which]) TRY(dalloc(ctx, &w.F64[which], sz));
+    if (prec == PF_FP32 && !w.F32[which]) TRY(dalloc(ctx, &w.F32[which], sz));
+    if (!w.fstatus[which][prec]) TRY(dalloc(ctx, &w.fstatus[which][prec], size_t(ctx->dc.ninst)));
+    return PF_OK;
+}
+
+void free_case_storage(pf_ctx *ctx) {
+    Workspace &w = ctx->ws;
+    for (int a = 0; a < 2; a++) {
+        dfree(ctx, w.A[a]); w.A[a] = nullptr;
+        dfree(ctx, w.F64[a]); w.F64[a] = nullptr;
+        dfree(ctx, w.F32[a]); w.F32[a] = nullptr;
+        for (int b = 0; b < 2; b++) {
+            dfree(ctx, w.fstatus[a][b]);
+            w.fstatus[a][b] = nullptr;
+            w.factored[a][b] = false;
+        }
+    }
+    dfree(ctx, w.ef); w.ef = nullptr;
+    dfree(ctx, w.vec); w.vec = nullptr;
+    dfree(ctx, w.res); w.res = nullptr;
+    dfree(ctx, ctx->dc.outage); ctx->dc.outage = nullptr;
+    dfree(ctx, ctx->dc.inst); ctx->dc.inst = nullptr;
+    dfree(ctx, ctx->dc.inst_outage); ctx->dc.inst_outage = nullptr;
+    dfree(ctx, ctx->dc.Psp); ctx->dc.Psp = nullptr;
+    dfree(ctx, ctx->dc.Qsp); ctx->dc.Qsp = nullptr;
+    ctx->dc.ncase = 0;
+    ctx->dc.ninst = 1;
+}
+
+pf_status assemble_ybus(pf_ctx *ctx, cudaStream_t s) {
+    cudaError_t e = counted(ctx, PF_K_YBUS, 1, s, [&] { return launch_ybus(ctx->dn, s); });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ybus launch");
+    return PF_OK;
+}
+
+// Assembles B' or B'' of every instance from the current admittance matrix
+// and factorises them.
+pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
+    TRY(ensure_factor_storage(ctx, which, prec));
+    Workspace &w = ctx->ws;
+    const DevMat &m = ctx->dm[which];
+    cudaError_t e = counted(ctx, PF_K_ASSEMBLE, 1, s, [&] {
+        return launch_assemble_slots(ctx->dn, ctx->dc, m, which, w.A[which], s);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble launch");
+    void *F = prec == PF_FP64 ? (void *)w.F64[which] : (void *)w.F32[which];
+    e = counted(ctx, PF_K_FACTOR, 1, s, [&] {
+        return launch_factor(m, prec, w.A[which], F, ctx->dc.ninst, w.fstatus[which][prec], s);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "factor launch");
+    w.factored[which][prec] = true;
+    return PF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+pf_status pf_create(const pf_bus *bus, int32_t nbus, const pf_branch *branch, int32_t nbranch,
+                    pf_ctx **out) {
+    if (!out) return PF_ERR_ARG;
+    *out = nullptr;
+    if (!bus || nbus < 2 || nbranch < 1 || !branch) return PF_ERR_ARG;
+    pf_ctx *ctx = new (std::nothrow) pf_ctx();
+    if (!ctx) return PF_ERR_OOM;
+    auto reject = [&](pf_status st) {
+        // keep the context alive only long enough to report
+        delete ctx;
+        return st;
+    };
+    ctx->nbus = nbus;
+    ctx->nbr = nbranch;
+    ctx->bus.assign(bus, bus + nbus);
+    ctx->branch.assign(branch, branch + nbranch);
+    int nslack = 0;
+    for (int i = 0; i < nbus; i++) {
+        const pf_bus &b = bus[i];
+        if (b.type < PF_BUS_PQ || b.type > PF_BUS_SLACK) return reject(PF_ERR_ARG);
+        if (b.type == PF_BUS_SLACK) { nslack++; ctx->slack = i; }
+        double v[7] = {b.pd, b.qd, b.gs, b.bs, b.pg, b.vset, b.va};
+        for (double x : v)
+            if (!std::isfinite(x)) return reject(PF_ERR_ARG);
+        if (b.type != PF_BUS_PQ && !(b.vset > 0)) return reject(PF_ERR_ARG);
+    }
+    if (nslack != 1) return reject(PF_ERR_ARG);
+    std::vector<std::vector<int>> adj(nbus);
+    for (int e = 0; e < nbranch; e++) {
+        const pf_branch &r = branch[e];
+        if (r.from < 0 || r.from >= nbus || r.to < 0 || r.to >= nbus || r.from == r.to)
+            return reject(PF_ERR_ARG);
+        double v[4] = {r.r, r.x, r.b, r.tap};
+        for (double x : v)
+            if (!std::isfinite(x)) return reject(PF_ERR_ARG);
+        if (r.x == 0.0 || r.tap < 0.0) return reject(PF_ERR_ARG);
+        if (r.status != 0 && r.status != 1) return reject(PF_ERR_ARG);
+        adj[r.from].push_back(r.to);
+        adj[r.to].push_back(r.from);
+    }
+    // connectivity to the slack through in-service branches
+    {
+        std::vector<std::vector<int>> live(nbus);
+        for (int e = 0; e < nbranch; e++)
+            if (branch[e].status) {
+                live[branch[e].from].push_back(branch[e].to);
+                live[branch[e].to].push_back(branch[e].from);
+            }
+        std::vector<char> seen(nbus, 0);
+        std::vector<int> stack{ctx->slack};
+        seen[ctx->slack] = 1;
+        int cnt = 1;
+        while (!stack.empty()) {
+            int v = stack.back();
+            stack.pop_back();
+            for (int u : live[v])
+                if (!seen[u]) { seen[u] = 1; cnt++; stack.push_back(u); }
+        }
+        if (cnt != nbus) return reject(PF_ERR_ISLAND);
+    }
+    // Ybus pattern: diagonal plus one entry per adjacent bus, ascending
+    ctx->rowptr.assign(nbus + 1, 0);
+    for (int i = 0; i < nbus; i++) {
+        adj[i].push_back(i);
+        std::sort(adj[i].begin(), adj[i].end());
+        adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
+        ctx->rowptr[i + 1] = ctx->rowptr[i] + int(adj[i].size());
+    }
+    ctx->col.reserve(ctx->rowptr[nbus]);
+    for (int i = 0; i < nbus; i++) ctx->col.insert(ctx->col.end(), adj[i].begin(), adj[i].end());
+
+    // host index tables used by the device kernels
+    ctx->ydiag.assign(nbus, 0);
+    ctx->inc_ptr.assign(nbus + 1, 0);
+    ctx->inc_br.assign(2 * size_t(nbranch), 0);
+    ctx->inc_side.assign(2 * size_t(nbranch), 0);
+    ctx->inc_pos.assign(2 * size_t(nbranch), 0);
+    ctx->br_pos.assign(4 * size_t(nbranch), 0);
+    for (int i = 0; i < nbus; i++) ctx->ydiag[i] = ypos(ctx, i, i);
+    for (int e = 0; e < nbranch; e++) { ctx->inc_ptr[branch[e].from + 1]++; ctx->inc_ptr[branch[e].to + 1]++; }
+    for (int i = 0; i < nbus; i++) ctx->inc_ptr[i + 1] += ctx->inc_ptr[i];
+    {
+        std::vector<int> f(ctx->inc_ptr.begin(), ctx->inc_ptr.end() - 1);
+        for (int e = 0; e < nbranch; e++) {  // ascending branch index per bus
+            const int a = branch[e].from, b = branch[e].to;
+            int q = f[a]++;
+            ctx->inc_br[q] = e; ctx->inc_side[q] = 0; ctx->inc_pos[q] = ypos(ctx, a, b);
+            q = f[b]++;
+            ctx->inc_br[q] = e; ctx->inc_side[q] = 1; ctx->inc_pos[q] = ypos(ctx, b, a);
+        }
+    }
+    for (int e = 0; e < nbranch; e++) {
+        const int a = branch[e].from, b = branch[e].to;
+        ctx->br_pos[4 * e + 0] = ctx->ydiag[a];
+        ctx->br_pos[4 * e + 1] = ctx->ydiag[b];
+        ctx->br_pos[4 * e + 2] = ypos(ctx, a, b);
+        ctx->br_pos[4 * e + 3] = ypos(ctx, b, a);
+    }
+    *out = ctx;
+    return PF_OK;
+}
+
+pf_status pf_analyze(pf_ctx *ctx, pf_symbolic_info *info) {
+    if (!ctx) return PF_ERR_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    if (!ctx->analyzed) {
+        for (int w = 0; w < 2; w++) {
+            TRY(analyze_matrix(ctx, w, ctx->hm[w]));
+            if (ctx->on_device) TRY(upload_matrix(ctx, ctx->hm[w], ctx->dm[w]));
+        }
+        ctx->analyzed = true;
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        for (int w = 0; w < 2; w++) {
+            info->n[w] = ctx->hm[w].n;
+            info->nnz_l[w] = ctx->hm[w].Lp[ctx->hm[w].n];
+            info->nlevels[w] = ctx->hm[w].nlev;
+            info->max_col[w] = ctx->hm[w].max_col;
+            info->nupdates[w] = ctx->hm[w].uoff.empty() ? 0 : ctx->hm[w].uoff.back();
+        }
+        info->nnz_ybus = ctx->rowptr[ctx->nbus];
+        info->analyze_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    }
+    return PF_OK;
+}
+
+pf_status pf_get_symbolic(const pf_ctx *ctx, int32_t which, int32_t *perm, int32_t *parent,
+                          int32_t *level, int64_t *Lp, int32_t *Li) {
+    if (!ctx || (which != PF_MAT_BP && which != PF_MAT_BPP)) return PF_ERR_ARG;
+    if (!ctx->analyzed) return PF_ERR_STATE;
+    const HostMat &H = ctx->hm[which];
+    if (perm) std::copy(H.perm.begin(), H.perm.end(), perm);
+    if (parent) std::copy(H.parent.begin(), H.parent.end(), parent);
+    if (level) std::copy(H.level.begin(), H.level.end(), level);
+    if (Lp) std::copy(H.Lp.begin(), H.Lp.end(), Lp);
+    if (Li) std::copy(H.Li.begin(), H.Li.end(), Li);
+    return PF_OK;
+}
+
+pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
+                       const int32_t *outage) {
+    if (!ctx || ncase < 1) return fail(ctx, PF_ERR_ARG, "ncase must be >= 1");
+    if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    std::vector<int> out(ncase, -1), inst(ncase, 0), inst_out(1, -1);
+    for (int c = 0; c < ncase; c++) {
+        if (outage) {
+            if (outage[c] < -1 || outage[c] >= ctx->nbr)
+                return fail(ctx, PF_ERR_ARG, "outage[%d] = %d out of range", c, outage[c]);
+            out[c] = outage[c];
+        }
+        if (out[c] >= 0) {
+            inst[c] = int(inst_out.size());
+            inst_out.push_back(out[c]);
+        }
+    }
+    if (load_scale)
+        for (size_t q = 0; q < size_t(ncase) * ctx->nbus; q++)
+            if (!std::isfinite(load_scale[q])) return fail(ctx, PF_ERR_ARG, "non-finite load scale");
+    TRY(ensure_device(ctx));
+    free_case_storage(ctx);
+    DevCases &dc = ctx->dc;
+    dc.ncase = ncase;
+    dc.ninst = int(inst_out.size());
+    TRY(upload(ctx, &dc.outage, out.data(), out.size()));
+    TRY(upload(ctx, &dc.inst, inst.data(), inst.size()));
+    TRY(upload(ctx, &dc.inst_outage, inst_out.data(), inst_out.size()));
+    TRY(dalloc(ctx, &dc.Psp, size_t(ncase) * ctx->nbus));
+    TRY(dalloc(ctx, &dc.Qsp, size_t(ncase) * ctx->nbus));
+    double *ls = nullptr;
+    if (load_scale) TRY(upload(ctx, &ls, load_scale, size_t(ncase) * ctx->nbus));
+    cudaError_t e = counted(ctx, PF_K_SPEC, 1, 0, [&] { return launch_case_spec(ctx->dn, dc, ls, 0); });
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (ls) dfree(ctx, ls);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "case spec");
+    Workspace &w = ctx->ws;
+    TRY(dalloc(ctx, &w.ef, size_t(ncase) * 2 * ctx->nbus));
+    TRY(dalloc(ctx, &w.vec, size_t(ncase) * 2 * ctx->nbus));
+    TRY(dalloc(ctx, &w.res, size_t(ncase)));
+    w.ncase_alloc = ncase;
+    return PF_OK;
+}
+
+pf_status pf_factor(pf_ctx *ctx, int32_t which, int32_t precision, void *stream) {
+    if (!ctx || (which != PF_MAT_BP && which != PF_MAT_BPP) ||
+        (precision != PF_FP64 && precision != PF_FP32))
+        return fail(ctx, PF_ERR_ARG, "bad matrix or precision");
+    if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    TRY(ensure_cases(ctx));
+    TRY(assemble_ybus(ctx, (cudaStream_t)stream));
+    return factor_matrix(ctx, which, precision, (cudaStream_t)stream);
+}
+
+pf_status pf_get_factor(pf_ctx *ctx, int32_t which, int32_t precision, int32_t c, double *D,
+                        double *Lx, int32_t *status) {
+    if (!ctx || (which != PF_MAT_BP && which != PF_MAT_BPP) ||
+        (precision != PF_FP64 && precision != PF_FP32))
+        return fail(ctx, PF_ERR_ARG, "bad matrix or precision");
+    if (!ctx->ws.factored[which][precision]) return fail(ctx, PF_ERR_STATE, "not factored");
+    if (c < 0 || c >= ctx->dc.ncase) return fail(ctx, PF_ERR_ARG, "case out of range");
+    const DevMat &m = ctx->dm[which];
+    int inst = 0;
+    cudaError_t e = cudaMemcpy(&inst, ctx->dc.inst + c, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "get_factor");
+    std::vector<double> v(m.n + m.nnz_l);
+    if (precision == PF_FP64) {
+        e = cudaMemcpy(v.data(), ctx->ws.F64[which] + size_t(inst) * m.stride,
+                       sizeof(double) * v.size(), cudaMemcpyDeviceToHost);
+    } else {
+        std::vector<float> f(v.size());
+        e = cudaMemcpy(f.data(), ctx->ws.F32[which] + size_t(inst) * m.stride,
+                       sizeof(float) * f.size(), cudaMemcpyDeviceToHost);
+        for (size_t q = 0; q < f.size(); q++) v[q] = f[q];
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "get_factor");
+    if (D) std::copy(v.begin(), v.begin() + m.n, D);
+    if (Lx) std::copy(v.begin() + m.n, v.end(), Lx);
+    if (status) {
+        e = cudaMemcpy(status, ctx->ws.fstatus[which][precision] + inst, sizeof(int),
+                       cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "get_factor status");
+    }
+    return PF_OK;
+}
+
+pf_status pf_solve(pf_ctx *ctx, int32_t which, int32_t precision, int32_t transpose,
+                   double *rhs_inout_dev, int32_t ncase, void *stream) {
+    (void)transpose;  // B' and B'' are symmetric
+    if (!ctx || (which != PF_MAT_BP && which != PF_MAT_BPP) || !rhs_inout_dev ||
+        (precision != PF_FP64 && precision != PF_FP32))
+        return fail(ctx, PF_ERR_ARG, "bad argument");
+    if (!ctx->ws.factored[which][precision]) return fail(ctx, PF_ERR_STATE, "pf_factor first");
+    if (ncase < 1 || ncase > ctx->dc.ncase) return fail(ctx, PF_ERR_ARG, "ncase out of range");
+    const void *F = precision == PF_FP64 ? (const void *)ctx->ws.F64[which]
+                                         : (const void *)ctx->ws.F32[which];
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = counted(ctx, PF_K_SOLVE, 1, s, [&] {
+        return launch_solve(ctx->dm[which], precision, F, ctx->dc.inst, rhs_inout_dev, ncase,
+                            ctx->ws.vec, ctx->smem_optin, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "solve launch");
+    return PF_OK;
+}
+
+pf_status pf_mismatch(pf_ctx *ctx, const double *vm_dev, const double *va_dev, double *dp_dev,
+                      double *dq_dev, double *maxmis_dev, int32_t ncase, void *stream) {
+    if (!ctx || !vm_dev || !va_dev || !dp_dev || !dq_dev || !maxmis_dev)
+        return fail(ctx, PF_ERR_ARG, "null pointer");
+    if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    TRY(ensure_cases(ctx));
+    if (ncase < 1 || ncase > ctx->dc.ncase) return fail(ctx, PF_ERR_ARG, "ncase out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(assemble_ybus(ctx, s));
+    cudaError_t e = counted(ctx, PF_K_MISMATCH, 2, s, [&] {
+        return launch_mismatch(ctx->dn, ctx->dc, vm_dev, va_dev, dp_dev, dq_dev, maxmis_dev,
+                               ctx->ws.ef, ncase, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mismatch launch");
+    return PF_OK;
+}
+
+pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                        pf_case_result *res_host, void *stream) {
+    if (!ctx || !opts || !vm_dev || !va_dev || !res_host) return fail(ctx, PF_ERR_ARG, "null pointer");
+    if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    if (opts->method != PF_FDPF)
+        return fail(ctx, PF_ERR_ARG, "method %d not available", opts->method);
+    if (opts->precision != PF_FP64 && opts->precision != PF_FP32)
+        return fail(ctx, PF_ERR_ARG, "bad precision");
+    if (!(opts->tol > 0) || opts->max_iter < 1) return fail(ctx, PF_ERR_ARG, "bad tol/max_iter");
+    TRY(ensure_cases(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int prec = opts->precision;
+    TRY(assemble_ybus(ctx, s));
+    TRY(factor_matrix(ctx, PF_MAT_BP, prec, s));
+    TRY(factor_matrix(ctx, PF_MAT_BPP, prec, s));
+    Workspace &w = ctx->ws;
+    const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
+    const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
+    cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
+        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, w.fstatus[0][prec],
+                           w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.vec, w.res,
+                           ctx->smem_optin, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
+    e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf run");
+    for (int c = 0; c < ctx->dc.ncase; c++)
+        if (res_host[c].status != PF_OK)
+            return fail(ctx, pf_status(res_host[c].status), "case %d: status %d after %d iterations",
+                        c, res_host[c].status, res_host[c].iters);
+    return PF_OK;
+}
+
+pf_status pf_set_profiling(pf_ctx *ctx, int32_t on) {
+    if (!ctx) return PF_ERR_ARG;
+    ctx->profiling = on != 0;
+    return PF_OK;
+}
+
+pf_status pf_get_profile(pf_ctx *ctx, int32_t kind, int64_t *launches, double *total_ms,
+                         int32_t reset) {
+    if (!ctx || kind < 0 || kind >= PF_K_COUNT) return PF_ERR_ARG;
+    KernelStat &k = ctx->kstat[kind];
+    drain_events(ctx, k);
+    if (launches) *launches = k.launches;
+    if (total_ms) *total_ms = k.ms;
+    if (reset) {
+        k.launches = 0;
+        k.ms = 0.0;
+    }
+    return PF_OK;
+}
+
+const char *pf_last_error(const pf_ctx *ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+pf_status pf_get_ybus(pf_ctx *ctx, int32_t *rowptr, int32_t *col, double *G, double *B) {
+    if (!ctx) return PF_ERR_ARG;
+    if (rowptr) std::copy(ctx->rowptr.begin(), ctx->rowptr.end(), rowptr);
+    if (col) std::copy(ctx->col.begin(), ctx->col.end(), col);
+    if (G || B) {
+        TRY(ensure_device(ctx));
+        TRY(assemble_ybus(ctx, 0));
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess && G)
+            e = cudaMemcpy(G, ctx->dn.G, sizeof(double) * ctx->dn.nnz, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && B)
+            e = cudaMemcpy(B, ctx->dn.B, sizeof(double) * ctx->dn.nnz, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "get_ybus");
+    }
+    return PF_OK;
+}
+
+void pf_destroy(pf_ctx *ctx) {
+    if (!ctx) return;
+    for (auto &k : ctx->kstat) {
+        for (auto &pr : k.pending) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        k.pending.clear();
+    }
+    for (void *p : ctx->allocations) cudaFree(p);
+    ctx->allocations.clear();
+    delete ctx;
+}
+
+}  // extern "C"

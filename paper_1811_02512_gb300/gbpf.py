@@ -1,0 +1,281 @@
+"""Thin ctypes binding of libgbpf (include/gbpf.h), same names as the C ABI.
+
+Only argument marshalling lives here: every step of the power flow runs in
+the CUDA library.  PyTorch supplies device memory (``Tensor.data_ptr()``) and
+streams.  If the shared library is missing the import of any entry point
+raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import gridgen
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libgbpf.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "gbpf.h")
+
+PF_OK, PF_ERR_ARG, PF_ERR_ISLAND, PF_ERR_SINGULAR, PF_ERR_NONFINITE = 0, 1, 2, 3, 4
+PF_ERR_NOT_CONVERGED, PF_ERR_TIMEOUT, PF_ERR_CUDA, PF_ERR_OOM, PF_ERR_STATE = 5, 6, 7, 8, 9
+STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_ISLAND", 3: "PF_ERR_SINGULAR",
+                4: "PF_ERR_NONFINITE", 5: "PF_ERR_NOT_CONVERGED", 6: "PF_ERR_TIMEOUT",
+                7: "PF_ERR_CUDA", 8: "PF_ERR_OOM", 9: "PF_ERR_STATE"}
+PF_BUS_PQ, PF_BUS_PV, PF_BUS_SLACK = 1, 2, 3
+PF_MAT_BP, PF_MAT_BPP = 0, 1
+PF_FDPF, PF_NR = 1, 2
+PF_FP64, PF_FP32 = 0, 1
+
+
+class pf_bus(C.Structure):
+    _fields_ = [("id", C.c_int32), ("type", C.c_int32), ("pd", C.c_double), ("qd", C.c_double),
+                ("gs", C.c_double), ("bs", C.c_double), ("pg", C.c_double), ("vset", C.c_double),
+                ("va", C.c_double)]
+
+
+class pf_branch(C.Structure):
+    _fields_ = [("from_", C.c_int32), ("to", C.c_int32), ("r", C.c_double), ("x", C.c_double),
+                ("b", C.c_double), ("tap", C.c_double), ("status", C.c_int32)]
+
+
+class pf_symbolic_info(C.Structure):
+    _fields_ = [("n", C.c_int32 * 2), ("nnz_l", C.c_int64 * 2), ("nlevels", C.c_int32 * 2),
+                ("max_col", C.c_int32 * 2), ("nupdates", C.c_int64 * 2), ("nnz_ybus", C.c_int32),
+                ("analyze_ms", C.c_double)]
+
+
+class pf_run_opts(C.Structure):
+    _fields_ = [("method", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("ir_max", C.c_int32), ("ir_tol", C.c_double),
+                ("flat_start", C.c_int32), ("spin_limit", C.c_int32)]
+
+
+class pf_case_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("ir_steps", C.c_int32),
+                ("pad", C.c_int32), ("max_mismatch", C.c_double)]
+
+
+assert C.sizeof(pf_bus) == gridgen.BUS_DTYPE.itemsize
+assert C.sizeof(pf_branch) == gridgen.BRANCH_DTYPE.itemsize
+CASE_RESULT_DTYPE = np.dtype([("status", "<i4"), ("iters", "<i4"), ("ir_steps", "<i4"),
+                              ("pad", "<i4"), ("max_mismatch", "<f8")], align=True)
+
+_lib = None
+_P = C.c_void_p
+
+
+def load():
+    """Loads libgbpf.so (built by paper_1811_02512_gb300.build); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                              "(the CUDA library is required; there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        S = C.c_int
+        L.pf_create.argtypes = [_P, C.c_int32, _P, C.c_int32, C.POINTER(_P)]
+        L.pf_analyze.argtypes = [_P, C.POINTER(pf_symbolic_info)]
+        L.pf_get_symbolic.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P]
+        L.pf_set_cases.argtypes = [_P, C.c_int32, _P, _P]
+        L.pf_factor.argtypes = [_P, C.c_int32, C.c_int32, _P]
+        L.pf_get_factor.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]
+        L.pf_solve.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32, _P]
+        L.pf_mismatch.argtypes = [_P, _P, _P, _P, _P, _P, C.c_int32, _P]
+        L.pf_run_to_tol.argtypes = [_P, C.POINTER(pf_run_opts), _P, _P, _P, _P]
+        L.pf_get_ybus.argtypes = [_P, _P, _P, _P, _P]
+        L.pf_set_profiling.argtypes = [_P, C.c_int32]
+        L.pf_get_profile.argtypes = [_P, C.c_int32, _P, _P, C.c_int32]
+        L.pf_last_error.argtypes = [_P]
+        L.pf_last_error.restype = C.c_char_p
+        L.pf_destroy.argtypes = [_P]
+        L.pf_destroy.restype = None
+        for name in ("pf_create", "pf_analyze", "pf_get_symbolic", "pf_set_cases", "pf_factor",
+                     "pf_get_factor", "pf_solve", "pf_mismatch", "pf_run_to_tol", "pf_get_ybus",
+                     "pf_set_profiling", "pf_get_profile"):
+            getattr(L, name).restype = S
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of every function the public header declares."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*?\**\s*\**(pf_\w+)\s*\(",
+                                 text, flags=re.M)))
+
+
+class PFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# ----------------------------------------------------------------- C ABI names
+
+def pf_create(bus_table: np.ndarray, branch_table: np.ndarray):
+    L = load()
+    bus_table = np.ascontiguousarray(bus_table, dtype=gridgen.BUS_DTYPE)
+    branch_table = np.ascontiguousarray(branch_table, dtype=gridgen.BRANCH_DTYPE)
+    out = C.c_void_p()
+    st = L.pf_create(_ptr(bus_table), len(bus_table), _ptr(branch_table), len(branch_table),
+                     C.byref(out))
+    if st != PF_OK:
+        raise PFError(st, "pf_create rejected the tables")
+    return out
+
+
+def _check(ctx, st, what):
+    if st != PF_OK:
+        raise PFError(st, f"{what}: {load().pf_last_error(ctx).decode()}")
+
+
+def pf_analyze(ctx):
+    info = pf_symbolic_info()
+    _check(ctx, load().pf_analyze(ctx, C.byref(info)), "pf_analyze")
+    return info
+
+
+def pf_get_symbolic(ctx, which, info):
+    n, nz = info.n[which], info.nnz_l[which]
+    perm = np.zeros(n, np.int32)
+    parent = np.zeros(n, np.int32)
+    level = np.zeros(n, np.int32)
+    Lp = np.zeros(n + 1, np.int64)
+    Li = np.zeros(max(nz, 1), np.int32)
+    _check(ctx, load().pf_get_symbolic(ctx, which, _ptr(perm), _ptr(parent), _ptr(level), _ptr(Lp),
+                                       _ptr(Li)), "pf_get_symbolic")
+    return dict(perm=perm, parent=parent, level=level, Lp=Lp, Li=Li[:nz])
+
+
+def pf_set_cases(ctx, ncase, load_scale=None, outage=None):
+    ls = None if load_scale is None else np.ascontiguousarray(load_scale, dtype=np.float64)
+    out = None if outage is None else np.ascontiguousarray(outage, dtype=np.int32)
+    _check(ctx, load().pf_set_cases(ctx, int(ncase), _ptr(ls), _ptr(out)), "pf_set_cases")
+
+
+def pf_factor(ctx, which, precision=PF_FP64, stream=None):
+    _check(ctx, load().pf_factor(ctx, which, precision, _stream(stream)), "pf_factor")
+
+
+def pf_get_factor(ctx, which, precision, case, info):
+    n, nz = info.n[which], info.nnz_l[which]
+    D = np.zeros(n)
+    Lx = np.zeros(max(nz, 1))
+    st = C.c_int32(0)
+    _check(ctx, load().pf_get_factor(ctx, which, precision, case, _ptr(D), _ptr(Lx), C.byref(st)),
+           "pf_get_factor")
+    return D, Lx[:nz], st.value
+
+
+def pf_solve(ctx, which, precision, rhs_dev, ncase, transpose=0, stream=None):
+    _check(ctx, load().pf_solve(ctx, which, precision, transpose, _ptr(rhs_dev), int(ncase),
+                                _stream(stream)), "pf_solve")
+
+
+def pf_mismatch(ctx, vm_dev, va_dev, dp_dev, dq_dev, maxmis_dev, ncase, stream=None):
+    _check(ctx, load().pf_mismatch(ctx, _ptr(vm_dev), _ptr(va_dev), _ptr(dp_dev), _ptr(dq_dev),
+                                   _ptr(maxmis_dev), int(ncase), _stream(stream)), "pf_mismatch")
+
+
+def run_opts(method=PF_FDPF, precision=PF_FP64, tol=1e-8, max_iter=None, ir_max=5, ir_tol=1e-10,
+             flat_start=1, spin_limit=0):
+    if max_iter is None:
+        max_iter = 200 if method == PF_FDPF else 20
+    return pf_run_opts(method, precision, tol, max_iter, ir_max, ir_tol, flat_start, spin_limit)
+
+
+def pf_run_to_tol(ctx, opts, vm_dev, va_dev, ncase, stream=None, check=True):
+    res = np.zeros(ncase, dtype=CASE_RESULT_DTYPE)
+    st = load().pf_run_to_tol(ctx, C.byref(opts), _ptr(vm_dev), _ptr(va_dev), _ptr(res),
+                              _stream(stream))
+    if check and st not in (PF_OK, PF_ERR_NOT_CONVERGED, PF_ERR_SINGULAR, PF_ERR_NONFINITE):
+        _check(ctx, st, "pf_run_to_tol")
+    return st, res
+
+
+def pf_get_ybus(ctx, nbus, nnz):
+    rowptr = np.zeros(nbus + 1, np.int32)
+    col = np.zeros(nnz, np.int32)
+    G = np.zeros(nnz)
+    B = np.zeros(nnz)
+    _check(ctx, load().pf_get_ybus(ctx, _ptr(rowptr), _ptr(col), _ptr(G), _ptr(B)), "pf_get_ybus")
+    return rowptr, col, G, B
+
+
+PF_K_YBUS, PF_K_SPEC, PF_K_ASSEMBLE, PF_K_FACTOR, PF_K_SOLVE, PF_K_MISMATCH, PF_K_RUN = range(7)
+KERNEL_KINDS = ["ybus", "spec", "assemble", "factor", "solve", "mismatch", "run"]
+
+
+def pf_set_profiling(ctx, on):
+    _check(ctx, load().pf_set_profiling(ctx, 1 if on else 0), "pf_set_profiling")
+
+
+def pf_get_profile(ctx, kind, reset=False):
+    n = C.c_int64(0)
+    ms = C.c_double(0.0)
+    _check(ctx, load().pf_get_profile(ctx, kind, C.byref(n), C.byref(ms), 1 if reset else 0),
+           "pf_get_profile")
+    return n.value, ms.value
+
+
+def pf_last_error(ctx):
+    return load().pf_last_error(ctx).decode()
+
+
+def pf_destroy(ctx):
+    if ctx:
+        load().pf_destroy(ctx)
+
+
+# ----------------------------------------------------------------- convenience
+
+class Grid:
+    """A context for one grid: ``Grid(case)`` runs pf_create and pf_analyze."""
+
+    def __init__(self, case):
+        self.case = case
+        self.ctx = pf_create(case.bus_table(), case.branch_table())
+        self.info = pf_analyze(self.ctx)
+        self.ncase = 0
+
+    @property
+    def nbus(self):
+        return self.case.n
+
+    def symbolic(self, which):
+        return pf_get_symbolic(self.ctx, which, self.info)
+
+    def set_cases(self, ncase=1, load_scale=None, outage=None):
+        pf_set_cases(self.ctx, ncase, load_scale, outage)
+        self.ncase = ncase
+
+    def close(self):
+        if self.ctx:
+            pf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

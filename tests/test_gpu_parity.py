@@ -1,0 +1,233 @@
+"""GPU parity of libgbpf against the CPU oracle, through the C ABI.
+
+Tolerances:
+  * admittance matrix, mismatch: FP64, different summation order only ->
+    1e-12 relative to the row scale;
+  * FP64 factor and solve: 1e-11 relative (left-looking vs the oracle's
+    dense-work-column LU: same operations, different rounding order);
+  * FP32 factor: the componentwise backward-error bound of LDL^T without
+    pivoting, |P A P^T - L D L^T| <= gamma_{c+1} |L||D||L^T|, u = 2^-24;
+  * voltages: |dV| <= 1e-8 p.u., |dtheta| <= 1e-8 rad with both sides run to
+    a tight mismatch (the power-flow solution is only defined to
+    ||J^-1|| * tol by a tolerance-based stop).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1811_02512_gb300 import gbpf, gridgen  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_02512_gb300 import build
+    build.build()
+    gbpf.load()
+
+
+def _grid(case, ncase=1, load_scale=None, outage=None):
+    g = gbpf.Grid(case)
+    g.set_cases(ncase, load_scale, outage)
+    return g
+
+
+CASES = {0: lambda: gridgen.config(0), 1: lambda: gridgen.config(1)}
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_ybus_parity(oracle, cfg):
+    case = CASES[cfg]()
+    case.gs = np.linspace(0, 0.01, case.n)
+    case.bs = np.linspace(-0.02, 0.02, case.n)
+    g = _grid(case)
+    rp, col, G, B = gbpf.pf_get_ybus(g.ctx, case.n, g.info.nnz_ybus)
+    rp0, col0, G0, B0 = oracle.ybus(case)
+    assert np.array_equal(rp, rp0) and np.array_equal(col, col0)
+    scale = np.repeat(np.maximum(np.abs(G0[rp0[1:] - rp0[1:] + rp0[:-1]]), 1.0), np.diff(rp0))
+    assert np.max(np.abs(G - G0)) < 1e-12 * np.max(np.abs(G0))
+    assert np.max(np.abs(B - B0)) < 1e-12 * np.max(np.abs(B0))
+    g.close()
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("which,name", [(gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")])
+def test_factor_parity_fp64_fp32(oracle, cfg, which, name):
+    case = CASES[cfg]()
+    g = _grid(case)
+    an, Lx0, d0, _ = oracle.factor_bmatrix(case, name)
+    gbpf.pf_factor(g.ctx, which, gbpf.PF_FP64)
+    D, Lx, st = gbpf.pf_get_factor(g.ctx, which, gbpf.PF_FP64, 0, g.info)
+    assert st == gbpf.PF_OK
+    assert np.max(np.abs(D - d0) / np.abs(d0)) < 1e-11
+    assert np.max(np.abs(Lx - Lx0)) < 1e-11 * max(1.0, np.max(np.abs(Lx0)))
+    gbpf.pf_factor(g.ctx, which, gbpf.PF_FP32)
+    D, Lx, st = gbpf.pf_get_factor(g.ctx, which, gbpf.PF_FP32, 0, g.info)
+    assert st == gbpf.PF_OK
+    # FP32 LDL^T without pivoting is backward stable (componentwise):
+    # |P A P^T - L D L^T| <= gamma_{c+1} |L| |D| |L^T|, gamma_k = k u / (1 - k u),
+    # u = 2^-24, c = largest column count.  Checked on the sparse product.
+    _check_backward_error(an, Lx, D, g.info.max_col[which], *_)
+    g.close()
+
+
+def _check_backward_error(an, Lx, D, max_col, Ap, Ai, Ax):
+    import scipy.sparse as sp
+    n = an["buses"].shape[0]
+    Lp, Li = an["Lp"], an["Li"]
+    cols = np.repeat(np.arange(n), np.diff(Lp))
+    L = sp.csc_matrix((np.concatenate([np.ones(n), Lx]),
+                       (np.concatenate([np.arange(n), Li]), np.concatenate([np.arange(n), cols]))),
+                      shape=(n, n))
+    A = sp.csc_matrix((Ax, Ai, Ap), shape=(n, n))
+    Dm = sp.diags(D)
+    R = (A - L @ Dm @ L.T).tocoo()
+    M = (abs(L) @ abs(Dm) @ abs(L).T).tocsr()
+    u = 2.0 ** -24
+    k = max_col + 1
+    gamma = k * u / (1 - k * u)
+    bound = np.asarray(M[R.row, R.col]).ravel() * gamma
+    assert np.all(np.abs(R.data) <= bound + 1e-300), float(np.max(np.abs(R.data) / (bound + 1e-300)))
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("which,name", [(gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")])
+def test_solve_parity(oracle, cfg, which, name):
+    case = CASES[cfg]()
+    g = _grid(case, ncase=3)
+    an, Lx0, d0, (Ap, Ai, Ax) = oracle.factor_bmatrix(case, name)
+    n = an["buses"].shape[0]
+    rng = np.random.default_rng(cfg * 10 + which)
+    rhs = rng.standard_normal((3, n))
+    iperm = np.empty(n, np.int64)
+    iperm[an["perm"]] = np.arange(n)
+    gbpf.pf_factor(g.ctx, which, gbpf.PF_FP64)
+    x_dev = torch.tensor(rhs, dtype=torch.float64, device=DEV)
+    gbpf.pf_solve(g.ctx, which, gbpf.PF_FP64, x_dev, 3)
+    torch.cuda.synchronize()
+    x = x_dev.cpu().numpy()
+    for c in range(3):
+        # oracle works in step order: x_step = solve(P A P^T, rhs_step)
+        xs = oracle.lu_solve(n, an["Lp"], an["Li"], Lx0, Lx0 * d0[np.repeat(np.arange(n), np.diff(an["Lp"]))],
+                             d0, rhs[c][an["perm"]])
+        ref = np.empty(n)
+        ref[an["perm"]] = xs
+        assert np.max(np.abs(x[c] - ref)) < 1e-11 * max(1.0, np.max(np.abs(ref)))
+    g.close()
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_mismatch_parity(oracle, cfg):
+    case = CASES[cfg]()
+    rng = np.random.default_rng(7)
+    g = _grid(case, ncase=2)
+    vm = rng.uniform(0.95, 1.05, (2, case.n))
+    va = rng.uniform(-0.2, 0.2, (2, case.n))
+    vm_d = torch.tensor(vm, device=DEV)
+    va_d = torch.tensor(va, device=DEV)
+    dp = torch.zeros_like(vm_d)
+    dq = torch.zeros_like(vm_d)
+    mx = torch.zeros(2, dtype=torch.float64, device=DEV)
+    gbpf.pf_mismatch(g.ctx, vm_d, va_d, dp, dq, mx, 2)
+    torch.cuda.synchronize()
+    rp, col, G, B = oracle.ybus(case)
+    for c in range(2):
+        dP0, dQ0, m0 = oracle.mismatch(case, rp, col, G, B, vm[c], va[c])
+        scale = max(1.0, np.max(np.abs(B)))
+        assert np.max(np.abs(dp[c].cpu().numpy() - dP0)) < 1e-12 * scale
+        assert np.max(np.abs(dq[c].cpu().numpy() - dQ0)) < 1e-12 * scale
+        assert abs(mx[c].item() - m0) < 1e-12 * scale
+    g.close()
+
+
+def _run(g, ncase, precision=gbpf.PF_FP64, tol=1e-8, max_iter=200):
+    vm = torch.zeros((ncase, g.nbus), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, precision, tol=tol, max_iter=max_iter)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+    return st, res, vm.cpu().numpy(), va.cpu().numpy()
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_fdpf_voltages_vs_oracle(oracle, cfg):
+    case = CASES[cfg]()
+    g = _grid(case)
+    st, res, vm, va = _run(g, 1, tol=1e-11, max_iter=300)
+    assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    rc, vm0, va0, it0, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
+    assert rc == oracle.OK
+    assert np.max(np.abs(vm[0] - vm0)) <= 1e-8
+    assert np.max(np.abs(va[0] - va0)) <= 1e-8
+    # at the production tolerance the iteration count matches the oracle's FDPF
+    st, res, vm, va = _run(g, 1, tol=1e-8)
+    rc, _, _, it1, _ = oracle.power_flow(case, oracle.FDPF, tol=1e-8)
+    assert st == gbpf.PF_OK and rc == oracle.OK
+    assert abs(int(res[0]["iters"]) - it1) <= 1
+    assert res[0]["max_mismatch"] <= 1e-8
+    g.close()
+
+
+def test_batched_load_and_outage_cases(oracle):
+    base = gridgen.config(0)
+    sc = gridgen.scenarios(base, n_load=5, n_outage=5, seed=11)
+    g = _grid(base, sc.ncase, sc.load_scale, sc.outage)
+    st, res, vm, va = _run(g, sc.ncase, tol=1e-11, max_iter=400)
+    assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    for c in range(sc.ncase):
+        cc = gridgen.apply_scenario(base, sc, c)
+        rc, vm0, va0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+        assert rc == oracle.OK
+        assert np.max(np.abs(vm[c] - vm0)) <= 1e-8, c
+        assert np.max(np.abs(va[c] - va0)) <= 1e-8, c
+    g.close()
+
+
+def test_singular_bpp_reported_not_trapped():
+    """A PQ bus whose B'' diagonal is exactly zero (charging cancels the series
+    susceptance) gives PF_ERR_SINGULAR from the pivot check."""
+    r, x = 0.01, 0.1
+    b = 2 * x / (r * r + x * x)
+    case = gridgen.Case(name="sing", btype=np.array([3, 1], np.int32), pd=np.array([0, 0.1]),
+                        qd=np.array([0, 0.05]), gs=np.zeros(2), bs=np.zeros(2), pg=np.zeros(2),
+                        vset=np.ones(2), va=np.zeros(2), f=np.array([0], np.int32),
+                        t=np.array([1], np.int32), r=np.array([r]), x=np.array([x]),
+                        b=np.array([b]), tap=np.ones(1), status=np.ones(1, np.int32))
+    g = _grid(case)
+    gbpf.pf_factor(g.ctx, gbpf.PF_MAT_BPP, gbpf.PF_FP64)
+    _, _, st = gbpf.pf_get_factor(g.ctx, gbpf.PF_MAT_BPP, gbpf.PF_FP64, 0, g.info)
+    assert st == gbpf.PF_ERR_SINGULAR
+    st, res, _, _ = _run(g, 1)
+    assert st == gbpf.PF_ERR_SINGULAR and res[0]["status"] == gbpf.PF_ERR_SINGULAR
+    g.close()
+
+
+def test_iteration_limit_reported():
+    g = _grid(gridgen.config(0))
+    st, res, _, _ = _run(g, 1, max_iter=1)
+    assert st == gbpf.PF_ERR_NOT_CONVERGED
+    assert res[0]["status"] == gbpf.PF_ERR_NOT_CONVERGED and res[0]["iters"] == 2
+    g.close()
+
+
+def test_no_pq_bus_empty_bpp(oracle):
+    """Degenerate grid: every non-slack bus is PV, so B'' is empty."""
+    case = gridgen.config(0)
+    case.btype = np.where(case.btype == gridgen.SLACK, gridgen.SLACK, gridgen.PV).astype(np.int32)
+    case.vset = np.where(case.vset == 1.0, 1.01, case.vset)
+    case.pg = case.pg - case.pd
+    case.pd = np.zeros(case.n)
+    case.qd = np.zeros(case.n)
+    g = _grid(case)
+    assert g.info.n[1] == 0
+    st, res, vm, va = _run(g, 1, tol=1e-11, max_iter=300)
+    assert st == gbpf.PF_OK
+    rc, vm0, va0, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12)
+    assert rc == oracle.OK
+    assert np.max(np.abs(va[0] - va0)) <= 1e-8
+    g.close()
