@@ -206,6 +206,35 @@ const char *pf_last_error(const pf_ctx *ctx);
  * B[nnz] (CSR, columns ascending, diagonal present).  Synchronous. */
 pf_status pf_get_ybus(pf_ctx *ctx, int32_t *rowptr, int32_t *col, double *G, double *B);
 
+/* Largest nbus accepted by pf_mismatch_static. */
+#define PF_STATIC_MAX_BUS 131072
+
+/* Allocation-free P/Q mismatch of one case (the paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * e.g. processes that reserve their whole device budget at start-up and
+ * forbid later allocation, or applications whose own allocator owns the GPU).
+ * It needs no context: every input and output is caller-owned device memory
+ * -- the admittance matrix rowptr[nbus+1], col[nnz], G[nnz], B[nnz] (CSR as
+ * returned by pf_get_ybus), btype[nbus] (PF_BUS_*), specified injections
+ * psp[nbus] = pg - pd and qsp[nbus] = -qd, the state vm/va[nbus]; outputs
+ * dp/dq[nbus] and maxmis[1] exactly as pf_mismatch computes them for one case
+ * without outage.  It calls no cudaMalloc, cudaFree or allocating routine:
+ * its only intermediate, the rectangular voltages, lives in a fixed device
+ * array of 2 * PF_STATIC_MAX_BUS doubles (2 MiB) that every GPU which loads
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address with the device current, so make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents: calls whose kernels can overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by
+ * the caller.  maxmis is cleared by the call.  Returns PF_ERR_ARG when nbus is
+ * < 1 or > PF_STATIC_MAX_BUS or a pointer is NULL, PF_ERR_CUDA when the
+ * address look-up or a launch fails.  Asynchronous on `stream`. */
+pf_status pf_mismatch_static(int32_t nbus, const int32_t *rowptr_dev, const int32_t *col_dev,
+                             const double *G_dev, const double *B_dev, const int32_t *btype_dev,
+                             const double *psp_dev, const double *qsp_dev, const double *vm_dev,
+                             const double *va_dev, double *dp_dev, double *dq_dev,
+                             double *maxmis_dev, void *stream);
+
 /* Releases the context and all its device memory.  NULL is accepted. */
 void pf_destroy(pf_ctx *ctx);
 

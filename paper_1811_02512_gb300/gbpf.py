@@ -88,6 +88,8 @@ def load():
         L.pf_get_ybus.argtypes = [_P, _P, _P, _P, _P]
         L.pf_set_profiling.argtypes = [_P, C.c_int32]
         L.pf_get_profile.argtypes = [_P, C.c_int32, _P, _P, C.c_int32]
+        L.pf_mismatch_static.argtypes = [C.c_int32] + [_P] * 13
+        L.pf_mismatch_static.restype = S
         L.pf_last_error.argtypes = [_P]
         L.pf_last_error.restype = C.c_char_p
         L.pf_destroy.argtypes = [_P]
@@ -236,6 +238,18 @@ def pf_get_profile(ctx, kind, reset=False):
     _check(ctx, load().pf_get_profile(ctx, kind, C.byref(n), C.byref(ms), 1 if reset else 0),
            "pf_get_profile")
     return n.value, ms.value
+
+
+PF_STATIC_MAX_BUS = 131072
+
+
+def pf_mismatch_static(nbus, rowptr_dev, col_dev, G_dev, B_dev, btype_dev, psp_dev, qsp_dev,
+                       vm_dev, va_dev, dp_dev, dq_dev, maxmis_dev, stream=None):
+    """Allocation-free single-case mismatch; returns the pf_status code."""
+    return load().pf_mismatch_static(int(nbus), _ptr(rowptr_dev), _ptr(col_dev), _ptr(G_dev),
+                                     _ptr(B_dev), _ptr(btype_dev), _ptr(psp_dev), _ptr(qsp_dev),
+                                     _ptr(vm_dev), _ptr(va_dev), _ptr(dp_dev), _ptr(dq_dev),
+                                     _ptr(maxmis_dev), _stream(stream))
 
 
 def pf_last_error(ctx):
