@@ -154,6 +154,185 @@ std::vector<int> min_degree_order(int n, std::vector<std::vector<int>> adj) {
 
 // ---------------------------------------------------------------- analysis
 
+
+// Device layout of one analysed matrix in level order (see DevMat).
+pf_status build_layout(pf_ctx *ctx, HostMat &H) {
+    const int n = H.n;
+    const int64_t nnz = H.Lp[n];
+    // level order: steps sorted by (level, step)
+    H.lvl_ptr.assign(H.nlev + 1, 0);
+    for (int j = 0; j < n; j++) H.lvl_ptr[H.level[j]]++;
+    for (int l = 0; l < H.nlev; l++) H.lvl_ptr[l + 1] += H.lvl_ptr[l];
+    H.neword.assign(n, 0);
+    H.new_of_step.assign(n, 0);
+    {
+        std::vector<int> f(H.lvl_ptr.begin(), H.lvl_ptr.end() - 1);
+        for (int j = 0; j < n; j++) {
+            int r = f[H.level[j] - 1]++;
+            H.neword[r] = j;
+            H.new_of_step[j] = r;
+        }
+    }
+    H.bus_new.assign(n, 0);
+    H.local_new.assign(n, 0);
+    H.new_of_bus.assign(ctx->nbus, -1);
+    for (int r = 0; r < n; r++) {
+        H.local_new[r] = H.perm[H.neword[r]];
+        H.bus_new[r] = H.bus[H.local_new[r]];
+        H.new_of_bus[H.bus_new[r]] = r;
+    }
+    // CSC in level order, rows ascending
+    H.Cp.assign(n + 1, 0);
+    for (int c = 0; c < n; c++) {
+        int s = H.neword[c];
+        H.Cp[c + 1] = H.Cp[c] + int(H.Lp[s + 1] - H.Lp[s]);
+    }
+    H.Cr.assign(nnz, 0);
+    H.csc_of_steppos.assign(nnz, 0);
+    {
+        std::vector<std::pair<int, int>> tmp;
+        for (int c = 0; c < n; c++) {
+            int s = H.neword[c];
+            tmp.clear();
+            for (int64_t p = H.Lp[s]; p < H.Lp[s + 1]; p++)
+                tmp.push_back({H.new_of_step[H.Li[p]], int(p)});
+            std::sort(tmp.begin(), tmp.end());
+            for (size_t t = 0; t < tmp.size(); t++) {
+                H.Cr[H.Cp[c] + t] = tmp[t].first;
+                H.csc_of_steppos[tmp[t].second] = H.Cp[c] + int(t);
+                if (tmp[t].first <= c)
+                    return fail(ctx, PF_ERR_ARG, "internal: level order is not triangular");
+            }
+        }
+    }
+    // CSR in level order (columns ascending, as c is visited ascending)
+    H.Fp.assign(n + 1, 0);
+    for (int64_t p = 0; p < nnz; p++) H.Fp[H.Cr[p] + 1]++;
+    for (int r = 0; r < n; r++) H.Fp[r + 1] += H.Fp[r];
+    H.Fc.assign(nnz, 0);
+    H.Fpos.assign(nnz, 0);
+    {
+        std::vector<int> f(H.Fp.begin(), H.Fp.end() - 1);
+        for (int c = 0; c < n; c++)
+            for (int p = H.Cp[c]; p < H.Cp[c + 1]; p++) {
+                int q = f[H.Cr[p]]++;
+                H.Fc[q] = c;
+                H.Fpos[q] = p;
+            }
+    }
+    // update maps of the left-looking factor: CSR entry (c, k) updates column
+    // c from the entries of column k at rows >= c (a contiguous tail of k)
+    H.uoff.assign(nnz + 1, 0);
+    for (int c = 0; c < n; c++)
+        for (int q = H.Fp[c]; q < H.Fp[c + 1]; q++) {
+            int k = H.Fc[q];
+            H.uoff[q + 1] = H.uoff[q] + (H.Cp[k + 1] - H.Fpos[q]);
+        }
+    H.nupd = H.uoff[nnz];
+    H.umap.assign(std::max<int64_t>(1, H.nupd), 0);
+    for (int c = 0; c < n; c++) {
+        const int *cb = H.Cr.data() + H.Cp[c];
+        const int *ce = H.Cr.data() + H.Cp[c + 1];
+        for (int q = H.Fp[c]; q < H.Fp[c + 1]; q++) {
+            int k = H.Fc[q];
+            int o = H.uoff[q];
+            for (int p = H.Fpos[q]; p < H.Cp[k + 1]; p++) {
+                int i = H.Cr[p];
+                int tgt = 0;
+                if (i != c) {
+                    const int *f = std::lower_bound(cb, ce, i);
+                    if (f == ce || *f != i) return fail(ctx, PF_ERR_ARG, "internal: fill not closed");
+                    tgt = 1 + int(f - cb);
+                }
+                H.umap[o++] = tgt;
+            }
+        }
+    }
+    auto pad32 = [](int64_t v) { return int((v + 31) / 32 * 32); };
+    H.offDi = pad32(n);
+    H.offLc = H.offDi + pad32(n);
+    H.offLr = H.offLc + pad32(nnz);
+    H.stride = H.offLr + pad32(nnz);
+    // slot sources from the Ybus pattern
+    H.src.assign(n + nnz, -1);
+    for (int r = 0; r < n; r++) H.src[r] = ypos(ctx, H.bus_new[r], H.bus_new[r]);
+    for (int c = 0; c < n; c++)
+        for (int p = H.Cp[c]; p < H.Cp[c + 1]; p++)
+            H.src[n + p] = ypos(ctx, H.bus_new[H.Cr[p]], H.bus_new[c]);
+    H.br_slot.assign(3 * size_t(ctx->nbr), -1);
+    for (int e = 0; e < ctx->nbr; e++) {
+        int a = H.new_of_bus[ctx->branch[e].from], b = H.new_of_bus[ctx->branch[e].to];
+        H.br_slot[3 * e + 0] = a;
+        H.br_slot[3 * e + 1] = b;
+        if (a >= 0 && b >= 0) {
+            int lo = std::min(a, b), hi = std::max(a, b);
+            const int *cb = H.Cr.data() + H.Cp[lo];
+            const int *ce = H.Cr.data() + H.Cp[lo + 1];
+            const int *f = std::lower_bound(cb, ce, hi);
+            if (f == ce || *f != hi) return fail(ctx, PF_ERR_ARG, "internal: branch slot missing");
+            H.br_slot[3 * e + 2] = H.offLc + int(f - H.Cr.data());
+        }
+    }
+    // staged pieces: runs of rows (columns) of one level whose pointers,
+    // indices and (8-byte) values fit one stage
+    auto make_pieces = [&](const std::vector<int> &ptr, bool ascending, std::vector<Piece> &out) {
+        out.clear();
+        const int budget = kPieceBytes - kPieceSlack;
+        auto level_bytes = [&](int l) {
+            int64_t b = 4;  // its level pointer
+            for (int r = H.lvl_ptr[l]; r < H.lvl_ptr[l + 1]; r++) b += 12 + 12 * int64_t(ptr[r + 1] - ptr[r]);
+            return b;
+        };
+        int li = 0;
+        while (li < H.nlev) {
+            int l = ascending ? li : H.nlev - 1 - li;
+            const int lrows = H.lvl_ptr[l + 1] - H.lvl_ptr[l];
+            if (lrows <= kNarrowRows) {
+                // whole narrow levels, as many consecutive ones as fit
+                int64_t bytes = 8 + level_bytes(l);
+                int lo = l, hi = l;
+                li++;
+                while (li < H.nlev) {
+                    int l2 = ascending ? li : H.nlev - 1 - li;
+                    if (H.lvl_ptr[l2 + 1] - H.lvl_ptr[l2] > kNarrowRows) break;
+                    int64_t add = level_bytes(l2);
+                    if (bytes + add > budget) break;
+                    bytes += add;
+                    lo = std::min(lo, l2);
+                    hi = std::max(hi, l2);
+                    li++;
+                }
+                if (bytes > budget) return fail(ctx, PF_ERR_ARG, "internal: narrow level exceeds a stage");
+                const int r0 = H.lvl_ptr[lo], r1 = H.lvl_ptr[hi + 1];
+                out.push_back(Piece{r0, r1, ptr[r0], ptr[r1], 2, 0, lo, hi});
+                continue;
+            }
+            const int mode = lrows <= 4 * kSweepWarps ? 1 : 0;
+            int r = H.lvl_ptr[l], rend = H.lvl_ptr[l + 1];
+            while (r < rend) {
+                int r0 = r;
+                int64_t bytes = 4;
+                while (r < rend) {
+                    int64_t add = 12 + 12 * int64_t(ptr[r + 1] - ptr[r]);
+                    if (r > r0 && bytes + add > budget) break;
+                    bytes += add;
+                    r++;
+                }
+                out.push_back(Piece{r0, r, ptr[r0], ptr[r], mode, 0, l, l});
+            }
+            li++;
+        }
+        // end of every run of single-warp pieces
+        int np = int(out.size());
+        for (int j = np - 1; j >= 0; j--)
+            if (out[j].mode == 2) out[j].run_end = (j + 1 < np && out[j + 1].mode == 2) ? out[j + 1].run_end : j + 1;
+        return PF_OK;
+    };
+    TRY(make_pieces(H.Fp, true, H.pf));
+    TRY(make_pieces(H.Cp, false, H.pb));
+    return PF_OK;
+}
+
 pf_status analyze_matrix(pf_ctx *ctx, int which, HostMat &H) {
     const int nbus = ctx->nbus;
     H = HostMat();
@@ -221,19 +400,8 @@ pf_status analyze_matrix(pf_ctx *ctx, int which, HostMat &H) {
     if (nnz_l > INT32_MAX / 2) return fail(ctx, PF_ERR_OOM, "factor too large (%lld)", (long long)nnz_l);
     H.Li.assign(nnz_l, 0);
     std::vector<int64_t> fill(H.Lp.begin(), H.Lp.end() - 1);
-    H.Rp.assign(n + 1, 0);
-    H.Rk.assign(nnz_l, 0);
-    H.Rpos.assign(nnz_l, 0);
-    for (int i = 0; i < n; i++) {
-        H.Rp[i + 1] = H.Rp[i] + int(rows[i].size());
-        for (size_t q = 0; q < rows[i].size(); q++) {
-            int k = rows[i][q];
-            int64_t p = fill[k]++;
-            H.Li[p] = i;
-            H.Rk[H.Rp[i] + q] = k;
-            H.Rpos[H.Rp[i] + q] = int(p);
-        }
-    }
+    for (int i = 0; i < n; i++)
+        for (int k : rows[i]) H.Li[fill[k]++] = i;
     H.max_col = 0;
     for (int k = 0; k < n; k++) H.max_col = std::max<int>(H.max_col, int(H.Lp[k + 1] - H.Lp[k]));
     // levels: leaves 1, parents 1 + max over children
@@ -242,92 +410,44 @@ pf_status analyze_matrix(pf_ctx *ctx, int which, HostMat &H) {
         if (H.parent[j] >= 0) H.level[H.parent[j]] = std::max(H.level[H.parent[j]], H.level[j] + 1);
     H.nlev = 0;
     for (int j = 0; j < n; j++) H.nlev = std::max(H.nlev, H.level[j]);
-    H.lvl_ptr.assign(H.nlev + 1, 0);
-    for (int j = 0; j < n; j++) H.lvl_ptr[H.level[j]]++;
-    for (int l = 0; l < H.nlev; l++) H.lvl_ptr[l + 1] += H.lvl_ptr[l];
-    H.lvl_cols.assign(n, 0);
-    {
-        std::vector<int> f(H.lvl_ptr.begin(), H.lvl_ptr.end() - 1);
-        for (int j = 0; j < n; j++) H.lvl_cols[f[H.level[j] - 1]++] = j;
-    }
-    // update maps of the left-looking factor: row-list entry (j, k) updates
-    // column j from the entries of column k at rows >= j
-    H.uoff.assign(nnz_l + 1, 0);
-    for (int j = 0; j < n; j++)
-        for (int q = H.Rp[j]; q < H.Rp[j + 1]; q++) {
-            int k = H.Rk[q];
-            H.uoff[q + 1] = H.uoff[q] + int(H.Lp[k + 1] - H.Rpos[q]);
-        }
-    H.umap.assign(std::max(1, H.uoff[nnz_l]), 0);
-    for (int j = 0; j < n; j++) {
-        const int *cb = H.Li.data() + H.Lp[j];
-        const int *ce = H.Li.data() + H.Lp[j + 1];
-        for (int q = H.Rp[j]; q < H.Rp[j + 1]; q++) {
-            int k = H.Rk[q];
-            int o = H.uoff[q];
-            for (int64_t p = H.Rpos[q]; p < H.Lp[k + 1]; p++) {
-                int i = H.Li[p];
-                int tgt;
-                if (i == j) {
-                    tgt = 0;
-                } else {
-                    const int *f = std::lower_bound(cb, ce, i);
-                    if (f == ce || *f != i)
-                        return fail(ctx, PF_ERR_ARG, "internal: fill pattern not closed");
-                    tgt = 1 + int(f - cb);
-                }
-                H.umap[o++] = tgt;
-            }
-        }
-    }
-    // slot sources: diagonal slots then L slots, from the Ybus pattern
-    H.src.assign(n + nnz_l, -1);
-    for (int k = 0; k < n; k++) H.src[k] = ypos(ctx, H.bus[H.perm[k]], H.bus[H.perm[k]]);
-    for (int k = 0; k < n; k++)
-        for (int64_t p = H.Lp[k]; p < H.Lp[k + 1]; p++)
-            H.src[n + p] = ypos(ctx, H.bus[H.perm[H.Li[p]]], H.bus[H.perm[k]]);
-    H.step_of_bus.assign(nbus, -1);
-    for (int k = 0; k < n; k++) H.step_of_bus[H.bus[H.perm[k]]] = k;
-    H.br_slot.assign(3 * size_t(ctx->nbr), -1);
-    for (int e = 0; e < ctx->nbr; e++) {
-        int sf = H.step_of_bus[ctx->branch[e].from], st = H.step_of_bus[ctx->branch[e].to];
-        H.br_slot[3 * e + 0] = sf;
-        H.br_slot[3 * e + 1] = st;
-        if (sf >= 0 && st >= 0) {
-            int lo = std::min(sf, st), hi = std::max(sf, st);
-            const int *cb = H.Li.data() + H.Lp[lo];
-            const int *ce = H.Li.data() + H.Lp[lo + 1];
-            const int *f = std::lower_bound(cb, ce, hi);
-            H.br_slot[3 * e + 2] = n + int(f - H.Li.data());
-        }
-    }
-    return PF_OK;
+    return build_layout(ctx, H);
+}
+
+// Uploads an int array padded by 16 bytes so that 16-byte-rounded bulk
+// copies of its tail stay inside the allocation.
+pf_status upload_padded(pf_ctx *ctx, int **dst, const std::vector<int> &v) {
+    std::vector<int> tmp(v);
+    tmp.resize(v.size() + 8, 0);
+    return upload(ctx, dst, tmp.data(), tmp.size());
 }
 
 pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
     D.n = H.n;
-    D.nnz_l = int(H.Lp[H.n]);
+    D.nnz = int(H.Lp[H.n]);
     D.nlev = H.nlev;
     D.max_col = H.max_col;
-    D.nupd = H.uoff.empty() ? 0 : H.uoff.back();
-    D.stride = ((H.n + D.nnz_l + 31) / 32) * 32;
-    std::vector<int> busstep(H.n), Lp32(H.n + 1);
-    for (int k = 0; k < H.n; k++) busstep[k] = H.bus[H.perm[k]];
-    for (int k = 0; k <= H.n; k++) Lp32[k] = int(H.Lp[k]);
-    TRY(upload(ctx, &D.bus, busstep.data(), busstep.size()));
-    TRY(upload(ctx, &D.perm, H.perm.data(), H.perm.size()));
-    TRY(upload(ctx, &D.Lp, Lp32.data(), Lp32.size()));
-    TRY(upload(ctx, &D.Li, H.Li.data(), H.Li.size()));
-    TRY(upload(ctx, &D.Rp, H.Rp.data(), H.Rp.size()));
-    TRY(upload(ctx, &D.Rk, H.Rk.data(), H.Rk.size()));
-    TRY(upload(ctx, &D.Rpos, H.Rpos.data(), H.Rpos.size()));
-    TRY(upload(ctx, &D.lvl_ptr, H.lvl_ptr.data(), H.lvl_ptr.size()));
-    TRY(upload(ctx, &D.lvl_cols, H.lvl_cols.data(), H.lvl_cols.size()));
-    TRY(upload(ctx, &D.uoff, H.uoff.data(), H.uoff.size()));
-    TRY(upload(ctx, &D.umap, H.umap.data(), H.umap.size()));
-    TRY(upload(ctx, &D.src, H.src.data(), H.src.size()));
-    TRY(upload(ctx, &D.step_of_bus, H.step_of_bus.data(), H.step_of_bus.size()));
-    TRY(upload(ctx, &D.br_slot, H.br_slot.data(), H.br_slot.size()));
+    D.nupd = H.nupd;
+    D.offDi = H.offDi;
+    D.offLc = H.offLc;
+    D.offLr = H.offLr;
+    D.stride = H.stride;
+    D.npf = int(H.pf.size());
+    D.npb = int(H.pb.size());
+    TRY(upload_padded(ctx, &D.bus, H.bus_new));
+    TRY(upload_padded(ctx, &D.local, H.local_new));
+    TRY(upload_padded(ctx, &D.new_of_bus, H.new_of_bus));
+    TRY(upload_padded(ctx, &D.lvl_ptr, H.lvl_ptr));
+    TRY(upload_padded(ctx, &D.Cp, H.Cp));
+    TRY(upload_padded(ctx, &D.Cr, H.Cr));
+    TRY(upload_padded(ctx, &D.Fp, H.Fp));
+    TRY(upload_padded(ctx, &D.Fc, H.Fc));
+    TRY(upload_padded(ctx, &D.Fpos, H.Fpos));
+    TRY(upload_padded(ctx, &D.uoff, H.uoff));
+    TRY(upload_padded(ctx, &D.umap, H.umap));
+    TRY(upload_padded(ctx, &D.src, H.src));
+    TRY(upload_padded(ctx, &D.br_slot, H.br_slot));
+    TRY(upload(ctx, &D.pf, H.pf.data(), H.pf.size()));
+    TRY(upload(ctx, &D.pb, H.pb.data(), H.pb.size()));
     return PF_OK;
 }
 
@@ -428,6 +548,8 @@ void free_case_storage(pf_ctx *ctx) {
     }
     dfree(ctx, w.ef); w.ef = nullptr;
     dfree(ctx, w.vec); w.vec = nullptr;
+    dfree(ctx, w.bmax); w.bmax = nullptr;
+    dfree(ctx, w.cstatus); w.cstatus = nullptr;
     dfree(ctx, w.res); w.res = nullptr;
     dfree(ctx, ctx->dc.outage); ctx->dc.outage = nullptr;
     dfree(ctx, ctx->dc.inst); ctx->dc.inst = nullptr;
@@ -589,7 +711,7 @@ pf_status pf_analyze(pf_ctx *ctx, pf_symbolic_info *info) {
             info->nnz_l[w] = ctx->hm[w].Lp[ctx->hm[w].n];
             info->nlevels[w] = ctx->hm[w].nlev;
             info->max_col[w] = ctx->hm[w].max_col;
-            info->nupdates[w] = ctx->hm[w].uoff.empty() ? 0 : ctx->hm[w].uoff.back();
+            info->nupdates[w] = ctx->hm[w].nupd;
         }
         info->nnz_ybus = ctx->rowptr[ctx->nbus];
         info->analyze_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -646,8 +768,12 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
     if (ls) dfree(ctx, ls);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "case spec");
     Workspace &w = ctx->ws;
-    TRY(dalloc(ctx, &w.ef, size_t(ncase) * 2 * ctx->nbus));
+    TRY(dalloc(ctx, &w.ef, size_t(ncase) * 4 * ctx->nbus));
     TRY(dalloc(ctx, &w.vec, size_t(ncase) * 2 * ctx->nbus));
+    TRY(dalloc(ctx, &w.bmax, size_t(ncase) * 16));
+    TRY(dalloc(ctx, &w.cstatus, size_t(ncase)));
+    if (cudaMemset(w.cstatus, 0, sizeof(int) * ncase) != cudaSuccess)
+        return fail(ctx, PF_ERR_CUDA, "memset");
     TRY(dalloc(ctx, &w.res, size_t(ncase)));
     w.ncase_alloc = ncase;
     return PF_OK;
@@ -671,10 +797,11 @@ pf_status pf_get_factor(pf_ctx *ctx, int32_t which, int32_t precision, int32_t c
     if (!ctx->ws.factored[which][precision]) return fail(ctx, PF_ERR_STATE, "not factored");
     if (c < 0 || c >= ctx->dc.ncase) return fail(ctx, PF_ERR_ARG, "case out of range");
     const DevMat &m = ctx->dm[which];
+    const HostMat &H = ctx->hm[which];
     int inst = 0;
     cudaError_t e = cudaMemcpy(&inst, ctx->dc.inst + c, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "get_factor");
-    std::vector<double> v(m.n + m.nnz_l);
+    std::vector<double> v(m.offLc + m.nnz);
     if (precision == PF_FP64) {
         e = cudaMemcpy(v.data(), ctx->ws.F64[which] + size_t(inst) * m.stride,
                        sizeof(double) * v.size(), cudaMemcpyDeviceToHost);
@@ -685,8 +812,11 @@ pf_status pf_get_factor(pf_ctx *ctx, int32_t which, int32_t precision, int32_t c
         for (size_t q = 0; q < f.size(); q++) v[q] = f[q];
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "get_factor");
-    if (D) std::copy(v.begin(), v.begin() + m.n, D);
-    if (Lx) std::copy(v.begin() + m.n, v.end(), Lx);
+    // back to step numbering
+    if (D)
+        for (int st = 0; st < m.n; st++) D[st] = v[H.new_of_step[st]];
+    if (Lx)
+        for (int p = 0; p < m.nnz; p++) Lx[p] = v[m.offLc + H.csc_of_steppos[p]];
     if (status) {
         e = cudaMemcpy(status, ctx->ws.fstatus[which][precision] + inst, sizeof(int),
                        cudaMemcpyDeviceToHost);
@@ -708,7 +838,7 @@ pf_status pf_solve(pf_ctx *ctx, int32_t which, int32_t precision, int32_t transp
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = counted(ctx, PF_K_SOLVE, 1, s, [&] {
         return launch_solve(ctx->dm[which], precision, F, ctx->dc.inst, rhs_inout_dev, ncase,
-                            ctx->ws.vec, ctx->smem_optin, s);
+                            ctx->ws.vec, ctx->ws.cstatus, ctx->smem_optin, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve launch");
     return PF_OK;
@@ -749,10 +879,12 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
     Workspace &w = ctx->ws;
     const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
     const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
+    const int cl = fdpf_cluster_size(ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin,
+                                     std::max(ctx->dm[0].n, ctx->dm[1].n));
     cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
         return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, w.fstatus[0][prec],
-                           w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.vec, w.res,
-                           ctx->smem_optin, s);
+                           w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.vec, w.bmax, w.res,
+                           ctx->smem_optin, cl, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
     e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,

@@ -13,33 +13,55 @@
 
 namespace gbpf {
 
-// Symbolic data of one factorised matrix (B' or B''), device copies.
-// Numbering: "step" k = position in the elimination order; every array below
-// is in step numbering unless named otherwise.
+// Payload budget of one staged piece of a substitution sweep (bytes): the
+// row pointers, column indices and values of a run of rows (columns) of one
+// level, copied into shared memory by one TMA bulk transfer group.
+constexpr int kPieceBytes = 8192;
+constexpr int kPieceSlack = 128;
+
+// One staged piece: rows (columns) [r0, r1) whose entries are [e0, e1) of
+// the CSR (CSC) arrays, all in level order.  mode: 0 one thread per row,
+// 1 one warp per row (whole block), 2 warp 0 alone; run_end: for mode 2, the
+// first piece after the run of mode-2 pieces.  A mode 0/1 piece lies inside
+// one level; a mode-2 piece holds whole narrow levels l0..l1.
+struct Piece {
+    int r0, r1, e0, e1;
+    int mode, run_end, l0, l1;
+};
+constexpr int kSweepWarps = 16;   // warps of the blocks that run the sweeps
+constexpr int kNarrowRows = 16;   // levels with at most this many rows run on one warp
+
+// Device layout of one factorised matrix (B' or B'').  All indices are in
+// "level order": the elimination steps sorted by (level, step), so every
+// level of the elimination tree is a contiguous range and the strict lower
+// factor L stays lower triangular (a parent is always on a higher level).
+// Per-instance factor values: [D: n | Dinv: 1/D | Lc: L by column (CSC) |
+// Lr: L by row (CSR)], regions starting at multiples of 32 elements.
 struct DevMat {
     int n = 0;           // dimension (buses in the matrix)
-    int nnz_l = 0;       // strict-lower nonzeros of L
+    int nnz = 0;         // strict-lower nonzeros of L
     int nlev = 0;        // levels of the elimination tree
     int max_col = 0;     // largest column count of L
-    int64_t nupd = 0;    // entries of the update map
-    int stride = 0;      // per-instance value stride: n diagonal slots + nnz_l, padded
-    int *bus = nullptr;      // [n]     step -> global bus
-    int *perm = nullptr;     // [n]     step -> local index (ascending-bus order)
-    int *Lp = nullptr;       // [n+1]   column pointers of L
-    int *Li = nullptr;       // [nnz_l] row (step) of every L entry, ascending per column
-    int *Rp = nullptr;       // [n+1]   row pointers of L (row lists)
-    int *Rk = nullptr;       // [nnz_l] column (step) of every row-list entry, ascending
-    int *Rpos = nullptr;     // [nnz_l] position in the column-ordered L values
-    int *lvl_ptr = nullptr;  // [nlev+1]
-    int *lvl_cols = nullptr; // [n]     steps grouped by level (ascending), ascending within
-    int *uoff = nullptr;     // [nnz_l+1] start of each row-list entry's map in umap
-    int *umap = nullptr;     // [nupd]  column-relative target (0 = diagonal, 1 + t = t-th L entry)
-    int *src = nullptr;      // [n + nnz_l] Ybus-pattern position feeding each slot, -1 = fill
-    int *step_of_bus = nullptr; // [nbus] global bus -> step, -1 if not in the matrix
-    int *br_slot = nullptr;  // [nbranch*3] slots of (diag f, diag t, L(f,t)) or -1
+    int64_t nupd = 0;    // scalar updates of one factorisation
+    int offDi = 0, offLc = 0, offLr = 0, stride = 0;
+    int npf = 0, npb = 0; // pieces of the forward / backward sweep
+    int *bus = nullptr;        // [n]   level-order index -> global bus
+    int *local = nullptr;      // [n]   level-order index -> local index
+    int *new_of_bus = nullptr; // [nbus] global bus -> level-order index, -1 if absent
+    int *lvl_ptr = nullptr;    // [nlev+1] level ranges
+    int *Cp = nullptr, *Cr = nullptr;    // CSC of L: [n+1], [nnz] rows ascending
+    int *Fp = nullptr, *Fc = nullptr;    // CSR of L: [n+1], [nnz] columns ascending
+    int *Fpos = nullptr;       // [nnz] CSR entry -> CSC position
+    int *uoff = nullptr;       // [nnz+1] CSR entry (c, k) -> start of its update map
+    int *umap = nullptr;       // [nupd] target in column c: 0 diagonal, 1 + t = t-th entry
+    int *src = nullptr;        // [n + nnz] Ybus position of every D and Lc slot, -1 = fill
+    int *br_slot = nullptr;    // [3 nbranch] value slots (D f, D t, Lc (f,t)) or -1
+    Piece *pf = nullptr, *pb = nullptr;  // forward (levels ascending), backward (descending)
 };
 
-// Host copy of the symbolic data of one matrix.
+// Host copy of the symbolic data of one matrix.  Step numbering (the
+// minimum-degree elimination order) for the published symbolic result;
+// level order for the device layout.
 struct HostMat {
     int n = 0;
     std::vector<int> bus;      // local -> global bus (ascending)
@@ -50,12 +72,16 @@ struct HostMat {
     std::vector<int> parent, level;
     int nlev = 0;
     int max_col = 0;
-    std::vector<int> lvl_ptr, lvl_cols;
-    std::vector<int> Rp, Rk, Rpos;
-    std::vector<int> uoff, umap;
-    std::vector<int> src;
-    std::vector<int> step_of_bus;
-    std::vector<int> br_slot;
+    int64_t nupd = 0;
+    // device layout (level order)
+    std::vector<int> neword;       // level order -> step
+    std::vector<int> new_of_step;  // step -> level order
+    std::vector<int> bus_new, local_new, new_of_bus;
+    std::vector<int> lvl_ptr;
+    std::vector<int> Cp, Cr, Fp, Fc, Fpos, uoff, umap, src, br_slot;
+    std::vector<int> csc_of_steppos;  // step-numbered CSC position -> level-order CSC position
+    std::vector<Piece> pf, pb;
+    int offDi = 0, offLc = 0, offLr = 0, stride = 0;
 };
 
 // Device arrays of the network and of the case batch.
@@ -93,8 +119,9 @@ struct Workspace {
     bool factored[2][2] = {{false, false}, {false, false}};
     int ninst_alloc = 0;
     // per-case scratch
-    double *ef = nullptr;     // [ncase][2*nbus] rectangular voltages
-    double *vec = nullptr;    // [ncase][2*nbus] global solve vectors when they exceed shared memory
+    double *ef = nullptr;     // [ncase][4*nbus] e, f, cos(theta), sin(theta)
+    double *vec = nullptr;    // [ncase][2*nbus] solve-vector exchange / global solve vectors
+    double *bmax = nullptr;   // [ncase][16] per-CTA mismatch maxima and solve flag
     int *cstatus = nullptr;   // [ncase] run status
     pf_case_result *res = nullptr; // [ncase]
     int ncase_alloc = 0;
@@ -146,13 +173,16 @@ cudaError_t launch_assemble_slots(const DevNet &dn, const DevCases &dc, const De
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
                           int *fstatus, cudaStream_t s);
 cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const int *inst_of_case,
-                         double *rhs, int ncase, void *gvec, size_t smem_optin, cudaStream_t s);
+                         double *rhs, int ncase, void *gvec, int *status, size_t smem_optin,
+                         cudaStream_t s);
 cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
                             double *dp, double *dq, double *maxmis, double *ef, int ncase,
                             cudaStream_t s);
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
                         const void *F0, const void *F1, const int *fstat0, const int *fstat1,
-                        const pf_run_opts &o, double *vm, double *va, double *ef, double *vec,
-                        pf_case_result *res, size_t smem_optin, cudaStream_t s);
+                        const pf_run_opts &o, double *vm, double *va, double *ef, double *xg,
+                        double *bmax, pf_case_result *res, size_t smem_optin, int cluster,
+                        cudaStream_t s);
+int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int nmax);
 
 }  // namespace gbpf
