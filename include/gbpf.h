@@ -96,7 +96,9 @@ typedef struct {
     double tol;         /* converged when max(|dP| non-slack, |dQ| PQ) <= tol */
     int32_t max_iter;   /* NR steps or FDPF half-iteration pairs */
     int32_t ir_max;     /* PF_FP32: refinement corrections per linear solve */
-    double ir_tol;      /* PF_FP32: stop refining at ||r||inf <= ir_tol ||rhs||inf */
+    double ir_tol;      /* PF_FP32: stop refining at ||r||inf <= ir_tol ||rhs||inf ... */
+    double ir_abs;      /* ... or at ||r||inf <= ir_abs (0 = 0.01 tol: a linear-solve
+                           residual that small cannot change a convergence decision) */
     int32_t flat_start; /* 1: theta = slack angle / 0, V = 1 (PQ) or vset; 0: use vm/va */
     int32_t spin_limit; /* bound on every device-side wait (0 = library default) */
 } pf_run_opts;
@@ -139,6 +141,13 @@ pf_status pf_get_symbolic(const pf_ctx *ctx, int32_t which, int32_t *perm, int32
  * Replaces any previous batch.  Synchronous. */
 pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
                        const int32_t *outage);
+
+/* Overrides the specified injections of the current batch with device
+ * arrays psp_dev / qsp_dev [ncase][nbus] (Psp used at non-slack buses, Qsp at
+ * PQ buses; other entries ignored), e.g. to differentiate the power flow with
+ * respect to them.  Asynchronous. */
+pf_status pf_set_injections(pf_ctx *ctx, const double *psp_dev, const double *qsp_dev,
+                            void *stream);
 
 /* Assembles the bus admittance matrix (Section III.A) and the values of B'
  * or B'' for every case and factorises them level by level (Section III.B):
@@ -198,6 +207,28 @@ pf_status pf_set_profiling(pf_ctx *ctx, int32_t on);
  * Synchronises with the recorded events. */
 pf_status pf_get_profile(pf_ctx *ctx, int32_t kind, int64_t *launches, double *total_ms,
                          int32_t reset);
+
+/* Adjoint of the Newton-Raphson power flow (transposed solve with the
+ * factors of the last PF_NR pf_run_to_tol of the same precision, refined in
+ * FP64 against the exact Jacobian at the given state).  For every case c,
+ * with J the Jacobian of the mismatch F(x) = Psp - P(x) at the state
+ * vm_dev/va_dev [ncase][nbus]: solves J^T y = g, where g holds dObj/dtheta
+ * (gva_dev) of every non-slack bus and dObj/dV (gvm_dev) of every PQ bus
+ * (other entries are ignored), and writes dObj/dPsp = y_P to dJdP_dev and
+ * dObj/dQsp = y_Q to dJdQ_dev [ncase][nbus] (0 at the slack, dJdQ 0 at PV
+ * buses).  If no Newton factors exist yet the Jacobian at the state is
+ * factorised first.  Returns after the device is done; per-case status in
+ * res_host[ncase]. */
+pf_status pf_adjoint(pf_ctx *ctx, int32_t precision, const double *vm_dev, const double *va_dev,
+                     const double *gva_dev, const double *gvm_dev, double *dJdP_dev,
+                     double *dJdQ_dev, pf_case_result *res_host, void *stream);
+
+/* Objective J = sum_i (V_i - 1)^2 + sum_i P_i (the total active losses) of
+ * every case at vm_dev/va_dev [ncase][nbus] into J_dev[ncase], and its
+ * gradient: gva_dev[ncase][nbus] = dJ/dtheta_k, gvm_dev[ncase][nbus] =
+ * dJ/dV_k for every bus.  Asynchronous. */
+pf_status pf_objective(pf_ctx *ctx, const double *vm_dev, const double *va_dev, double *J_dev,
+                       double *gva_dev, double *gvm_dev, void *stream);
 
 /* Message of the last failing call on this context (never NULL). */
 const char *pf_last_error(const pf_ctx *ctx);

@@ -31,7 +31,7 @@ def cuda_home() -> str:
 
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
-                  if f.endswith((".cu", ".cpp", ".h")))
+                  if f.endswith((".cu", ".cpp", ".h", ".cuh")))
 
 
 def up_to_date() -> bool:

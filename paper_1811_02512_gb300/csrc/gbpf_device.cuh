@@ -1,0 +1,449 @@
+// gbpf_device.cuh -- device helpers shared by the CUDA translation units of
+// libgbpf: reductions, TMA bulk copies and mbarriers, cluster barriers, the
+// TMA-staged level sweeps of the substitutions (Section III.C of arxiv
+// 1811.02512) and the nodal injection (Section II.A).
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "gbpf_internal.h"
+
+namespace gbpf {
+namespace {
+
+constexpr int kFactorThreads = 512;
+constexpr int kSolveThreads = 512;
+constexpr int kRunThreads = 512;
+constexpr int kStages = 4;                  // ring depth of the staged sweeps
+constexpr int kStageBytes = kPieceBytes;    // one piece per stage
+constexpr unsigned kDefaultSpin = 1u << 22; // bound of every mbarrier wait
+
+// ------------------------------------------------------------ small helpers
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = (w > v || w != w) ? w : v;  // NaN wins
+    }
+    return v;
+}
+
+// Block-wide maximum of v (NaN wins); every thread receives the result.
+// `red` is a 33-entry shared array.  Contains two __syncthreads.
+__device__ double block_max(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_max(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double w = (lane < int(blockDim.x >> 5)) ? red[lane] : 0.0;
+        w = warp_max(w);
+        if (lane == 0) red[32] = w;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// Atomic maximum of a non-negative double through its bit pattern (IEEE order
+// of non-negative doubles equals integer order; NaN patterns sort above Inf).
+__device__ void atomic_max_nonneg(double *addr, double v) {
+    atomicMax(reinterpret_cast<unsigned long long *>(addr),
+              static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// ------------------------------------------------------------ TMA / mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy global -> this CTA's shared memory, completion counted on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of `bar`, giving up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ------------------------------------------------------------ cluster barrier
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+template <int C>
+__device__ __forceinline__ void cluster_sync() {
+    if constexpr (C == 1) {
+        __syncthreads();
+    } else {
+        __threadfence();
+        asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
+                         : "memory");
+    }
+}
+
+// ------------------------------------------------------------ staged sweeps
+
+// Shared-memory ring of kStages stages; each stage holds one piece: row
+// pointers, indices and values of a run of rows of one level.
+struct Ring {
+    uint64_t bar[kStages];
+    int hdr[kStages][20]; // r0, r1, e0, p_lo, i_lo, v_lo, idx off, val off, mode, run_end,
+                          // diag off (-1: none), d_lo, level-pointer off, lp_lo, l0, l1, e1
+    int err;              // set when a wait gave up
+    unsigned gcount;      // pieces consumed so far (phase bookkeeping)
+};
+
+__device__ void ring_init(Ring *R) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) mbar_init(&R->bar[s], 1);
+        R->err = 0;
+        R->gcount = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// Issues piece `pc` of a sweep over (ptr, idx, val) into stage `st`.  Values
+// are NB x NB blocks (NB = 1: scalars) of type T; `dinv` (optional) holds the
+// inverse diagonal blocks of the rows.  Called by one thread.  Ranges are
+// widened to 16-byte boundaries; the arrays are padded so the widened ranges
+// stay inside their allocations.
+template <class T, int NB>
+__device__ void ring_issue(Ring *R, unsigned char *stages, int st, const Piece &pc, const int *ptr,
+                           const int *idx, const T *val, const T *dinv, const int *lvl_ptr) {
+    constexpr int V = 16 / int(sizeof(T));
+    constexpr int NB2 = NB * NB;
+    const int p_lo = pc.r0 & ~3, p_hi = (pc.r1 + 1 + 3) & ~3;
+    const int i_lo = pc.e0 & ~3, i_hi = (pc.e1 + 3) & ~3;
+    const int v_lo = (pc.e0 * NB2) & ~(V - 1), v_hi = (pc.e1 * NB2 + V - 1) & ~(V - 1);
+    const int d_lo = (pc.r0 * NB2) & ~(V - 1), d_hi = (pc.r1 * NB2 + V - 1) & ~(V - 1);
+    const uint32_t pbytes = uint32_t(p_hi - p_lo) * 4u;
+    const uint32_t ibytes = pc.e1 > pc.e0 ? uint32_t(i_hi - i_lo) * 4u : 0u;
+    const uint32_t vbytes = pc.e1 > pc.e0 ? uint32_t(v_hi - v_lo) * uint32_t(sizeof(T)) : 0u;
+    const uint32_t dbytes = dinv ? uint32_t(d_hi - d_lo) * uint32_t(sizeof(T)) : 0u;
+    const int lp_lo = pc.l0 & ~3, lp_hi = (pc.l1 + 2 + 3) & ~3;
+    const uint32_t lbytes = pc.mode == 2 ? uint32_t(lp_hi - lp_lo) * 4u : 0u;
+    const int ioff = int(pbytes);
+    const int voff = ioff + int(ibytes);
+    const int doff = voff + int(vbytes);
+    const int loff = doff + int(dbytes);
+    int *h = R->hdr[st];
+    h[0] = pc.r0; h[1] = pc.r1; h[2] = pc.e0; h[3] = p_lo; h[4] = i_lo; h[5] = v_lo;
+    h[6] = ioff; h[7] = voff; h[8] = pc.mode; h[9] = pc.run_end;
+    h[10] = dinv ? doff : -1; h[11] = d_lo; h[12] = loff; h[13] = lp_lo; h[14] = pc.l0; h[15] = pc.l1;
+    h[16] = pc.e1;
+    unsigned char *dst = stages + size_t(st) * kStageBytes;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&R->bar[st], pbytes + ibytes + vbytes + dbytes + lbytes);
+    tma_g2s(dst, ptr + p_lo, pbytes, &R->bar[st]);
+    if (ibytes) {
+        tma_g2s(dst + ioff, idx + i_lo, ibytes, &R->bar[st]);
+        tma_g2s(dst + voff, val + v_lo, vbytes, &R->bar[st]);
+    }
+    if (dbytes) tma_g2s(dst + doff, dinv + d_lo, dbytes, &R->bar[st]);
+    if (lbytes) tma_g2s(dst + loff, lvl_ptr + lp_lo, lbytes, &R->bar[st]);
+}
+
+template <class X>
+__device__ __forceinline__ X warp_sum(X v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Small fixed-size vector for the NB unknowns of one row.
+template <class X, int NB>
+struct Vec {
+    X v[NB];
+};
+
+// y += B x for an NB x NB block B (row-major, TRANS: B^T).
+template <class T, class X, int NB, bool TRANS>
+__device__ __forceinline__ void blk_mac(Vec<X, NB> &y, const T *B, const X *x) {
+#pragma unroll
+    for (int i = 0; i < NB; i++)
+#pragma unroll
+        for (int j = 0; j < NB; j++) y.v[i] += X(B[TRANS ? j * NB + i : i * NB + j]) * x[j];
+}
+
+// Row r of a piece: x_r = (Dinv_r x_r when the piece carries the inverse
+// diagonal) - sum over the entries (B_e or B_e^T) x_{idx_e}, over lanes
+// [gl, len) with step gsz; the caller reduces `acc` over the lanes.
+template <class T, class X, int NB, bool TRANS>
+__device__ __forceinline__ void row_partial(Vec<X, NB> &acc, const int *P, const int *I, const T *Vv,
+                                            X *x, int r, int p_lo, int i_lo, int v_lo, int gl,
+                                            int gsz) {
+    const int a = P[r - p_lo], b = P[r + 1 - p_lo];
+    for (int e = a + gl; e < b; e += gsz)
+        blk_mac<T, X, NB, TRANS>(acc, Vv + (e * NB * NB - v_lo), x + size_t(I[e - i_lo]) * NB);
+}
+
+template <class T, class X, int NB, bool TRANS>
+__device__ __forceinline__ void row_finish(const Vec<X, NB> &acc, const T *Dv, int d_lo, X *x, int r) {
+    X xr[NB], out[NB];
+#pragma unroll
+    for (int i = 0; i < NB; i++) xr[i] = x[size_t(r) * NB + i];
+    if (Dv) {
+        Vec<X, NB> t;
+#pragma unroll
+        for (int i = 0; i < NB; i++) t.v[i] = X(0);
+        blk_mac<T, X, NB, TRANS>(t, Dv + (r * NB * NB - d_lo), xr);
+#pragma unroll
+        for (int i = 0; i < NB; i++) out[i] = t.v[i] - acc.v[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < NB; i++) out[i] = xr[i] - acc.v[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NB; i++) x[size_t(r) * NB + i] = out[i];
+}
+
+// Rows of one staged piece.  mode 0: thread per row; mode 1: warp per row
+// over all warps; mode 2: the calling warp alone walks the narrow levels
+// l0..l1 of the piece (ascending forward, descending when the piece carries
+// the diagonal, i.e. in the back substitution), split into groups of 32/R
+// lanes for the R rows of each level.  Entries of a row are spread over the
+// lanes of its warp or group and summed by shuffles.
+template <class T, class X, int NB, bool TRANS>
+__device__ __forceinline__ void piece_rows(const int *h, const unsigned char *base, X *x, int mode,
+                                           int first, int stride) {
+    const int *P = reinterpret_cast<const int *>(base);
+    const int *I = reinterpret_cast<const int *>(base + h[6]);
+    const T *Vv = reinterpret_cast<const T *>(base + h[7]);
+    const T *Dv = h[10] >= 0 ? reinterpret_cast<const T *>(base + h[10]) : nullptr;
+    const int r0 = h[0], r1 = h[1], p_lo = h[3], i_lo = h[4], v_lo = h[5], d_lo = h[11];
+    const int lane = threadIdx.x & 31;
+    if (mode == 0) {
+        for (int r = r0 + first; r < r1; r += stride) {
+            Vec<X, NB> acc;
+#pragma unroll
+            for (int i = 0; i < NB; i++) acc.v[i] = X(0);
+            row_partial<T, X, NB, TRANS>(acc, P, I, Vv, x, r, p_lo, i_lo, v_lo, 0, 1);
+            row_finish<T, X, NB, TRANS>(acc, Dv, d_lo, x, r);
+        }
+    } else if (mode == 3) {
+        // part [e0, e1) of row r0 on the calling warp; the diagonal is applied
+        // by the part that starts the row
+        const int e0 = h[2], e1 = h[16];
+        Vec<X, NB> acc;
+#pragma unroll
+        for (int i = 0; i < NB; i++) acc.v[i] = X(0);
+        for (int e = e0 + lane; e < e1; e += 32)
+            blk_mac<T, X, NB, TRANS>(acc, Vv + (e * NB * NB - v_lo), x + size_t(I[e - i_lo]) * NB);
+#pragma unroll
+        for (int i = 0; i < NB; i++) acc.v[i] = warp_sum(acc.v[i]);
+        if (lane == 0)
+            row_finish<T, X, NB, TRANS>(acc, e0 == P[r0 - p_lo] ? Dv : nullptr, d_lo, x, r0);
+    } else if (mode == 1) {
+        for (int r = r0 + first; r < r1; r += stride) {
+            Vec<X, NB> acc;
+#pragma unroll
+            for (int i = 0; i < NB; i++) acc.v[i] = X(0);
+            row_partial<T, X, NB, TRANS>(acc, P, I, Vv, x, r, p_lo, i_lo, v_lo, lane, 32);
+#pragma unroll
+            for (int i = 0; i < NB; i++) acc.v[i] = warp_sum(acc.v[i]);
+            if (lane == 0) row_finish<T, X, NB, TRANS>(acc, Dv, d_lo, x, r);
+        }
+    } else {
+        const int *LP = reinterpret_cast<const int *>(base + h[12]) - h[13];
+        const int l0 = h[14], l1 = h[15];
+        const bool down = Dv != nullptr;
+        for (int li = 0; li <= l1 - l0; li++) {
+            const int l = down ? l1 - li : l0 + li;
+            const int lr0 = max(LP[l], r0), lr1 = min(LP[l + 1], r1);
+            const int lrows = lr1 - lr0;
+            const int gsz = lrows <= 1 ? 32 : lrows <= 2 ? 16 : lrows <= 4 ? 8 : lrows <= 8 ? 4 : 2;
+            const int grp = lane / gsz, gl = lane % gsz;
+            for (int i0 = 0; i0 < lrows; i0 += 32 / gsz) {
+                const int i = i0 + grp;
+                Vec<X, NB> acc;
+#pragma unroll
+                for (int k = 0; k < NB; k++) acc.v[k] = X(0);
+                const int r = i < lrows ? lr0 + i : -1;
+                if (r >= 0) row_partial<T, X, NB, TRANS>(acc, P, I, Vv, x, r, p_lo, i_lo, v_lo, gl, gsz);
+                for (int o = gsz >> 1; o > 0; o >>= 1)
+#pragma unroll
+                    for (int k = 0; k < NB; k++) acc.v[k] += __shfl_xor_sync(0xffffffffu, acc.v[k], o);
+                if (r >= 0 && gl == 0) row_finish<T, X, NB, TRANS>(acc, Dv, d_lo, x, r);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// One substitution sweep: for every piece in order, every row r of the piece
+// gets x_r -= sum_e val_e x_{idx_e} (NB x NB blocks, optionally transposed,
+// with the inverse diagonal applied first when given).  Pieces of the same
+// level are independent.  Block-wide pieces end with a block barrier that
+// also releases their stage; runs of narrow levels (mode 2) are consumed by
+// warp 0 alone with warp barriers while the other warps wait at the end of
+// the run.  Returns false if a wait gave up (then no copy is left in flight).
+template <class T, class X, int NB, bool TRANS>
+__device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces, int np,
+                             const int *ptr, const int *idx, const T *val, const T *dinv,
+                             const int *lvl_ptr, X *x, unsigned spin) {
+    const unsigned g0 = R->gcount;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    Piece next{};     // thread 0: descriptor of the next piece to issue, loaded ahead
+    int issued = 0;   // thread 0: pieces issued so far in this sweep
+    if (threadIdx.x == 0) {
+        const int pre = np < kStages ? np : kStages;
+        for (int j = 0; j < pre; j++)
+            ring_issue<T, NB>(R, stages, int((g0 + j) % kStages), pieces[j], ptr, idx, val, dinv,
+                              lvl_ptr);
+        issued = pre;
+        if (kStages < np) next = pieces[kStages];
+    }
+    auto issue_after = [&](int j) {  // stage of piece j is free: refill it with j + kStages
+        if (j + kStages < np) {
+            ring_issue<T, NB>(R, stages, int((g0 + j) % kStages), next, ptr, idx, val, dinv, lvl_ptr);
+            issued = j + kStages + 1;
+            if (j + kStages + 1 < np) next = pieces[j + kStages + 1];
+        }
+    };
+    bool ok = true;
+    int j = 0;
+    while (j < np) {
+        const unsigned g = g0 + unsigned(j);
+        const int st = int(g % kStages);
+        if (!mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin)) atomicExch(&R->err, 1);
+        const int *h = R->hdr[st];
+        const int mode = h[8];
+        if (mode >= 2) {
+            const int jr = h[9];
+            __syncthreads();  // every warp has read this header before warp 0 refills the stage
+            if (warp == 0) {
+                for (int jj = j; jj < jr; jj++) {
+                    const unsigned gg = g0 + unsigned(jj);
+                    const int s2 = int(gg % kStages);
+                    if (jj > j && !mbar_wait_bounded(&R->bar[s2], (gg / kStages) & 1u, spin))
+                        atomicExch(&R->err, 1);
+                    __syncwarp();
+                    if (R->err) break;
+                    piece_rows<T, X, NB, TRANS>(R->hdr[s2], stages + size_t(s2) * kStageBytes, x,
+                                                R->hdr[s2][8], 0, 1);
+                    __syncwarp();
+                    if (lane == 0) issue_after(jj);
+                }
+            }
+            __syncthreads();
+            if (R->err) { ok = false; break; }
+            j = jr;
+        } else {
+            if (!R->err)
+                piece_rows<T, X, NB, TRANS>(h, stages + size_t(st) * kStageBytes, x, mode,
+                                            mode == 0 ? int(threadIdx.x) : warp,
+                                            mode == 0 ? int(blockDim.x) : nwarps);
+            __syncthreads();
+            if (R->err) { ok = false; break; }
+            if (threadIdx.x == 0) issue_after(j);
+            j++;
+        }
+    }
+    if (!ok && threadIdx.x == 0) {
+        // drain: at most the last kStages issued pieces can still be in flight
+        for (int q = (issued > kStages ? issued - kStages : 0); q < issued; q++) {
+            const unsigned gq = g0 + unsigned(q);
+            mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, spin);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) R->gcount = g0 + unsigned(np);
+    __syncthreads();
+    return ok;
+}
+
+// L D L^T x = x in place (level order): forward substitution over the rows
+// of L (levels ascending), then back substitution over the columns of L
+// (levels descending) with the normalisation y = z / d of Eq. 4 fused in as
+// a multiplication by the stored inverse diagonal.
+template <class T, class X>
+__device__ bool block_solve(Ring *R, unsigned char *stages, const DevMat &m, const T *F, X *x,
+                            unsigned spin) {
+    if (!staged_sweep<T, X, 1, false>(R, stages, m.pf, m.npf, m.Fp, m.Fc, F + m.offLr, nullptr,
+                                      m.lvl_ptr, x, spin))
+        return false;
+    return staged_sweep<T, X, 1, false>(R, stages, m.pb, m.npb, m.Cp, m.Cr, F + m.offLc,
+                                        F + m.offDi, m.lvl_ptr, x, spin);
+}
+
+// Injection at bus i of one case: I_i = sum_k Y_ik V_k on the base admittance
+// matrix, minus the terms of the case's outaged branch (if any) at its end
+// buses; returns S_i = V_i conj(I_i) as (P, Q).
+__device__ __forceinline__ void bus_injection(const DevNet &dn, int i, int outage,
+                                              const double *e, const double *f, double &P,
+                                              double &Q) {
+    double ir = 0.0, ii = 0.0;
+    for (int p = dn.rowptr[i]; p < dn.rowptr[i + 1]; p++) {
+        const int k = dn.col[p];
+        const double g = dn.G[p], b = dn.B[p];
+        ir += g * e[k] - b * f[k];
+        ii += g * f[k] + b * e[k];
+    }
+    if (outage >= 0 && dn.bstatus[outage] && (i == dn.bf[outage] || i == dn.bt[outage])) {
+        const double r = dn.br[outage], x = dn.bx[outage], bc = dn.bb[outage], t = dn.btap[outage];
+        const double den = r * r + x * x;
+        const double ys_re = r / den, ys_im = -x / den;
+        const int o = (i == dn.bf[outage]) ? dn.bt[outage] : dn.bf[outage];
+        double gs, bs;  // self term of the branch at bus i
+        if (i == dn.bf[outage]) {
+            gs = ys_re / (t * t);
+            bs = (ys_im + 0.5 * bc) / (t * t);
+        } else {
+            gs = ys_re;
+            bs = ys_im + 0.5 * bc;
+        }
+        const double gm = -ys_re / t, bm = -ys_im / t;  // mutual term
+        ir -= gs * e[i] - bs * f[i] + gm * e[o] - bm * f[o];
+        ii -= gs * f[i] + bs * e[i] + gm * f[o] + bm * e[o];
+    }
+    P = e[i] * ir + f[i] * ii;
+    Q = f[i] * ir - e[i] * ii;
+}
+
+}  // namespace
+}  // namespace gbpf

@@ -275,21 +275,54 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
     }
     // staged pieces: runs of rows (columns) of one level whose pointers,
     // indices and (8-byte) values fit one stage
-    auto make_pieces = [&](const std::vector<int> &ptr, bool ascending, std::vector<Piece> &out) {
+    // staged pieces: runs of rows (columns) of one level, or whole narrow
+    // levels, whose pointers, indices and values fit one stage; ebytes and
+    // rbytes are the staged bytes per entry and per row
+    auto make_pieces = [&](const std::vector<int> &ptr, bool ascending, int ebytes, int rbytes,
+                           std::vector<Piece> &out) {
         out.clear();
         const int budget = kPieceBytes - kPieceSlack;
+        auto row_bytes = [&](int r) { return int64_t(rbytes) + int64_t(ebytes) * (ptr[r + 1] - ptr[r]); };
         auto level_bytes = [&](int l) {
             int64_t b = 4;  // its level pointer
-            for (int r = H.lvl_ptr[l]; r < H.lvl_ptr[l + 1]; r++) b += 12 + 12 * int64_t(ptr[r + 1] - ptr[r]);
+            for (int r = H.lvl_ptr[l]; r < H.lvl_ptr[l + 1]; r++) b += row_bytes(r);
             return b;
+        };
+        auto split_rows = [&](int l, int mode) {  // one level in row runs
+            int r = H.lvl_ptr[l], rend = H.lvl_ptr[l + 1];
+            while (r < rend) {
+                if (12 + row_bytes(r) > budget) {
+                    // a row longer than one stage: consecutive parts of its entries
+                    const int per = int((budget - 12 - rbytes - 32) / ebytes);
+                    for (int e = ptr[r]; e < ptr[r + 1]; e += per)
+                        out.push_back(Piece{r, r + 1, e, std::min(ptr[r + 1], e + per), 3, 0, l, l});
+                    r++;
+                    continue;
+                }
+                int r0 = r;
+                int64_t bytes = 8 + 4;
+                while (r < rend) {
+                    if (r > r0 && bytes + row_bytes(r) > budget) break;
+                    if (12 + row_bytes(r) > budget) break;
+                    bytes += row_bytes(r);
+                    r++;
+                }
+                out.push_back(Piece{r0, r, ptr[r0], ptr[r], mode, 0, l, l});
+            }
+            return true;
         };
         int li = 0;
         while (li < H.nlev) {
             int l = ascending ? li : H.nlev - 1 - li;
             const int lrows = H.lvl_ptr[l + 1] - H.lvl_ptr[l];
             if (lrows <= kNarrowRows) {
-                // whole narrow levels, as many consecutive ones as fit
                 int64_t bytes = 8 + level_bytes(l);
+                if (bytes > budget) {  // a narrow level too large for one stage
+                    if (!split_rows(l, 2)) return fail(ctx, PF_ERR_ARG, "internal: row exceeds a stage");
+                    li++;
+                    continue;
+                }
+                // whole narrow levels, as many consecutive ones as fit
                 int lo = l, hi = l;
                 li++;
                 while (li < H.nlev) {
@@ -302,34 +335,59 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
                     hi = std::max(hi, l2);
                     li++;
                 }
-                if (bytes > budget) return fail(ctx, PF_ERR_ARG, "internal: narrow level exceeds a stage");
                 const int r0 = H.lvl_ptr[lo], r1 = H.lvl_ptr[hi + 1];
                 out.push_back(Piece{r0, r1, ptr[r0], ptr[r1], 2, 0, lo, hi});
                 continue;
             }
-            const int mode = lrows <= 4 * kSweepWarps ? 1 : 0;
-            int r = H.lvl_ptr[l], rend = H.lvl_ptr[l + 1];
-            while (r < rend) {
-                int r0 = r;
-                int64_t bytes = 4;
-                while (r < rend) {
-                    int64_t add = 12 + 12 * int64_t(ptr[r + 1] - ptr[r]);
-                    if (r > r0 && bytes + add > budget) break;
-                    bytes += add;
-                    r++;
-                }
-                out.push_back(Piece{r0, r, ptr[r0], ptr[r], mode, 0, l, l});
-            }
+            if (!split_rows(l, lrows <= 4 * kSweepWarps ? 1 : 0))
+                return fail(ctx, PF_ERR_ARG, "internal: row exceeds a stage");
             li++;
         }
         // end of every run of single-warp pieces
         int np = int(out.size());
         for (int j = np - 1; j >= 0; j--)
-            if (out[j].mode == 2) out[j].run_end = (j + 1 < np && out[j + 1].mode == 2) ? out[j + 1].run_end : j + 1;
+            if (out[j].mode >= 2)
+                out[j].run_end = (j + 1 < np && out[j + 1].mode >= 2) ? out[j + 1].run_end : j + 1;
         return PF_OK;
     };
-    TRY(make_pieces(H.Fp, true, H.pf));
-    TRY(make_pieces(H.Cp, false, H.pb));
+    // off-diagonal pattern of A by row, both triangles, fill excluded
+    {
+        std::vector<std::vector<std::pair<int, int>>> rowsA(n);
+        for (int c = 0; c < n; c++)
+            for (int p = H.Cp[c]; p < H.Cp[c + 1]; p++)
+                if (H.src[n + p] >= 0) {
+                    rowsA[H.Cr[p]].push_back({c, H.offLc + p});
+                    rowsA[c].push_back({H.Cr[p], H.offLc + p});
+                }
+        H.Ap.assign(n + 1, 0);
+        H.Aj.clear();
+        H.Apos.clear();
+        for (int r = 0; r < n; r++) {
+            std::sort(rowsA[r].begin(), rowsA[r].end());
+            for (auto &e : rowsA[r]) {
+                H.Aj.push_back(e.first);
+                H.Apos.push_back(e.second);
+            }
+            H.Ap[r + 1] = int(H.Aj.size());
+        }
+    }
+    TRY(make_pieces(H.Fp, true, 12, 12, H.pf));
+    TRY(make_pieces(H.Cp, false, 12, 12, H.pb));
+    // Newton-Raphson Jacobian on the same pattern: 2 x 2 blocks (36 staged
+    // bytes per FP64 block entry and per row), transposed slot sources, and
+    // the block value layout [D | Dinv | Lc | Uc | Lr | Ur]
+    TRY(make_pieces(H.Fp, true, 36, 36, H.pfJ));
+    TRY(make_pieces(H.Cp, false, 36, 36, H.pbJ));
+    H.srcT.assign(nnz, -1);
+    for (int c = 0; c < n; c++)
+        for (int p = H.Cp[c]; p < H.Cp[c + 1]; p++) H.srcT[p] = ypos(ctx, H.bus_new[c], H.bus_new[H.Cr[p]]);
+    H.jD = 0;
+    H.jDi = pad32(4 * int64_t(n));
+    H.jLc = H.jDi + pad32(4 * int64_t(n));
+    H.jUc = H.jLc + pad32(4 * nnz);
+    H.jLr = H.jUc + pad32(4 * nnz);
+    H.jUr = H.jLr + pad32(4 * nnz);
+    H.jstride = H.jUr + pad32(4 * nnz);
     return PF_OK;
 }
 
@@ -446,6 +504,16 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
     TRY(upload_padded(ctx, &D.umap, H.umap));
     TRY(upload_padded(ctx, &D.src, H.src));
     TRY(upload_padded(ctx, &D.br_slot, H.br_slot));
+    TRY(upload_padded(ctx, &D.Ap, H.Ap));
+    TRY(upload_padded(ctx, &D.Aj, H.Aj));
+    TRY(upload_padded(ctx, &D.Apos, H.Apos));
+    TRY(upload(ctx, &D.pfJ, H.pfJ.data(), H.pfJ.size()));
+    TRY(upload(ctx, &D.pbJ, H.pbJ.data(), H.pbJ.size()));
+    TRY(upload_padded(ctx, &D.srcT, H.srcT));
+    D.npfJ = int(H.pfJ.size());
+    D.npbJ = int(H.pbJ.size());
+    D.jD = H.jD; D.jDi = H.jDi; D.jLc = H.jLc; D.jUc = H.jUc; D.jLr = H.jLr; D.jUr = H.jUr;
+    D.jstride = H.jstride;
     TRY(upload(ctx, &D.pf, H.pf.data(), H.pf.size()));
     TRY(upload(ctx, &D.pb, H.pb.data(), H.pb.size()));
     return PF_OK;
@@ -546,6 +614,13 @@ void free_case_storage(pf_ctx *ctx) {
             w.factored[a][b] = false;
         }
     }
+    for (int q = 0; q < 2; q++) {
+        dfree(ctx, w.JF[q]); w.JF[q] = nullptr;
+        dfree(ctx, w.jfstat[q]); w.jfstat[q] = nullptr;
+        w.jfactored[q] = false;
+    }
+    dfree(ctx, w.JA); w.JA = nullptr;
+    dfree(ctx, w.xg6); w.xg6 = nullptr;
     dfree(ctx, w.ef); w.ef = nullptr;
     dfree(ctx, w.vec); w.vec = nullptr;
     dfree(ctx, w.bmax); w.bmax = nullptr;
@@ -583,6 +658,46 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "factor launch");
     w.factored[which][prec] = true;
     return PF_OK;
+}
+
+pf_status ensure_nr_storage(pf_ctx *ctx, int prec) {
+    Workspace &w = ctx->ws;
+    const DevMat &m = ctx->dm[PF_MAT_BP];
+    const size_t n = size_t(ctx->dc.ncase) * size_t(m.jstride);
+    if (!w.JA) TRY(dalloc(ctx, &w.JA, n));
+    if (!w.xg6) TRY(dalloc(ctx, &w.xg6, size_t(ctx->dc.ncase) * 6 * ctx->nbus));
+    if (!w.JF[prec]) {
+        if (prec == PF_FP64) {
+            double *p = nullptr;
+            TRY(dalloc(ctx, &p, n));
+            w.JF[prec] = p;
+        } else {
+            float *p = nullptr;
+            TRY(dalloc(ctx, &p, n));
+            w.JF[prec] = p;
+        }
+    }
+    if (!w.jfstat[prec]) TRY(dalloc(ctx, &w.jfstat[prec], size_t(ctx->dc.ncase)));
+    return PF_OK;
+}
+
+NrLaunch nr_launch(pf_ctx *ctx, int prec) {
+    Workspace &w = ctx->ws;
+    NrLaunch L;
+    L.dn = ctx->dn;
+    L.dc = ctx->dc;
+    L.m = ctx->dm[PF_MAT_BP];
+    L.F = w.JF[prec];
+    L.A = w.JA;
+    L.fstat = w.jfstat[prec];
+    L.prec = prec;
+    L.ef = w.ef;
+    L.xg = w.xg6;
+    L.bmax = w.bmax;
+    L.res = w.res;
+    L.smem_optin = ctx->smem_optin;
+    L.cluster = nr_cluster_size(L.m, ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin);
+    return L;
 }
 
 }  // namespace
@@ -769,13 +884,26 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
     if (e != cudaSuccess) return cuda_fail(ctx, e, "case spec");
     Workspace &w = ctx->ws;
     TRY(dalloc(ctx, &w.ef, size_t(ncase) * 4 * ctx->nbus));
-    TRY(dalloc(ctx, &w.vec, size_t(ncase) * 2 * ctx->nbus));
+    TRY(dalloc(ctx, &w.vec, size_t(ncase) * 3 * ctx->nbus));
     TRY(dalloc(ctx, &w.bmax, size_t(ncase) * 16));
     TRY(dalloc(ctx, &w.cstatus, size_t(ncase)));
     if (cudaMemset(w.cstatus, 0, sizeof(int) * ncase) != cudaSuccess)
         return fail(ctx, PF_ERR_CUDA, "memset");
     TRY(dalloc(ctx, &w.res, size_t(ncase)));
     w.ncase_alloc = ncase;
+    return PF_OK;
+}
+
+pf_status pf_set_injections(pf_ctx *ctx, const double *psp_dev, const double *qsp_dev,
+                            void *stream) {
+    if (!ctx || !psp_dev || !qsp_dev) return fail(ctx, PF_ERR_ARG, "null pointer");
+    if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    TRY(ensure_cases(ctx));
+    const size_t bytes = sizeof(double) * size_t(ctx->dc.ncase) * ctx->nbus;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->dc.Psp, psp_dev, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->dc.Qsp, qsp_dev, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set injections");
     return PF_OK;
 }
 
@@ -865,15 +993,36 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
                         pf_case_result *res_host, void *stream) {
     if (!ctx || !opts || !vm_dev || !va_dev || !res_host) return fail(ctx, PF_ERR_ARG, "null pointer");
     if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
-    if (opts->method != PF_FDPF)
+    if (opts->method != PF_FDPF && opts->method != PF_NR)
         return fail(ctx, PF_ERR_ARG, "method %d not available", opts->method);
     if (opts->precision != PF_FP64 && opts->precision != PF_FP32)
         return fail(ctx, PF_ERR_ARG, "bad precision");
     if (!(opts->tol > 0) || opts->max_iter < 1) return fail(ctx, PF_ERR_ARG, "bad tol/max_iter");
+    if (opts->precision == PF_FP32 && (opts->ir_max < 0 || opts->ir_max > 100 || !(opts->ir_tol >= 0)))
+        return fail(ctx, PF_ERR_ARG, "bad refinement options");
     TRY(ensure_cases(ctx));
     cudaStream_t s = (cudaStream_t)stream;
     const int prec = opts->precision;
     TRY(assemble_ybus(ctx, s));
+    if (opts->method == PF_NR) {
+        TRY(ensure_nr_storage(ctx, prec));
+        NrLaunch L = nr_launch(ctx, prec);
+        L.o = *opts;
+        L.vm = vm_dev;
+        L.va = va_dev;
+        cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] { return launch_nr(L, s); });
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "nr launch");
+        ctx->ws.jfactored[prec] = true;
+        e = cudaMemcpyAsync(res_host, ctx->ws.res, sizeof(pf_case_result) * ctx->dc.ncase,
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "nr run");
+        for (int c = 0; c < ctx->dc.ncase; c++)
+            if (res_host[c].status != PF_OK)
+                return fail(ctx, pf_status(res_host[c].status), "case %d: status %d after %d iterations",
+                            c, res_host[c].status, res_host[c].iters);
+        return PF_OK;
+    }
     TRY(factor_matrix(ctx, PF_MAT_BP, prec, s));
     TRY(factor_matrix(ctx, PF_MAT_BPP, prec, s));
     Workspace &w = ctx->ws;
@@ -882,9 +1031,9 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
     const int cl = fdpf_cluster_size(ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin,
                                      std::max(ctx->dm[0].n, ctx->dm[1].n));
     cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
-        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, w.fstatus[0][prec],
-                           w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.vec, w.bmax, w.res,
-                           ctx->smem_optin, cl, s);
+        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, w.A[0], w.A[1],
+                           w.fstatus[0][prec], w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef,
+                           w.vec, w.bmax, w.res, ctx->smem_optin, cl, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
     e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,
@@ -895,6 +1044,59 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
         if (res_host[c].status != PF_OK)
             return fail(ctx, pf_status(res_host[c].status), "case %d: status %d after %d iterations",
                         c, res_host[c].status, res_host[c].iters);
+    return PF_OK;
+}
+
+pf_status pf_adjoint(pf_ctx *ctx, int32_t precision, const double *vm_dev, const double *va_dev,
+                     const double *gva_dev, const double *gvm_dev, double *dJdP_dev,
+                     double *dJdQ_dev, pf_case_result *res_host, void *stream) {
+    if (!ctx || !vm_dev || !va_dev || !gva_dev || !gvm_dev || !dJdP_dev || !dJdQ_dev || !res_host ||
+        (precision != PF_FP64 && precision != PF_FP32))
+        return fail(ctx, PF_ERR_ARG, "bad argument");
+    if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    TRY(ensure_cases(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(assemble_ybus(ctx, s));
+    TRY(ensure_nr_storage(ctx, precision));
+    NrLaunch L = nr_launch(ctx, precision);
+    L.o.tol = 1e-8;
+    L.o.ir_max = 20;
+    L.o.ir_tol = 1e-14;
+    L.o.ir_abs = 1e-300;
+    L.vm = const_cast<double *>(vm_dev);
+    L.va = const_cast<double *>(va_dev);
+    L.gva = gva_dev;
+    L.gvm = gvm_dev;
+    L.dJdP = dJdP_dev;
+    L.dJdQ = dJdQ_dev;
+    L.adjoint = true;
+    L.factor_now = ctx->ws.jfactored[precision] ? 0 : 1;
+    cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] { return launch_nr(L, s); });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
+    ctx->ws.jfactored[precision] = true;
+    e = cudaMemcpyAsync(res_host, ctx->ws.res, sizeof(pf_case_result) * ctx->dc.ncase,
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint");
+    for (int c = 0; c < ctx->dc.ncase; c++)
+        if (res_host[c].status != PF_OK)
+            return fail(ctx, pf_status(res_host[c].status), "adjoint case %d: status %d", c,
+                        res_host[c].status);
+    return PF_OK;
+}
+
+pf_status pf_objective(pf_ctx *ctx, const double *vm_dev, const double *va_dev, double *J_dev,
+                       double *gva_dev, double *gvm_dev, void *stream) {
+    if (!ctx || !vm_dev || !va_dev || !J_dev || !gva_dev || !gvm_dev)
+        return fail(ctx, PF_ERR_ARG, "null pointer");
+    if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    TRY(ensure_cases(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(assemble_ybus(ctx, s));
+    cudaError_t e = counted(ctx, PF_K_MISMATCH, 1, s, [&] {
+        return launch_objective(ctx->dn, ctx->dc, vm_dev, va_dev, ctx->ws.ef, J_dev, gva_dev, gvm_dev, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "objective launch");
     return PF_OK;
 }
 

@@ -21,9 +21,10 @@ constexpr int kPieceSlack = 128;
 
 // One staged piece: rows (columns) [r0, r1) whose entries are [e0, e1) of
 // the CSR (CSC) arrays, all in level order.  mode: 0 one thread per row,
-// 1 one warp per row (whole block), 2 warp 0 alone; run_end: for mode 2, the
-// first piece after the run of mode-2 pieces.  A mode 0/1 piece lies inside
-// one level; a mode-2 piece holds whole narrow levels l0..l1.
+// 1 one warp per row (whole block), 2 warp 0 alone over rows of the narrow
+// levels l0..l1, 3 warp 0 alone over part [e0, e1) of the single row r0 (a
+// row too long for one stage); run_end: for modes 2 and 3, the first piece
+// after the run of single-warp pieces.  Mode 0/1/3 pieces lie in one level.
 struct Piece {
     int r0, r1, e0, e1;
     int mode, run_end, l0, l1;
@@ -57,6 +58,13 @@ struct DevMat {
     int *src = nullptr;        // [n + nnz] Ybus position of every D and Lc slot, -1 = fill
     int *br_slot = nullptr;    // [3 nbranch] value slots (D f, D t, Lc (f,t)) or -1
     Piece *pf = nullptr, *pb = nullptr;  // forward (levels ascending), backward (descending)
+    int *Ap = nullptr, *Aj = nullptr, *Apos = nullptr;  // off-diagonal A (no fill), by row:
+                                                       // column and value slot of each entry
+    // Newton-Raphson Jacobian (2 x 2 blocks on the same pattern, B' only)
+    int npfJ = 0, npbJ = 0;
+    Piece *pfJ = nullptr, *pbJ = nullptr;
+    int *srcT = nullptr;       // [nnz] Ybus position of the transposed entry (c, r) of each slot
+    int jD = 0, jDi = 0, jLc = 0, jUc = 0, jLr = 0, jUr = 0, jstride = 0;  // block layout (elements)
 };
 
 // Host copy of the symbolic data of one matrix.  Step numbering (the
@@ -80,6 +88,10 @@ struct HostMat {
     std::vector<int> lvl_ptr;
     std::vector<int> Cp, Cr, Fp, Fc, Fpos, uoff, umap, src, br_slot;
     std::vector<int> csc_of_steppos;  // step-numbered CSC position -> level-order CSC position
+    std::vector<int> Ap, Aj, Apos;    // off-diagonal pattern of A by row (both triangles, no fill)
+    std::vector<Piece> pfJ, pbJ;
+    std::vector<int> srcT;
+    int jD = 0, jDi = 0, jLc = 0, jUc = 0, jLr = 0, jUr = 0, jstride = 0;
     std::vector<Piece> pf, pb;
     int offDi = 0, offLc = 0, offLr = 0, stride = 0;
 };
@@ -120,11 +132,18 @@ struct Workspace {
     int ninst_alloc = 0;
     // per-case scratch
     double *ef = nullptr;     // [ncase][4*nbus] e, f, cos(theta), sin(theta)
-    double *vec = nullptr;    // [ncase][2*nbus] solve-vector exchange / global solve vectors
+    double *vec = nullptr;    // [ncase][3*nbus] rhs, refined FP64 solution, FP32 work vector
     double *bmax = nullptr;   // [ncase][16] per-CTA mismatch maxima and solve flag
     int *cstatus = nullptr;   // [ncase] run status
     pf_case_result *res = nullptr; // [ncase]
     int ncase_alloc = 0;
+    // Newton-Raphson workspace (allocated on first use): block factors per
+    // precision, the FP64 Jacobian and per-case factor status, [ncase][jstride]
+    void *JF[2] = {nullptr, nullptr};
+    double *JA = nullptr;
+    int *jfstat[2] = {nullptr, nullptr};
+    bool jfactored[2] = {false, false};
+    double *xg6 = nullptr;    // [ncase][6*nbus] Newton right-hand side, refined x, FP32 work
 };
 
 }  // namespace gbpf
@@ -179,10 +198,35 @@ cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *
                             double *dp, double *dq, double *maxmis, double *ef, int ncase,
                             cudaStream_t s);
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
-                        const void *F0, const void *F1, const int *fstat0, const int *fstat1,
-                        const pf_run_opts &o, double *vm, double *va, double *ef, double *xg,
-                        double *bmax, pf_case_result *res, size_t smem_optin, int cluster,
-                        cudaStream_t s);
+                        const void *F0, const void *F1, const double *A0, const double *A1,
+                        const int *fstat0, const int *fstat1, const pf_run_opts &o, double *vm,
+                        double *va, double *ef, double *xg, double *bmax, pf_case_result *res,
+                        size_t smem_optin, int cluster, cudaStream_t s);
 int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int nmax);
+
+// One launch of the Newton-Raphson kernel (adjoint = false) or of the
+// adjoint kernel (adjoint = true).
+struct NrLaunch {
+    DevNet dn;
+    DevCases dc;
+    DevMat m;
+    void *F = nullptr;
+    double *A = nullptr;
+    int *fstat = nullptr;
+    pf_run_opts o{};
+    int prec = PF_FP64;
+    double *vm = nullptr, *va = nullptr, *ef = nullptr, *xg = nullptr, *bmax = nullptr;
+    pf_case_result *res = nullptr;
+    const double *gva = nullptr, *gvm = nullptr;
+    double *dJdP = nullptr, *dJdQ = nullptr;
+    size_t smem_optin = 0;
+    int cluster = 1;
+    bool adjoint = false;
+    int factor_now = 0;
+};
+cudaError_t launch_nr(const NrLaunch &L, cudaStream_t s);
+int nr_cluster_size(const DevMat &m, int ncase, int num_sms, int prec, size_t smem_optin);
+cudaError_t launch_objective(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
+                             double *ef, double *J, double *gva, double *gvm, cudaStream_t s);
 
 }  // namespace gbpf

@@ -18,345 +18,11 @@
 #include <cmath>
 #include <cstdint>
 
-#include "gbpf_internal.h"
+#include "gbpf_device.cuh"
 
 namespace gbpf {
 
 namespace {
-
-constexpr int kFactorThreads = 512;
-constexpr int kSolveThreads = 512;
-constexpr int kRunThreads = 512;
-constexpr int kStages = 4;                  // ring depth of the staged sweeps
-constexpr int kStageBytes = kPieceBytes;    // one piece per stage
-constexpr unsigned kDefaultSpin = 1u << 22; // bound of every mbarrier wait
-
-// ------------------------------------------------------------ small helpers
-
-__device__ __forceinline__ double warp_max(double v) {
-    for (int o = 16; o > 0; o >>= 1) {
-        double w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = (w > v || w != w) ? w : v;  // NaN wins
-    }
-    return v;
-}
-
-// Block-wide maximum of v (NaN wins); every thread receives the result.
-// `red` is a 33-entry shared array.  Contains two __syncthreads.
-__device__ double block_max(double v, double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_max(v);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double w = (lane < int(blockDim.x >> 5)) ? red[lane] : 0.0;
-        w = warp_max(w);
-        if (lane == 0) red[32] = w;
-    }
-    __syncthreads();
-    return red[32];
-}
-
-__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
-
-// Atomic maximum of a non-negative double through its bit pattern (IEEE order
-// of non-negative doubles equals integer order; NaN patterns sort above Inf).
-__device__ void atomic_max_nonneg(double *addr, double v) {
-    atomicMax(reinterpret_cast<unsigned long long *>(addr),
-              static_cast<unsigned long long>(__double_as_longlong(v)));
-}
-
-// ------------------------------------------------------------ TMA / mbarrier
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// Bulk copy global -> this CTA's shared memory, completion counted on `bar`.
-// Both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void tma_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for phase `parity` of `bar`, giving up after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned limit) {
-    for (unsigned i = 0; i < limit; i++)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-// ------------------------------------------------------------ cluster barrier
-
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-template <int C>
-__device__ __forceinline__ void cluster_sync() {
-    if constexpr (C == 1) {
-        __syncthreads();
-    } else {
-        __threadfence();
-        asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
-                         : "memory");
-    }
-}
-
-// ------------------------------------------------------------ staged sweeps
-
-// Shared-memory ring of kStages stages; each stage holds one piece: row
-// pointers, indices and values of a run of rows of one level.
-struct Ring {
-    uint64_t bar[kStages];
-    int hdr[kStages][16]; // r0, r1, e0, p_lo, i_lo, v_lo, idx off, val off, mode, run_end,
-                          // diag off (-1: none), d_lo, level-pointer off, lp_lo, l0, l1
-    int err;              // set when a wait gave up
-    unsigned gcount;      // pieces consumed so far (phase bookkeeping)
-};
-
-__device__ void ring_init(Ring *R) {
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; s++) mbar_init(&R->bar[s], 1);
-        R->err = 0;
-        R->gcount = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-}
-
-// Issues piece `pc` of a sweep over (ptr, idx, val) into stage `st`.
-// Called by one thread.  Ranges are widened to 16-byte boundaries; the arrays
-// are padded so the widened ranges stay inside their allocations.
-template <class T>
-__device__ void ring_issue(Ring *R, unsigned char *stages, int st, const Piece &pc, const int *ptr,
-                           const int *idx, const T *val, const T *dinv, const int *lvl_ptr) {
-    constexpr int V = 16 / int(sizeof(T));
-    const int p_lo = pc.r0 & ~3, p_hi = (pc.r1 + 1 + 3) & ~3;
-    const int i_lo = pc.e0 & ~3, i_hi = (pc.e1 + 3) & ~3;
-    const int v_lo = pc.e0 & ~(V - 1), v_hi = (pc.e1 + V - 1) & ~(V - 1);
-    const int d_lo = pc.r0 & ~(V - 1), d_hi = (pc.r1 + V - 1) & ~(V - 1);
-    const uint32_t pbytes = uint32_t(p_hi - p_lo) * 4u;
-    const uint32_t ibytes = pc.e1 > pc.e0 ? uint32_t(i_hi - i_lo) * 4u : 0u;
-    const uint32_t vbytes = pc.e1 > pc.e0 ? uint32_t(v_hi - v_lo) * uint32_t(sizeof(T)) : 0u;
-    const uint32_t dbytes = dinv ? uint32_t(d_hi - d_lo) * uint32_t(sizeof(T)) : 0u;
-    const int lp_lo = pc.l0 & ~3, lp_hi = (pc.l1 + 2 + 3) & ~3;
-    const uint32_t lbytes = pc.mode == 2 ? uint32_t(lp_hi - lp_lo) * 4u : 0u;
-    const int ioff = int(pbytes);
-    const int voff = ioff + int(ibytes);
-    const int doff = voff + int(vbytes);
-    const int loff = doff + int(dbytes);
-    int *h = R->hdr[st];
-    h[0] = pc.r0; h[1] = pc.r1; h[2] = pc.e0; h[3] = p_lo; h[4] = i_lo; h[5] = v_lo;
-    h[6] = ioff; h[7] = voff; h[8] = pc.mode; h[9] = pc.run_end;
-    h[10] = dinv ? doff : -1; h[11] = d_lo; h[12] = loff; h[13] = lp_lo; h[14] = pc.l0; h[15] = pc.l1;
-    unsigned char *dst = stages + size_t(st) * kStageBytes;
-    fence_proxy_async();
-    mbar_arrive_expect_tx(&R->bar[st], pbytes + ibytes + vbytes + dbytes + lbytes);
-    tma_g2s(dst, ptr + p_lo, pbytes, &R->bar[st]);
-    if (ibytes) {
-        tma_g2s(dst + ioff, idx + i_lo, ibytes, &R->bar[st]);
-        tma_g2s(dst + voff, val + v_lo, vbytes, &R->bar[st]);
-    }
-    if (dbytes) tma_g2s(dst + doff, dinv + d_lo, dbytes, &R->bar[st]);
-    if (lbytes) tma_g2s(dst + loff, lvl_ptr + lp_lo, lbytes, &R->bar[st]);
-}
-
-template <class X>
-__device__ __forceinline__ X warp_sum(X v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Rows of one staged piece: x[r] = x[r] (* dinv[r] when the piece carries
-// the inverse diagonal, i.e. back substitution with the normalisation of
-// Eq. 4 fused in) - sum_e val[e] x[idx[e]].  mode 0: thread per row; mode 1:
-// warp per row over all warps; mode 2: the calling warp alone, split into
-// groups of 32/R lanes for the R <= 16 rows of the piece.  Entries of a row
-// are spread over the lanes of its warp or group and summed by shuffles.
-template <class T, class X>
-__device__ __forceinline__ void piece_rows(const int *h, const unsigned char *base, X *x, int mode,
-                                           int first, int stride) {
-    const int *P = reinterpret_cast<const int *>(base);
-    const int *I = reinterpret_cast<const int *>(base + h[6]);
-    const T *Vv = reinterpret_cast<const T *>(base + h[7]);
-    const T *Dv = h[10] >= 0 ? reinterpret_cast<const T *>(base + h[10]) : nullptr;
-    const int r0 = h[0], rows = h[1] - h[0], p_lo = h[3], i_lo = h[4], v_lo = h[5], d_lo = h[11];
-    if (mode == 0) {
-        for (int i = first; i < rows; i += stride) {
-            const int r = r0 + i;
-            const int a = P[r - p_lo], b = P[r + 1 - p_lo];
-            X s = Dv ? x[r] * X(Dv[r - d_lo]) : x[r];
-            for (int e = a; e < b; e++) s -= X(Vv[e - v_lo]) * x[I[e - i_lo]];
-            x[r] = s;
-        }
-    } else if (mode == 1) {
-        const int lane = threadIdx.x & 31;
-        for (int i = first; i < rows; i += stride) {
-            const int r = r0 + i;
-            const int a = P[r - p_lo], b = P[r + 1 - p_lo];
-            X s = X(0);
-            for (int e = a + lane; e < b; e += 32) s += X(Vv[e - v_lo]) * x[I[e - i_lo]];
-            s = warp_sum(s);
-            if (lane == 0) x[r] = (Dv ? x[r] * X(Dv[r - d_lo]) : x[r]) - s;
-        }
-    } else {
-        // whole narrow levels l0..l1: ascending in the forward sweep,
-        // descending in the backward sweep (the one carrying the diagonal)
-        const int lane = threadIdx.x & 31;
-        const int *LP = reinterpret_cast<const int *>(base + h[12]) - h[13];
-        const int l0 = h[14], l1 = h[15];
-        const bool down = Dv != nullptr;
-        for (int li = 0; li <= l1 - l0; li++) {
-            const int l = down ? l1 - li : l0 + li;
-            const int lr0 = LP[l], lrows = LP[l + 1] - LP[l];
-            const int gsz = lrows <= 1 ? 32 : lrows <= 2 ? 16 : lrows <= 4 ? 8 : lrows <= 8 ? 4 : 2;
-            const int grp = lane / gsz, gl = lane % gsz;
-            for (int i0 = 0; i0 < lrows; i0 += 32 / gsz) {
-                const int i = i0 + grp;
-                X s = X(0);
-                int r = -1;
-                if (i < lrows) {
-                    r = lr0 + i;
-                    const int a = P[r - p_lo], b = P[r + 1 - p_lo];
-                    for (int e = a + gl; e < b; e += gsz) s += X(Vv[e - v_lo]) * x[I[e - i_lo]];
-                }
-                for (int o = gsz >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (r >= 0 && gl == 0) x[r] = (Dv ? x[r] * X(Dv[r - d_lo]) : x[r]) - s;
-            }
-            __syncwarp();
-        }
-    }
-    (void)r0;
-    (void)rows;
-}
-
-// One substitution sweep: for every piece in order, every row r of the piece
-// gets x[r] -= sum_e val[e] * x[idx[e]] over its entries.  Pieces of the same
-// level are independent.  Block-wide pieces end with a block barrier that
-// also releases their stage; runs of narrow levels (mode 2) are consumed by
-// warp 0 alone with warp barriers while the other warps wait at the end of
-// the run.  Returns false if a wait gave up (then no copy is left in flight).
-template <class T, class X>
-__device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces, int np,
-                             const int *ptr, const int *idx, const T *val, const T *dinv,
-                             const int *lvl_ptr, X *x, unsigned spin) {
-    const unsigned g0 = R->gcount;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    Piece next{};     // thread 0: descriptor of the next piece to issue, loaded ahead
-    int issued = 0;   // thread 0: pieces issued so far in this sweep
-    if (threadIdx.x == 0) {
-        const int pre = np < kStages ? np : kStages;
-        for (int j = 0; j < pre; j++)
-            ring_issue<T>(R, stages, int((g0 + j) % kStages), pieces[j], ptr, idx, val, dinv, lvl_ptr);
-        issued = pre;
-        if (kStages < np) next = pieces[kStages];
-    }
-    auto issue_after = [&](int j) {  // stage of piece j is free: refill it with j + kStages
-        if (j + kStages < np) {
-            ring_issue<T>(R, stages, int((g0 + j) % kStages), next, ptr, idx, val, dinv, lvl_ptr);
-            issued = j + kStages + 1;
-            if (j + kStages + 1 < np) next = pieces[j + kStages + 1];
-        }
-    };
-    bool ok = true;
-    int j = 0;
-    while (j < np) {
-        const unsigned g = g0 + unsigned(j);
-        const int st = int(g % kStages);
-        if (!mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin)) atomicExch(&R->err, 1);
-        const int *h = R->hdr[st];
-        const int mode = h[8];
-        if (mode == 2) {
-            const int jr = h[9];
-            __syncthreads();  // every warp has read this header before warp 0 refills the stage
-            if (warp == 0) {
-                for (int jj = j; jj < jr; jj++) {
-                    const unsigned gg = g0 + unsigned(jj);
-                    const int s2 = int(gg % kStages);
-                    if (jj > j && !mbar_wait_bounded(&R->bar[s2], (gg / kStages) & 1u, spin))
-                        atomicExch(&R->err, 1);
-                    __syncwarp();
-                    if (R->err) break;
-                    piece_rows<T, X>(R->hdr[s2], stages + size_t(s2) * kStageBytes, x, 2, 0, 1);
-                    __syncwarp();
-                    if (lane == 0) issue_after(jj);
-                }
-            }
-            __syncthreads();
-            if (R->err) { ok = false; break; }
-            j = jr;
-        } else {
-            if (!R->err)
-                piece_rows<T, X>(h, stages + size_t(st) * kStageBytes, x, mode,
-                                 mode == 0 ? int(threadIdx.x) : warp,
-                                 mode == 0 ? int(blockDim.x) : nwarps);
-            __syncthreads();
-            if (R->err) { ok = false; break; }
-            if (threadIdx.x == 0) issue_after(j);
-            j++;
-        }
-    }
-    if (!ok && threadIdx.x == 0) {
-        // drain: at most the last kStages issued pieces can still be in flight
-        for (int q = (issued > kStages ? issued - kStages : 0); q < issued; q++) {
-            const unsigned gq = g0 + unsigned(q);
-            mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, spin);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) R->gcount = g0 + unsigned(np);
-    __syncthreads();
-    return ok;
-}
-
-// L D L^T x = x in place (level order): forward substitution over the rows
-// of L (levels ascending), then back substitution over the columns of L
-// (levels descending) with the normalisation y = z / d of Eq. 4 fused in as
-// a multiplication by the stored inverse diagonal.
-template <class T, class X>
-__device__ bool block_solve(Ring *R, unsigned char *stages, const DevMat &m, const T *F, X *x,
-                            unsigned spin) {
-    if (!staged_sweep<T, X>(R, stages, m.pf, m.npf, m.Fp, m.Fc, F + m.offLr, nullptr, m.lvl_ptr, x,
-                            spin))
-        return false;
-    return staged_sweep<T, X>(R, stages, m.pb, m.npb, m.Cp, m.Cr, F + m.offLc, F + m.offDi,
-                              m.lvl_ptr, x, spin);
-}
 
 // ------------------------------------------------------------ Section III.A
 
@@ -583,40 +249,6 @@ __global__ void k_polar_to_rect(int nbus, int ncase, const double *vm, const dou
     }
 }
 
-// Injection at bus i of one case: I_i = sum_k Y_ik V_k on the base admittance
-// matrix, minus the terms of the case's outaged branch (if any) at its end
-// buses; returns S_i = V_i conj(I_i) as (P, Q).
-__device__ __forceinline__ void bus_injection(const DevNet &dn, int i, int outage,
-                                              const double *e, const double *f, double &P,
-                                              double &Q) {
-    double ir = 0.0, ii = 0.0;
-    for (int p = dn.rowptr[i]; p < dn.rowptr[i + 1]; p++) {
-        const int k = dn.col[p];
-        const double g = dn.G[p], b = dn.B[p];
-        ir += g * e[k] - b * f[k];
-        ii += g * f[k] + b * e[k];
-    }
-    if (outage >= 0 && dn.bstatus[outage] && (i == dn.bf[outage] || i == dn.bt[outage])) {
-        const double r = dn.br[outage], x = dn.bx[outage], bc = dn.bb[outage], t = dn.btap[outage];
-        const double den = r * r + x * x;
-        const double ys_re = r / den, ys_im = -x / den;
-        const int o = (i == dn.bf[outage]) ? dn.bt[outage] : dn.bf[outage];
-        double gs, bs;  // self term of the branch at bus i
-        if (i == dn.bf[outage]) {
-            gs = ys_re / (t * t);
-            bs = (ys_im + 0.5 * bc) / (t * t);
-        } else {
-            gs = ys_re;
-            bs = ys_im + 0.5 * bc;
-        }
-        const double gm = -ys_re / t, bm = -ys_im / t;  // mutual term
-        ir -= gs * e[i] - bs * f[i] + gm * e[o] - bm * f[o];
-        ii -= gs * f[i] + bs * e[i] + gm * f[o] + bm * e[o];
-    }
-    P = e[i] * ir + f[i] * ii;
-    Q = f[i] * ir - e[i] * ii;
-}
-
 __global__ void k_mismatch_rows(DevNet dn, DevCases dc, const double *ef, double *dp, double *dq,
                                 double *maxmis) {
     const int c = blockIdx.y;
@@ -649,14 +281,17 @@ struct RunArgs {
     DevCases dc;
     DevMat m0, m1;  // B', B''
     const void *F0, *F1;
+    const double *A0, *A1;  // FP64 assembled values of B', B'' (refinement residuals)
     const int *fs0, *fs1;
     double tol;
     int max_iter;
+    int ir_max;
+    double ir_tol, ir_abs;
     int flat;
     unsigned spin;
     double *vm, *va;
     double *ef;    // [ncase][4 nbus]: e, f, cos(theta), sin(theta)
-    double *xg;    // [ncase][2 nbus]: right-hand side / solution exchange
+    double *xg;    // [ncase][3 nbus]: right-hand side / solution, refined FP64 x, FP32 work
     double *bmax;  // [ncase][16]: per-CTA mismatch maxima, [15] = solve status
     pf_case_result *res;
     int use_smem;
@@ -685,7 +320,7 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
     cluster_sync<C>();
     const int outage = a.dc.outage[c];
     const int *nob = which == 0 ? a.m0.new_of_bus : a.m1.new_of_bus;
-    double *xg = a.xg + (long long)c * 2 * nbus;
+    double *xg = a.xg + (long long)c * 3 * nbus;
     double mx = 0.0;
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         double P, Q;
@@ -710,19 +345,54 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
 
 // Solves one matrix of case c in the cluster's CTA 0 (the others wait at the
 // following cluster barrier): the exchange vector is staged into shared
-// memory, solved with the TMA-staged sweeps and written back.
+// memory, solved with the TMA-staged sweeps and written back.  With an FP32
+// factor the solve is refined in FP64: x += solve32(r), r = b - A x with the
+// FP64 assembled A, until ||r||inf <= ir_tol ||b||inf or ir_max corrections
+// (the refined x lives in the second half of the exchange vector).
 template <class T>
 __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T *xs,
-                            const DevMat &m, const T *F, int c) {
-    double *xg = a.xg + (long long)c * 2 * a.dn.nbus;
-    bool ok;
-    if (xs) {
-        for (int r = threadIdx.x; r < m.n; r += blockDim.x) xs[r] = T(xg[r]);
-        __syncthreads();
-        ok = block_solve<T, T>(R, stages, m, F, xs, a.spin);
-        for (int r = threadIdx.x; r < m.n; r += blockDim.x) xg[r] = double(xs[r]);
+                            const DevMat &m, const T *F, const double *A, int c, double *red,
+                            int &ir_steps) {
+    const int nbus = a.dn.nbus;
+    double *xg = a.xg + (long long)c * 3 * nbus;
+    bool ok = true;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        if (xs) {
+            for (int r = threadIdx.x; r < m.n; r += blockDim.x) xs[r] = T(xg[r]);
+            __syncthreads();
+            ok = block_solve<T, T>(R, stages, m, F, xs, a.spin);
+            for (int r = threadIdx.x; r < m.n; r += blockDim.x) xg[r] = double(xs[r]);
+        } else {
+            ok = block_solve<T, double>(R, stages, m, F, xg, a.spin);
+        }
     } else {
-        ok = block_solve<T, double>(R, stages, m, F, xg, a.spin);
+        double *x64 = xg + nbus;
+        T *xv = xs ? xs : reinterpret_cast<T *>(x64 + m.n);  // FP32 work vector
+        double bn = 0.0;
+        for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
+            xv[r] = T(xg[r]);
+            bn = fmax(bn, fabs(xg[r]));
+        }
+        bn = block_max(bn, red);
+        for (int k = 0;; k++) {
+            ok = block_solve<T, T>(R, stages, m, F, xv, a.spin);
+            if (!ok) break;
+            for (int r = threadIdx.x; r < m.n; r += blockDim.x)
+                x64[r] = (k == 0 ? 0.0 : x64[r]) + double(xv[r]);
+            __syncthreads();
+            if (k >= a.ir_max) break;
+            double rn = 0.0;
+            for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
+                double s = xg[r] - A[r] * x64[r];
+                for (int e = m.Ap[r]; e < m.Ap[r + 1]; e++) s -= A[m.Apos[e]] * x64[m.Aj[e]];
+                xv[r] = T(s);
+                rn = nan_max(rn, fabs(s));
+            }
+            rn = block_max(rn, red);
+            if (!(rn > a.ir_tol * bn) || !(rn > a.ir_abs)) break;
+            ir_steps++;
+        }
+        for (int r = threadIdx.x; r < m.n; r += blockDim.x) xg[r] = x64[r];
     }
     return ok;
 }
@@ -749,10 +419,13 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
     double *va = a.va + (long long)c * nbus;
     double *cs = a.ef + (long long)c * 4 * nbus + 2 * nbus;
     double *sn = cs + nbus;
-    const double *xg = a.xg + (long long)c * 2 * nbus;
+    const double *xg = a.xg + (long long)c * 3 * nbus;
     double *flag = a.bmax + (long long)c * 16 + 15;
     const T *F0 = static_cast<const T *>(a.F0) + (long long)inst * a.m0.stride;
     const T *F1 = static_cast<const T *>(a.F1) + (long long)inst * a.m1.stride;
+    const double *A0 = a.A0 + (long long)inst * a.m0.stride;
+    const double *A1 = a.A1 + (long long)inst * a.m1.stride;
+    int ir_steps = 0;
     const int slice = (nbus + C - 1) / C;
     const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
     int status = PF_ERR_NOT_CONVERGED;
@@ -775,7 +448,7 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, c);
+                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, A0, c, red, ir_steps);
                 if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
             }
             cluster_sync<C>();
@@ -792,7 +465,7 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, c);
+                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, A1, c, red, ir_steps);
                 if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
             }
             cluster_sync<C>();
@@ -811,7 +484,7 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
     if (rank == 0 && threadIdx.x == 0) {
         a.res[c].status = status;
         a.res[c].iters = iters;
-        a.res[c].ir_steps = 0;
+        a.res[c].ir_steps = ir_steps;
         a.res[c].pad = 0;
         a.res[c].max_mismatch = mis;
     }
@@ -970,11 +643,16 @@ int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int n
 }
 
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
-                        const void *F0, const void *F1, const int *fstat0, const int *fstat1,
-                        const pf_run_opts &o, double *vm, double *va, double *ef, double *xg,
-                        double *bmax, pf_case_result *res, size_t smem_optin, int cluster,
-                        cudaStream_t s) {
+                        const void *F0, const void *F1, const double *A0, const double *A1,
+                        const int *fstat0, const int *fstat1, const pf_run_opts &o, double *vm,
+                        double *va, double *ef, double *xg, double *bmax, pf_case_result *res,
+                        size_t smem_optin, int cluster, cudaStream_t s) {
     RunArgs a;
+    a.A0 = A0;
+    a.A1 = A1;
+    a.ir_max = o.ir_max;
+    a.ir_tol = o.ir_tol;
+    a.ir_abs = o.ir_abs > 0 ? o.ir_abs : 0.01 * o.tol;
     a.dn = dn;
     a.dc = dc;
     a.m0 = m[0];

@@ -1,0 +1,764 @@
+// gbpf_nr.cu -- Newton-Raphson power flow (Section III of arxiv 1811.02512)
+// and its adjoint, for sm_103a.
+//
+// Unknowns: (theta_i, V_i) of every non-slack bus i, one 2 x 2 block per
+// entry of the bus-graph pattern of B' (the same ordering, elimination tree
+// and levels).  The V unknown of a PV bus is pinned by an identity row and
+// column, which keeps the block pattern equal to the bus graph.  The
+// Jacobian is factorised without pivoting as J = L D U (unit block-lower L,
+// unit block-upper U, 2 x 2 block diagonal D), level by level with the same
+// left-looking update lists as the scalar LDL^T, and solved with the
+// TMA-staged sweeps: J x = b uses L by rows and U by columns; J^T y = g uses
+// U^T by rows and L^T by columns with the same factors (the adjoint).
+#include "gbpf_device.cuh"
+
+namespace gbpf {
+
+namespace {
+
+// ------------------------------------------------------------ 2 x 2 blocks
+
+template <class T>
+struct B2 {
+    T a, b, c, d;  // [[a, b], [c, d]]
+};
+
+template <class T>
+__device__ __forceinline__ B2<T> ld2(const T *p) { return B2<T>{p[0], p[1], p[2], p[3]}; }
+
+template <class T>
+__device__ __forceinline__ void st2(T *p, const B2<T> &m) {
+    p[0] = m.a; p[1] = m.b; p[2] = m.c; p[3] = m.d;
+}
+
+template <class T>
+__device__ __forceinline__ B2<T> mul2(const B2<T> &x, const B2<T> &y) {
+    return B2<T>{x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c,
+                 x.c * y.b + x.d * y.d};
+}
+
+// Injection terms of branch-aware admittance entry (i, k) of case `outage`:
+// the base Y entry at Ybus position p minus the outaged branch's share.
+__device__ __forceinline__ void y_entry(const DevNet &dn, int outage, int i, int k, int p,
+                                        double &G, double &B) {
+    G = p >= 0 ? dn.G[p] : 0.0;
+    B = p >= 0 ? dn.B[p] : 0.0;
+    if (outage < 0 || !dn.bstatus[outage]) return;
+    const int f = dn.bf[outage], t = dn.bt[outage];
+    if (!((i == f || i == t) && (k == f || k == t))) return;
+    const double r = dn.br[outage], x = dn.bx[outage], bc = dn.bb[outage], tp = dn.btap[outage];
+    const double den = r * r + x * x;
+    const double ys_re = r / den, ys_im = -x / den;
+    if (i != k) {
+        G += ys_re / tp;
+        B += ys_im / tp;
+    } else if (i == f) {
+        G -= ys_re / (tp * tp);
+        B -= (ys_im + 0.5 * bc) / (tp * tp);
+    } else {
+        G -= ys_re;
+        B -= ys_im + 0.5 * bc;
+    }
+}
+
+// Off-diagonal Jacobian block J_ik = d(P_i, Q_i)/d(theta_k, V_k) from the
+// rectangular voltages; PV rows/columns pinned.
+__device__ __forceinline__ B2<double> jac_off(double G, double B, double ei, double fi, double ek,
+                                              double fk, double vk, bool pv_i, bool pv_k) {
+    const double a = ei * ek + fi * fk;  // V_i V_k cos(theta_ik)
+    const double b = fi * ek - ei * fk;  // V_i V_k sin(theta_ik)
+    B2<double> J;
+    J.a = G * b - B * a;                 // dP_i / dtheta_k
+    J.b = (G * a + B * b) / vk;          // dP_i / dV_k
+    J.c = -(G * a + B * b);              // dQ_i / dtheta_k
+    J.d = (G * b - B * a) / vk;          // dQ_i / dV_k
+    if (pv_i) { J.c = 0.0; J.d = 0.0; }
+    if (pv_k) { J.b = 0.0; J.d = 0.0; }
+    return J;
+}
+
+__device__ __forceinline__ B2<double> jac_diag(double G, double B, double P, double Q, double v,
+                                               bool pv) {
+    B2<double> J;
+    J.a = -Q - B * v * v;     // dP_i / dtheta_i
+    J.b = P / v + G * v;      // dP_i / dV_i
+    J.c = P - G * v * v;      // dQ_i / dtheta_i
+    J.d = Q / v - B * v;      // dQ_i / dV_i
+    if (pv) { J.b = 0.0; J.c = 0.0; J.d = 1.0; }
+    return J;
+}
+
+struct NrArgs {
+    DevNet dn;
+    DevCases dc;
+    DevMat m;          // pattern of B' (non-slack buses)
+    void *F;           // [ncase][jstride] block factors (T)
+    double *A;         // [ncase][jstride] FP64 Jacobian: D, Lc (J_rc), Uc (J_cr) regions
+    int *fstat;        // [ncase] factor status of the last factorisation
+    double tol;
+    int max_iter;
+    int flat;
+    unsigned spin;
+    int ir_max;
+    double ir_tol, ir_abs;
+    double *vm, *va;
+    double *ef;        // [ncase][4 nbus]: e, f, P, Q
+    double *xg;        // [ncase][6 nbus]: rhs (2n), refined x (2n), FP32 work (2n)
+    double *bmax;      // [ncase][16]
+    pf_case_result *res;
+    const double *gva, *gvm;    // adjoint right-hand side per bus
+    double *dJdP, *dJdQ;        // adjoint outputs per bus
+    int use_smem;
+};
+
+// Rectangular voltages of the CTA's bus slice.
+__device__ void nr_rect(const NrArgs &a, int c, int i0, int i1) {
+    const int nbus = a.dn.nbus;
+    const double *vm = a.vm + (long long)c * nbus;
+    const double *va = a.va + (long long)c * nbus;
+    double *e = a.ef + (long long)c * 4 * nbus;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        double s, co;
+        sincos(va[i], &s, &co);
+        e[i] = vm[i] * co;
+        e[nbus + i] = vm[i] * s;
+    }
+}
+
+// Injections, mismatch and Newton right-hand side of the slice; returns the
+// CTA maximum (NaN wins).
+__device__ double nr_mismatch_slice(const NrArgs &a, int c, int i0, int i1, double *red) {
+    const DevNet &dn = a.dn;
+    const int nbus = dn.nbus;
+    const double *e = a.ef + (long long)c * 4 * nbus;
+    const double *f = e + nbus;
+    double *P = const_cast<double *>(e) + 2 * nbus;
+    double *Q = P + nbus;
+    double *rhs = a.xg + (long long)c * 6 * nbus;
+    const int outage = a.dc.outage[c];
+    double mx = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        double p, q;
+        bus_injection(dn, i, outage, e, f, p, q);
+        P[i] = p;
+        Q[i] = q;
+        const int t = dn.btype[i];
+        const long long idx = (long long)c * nbus + i;
+        const double dP = (t != PF_BUS_SLACK) ? a.dc.Psp[idx] - p : 0.0;
+        const double dQ = (t == PF_BUS_PQ) ? a.dc.Qsp[idx] - q : 0.0;
+        double l = fmax(fabs(dP), fabs(dQ));
+        if (dP != dP || dQ != dQ) l = __longlong_as_double(0x7ff8000000000000ll);
+        mx = nan_max(mx, l);
+        const int k = a.m.new_of_bus[i];
+        if (k >= 0) {
+            rhs[2 * k] = dP;
+            rhs[2 * k + 1] = dQ;
+        }
+    }
+    return block_max(mx, red);
+}
+
+// FP64 Jacobian of case c into A: the diagonal blocks of the slots [s0, s1)
+// of the (n + nnz) slot range and the lower / upper blocks of the others.
+__device__ void nr_assemble(const NrArgs &a, int c, int s0, int s1) {
+    const DevNet &dn = a.dn;
+    const DevMat &m = a.m;
+    const int nbus = dn.nbus;
+    const double *e = a.ef + (long long)c * 4 * nbus;
+    const double *f = e + nbus;
+    const double *P = e + 2 * nbus;
+    const double *Q = e + 3 * nbus;
+    const double *vm = a.vm + (long long)c * nbus;
+    double *A = a.A + (long long)c * m.jstride;
+    const int outage = a.dc.outage[c];
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        if (s < m.n) {
+            const int i = m.bus[s];
+            double G, B;
+            y_entry(dn, outage, i, i, dn.ydiag[i], G, B);
+            st2(A + m.jD + 4 * s, jac_diag(G, B, P[i], Q[i], vm[i], dn.btype[i] == PF_BUS_PV));
+        } else {
+            const int p = s - m.n;
+            int col = 0;
+            {  // column of CSC slot p: binary search in Cp
+                int lo = 0, hi = m.n;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (m.Cp[mid] <= p) lo = mid; else hi = mid;
+                }
+                col = lo;
+            }
+            const int r = m.Cr[p];
+            const int i = m.bus[r], k = m.bus[col];
+            const bool pvi = dn.btype[i] == PF_BUS_PV, pvk = dn.btype[k] == PF_BUS_PV;
+            double G, B;
+            y_entry(dn, outage, i, k, m.src[m.n + p], G, B);
+            st2(A + m.jLc + 4 * p, jac_off(G, B, e[i], f[i], e[k], f[k], vm[k], pvi, pvk));
+            y_entry(dn, outage, k, i, m.srcT[p], G, B);
+            st2(A + m.jUc + 4 * p, jac_off(G, B, e[k], f[k], e[i], f[i], vm[i], pvk, pvi));
+        }
+    }
+}
+
+// Block LDU factor of one Jacobian by one block (Section III.B with 2 x 2
+// blocks): left-looking, level by level; wide levels one warp per column,
+// narrow levels one column at a time with the warps' partial sums reduced in
+// warp order.  Column c gathers, from every descendant k in row c of L,
+//   A_ic -= L_ik (D_k U_kc)   (i >= c, the diagonal when i = c)
+//   A_ci -= (L_ck D_k) U_ki   (i > c)
+// then D_c = A_cc, L_ic = A_ic D_c^-1, U_ci = D_c^-1 A_ci.  The pivot check
+// is on det(D_c) against the largest diagonal-block entry.  Returns status.
+template <class T>
+__device__ int block_factor(const DevMat &m, const double *Aj, T *F, unsigned char *scratch,
+                            double *red) {
+    __shared__ int bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int sa = 8 * (m.max_col + 1);  // per-warp accumulator: L blocks then U blocks
+    T *accw = reinterpret_cast<T *>(scratch) + warp * sa;
+    T *fin = reinterpret_cast<T *>(scratch) + nwarps * sa;
+    T *D = F + m.jD, *Di = F + m.jDi, *Lc = F + m.jLc, *Uc = F + m.jUc;
+    if (threadIdx.x == 0) bad = PF_OK;
+    double amax = 0.0;
+    for (int j = threadIdx.x; j < 4 * m.n; j += blockDim.x) amax = fmax(amax, fabs(Aj[m.jD + j]));
+    amax = block_max(amax, red);
+    const double piv = 1e-14 * amax * amax;
+    auto finalize = [&](int c, const T *accL, const T *accU, int cnt, int first, int step) {
+        const B2<T> Dc = ld2(accL);
+        const T det = Dc.a * Dc.d - Dc.b * Dc.c;
+        const B2<T> inv{Dc.d / det, -Dc.b / det, -Dc.c / det, Dc.a / det};
+        if (first == 0) {
+            st2(D + 4 * c, Dc);
+            st2(Di + 4 * c, inv);
+            const double dd = double(det);
+            if (!isfinite(dd) || !isfinite(double(Dc.a)) || !isfinite(double(Dc.d)))
+                atomicCAS(&bad, PF_OK, PF_ERR_NONFINITE);
+            else if (fabs(dd) <= piv)
+                atomicCAS(&bad, PF_OK, PF_ERR_SINGULAR);
+        }
+        const int c0 = m.Cp[c];
+        for (int t = first; t < cnt; t += step) {
+            st2(Lc + 4 * (c0 + t), mul2(ld2(accL + 4 * (1 + t)), inv));
+            st2(Uc + 4 * (c0 + t), mul2(inv, ld2(accU + 4 * (1 + t))));
+        }
+    };
+    for (int lev = 0; lev < m.nlev; lev++) {
+        const int cb = m.lvl_ptr[lev], c1 = m.lvl_ptr[lev + 1];
+        if (c1 - cb > kNarrowRows) {
+            for (int c = cb + warp; c < c1; c += nwarps) {
+                const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0;
+                T *accL = accw, *accU = accw + 4 * (m.max_col + 1);
+                for (int t = lane; t <= cnt; t += 32) {
+                    const double *src = t == 0 ? Aj + m.jD + 4 * c : Aj + m.jLc + 4 * (c0 + t - 1);
+                    for (int q = 0; q < 4; q++) accL[4 * t + q] = T(src[q]);
+                    if (t > 0)
+                        for (int q = 0; q < 4; q++) accU[4 * t + q] = T(Aj[m.jUc + 4 * (c0 + t - 1) + q]);
+                }
+                __syncwarp();
+                for (int q = m.Fp[c]; q < m.Fp[c + 1]; q++) {
+                    const int k = m.Fc[q], pkc = m.Fpos[q];
+                    const B2<T> Dk = ld2(D + 4 * k);
+                    const B2<T> M1 = mul2(Dk, ld2(Uc + 4 * pkc));   // D_k U_kc
+                    const B2<T> M2 = mul2(ld2(Lc + 4 * pkc), Dk);   // L_ck D_k
+                    const int len = m.Cp[k + 1] - pkc, o = m.uoff[q];
+                    for (int t = lane; t < len; t += 32) {
+                        const int tg = m.umap[o + t];
+                        const B2<T> lo = mul2(ld2(Lc + 4 * (pkc + t)), M1);
+                        T *al = accL + 4 * tg;
+                        al[0] -= lo.a; al[1] -= lo.b; al[2] -= lo.c; al[3] -= lo.d;
+                        if (t > 0) {
+                            const B2<T> up = mul2(M2, ld2(Uc + 4 * (pkc + t)));
+                            T *au = accU + 4 * tg;
+                            au[0] -= up.a; au[1] -= up.b; au[2] -= up.c; au[3] -= up.d;
+                        }
+                    }
+                    __syncwarp();
+                }
+                finalize(c, accL, accU, cnt, lane, 32);
+                __syncwarp();
+            }
+        } else {
+            for (int c = cb; c < c1; c++) {
+                const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0;
+                T *accL = accw, *accU = accw + 4 * (m.max_col + 1);
+                for (int t = lane; t < 8 * (cnt + 1); t += 32) accw[t < 4 * (cnt + 1) ? t : 4 * (m.max_col + 1) + t - 4 * (cnt + 1)] = T(0);
+                __syncwarp();
+                for (int q = m.Fp[c] + warp; q < m.Fp[c + 1]; q += nwarps) {
+                    const int k = m.Fc[q], pkc = m.Fpos[q];
+                    const B2<T> Dk = ld2(D + 4 * k);
+                    const B2<T> M1 = mul2(Dk, ld2(Uc + 4 * pkc));
+                    const B2<T> M2 = mul2(ld2(Lc + 4 * pkc), Dk);
+                    const int len = m.Cp[k + 1] - pkc, o = m.uoff[q];
+                    for (int t = lane; t < len; t += 32) {
+                        const int tg = m.umap[o + t];
+                        const B2<T> lo = mul2(ld2(Lc + 4 * (pkc + t)), M1);
+                        T *al = accL + 4 * tg;
+                        al[0] += lo.a; al[1] += lo.b; al[2] += lo.c; al[3] += lo.d;
+                        if (t > 0) {
+                            const B2<T> up = mul2(M2, ld2(Uc + 4 * (pkc + t)));
+                            T *au = accU + 4 * tg;
+                            au[0] += up.a; au[1] += up.b; au[2] += up.c; au[3] += up.d;
+                        }
+                    }
+                    __syncwarp();
+                }
+                __syncthreads();
+                // reduce the warps' partial sums in warp order into fin (L then U)
+                T *finL = fin, *finU = fin + 4 * (m.max_col + 1);
+                for (int t = threadIdx.x; t < 4 * (cnt + 1); t += blockDim.x) {
+                    const int blk = t >> 2, q4 = t & 3;
+                    double sl = blk == 0 ? Aj[m.jD + 4 * c + q4] : Aj[m.jLc + 4 * (c0 + blk - 1) + q4];
+                    double su = blk == 0 ? 0.0 : Aj[m.jUc + 4 * (c0 + blk - 1) + q4];
+                    T vl = T(sl), vu = T(su);
+                    for (int w = 0; w < nwarps; w++) {
+                        vl -= reinterpret_cast<T *>(scratch)[w * sa + t];
+                        vu -= reinterpret_cast<T *>(scratch)[w * sa + 4 * (m.max_col + 1) + t];
+                    }
+                    finL[t] = vl;
+                    finU[t] = vu;
+                }
+                __syncthreads();
+                finalize(c, finL, finU, cnt, int(threadIdx.x), int(blockDim.x));
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+    // row-ordered copies for the forward sweeps
+    T *Lr = F + m.jLr, *Ur = F + m.jUr;
+    for (int q = threadIdx.x; q < m.nnz; q += blockDim.x) {
+        st2(Lr + 4 * q, ld2(Lc + 4 * m.Fpos[q]));
+        st2(Ur + 4 * q, ld2(Uc + 4 * m.Fpos[q]));
+    }
+    __syncthreads();
+    return bad;
+}
+
+// J x = x (TRANS = false) or J^T x = x (TRANS = true) with the block factors.
+template <class T, class X, bool TRANS>
+__device__ bool block_solve2(Ring *R, unsigned char *stages, const DevMat &m, const T *F, X *x,
+                             unsigned spin) {
+    if (!staged_sweep<T, X, 2, TRANS>(R, stages, m.pfJ, m.npfJ, m.Fp, m.Fc,
+                                      F + (TRANS ? m.jUr : m.jLr), nullptr, m.lvl_ptr, x, spin))
+        return false;
+    return staged_sweep<T, X, 2, TRANS>(R, stages, m.pbJ, m.npbJ, m.Cp, m.Cr,
+                                        F + (TRANS ? m.jLc : m.jUc), F + m.jDi, m.lvl_ptr, x, spin);
+}
+
+// r = b - J x (TRANS: b - J^T x) for row r of the FP64 Jacobian A.
+template <bool TRANS>
+__device__ __forceinline__ void jac_residual_row(const DevMat &m, const double *A, const double *b,
+                                                 const double *x, int r, double &r0, double &r1) {
+    double s0 = b[2 * r], s1 = b[2 * r + 1];
+    const double *D = A + m.jD + 4 * r;
+    const double x0 = x[2 * r], x1 = x[2 * r + 1];
+    if (!TRANS) {
+        s0 -= D[0] * x0 + D[1] * x1;
+        s1 -= D[2] * x0 + D[3] * x1;
+    } else {
+        s0 -= D[0] * x0 + D[2] * x1;
+        s1 -= D[1] * x0 + D[3] * x1;
+    }
+    // entries of row r with columns c < r (CSR), and i > r (CSC of column r)
+    for (int q = m.Fp[r]; q < m.Fp[r + 1]; q++) {
+        const int c = m.Fc[q], p = m.Fpos[q];
+        const double *Bk = A + (TRANS ? m.jUc : m.jLc) + 4 * p;  // J_rc, or J_cr for J^T
+        const double y0 = x[2 * c], y1 = x[2 * c + 1];
+        if (!TRANS) { s0 -= Bk[0] * y0 + Bk[1] * y1; s1 -= Bk[2] * y0 + Bk[3] * y1; }
+        else { s0 -= Bk[0] * y0 + Bk[2] * y1; s1 -= Bk[1] * y0 + Bk[3] * y1; }
+    }
+    for (int p = m.Cp[r]; p < m.Cp[r + 1]; p++) {
+        const int i = m.Cr[p];
+        const double *Bk = A + (TRANS ? m.jLc : m.jUc) + 4 * p;  // J_ri, or J_ir for J^T
+        const double y0 = x[2 * i], y1 = x[2 * i + 1];
+        if (!TRANS) { s0 -= Bk[0] * y0 + Bk[1] * y1; s1 -= Bk[2] * y0 + Bk[3] * y1; }
+        else { s0 -= Bk[0] * y0 + Bk[2] * y1; s1 -= Bk[1] * y0 + Bk[3] * y1; }
+    }
+    r0 = s0;
+    r1 = s1;
+}
+
+// Refined block solve of case c in one block: x = J^-1 b (or J^-T b) into
+// the refined-x region, with FP64 residuals against A when the factor is
+// FP32 (or when `always_refine`, e.g. factors of an earlier state).
+template <class T, bool TRANS>
+__device__ bool nr_solve(const NrArgs &a, Ring *R, unsigned char *stages, T *xs, const T *F,
+                         const double *A, int c, double *red, int &ir_steps, bool always_refine) {
+    const DevMat &m = a.m;
+    const int nbus = a.dn.nbus;
+    const int N = 2 * m.n;
+    double *b = a.xg + (long long)c * 6 * nbus;
+    double *x64 = b + 2 * nbus;
+    T *xv = xs ? xs : reinterpret_cast<T *>(x64 + 2 * nbus);
+    const bool refine = always_refine || sizeof(T) != sizeof(double);
+    double bn = 0.0;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+        xv[r] = T(b[r]);
+        bn = fmax(bn, fabs(b[r]));
+    }
+    bn = block_max(bn, red);
+    bool ok = true;
+    for (int k = 0;; k++) {
+        ok = block_solve2<T, T, TRANS>(R, stages, m, F, xv, a.spin);
+        if (!ok) break;
+        for (int r = threadIdx.x; r < N; r += blockDim.x)
+            x64[r] = (k == 0 ? 0.0 : x64[r]) + double(xv[r]);
+        __syncthreads();
+        if (!refine || k >= a.ir_max) break;
+        double rn = 0.0;
+        for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
+            double r0, r1;
+            jac_residual_row<TRANS>(m, A, b, x64, r, r0, r1);
+            xv[2 * r] = T(r0);
+            xv[2 * r + 1] = T(r1);
+            rn = nan_max(rn, fmax(fabs(r0), fabs(r1)));
+        }
+        rn = block_max(rn, red);
+        if (!(rn > a.ir_tol * bn) || !(rn > a.ir_abs)) break;
+        ir_steps++;
+    }
+    return ok;
+}
+
+// Newton-Raphson power flow of one case per cluster of C CTAs: mismatch and
+// Jacobian assembly spread over the cluster, factor and solve in CTA 0.
+template <class T, int C>
+__global__ void __launch_bounds__(512) k_nr(NrArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[33];
+    __shared__ Ring R;
+    const DevNet &dn = a.dn;
+    const DevMat &m = a.m;
+    const int nbus = dn.nbus;
+    const int c = blockIdx.x / C;
+    const int rank = C == 1 ? 0 : int(cluster_rank());
+    unsigned char *stages = smem_raw;
+    unsigned char *scratch = smem_raw + kStages * kStageBytes;
+    T *xs = a.use_smem ? reinterpret_cast<T *>(scratch) : nullptr;  // shares the factor scratch
+    ring_init(&R);
+    double *vm = a.vm + (long long)c * nbus;
+    double *va = a.va + (long long)c * nbus;
+    double *flag = a.bmax + (long long)c * 16 + 15;
+    T *F = static_cast<T *>(a.F) + (long long)c * m.jstride;
+    const double *A = a.A + (long long)c * m.jstride;
+    const int slice = (nbus + C - 1) / C;
+    const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
+    const int nslot = m.n + m.nnz;
+    const int sslice = (nslot + C - 1) / C;
+    const int s0 = rank * sslice, s1 = min(nslot, s0 + sslice);
+    if (a.flat)
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int t = dn.btype[i];
+            vm[i] = (t == PF_BUS_PQ) ? 1.0 : dn.vset[i];
+            va[i] = (t == PF_BUS_SLACK) ? dn.va0[i] : 0.0;
+        }
+    int status = PF_ERR_NOT_CONVERGED, iters = 0, ir_steps = 0;
+    double mis = INFINITY;
+    for (int it = 0;; it++) {
+        nr_rect(a, c, i0, i1);
+        cluster_sync<C>();
+        const double mx = nr_mismatch_slice(a, c, i0, i1, red);
+        if (threadIdx.x == 0) a.bmax[(long long)c * 16 + rank] = mx;
+        cluster_sync<C>();
+        mis = 0.0;
+        for (int r = 0; r < C; r++) mis = nan_max(mis, a.bmax[(long long)c * 16 + r]);
+        if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
+        if (mis <= a.tol) { status = PF_OK; break; }
+        if (it >= a.max_iter) break;
+        nr_assemble(a, c, s0, s1);
+        cluster_sync<C>();
+        if (rank == 0) {
+            const int fs = block_factor<T>(m, A, F, scratch, red);
+            bool ok = fs == PF_OK;
+            if (ok) ok = nr_solve<T, false>(a, &R, stages, xs, F, A, c, red, ir_steps, false);
+            if (threadIdx.x == 0) {
+                a.fstat[c] = fs;
+                *flag = fs != PF_OK ? double(fs) : (ok ? 0.0 : double(PF_ERR_TIMEOUT));
+            }
+        }
+        cluster_sync<C>();
+        if (*flag != 0.0) { status = int(*flag); break; }
+        const double *dx = a.xg + (long long)c * 6 * nbus + 2 * nbus;
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int k = m.new_of_bus[i];
+            if (k >= 0) {
+                va[i] += dx[2 * k];
+                if (dn.btype[i] == PF_BUS_PQ) vm[i] += dx[2 * k + 1];
+            }
+        }
+        iters++;
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        a.res[c].status = status;
+        a.res[c].iters = iters;
+        a.res[c].ir_steps = ir_steps;
+        a.res[c].pad = 0;
+        a.res[c].max_mismatch = mis;
+    }
+    cluster_sync<C>();
+}
+
+// Adjoint of case c: J(x)^T y = g with the stored factors (from the last
+// Newton step, i.e. of an earlier state) refined in FP64 against the exact
+// J(x) assembled here; dJ/dP_i = y_P(i), dJ/dQ_i = y_Q(i) (PQ), 0 elsewhere.
+template <class T, int C>
+__global__ void __launch_bounds__(512) k_adjoint(NrArgs a, int factor_now) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[33];
+    __shared__ Ring R;
+    const DevNet &dn = a.dn;
+    const DevMat &m = a.m;
+    const int nbus = dn.nbus;
+    const int c = blockIdx.x / C;
+    const int rank = C == 1 ? 0 : int(cluster_rank());
+    unsigned char *stages = smem_raw;
+    unsigned char *scratch = smem_raw + kStages * kStageBytes;
+    T *xs = a.use_smem ? reinterpret_cast<T *>(scratch) : nullptr;
+    ring_init(&R);
+    T *F = static_cast<T *>(a.F) + (long long)c * m.jstride;
+    const double *A = a.A + (long long)c * m.jstride;
+    const int slice = (nbus + C - 1) / C;
+    const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
+    const int nslot = m.n + m.nnz;
+    const int sslice = (nslot + C - 1) / C;
+    const int s0 = rank * sslice, s1 = min(nslot, s0 + sslice);
+    double *flag = a.bmax + (long long)c * 16 + 15;
+    nr_rect(a, c, i0, i1);
+    cluster_sync<C>();
+    (void)nr_mismatch_slice(a, c, i0, i1, red);  // P, Q at the state
+    double *b = a.xg + (long long)c * 6 * nbus;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int k = m.new_of_bus[i];
+        if (k >= 0) {
+            b[2 * k] = a.gva[(long long)c * nbus + i];
+            b[2 * k + 1] = dn.btype[i] == PF_BUS_PQ ? a.gvm[(long long)c * nbus + i] : 0.0;
+        }
+    }
+    cluster_sync<C>();
+    nr_assemble(a, c, s0, s1);
+    cluster_sync<C>();
+    if (rank == 0) {
+        int fs = factor_now ? PF_OK : a.fstat[c];
+        if (factor_now) fs = block_factor<T>(m, A, F, scratch, red);
+        int irs = 0;
+        bool ok = fs == PF_OK;
+        if (ok) ok = nr_solve<T, true>(a, &R, stages, xs, F, A, c, red, irs, true);
+        if (threadIdx.x == 0) *flag = fs != PF_OK ? double(fs) : (ok ? 0.0 : double(PF_ERR_TIMEOUT));
+    }
+    cluster_sync<C>();
+    const double *y = a.xg + (long long)c * 6 * nbus + 2 * nbus;
+    const bool okall = *flag == 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int k = m.new_of_bus[i];
+        const long long idx = (long long)c * nbus + i;
+        double p = 0.0, q = 0.0;
+        if (k >= 0 && okall) {
+            p = y[2 * k];
+            q = dn.btype[i] == PF_BUS_PQ ? y[2 * k + 1] : 0.0;
+        } else if (!okall) {
+            p = q = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        a.dJdP[idx] = p;
+        a.dJdQ[idx] = q;
+    }
+    if (rank == 0 && threadIdx.x == 0) a.res[c].status = okall ? PF_OK : int(*flag);
+    cluster_sync<C>();
+}
+
+// Objective J = sum_i (V_i - 1)^2 + sum_i P_i (total active losses) of case c
+// (one block per case) and its gradient with respect to every bus angle and
+// magnitude: dJ/dtheta_k = sum_l dP_l/dtheta_k, dJ/dV_k = 2 (V_k - 1) +
+// sum_l dP_l/dV_k, summed over every row l including the slack.
+__global__ void __launch_bounds__(512) k_objective(DevNet dn, DevCases dc, const double *vm,
+                                                   const double *va, double *ef, double *Jv,
+                                                   double *gva, double *gvm) {
+    __shared__ double red[33];
+    const int c = blockIdx.x;
+    const int nbus = dn.nbus;
+    const double *v = vm + (long long)c * nbus;
+    const double *th = va + (long long)c * nbus;
+    double *e = ef + (long long)c * 4 * nbus;
+    double *f = e + nbus;
+    double *P = e + 2 * nbus;
+    double *Q = e + 3 * nbus;
+    const int outage = dc.outage[c];
+    for (int i = threadIdx.x; i < nbus; i += blockDim.x) {
+        double s, co;
+        sincos(th[i], &s, &co);
+        e[i] = v[i] * co;
+        f[i] = v[i] * s;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int i = threadIdx.x; i < nbus; i += blockDim.x) {
+        double p, q;
+        bus_injection(dn, i, outage, e, f, p, q);
+        P[i] = p;
+        Q[i] = q;
+        part += (v[i] - 1.0) * (v[i] - 1.0) + p;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nbus; k += blockDim.x) {
+        double gt = 0.0, gv = 2.0 * (v[k] - 1.0);
+        for (int p = dn.rowptr[k]; p < dn.rowptr[k + 1]; p++) {
+            const int l = dn.col[p];
+            double G, B;
+            y_entry(dn, outage, l, k, p, G, B);  // Y is symmetric: Y_lk at row k's slot
+            if (l != k) {
+                const B2<double> J = jac_off(G, B, e[l], f[l], e[k], f[k], v[k], false, false);
+                gt += J.a;
+                gv += J.b;
+            } else {
+                const B2<double> J = jac_diag(G, B, P[k], Q[k], v[k], false);
+                gt += J.a;
+                gv += J.b;
+            }
+        }
+        gva[(long long)c * nbus + k] = gt;
+        gvm[(long long)c * nbus + k] = gv;
+    }
+    // block sum of the objective (fixed order: warp shuffles then warps)
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); w++) s += red[w];
+        Jv[c] = s;
+    }
+}
+
+template <int C, class... Args>
+cudaError_t launch_cluster(void (*kernel)(Args...), size_t smem, cudaStream_t s, int ncase,
+                           Args... args) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(ncase) * C);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cfg.numAttrs = 0;
+    if (C > 1) {
+        if (C > 8) {
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+
+size_t nr_smem(const DevMat &m, int prec, size_t smem_optin, int *use_smem) {
+    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
+    const size_t ring = size_t(kStages) * kStageBytes;
+    const size_t fac = elt * size_t(8 * (m.max_col + 1)) * (512 / 32 + 1);
+    const size_t vec = elt * size_t(2 * m.n);
+    size_t smem = ring + (fac > vec ? fac : vec);
+    *use_smem = smem + 2048 <= smem_optin;
+    if (!*use_smem) smem = ring + fac;
+    return smem;
+}
+
+int nr_cluster_size(const DevMat &m, int ncase, int num_sms, int prec, size_t smem_optin) {
+    int use = 0;
+    const size_t smem = nr_smem(m, prec, smem_optin, &use);
+    for (int C : {16, 8}) {
+        if (ncase * C > num_sms) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(C));
+        cfg.blockDim = dim3(512);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        cudaError_t e;
+        if (prec == PF_FP64) {
+            auto *k = (C == 16) ? k_nr<double, 16> : k_nr<double, 8>;
+            if (C == 16) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            e = cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg);
+        } else {
+            auto *k = (C == 16) ? k_nr<float, 16> : k_nr<float, 8>;
+            if (C == 16) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            e = cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg);
+        }
+        if (e == cudaSuccess && nclusters >= ncase) return C;
+        cudaGetLastError();
+    }
+    return 1;
+}
+
+cudaError_t launch_nr(const NrLaunch &L, cudaStream_t s) {
+    NrArgs a;
+    a.dn = L.dn;
+    a.dc = L.dc;
+    a.m = L.m;
+    a.F = L.F;
+    a.A = L.A;
+    a.fstat = L.fstat;
+    a.tol = L.o.tol;
+    a.max_iter = L.o.max_iter;
+    a.flat = L.o.flat_start;
+    a.spin = L.o.spin_limit > 0 ? unsigned(L.o.spin_limit) : kDefaultSpin;
+    a.ir_max = L.o.ir_max;
+    a.ir_tol = L.o.ir_tol;
+    a.ir_abs = L.o.ir_abs > 0 ? L.o.ir_abs : 0.01 * L.o.tol;
+    a.vm = L.vm;
+    a.va = L.va;
+    a.ef = L.ef;
+    a.xg = L.xg;
+    a.bmax = L.bmax;
+    a.res = L.res;
+    a.gva = L.gva;
+    a.gvm = L.gvm;
+    a.dJdP = L.dJdP;
+    a.dJdQ = L.dJdQ;
+    int use = 0;
+    const size_t smem = nr_smem(L.m, L.prec, L.smem_optin, &use);
+    a.use_smem = use;
+    const int C = L.cluster;
+    const int nc = L.dc.ncase;
+    const int fnow = L.factor_now;
+    if (L.adjoint) {
+        if (L.prec == PF_FP64) {
+            if (C >= 16) return launch_cluster<16>(k_adjoint<double, 16>, smem, s, nc, a, fnow);
+            if (C >= 8) return launch_cluster<8>(k_adjoint<double, 8>, smem, s, nc, a, fnow);
+            return launch_cluster<1>(k_adjoint<double, 1>, smem, s, nc, a, fnow);
+        }
+        if (C >= 16) return launch_cluster<16>(k_adjoint<float, 16>, smem, s, nc, a, fnow);
+        if (C >= 8) return launch_cluster<8>(k_adjoint<float, 8>, smem, s, nc, a, fnow);
+        return launch_cluster<1>(k_adjoint<float, 1>, smem, s, nc, a, fnow);
+    }
+    if (L.prec == PF_FP64) {
+        if (C >= 16) return launch_cluster<16>(k_nr<double, 16>, smem, s, nc, a);
+        if (C >= 8) return launch_cluster<8>(k_nr<double, 8>, smem, s, nc, a);
+        return launch_cluster<1>(k_nr<double, 1>, smem, s, nc, a);
+    }
+    if (C >= 16) return launch_cluster<16>(k_nr<float, 16>, smem, s, nc, a);
+    if (C >= 8) return launch_cluster<8>(k_nr<float, 8>, smem, s, nc, a);
+    return launch_cluster<1>(k_nr<float, 1>, smem, s, nc, a);
+}
+
+cudaError_t launch_objective(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
+                             double *ef, double *J, double *gva, double *gvm, cudaStream_t s) {
+    k_objective<<<dc.ncase, 512, 0, s>>>(dn, dc, vm, va, ef, J, gva, gvm);
+    return cudaGetLastError();
+}
+
+}  // namespace gbpf

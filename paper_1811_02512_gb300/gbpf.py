@@ -50,7 +50,7 @@ class pf_symbolic_info(C.Structure):
 class pf_run_opts(C.Structure):
     _fields_ = [("method", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("max_iter", C.c_int32), ("ir_max", C.c_int32), ("ir_tol", C.c_double),
-                ("flat_start", C.c_int32), ("spin_limit", C.c_int32)]
+                ("ir_abs", C.c_double), ("flat_start", C.c_int32), ("spin_limit", C.c_int32)]
 
 
 class pf_case_result(C.Structure):
@@ -88,6 +88,11 @@ def load():
         L.pf_get_ybus.argtypes = [_P, _P, _P, _P, _P]
         L.pf_set_profiling.argtypes = [_P, C.c_int32]
         L.pf_get_profile.argtypes = [_P, C.c_int32, _P, _P, C.c_int32]
+        L.pf_set_injections.argtypes = [_P, _P, _P, _P]
+        L.pf_adjoint.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]
+        L.pf_objective.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+        for nm in ("pf_set_injections", "pf_adjoint", "pf_objective"):
+            getattr(L, nm).restype = S
         L.pf_mismatch_static.argtypes = [C.c_int32] + [_P] * 13
         L.pf_mismatch_static.restype = S
         L.pf_last_error.argtypes = [_P]
@@ -200,10 +205,11 @@ def pf_mismatch(ctx, vm_dev, va_dev, dp_dev, dq_dev, maxmis_dev, ncase, stream=N
 
 
 def run_opts(method=PF_FDPF, precision=PF_FP64, tol=1e-8, max_iter=None, ir_max=5, ir_tol=1e-10,
-             flat_start=1, spin_limit=0):
+             ir_abs=0.0, flat_start=1, spin_limit=0):
     if max_iter is None:
         max_iter = 200 if method == PF_FDPF else 20
-    return pf_run_opts(method, precision, tol, max_iter, ir_max, ir_tol, flat_start, spin_limit)
+    return pf_run_opts(method, precision, tol, max_iter, ir_max, ir_tol, ir_abs, flat_start,
+                       spin_limit)
 
 
 def pf_run_to_tol(ctx, opts, vm_dev, va_dev, ncase, stream=None, check=True):
@@ -238,6 +244,25 @@ def pf_get_profile(ctx, kind, reset=False):
     _check(ctx, load().pf_get_profile(ctx, kind, C.byref(n), C.byref(ms), 1 if reset else 0),
            "pf_get_profile")
     return n.value, ms.value
+
+
+def pf_set_injections(ctx, psp_dev, qsp_dev, stream=None):
+    _check(ctx, load().pf_set_injections(ctx, _ptr(psp_dev), _ptr(qsp_dev), _stream(stream)),
+           "pf_set_injections")
+
+
+def pf_adjoint(ctx, precision, vm_dev, va_dev, gva_dev, gvm_dev, dJdP_dev, dJdQ_dev, ncase,
+               stream=None):
+    res = np.zeros(ncase, dtype=CASE_RESULT_DTYPE)
+    _check(ctx, load().pf_adjoint(ctx, precision, _ptr(vm_dev), _ptr(va_dev), _ptr(gva_dev),
+                                  _ptr(gvm_dev), _ptr(dJdP_dev), _ptr(dJdQ_dev), _ptr(res),
+                                  _stream(stream)), "pf_adjoint")
+    return res
+
+
+def pf_objective(ctx, vm_dev, va_dev, J_dev, gva_dev, gvm_dev, stream=None):
+    _check(ctx, load().pf_objective(ctx, _ptr(vm_dev), _ptr(va_dev), _ptr(J_dev), _ptr(gva_dev),
+                                    _ptr(gvm_dev), _stream(stream)), "pf_objective")
 
 
 PF_STATIC_MAX_BUS = 131072
@@ -293,3 +318,86 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- autograd
+
+def _torch():
+    import torch
+    return torch
+
+
+class PowerFlowFn:
+    """torch.autograd.Function: (Psp, Qsp) [ncase, nbus] -> (vm, va) by
+    Newton-Raphson in libgbpf; backward by the adjoint kernel (transposed
+    solve with the forward factors, FP64-refined)."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, grid, psp, qsp, precision=PF_FP64, tol=1e-10, max_iter=30):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _PF(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx_, psp_, qsp_, g, prec, tol_, mi):
+                    psp_c = psp_.detach().contiguous()
+                    qsp_c = qsp_.detach().contiguous()
+                    ncase = psp_c.shape[0]
+                    pf_set_injections(g.ctx, psp_c, qsp_c)
+                    vm = torch.zeros_like(psp_c)
+                    va = torch.zeros_like(psp_c)
+                    st, res = pf_run_to_tol(g.ctx, run_opts(PF_NR, prec, tol=tol_, max_iter=mi), vm,
+                                            va, ncase)
+                    if st != PF_OK:
+                        raise PFError(st, pf_last_error(g.ctx))
+                    ctx_.save_for_backward(vm, va)
+                    ctx_.g, ctx_.prec = g, prec
+                    ctx_.mark_non_differentiable()
+                    return vm, va
+
+                @staticmethod
+                def backward(ctx_, gvm, gva):
+                    vm, va = ctx_.saved_tensors
+                    g = ctx_.g
+                    gvm = torch.zeros_like(vm) if gvm is None else gvm.contiguous()
+                    gva = torch.zeros_like(va) if gva is None else gva.contiguous()
+                    dP = torch.empty_like(vm)
+                    dQ = torch.empty_like(vm)
+                    pf_adjoint(g.ctx, ctx_.prec, vm, va, gva, gvm, dP, dQ, vm.shape[0])
+                    return dP, dQ, None, None, None, None
+
+            cls._fn = _PF
+        return cls._fn.apply(psp, qsp, grid, precision, tol, max_iter)
+
+
+class ObjectiveFn:
+    """torch.autograd.Function: (vm, va) -> J = sum (V - 1)^2 + total losses
+    per case, value and gradient from the objective kernel."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, grid, vm, va):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _Obj(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx_, vm_, va_, g):
+                    vm_c, va_c = vm_.detach().contiguous(), va_.detach().contiguous()
+                    J = torch.empty(vm_c.shape[0], dtype=torch.float64, device=vm_c.device)
+                    gva = torch.empty_like(vm_c)
+                    gvm = torch.empty_like(vm_c)
+                    pf_objective(g.ctx, vm_c, va_c, J, gva, gvm)
+                    ctx_.save_for_backward(gvm, gva)
+                    return J
+
+                @staticmethod
+                def backward(ctx_, gJ):
+                    gvm, gva = ctx_.saved_tensors
+                    return gJ[:, None] * gvm, gJ[:, None] * gva, None
+
+            cls._fn = _Obj
+        return cls._fn.apply(vm, va, grid)

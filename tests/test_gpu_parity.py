@@ -231,3 +231,36 @@ def test_no_pq_bus_empty_bpp(oracle):
     assert rc == oracle.OK
     assert np.max(np.abs(va[0] - va0)) <= 1e-8
     g.close()
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_fp32_factor_with_fp64_refinement(oracle, cfg):
+    """FP32 factor and substitution, FP64 mismatch and FP64 refinement of every
+    linear solve: voltages reach the FP64 oracle's within 1e-8."""
+    case = CASES[cfg]()
+    g = _grid(case)
+    vm = torch.zeros((1, case.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP32, tol=1e-11, max_iter=300, ir_max=5,
+                         ir_tol=1e-10)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, 1)
+    assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    assert res[0]["ir_steps"] > 0
+    rc, vm0, va0, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
+    assert np.max(np.abs(vm.cpu().numpy()[0] - vm0)) <= 1e-8
+    assert np.max(np.abs(va.cpu().numpy()[0] - va0)) <= 1e-8
+    g.close()
+
+
+def test_fp32_batched_cases_refined(oracle):
+    base = gridgen.config(0)
+    sc = gridgen.scenarios(base, n_load=4, n_outage=4, seed=21)
+    g = _grid(base, sc.ncase, sc.load_scale, sc.outage)
+    st, res, vm, va = _run(g, sc.ncase, precision=gbpf.PF_FP32, tol=1e-11, max_iter=400)
+    assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    for c in range(sc.ncase):
+        cc = gridgen.apply_scenario(base, sc, c)
+        rc, vm0, va0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+        assert np.max(np.abs(vm[c] - vm0)) <= 1e-8, c
+        assert np.max(np.abs(va[c] - va0)) <= 1e-8, c
+    g.close()
