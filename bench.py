@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--impl", default="gbpf", choices=["gbpf", "reference"])
     ap.add_argument("--workload", default="plain10k", choices=["plain10k", "batch10k"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
+    ap.add_argument("--method", default="fdpf", choices=["fdpf", "nr"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "block", "lanes"])
+    ap.add_argument("--ncase", type=int, default=1024,
+                    help="batch10k: number of cases (half load scenarios, half outages)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     return ap.parse_args()
@@ -59,12 +63,12 @@ def dist_env():
 
 # ------------------------------------------------------------------ workloads
 
-def make_workload(name):
+def make_workload(name, ncase=1024):
     from paper_1811_02512_gb300 import gridgen
     base = gridgen.config(1)
     if name == "plain10k":
         return base, 1, None, None
-    sc = gridgen.scenarios(base, n_load=512, n_outage=512)
+    sc = gridgen.scenarios(base, n_load=ncase // 2, n_outage=ncase - ncase // 2)
     return base, sc.ncase, sc.load_scale, sc.outage
 
 
@@ -247,14 +251,18 @@ def main():
         dist.barrier()
     from paper_1811_02512_gb300 import gbpf
 
-    base, ncase, load_scale, outage = make_workload(args.workload)
+    base, ncase, load_scale, outage = make_workload(args.workload, args.ncase)
     prec_name = workload_precision(args.workload, args.precision)
     prec = gbpf.PF_FP64 if prec_name == "fp64" else gbpf.PF_FP32
     t0 = time.perf_counter()
     g = gbpf.Grid(base)
     analyze_ms = (time.perf_counter() - t0) * 1e3
     g.set_cases(ncase, load_scale, outage)
-    opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=TOL, max_iter=200)
+    method = gbpf.PF_FDPF if args.method == "fdpf" else gbpf.PF_NR
+    engine = {"auto": gbpf.PF_ENGINE_AUTO, "block": gbpf.PF_ENGINE_BLOCK,
+              "lanes": gbpf.PF_ENGINE_LANES}[args.engine]
+    opts = gbpf.run_opts(method, prec, tol=TOL, max_iter=200 if method == gbpf.PF_FDPF else 20,
+                         engine=engine)
     vm = torch.zeros((ncase, base.n), dtype=torch.float64, device=dev)
     va = torch.zeros_like(vm)
     stream = torch.cuda.current_stream(dev)
@@ -351,6 +359,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "nbus": base.n, "nbranch": base.m,
                        "ncase": ncase, "precision": prec_name, "tol_pu": TOL,
+                       "method": args.method, "engine": args.engine,
                        "l2": "flushed between timed steps (2.5x L2 buffer write)",
                        "loading_factor": base.lam, "analyze_ms": analyze_ms,
                        "parallelism": "replicas" if ncase == 1 else "cases-in-blocks"},

@@ -101,7 +101,18 @@ typedef struct {
                            residual that small cannot change a convergence decision) */
     int32_t flat_start; /* 1: theta = slack angle / 0, V = 1 (PQ) or vset; 0: use vm/va */
     int32_t spin_limit; /* bound on every device-side wait (0 = library default) */
+    int32_t engine;     /* PF_ENGINE_AUTO, PF_ENGINE_BLOCK or PF_ENGINE_LANES (FDPF only) */
 } pf_run_opts;
+
+/* Engines of pf_run_to_tol.  BLOCK: one thread block (or, for a few large
+ * cases, a 16-block cluster) per case, each case iterating independently in
+ * one persistent launch.  LANES (FDPF only): the batch advances in lockstep
+ * in groups of 32 cases, one case per lane; the mismatch, convergence test
+ * and update run over (bus, case) pairs, each substitution over blocks of
+ * 4, 2 or 1 cases whose vectors fit in shared memory, and one half-iteration
+ * pair is a CUDA graph replayed until every case has retired.  AUTO picks
+ * BLOCK; LANES falls back to BLOCK where not even one case fits. */
+enum { PF_ENGINE_AUTO = 0, PF_ENGINE_BLOCK = 1, PF_ENGINE_LANES = 2 };
 
 /* Per-case outcome of pf_run_to_tol. */
 typedef struct {

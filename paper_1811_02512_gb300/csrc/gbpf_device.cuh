@@ -164,7 +164,7 @@ __device__ void ring_issue(Ring *R, unsigned char *stages, int st, const Piece &
     const int d_lo = (pc.r0 * NB2) & ~(V - 1), d_hi = (pc.r1 * NB2 + V - 1) & ~(V - 1);
     const uint32_t pbytes = uint32_t(p_hi - p_lo) * 4u;
     const uint32_t ibytes = pc.e1 > pc.e0 ? uint32_t(i_hi - i_lo) * 4u : 0u;
-    const uint32_t vbytes = pc.e1 > pc.e0 ? uint32_t(v_hi - v_lo) * uint32_t(sizeof(T)) : 0u;
+    const uint32_t vbytes = (pc.e1 > pc.e0 && val) ? uint32_t(v_hi - v_lo) * uint32_t(sizeof(T)) : 0u;
     const uint32_t dbytes = dinv ? uint32_t(d_hi - d_lo) * uint32_t(sizeof(T)) : 0u;
     const int lp_lo = pc.l0 & ~3, lp_hi = (pc.l1 + 2 + 3) & ~3;
     const uint32_t lbytes = pc.mode == 2 ? uint32_t(lp_hi - lp_lo) * 4u : 0u;
@@ -181,10 +181,8 @@ __device__ void ring_issue(Ring *R, unsigned char *stages, int st, const Piece &
     fence_proxy_async();
     mbar_arrive_expect_tx(&R->bar[st], pbytes + ibytes + vbytes + dbytes + lbytes);
     tma_g2s(dst, ptr + p_lo, pbytes, &R->bar[st]);
-    if (ibytes) {
-        tma_g2s(dst + ioff, idx + i_lo, ibytes, &R->bar[st]);
-        tma_g2s(dst + voff, val + v_lo, vbytes, &R->bar[st]);
-    }
+    if (ibytes) tma_g2s(dst + ioff, idx + i_lo, ibytes, &R->bar[st]);
+    if (vbytes) tma_g2s(dst + voff, val + v_lo, vbytes, &R->bar[st]);
     if (dbytes) tma_g2s(dst + doff, dinv + d_lo, dbytes, &R->bar[st]);
     if (lbytes) tma_g2s(dst + loff, lvl_ptr + lp_lo, lbytes, &R->bar[st]);
 }
@@ -409,6 +407,31 @@ __device__ bool block_solve(Ring *R, unsigned char *stages, const DevMat &m, con
         return false;
     return staged_sweep<T, X, 1, false>(R, stages, m.pb, m.npb, m.Cp, m.Cr, F + m.offLc,
                                         F + m.offDi, m.lvl_ptr, x, spin);
+}
+
+// sin and cos of a small angle (|x| <= kRotMax) from their Maclaurin series,
+// truncated after the x^11 (sin) and x^12 (cos) terms in Horner form; for
+// |x| <= 0.2 the first omitted terms are below 2e-19, far under one unit in
+// the last place.  Used to rotate cached (cos theta, sin theta) by a
+// Newton/FDPF angle step instead of re-evaluating both functions.
+constexpr double kRotMax = 0.2;
+
+__device__ __forceinline__ void small_sincos(double x, double *s, double *c) {
+    const double x2 = x * x;
+    const double ps = 1.0 / 39916800.0;   // 1/11!
+    double t = -ps;
+    t = t * x2 + 1.0 / 362880.0;          // 1/9!
+    t = t * x2 - 1.0 / 5040.0;            // 1/7!
+    t = t * x2 + 1.0 / 120.0;             // 1/5!
+    t = t * x2 - 1.0 / 6.0;               // 1/3!
+    *s = x + x * x2 * t;
+    double u = 1.0 / 479001600.0;         // 1/12!
+    u = u * x2 - 1.0 / 3628800.0;         // 1/10!
+    u = u * x2 + 1.0 / 40320.0;           // 1/8!
+    u = u * x2 - 1.0 / 720.0;             // 1/6!
+    u = u * x2 + 1.0 / 24.0;              // 1/4!
+    u = u * x2 - 0.5;                     // 1/2!
+    *c = 1.0 + x2 * u;
 }
 
 // Injection at bus i of one case: I_i = sum_k Y_ik V_k on the base admittance

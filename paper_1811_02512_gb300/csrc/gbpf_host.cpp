@@ -620,10 +620,19 @@ void free_case_storage(pf_ctx *ctx) {
         w.jfactored[q] = false;
     }
     dfree(ctx, w.JA); w.JA = nullptr;
+    {
+        LaneSet &L = w.lanes;
+        void *ptrs[] = {L.gcase, L.ginst, L.gshared, L.gown, L.owngroup, L.vm, L.va, L.cs, L.sn,
+                        L.iv, L.e, L.f, L.psp, L.qsp, L.maxmis, L.lastmis, L.active, L.status,
+                        L.iters, L.irs, L.nactive, L.X, L.b, L.x64, L.LF0, L.LF1};
+        for (void *p : ptrs) dfree(ctx, p);
+        L = LaneSet();
+    }
     dfree(ctx, w.xg6); w.xg6 = nullptr;
     dfree(ctx, w.ef); w.ef = nullptr;
     dfree(ctx, w.vec); w.vec = nullptr;
     dfree(ctx, w.bmax); w.bmax = nullptr;
+    dfree(ctx, w.iv); w.iv = nullptr;
     dfree(ctx, w.cstatus); w.cstatus = nullptr;
     dfree(ctx, w.res); w.res = nullptr;
     dfree(ctx, ctx->dc.outage); ctx->dc.outage = nullptr;
@@ -657,6 +666,72 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "factor launch");
     w.factored[which][prec] = true;
+    return PF_OK;
+}
+
+// Lane groups of the current batch: shared-factor cases first, then
+// own-factor (outage) cases, 32 lanes per group; state and vectors for prec.
+pf_status ensure_lanes(pf_ctx *ctx, int prec) {
+    LaneSet &L = ctx->ws.lanes;
+    if (L.gcase && L.prec == prec) return PF_OK;
+    if (L.gcase) {  // other precision: rebuild the precision-dependent arrays only
+        dfree(ctx, L.X); dfree(ctx, L.LF0); dfree(ctx, L.LF1);
+        L.X = L.LF0 = L.LF1 = nullptr;
+    } else {
+        const int ncase = ctx->dc.ncase;
+        std::vector<int> inst(ncase);
+        if (cudaMemcpy(inst.data(), ctx->dc.inst, sizeof(int) * ncase, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(ctx, PF_ERR_CUDA, "lanes: read instances");
+        std::vector<int> sh, own;
+        for (int c = 0; c < ncase; c++) (inst[c] == 0 ? sh : own).push_back(c);
+        const int gs = (int(sh.size()) + 31) / 32, go = (int(own.size()) + 31) / 32;
+        L.ngroups = gs + go;
+        L.ncp = 32 * L.ngroups;
+        L.nown = go;
+        std::vector<int> gcase(L.ncp, -1), ginst(L.ncp, 0), gshared(L.ngroups), gown(L.ngroups, -1),
+            owngroup(go);
+        for (size_t q = 0; q < sh.size(); q++) gcase[q] = sh[q];
+        for (size_t q = 0; q < own.size(); q++) {
+            gcase[32 * gs + q] = own[q];
+            ginst[32 * gs + q] = inst[own[q]];
+        }
+        for (int g = 0; g < L.ngroups; g++) {
+            gshared[g] = g < gs ? 1 : 0;
+            if (g >= gs) { gown[g] = g - gs; owngroup[g - gs] = g; }
+        }
+        TRY(upload(ctx, &L.gcase, gcase.data(), gcase.size()));
+        TRY(upload(ctx, &L.ginst, ginst.data(), ginst.size()));
+        TRY(upload(ctx, &L.gshared, gshared.data(), gshared.size()));
+        TRY(upload(ctx, &L.gown, gown.data(), gown.size()));
+        TRY(upload(ctx, &L.owngroup, owngroup.data(), std::max<size_t>(1, owngroup.size())));
+        const size_t ns = size_t(ctx->nbus) * L.ncp;
+        double **st[] = {&L.vm, &L.va, &L.cs, &L.sn, &L.iv, &L.e, &L.f, &L.psp, &L.qsp};
+        for (double **p : st) TRY(dalloc(ctx, p, ns));
+        TRY(dalloc(ctx, &L.maxmis, size_t(L.ncp)));
+        TRY(dalloc(ctx, &L.lastmis, size_t(L.ncp)));
+        TRY(dalloc(ctx, &L.active, size_t(L.ncp)));
+        TRY(dalloc(ctx, &L.status, size_t(L.ncp)));
+        TRY(dalloc(ctx, &L.iters, size_t(L.ncp)));
+        TRY(dalloc(ctx, &L.irs, size_t(L.ncp)));
+        TRY(dalloc(ctx, &L.nactive, size_t(1)));
+        TRY(dalloc(ctx, &L.b, ns));
+        TRY(dalloc(ctx, &L.x64, ns));
+        if (cudaMemset(L.maxmis, 0, sizeof(double) * L.ncp) != cudaSuccess)
+            return fail(ctx, PF_ERR_CUDA, "memset");
+    }
+    const size_t ns = size_t(ctx->nbus) * L.ncp;
+    const size_t nl0 = size_t(std::max(1, L.nown)) * ctx->dm[0].stride * 32;
+    const size_t nl1 = size_t(std::max(1, L.nown)) * ctx->dm[1].stride * 32;
+    if (prec == PF_FP64) {
+        double *x = nullptr, *l0 = nullptr, *l1 = nullptr;
+        TRY(dalloc(ctx, &x, ns)); TRY(dalloc(ctx, &l0, nl0)); TRY(dalloc(ctx, &l1, nl1));
+        L.X = x; L.LF0 = l0; L.LF1 = l1;
+    } else {
+        float *x = nullptr, *l0 = nullptr, *l1 = nullptr;
+        TRY(dalloc(ctx, &x, ns)); TRY(dalloc(ctx, &l0, nl0)); TRY(dalloc(ctx, &l1, nl1));
+        L.X = x; L.LF0 = l0; L.LF1 = l1;
+    }
+    L.prec = prec;
     return PF_OK;
 }
 
@@ -886,6 +961,7 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
     TRY(dalloc(ctx, &w.ef, size_t(ncase) * 4 * ctx->nbus));
     TRY(dalloc(ctx, &w.vec, size_t(ncase) * 3 * ctx->nbus));
     TRY(dalloc(ctx, &w.bmax, size_t(ncase) * 16));
+    TRY(dalloc(ctx, &w.iv, size_t(ncase) * ctx->nbus));
     TRY(dalloc(ctx, &w.cstatus, size_t(ncase)));
     if (cudaMemset(w.cstatus, 0, sizeof(int) * ncase) != cudaSuccess)
         return fail(ctx, PF_ERR_CUDA, "memset");
@@ -1028,12 +1104,47 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
     Workspace &w = ctx->ws;
     const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
     const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
+    const int nmax = std::max(ctx->dm[0].n, ctx->dm[1].n);
+    const bool lanes_ok = opts->method == PF_FDPF && lane_width(nmax, prec, ctx->smem_optin) > 0;
+    const int engine = opts->engine == PF_ENGINE_LANES && lanes_ok ? PF_ENGINE_LANES : PF_ENGINE_BLOCK;
+    if (engine == PF_ENGINE_LANES) {
+        TRY(ensure_lanes(ctx, prec));
+        LaneRun r;
+        r.dn = ctx->dn;
+        r.dc = ctx->dc;
+        r.m0 = ctx->dm[0];
+        r.m1 = ctx->dm[1];
+        r.L = ctx->ws.lanes;
+        r.F0 = F0;
+        r.F1 = F1;
+        r.fs0 = w.fstatus[0][prec];
+        r.fs1 = w.fstatus[1][prec];
+        r.A0 = w.A[0];
+        r.A1 = w.A[1];
+        r.o = *opts;
+        r.prec = prec;
+        r.vm = vm_dev;
+        r.va = va_dev;
+        r.res = w.res;
+        r.smem_optin = ctx->smem_optin;
+        cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] { return lane_run(r, s); });
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "lane engine");
+        e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "lane engine");
+        for (int c = 0; c < ctx->dc.ncase; c++)
+            if (res_host[c].status != PF_OK)
+                return fail(ctx, pf_status(res_host[c].status), "case %d: status %d after %d iterations",
+                            c, res_host[c].status, res_host[c].iters);
+        return PF_OK;
+    }
     const int cl = fdpf_cluster_size(ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin,
                                      std::max(ctx->dm[0].n, ctx->dm[1].n));
     cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
         return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, w.A[0], w.A[1],
                            w.fstatus[0][prec], w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef,
-                           w.vec, w.bmax, w.res, ctx->smem_optin, cl, s);
+                           w.iv, w.vec, w.bmax, w.res, ctx->smem_optin, cl, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
     e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,

@@ -122,6 +122,26 @@ struct DevCases {
     double *Psp = nullptr, *Qsp = nullptr; // [ncase][nbus]
 };
 
+// Cases in lane groups of 32 for the lockstep batched engine (gbpf_batch.cu).
+// State arrays are [bus][ncp] (lane fastest), solve vectors [group][nbus][32].
+struct LaneSet {
+    int ngroups = 0, ncp = 0, nown = 0;
+    int *gcase = nullptr;    // [ncp] case of each lane, -1 = empty lane
+    int *ginst = nullptr;    // [ncp] factor instance of each lane (0 for empty lanes)
+    int *gshared = nullptr;  // [ngroups] 1: all lanes use instance 0
+    int *gown = nullptr;     // [ngroups] index among own-factor groups, -1 if shared
+    int *owngroup = nullptr; // [nown] group of each own-factor group
+    double *vm = nullptr, *va = nullptr, *cs = nullptr, *sn = nullptr, *iv = nullptr;
+    double *e = nullptr, *f = nullptr, *psp = nullptr, *qsp = nullptr;  // [nbus][ncp]
+    double *maxmis = nullptr, *lastmis = nullptr;                       // [ncp]
+    int *active = nullptr, *status = nullptr, *iters = nullptr, *irs = nullptr;  // [ncp]
+    int *nactive = nullptr;
+    void *X = nullptr;       // [ngroups][nbus][32] in the solve precision
+    double *b = nullptr, *x64 = nullptr;  // [ngroups][nbus][32]
+    void *LF0 = nullptr, *LF1 = nullptr;  // [nown][stride][32] interleaved own factors
+    int prec = -1;
+};
+
 struct Workspace {
     // factor storage per matrix and precision: [ninst][stride]
     double *A[2] = {nullptr, nullptr};       // assembled values (FP64), per instance
@@ -134,6 +154,7 @@ struct Workspace {
     double *ef = nullptr;     // [ncase][4*nbus] e, f, cos(theta), sin(theta)
     double *vec = nullptr;    // [ncase][3*nbus] rhs, refined FP64 solution, FP32 work vector
     double *bmax = nullptr;   // [ncase][16] per-CTA mismatch maxima and solve flag
+    double *iv = nullptr;     // [ncase][nbus] 1 / V
     int *cstatus = nullptr;   // [ncase] run status
     pf_case_result *res = nullptr; // [ncase]
     int ncase_alloc = 0;
@@ -144,6 +165,7 @@ struct Workspace {
     int *jfstat[2] = {nullptr, nullptr};
     bool jfactored[2] = {false, false};
     double *xg6 = nullptr;    // [ncase][6*nbus] Newton right-hand side, refined x, FP32 work
+    LaneSet lanes;
 };
 
 }  // namespace gbpf
@@ -200,8 +222,8 @@ cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
                         const void *F0, const void *F1, const double *A0, const double *A1,
                         const int *fstat0, const int *fstat1, const pf_run_opts &o, double *vm,
-                        double *va, double *ef, double *xg, double *bmax, pf_case_result *res,
-                        size_t smem_optin, int cluster, cudaStream_t s);
+                        double *va, double *ef, double *iv, double *xg, double *bmax,
+                        pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s);
 int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int nmax);
 
 // One launch of the Newton-Raphson kernel (adjoint = false) or of the
@@ -226,6 +248,24 @@ struct NrLaunch {
 };
 cudaError_t launch_nr(const NrLaunch &L, cudaStream_t s);
 int nr_cluster_size(const DevMat &m, int ncase, int num_sms, int prec, size_t smem_optin);
+struct LaneRun {
+    DevNet dn;
+    DevCases dc;
+    DevMat m0, m1;
+    LaneSet L;
+    const void *F0 = nullptr, *F1 = nullptr;
+    const int *fs0 = nullptr, *fs1 = nullptr;
+    const double *A0 = nullptr, *A1 = nullptr;
+    pf_run_opts o{};
+    int prec = PF_FP64;
+    double *vm = nullptr, *va = nullptr;
+    pf_case_result *res = nullptr;
+    int use_graph = 1;
+    size_t smem_optin = 0;
+};
+cudaError_t lane_run(const LaneRun &r, cudaStream_t s);
+int lane_width(int nmax, int prec, size_t smem_optin);
+
 cudaError_t launch_objective(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
                              double *ef, double *J, double *gva, double *gvm, cudaStream_t s);
 

@@ -291,6 +291,7 @@ struct RunArgs {
     unsigned spin;
     double *vm, *va;
     double *ef;    // [ncase][4 nbus]: e, f, cos(theta), sin(theta)
+    double *iv;    // [ncase][nbus]: 1 / V
     double *xg;    // [ncase][3 nbus]: right-hand side / solution, refined FP64 x, FP32 work
     double *bmax;  // [ncase][16]: per-CTA mismatch maxima, [15] = solve status
     pf_case_result *res;
@@ -333,7 +334,7 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
         if (dP != dP || dQ != dQ) l = __longlong_as_double(0x7ff8000000000000ll);
         mx = nan_max(mx, l);
         const int k = nob[i];
-        if (k >= 0) xg[k] = (which == 0 ? dP : dQ) / vm[i];
+        if (k >= 0) xg[k] = (which == 0 ? dP : dQ) * a.iv[(long long)c * nbus + i];
     }
     mx = block_max(mx, red);
     if (threadIdx.x == 0) a.bmax[(long long)c * 16 + rank] = mx;
@@ -433,6 +434,7 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
     else if (a.fs1[inst] != PF_OK) status = a.fs1[inst];
     int iters = 0;
     double mis = INFINITY;
+    double *iv = a.iv + (long long)c * nbus;
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         if (a.flat) {
             const int t = dn.btype[i];
@@ -440,11 +442,22 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
             va[i] = (t == PF_BUS_SLACK) ? dn.va0[i] : 0.0;
         }
         sincos(va[i], &sn[i], &cs[i]);
+        iv[i] = 1.0 / vm[i];
     }
     cluster_sync<C>();
+    // cos/sin of the angles are rotated by each step (small_sincos) rather than
+    // re-evaluated; before a convergence decision they are recomputed exactly
+    // and the mismatch re-checked, so the decision is taken at the exact state
+    bool rotated = false;
+    auto exact_check = [&](int which) {
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) sincos(va[i], &sn[i], &cs[i]);
+        rotated = false;
+        return cluster_mismatch<C>(a, c, rank, which, red);
+    };
     if (status == PF_ERR_NOT_CONVERGED) {
         for (int it = 0; it < a.max_iter; it++) {
             mis = cluster_mismatch<C>(a, c, rank, 0, red);
+            if (mis <= a.tol && rotated) mis = exact_check(0);
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
@@ -456,12 +469,23 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
             for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
                 const int k = a.m0.new_of_bus[i];
                 if (k >= 0) {
-                    va[i] += xg[k];
-                    sincos(va[i], &sn[i], &cs[i]);
+                    const double d = xg[k];
+                    va[i] += d;
+                    if (fabs(d) <= kRotMax) {
+                        double sd, cd;
+                        small_sincos(d, &sd, &cd);
+                        const double c0 = cs[i], s0 = sn[i];
+                        cs[i] = c0 * cd - s0 * sd;
+                        sn[i] = s0 * cd + c0 * sd;
+                    } else {
+                        sincos(va[i], &sn[i], &cs[i]);
+                    }
                 }
             }
+            rotated = true;
             iters++;
             mis = cluster_mismatch<C>(a, c, rank, 1, red);
+            if (mis <= a.tol && rotated) mis = exact_check(1);
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
@@ -472,12 +496,15 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
             if (*flag != 0.0) { status = PF_ERR_TIMEOUT; break; }
             for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
                 const int k = a.m1.new_of_bus[i];
-                if (k >= 0) vm[i] += xg[k];
+                if (k >= 0) {
+                    vm[i] += xg[k];
+                    iv[i] = 1.0 / vm[i];
+                }
             }
             iters++;
         }
         if (status == PF_ERR_NOT_CONVERGED) {
-            mis = cluster_mismatch<C>(a, c, rank, 0, red);
+            mis = exact_check(0);
             if (mis <= a.tol) status = PF_OK;
         }
     }
@@ -645,9 +672,10 @@ int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int n
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
                         const void *F0, const void *F1, const double *A0, const double *A1,
                         const int *fstat0, const int *fstat1, const pf_run_opts &o, double *vm,
-                        double *va, double *ef, double *xg, double *bmax, pf_case_result *res,
-                        size_t smem_optin, int cluster, cudaStream_t s) {
+                        double *va, double *ef, double *iv, double *xg, double *bmax,
+                        pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s) {
     RunArgs a;
+    a.iv = iv;
     a.A0 = A0;
     a.A1 = A1;
     a.ir_max = o.ir_max;
@@ -688,3 +716,24 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
 }
 
 }  // namespace gbpf
+
+// Self-test hook of small_sincos: s[i], c[i] for x[i] (|x| <= 0.2), so tests
+// can compare it with the CUDA math library's sincos on the device.
+namespace {
+__global__ void k_small_sincos(const double *x, double *s, double *c, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) gbpf::small_sincos(x[i], s + i, c + i);
+}
+__global__ void k_ref_sincos(const double *x, double *s, double *c, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) sincos(x[i], s + i, c + i);
+}
+}  // namespace
+
+extern "C" int gbpf_selftest_small_sincos(const double *x_dev, double *s_dev, double *c_dev,
+                                          double *s_ref_dev, double *c_ref_dev, int n) {
+    if (n < 1) return 1;
+    k_small_sincos<<<(n + 255) / 256, 256>>>(x_dev, s_dev, c_dev, n);
+    k_ref_sincos<<<(n + 255) / 256, 256>>>(x_dev, s_ref_dev, c_ref_dev, n);
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
+}

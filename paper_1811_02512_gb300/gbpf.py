@@ -50,7 +50,8 @@ class pf_symbolic_info(C.Structure):
 class pf_run_opts(C.Structure):
     _fields_ = [("method", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("max_iter", C.c_int32), ("ir_max", C.c_int32), ("ir_tol", C.c_double),
-                ("ir_abs", C.c_double), ("flat_start", C.c_int32), ("spin_limit", C.c_int32)]
+                ("ir_abs", C.c_double), ("flat_start", C.c_int32), ("spin_limit", C.c_int32),
+                ("engine", C.c_int32)]
 
 
 class pf_case_result(C.Structure):
@@ -204,12 +205,15 @@ def pf_mismatch(ctx, vm_dev, va_dev, dp_dev, dq_dev, maxmis_dev, ncase, stream=N
                                    _ptr(maxmis_dev), int(ncase), _stream(stream)), "pf_mismatch")
 
 
+PF_ENGINE_AUTO, PF_ENGINE_BLOCK, PF_ENGINE_LANES = 0, 1, 2
+
+
 def run_opts(method=PF_FDPF, precision=PF_FP64, tol=1e-8, max_iter=None, ir_max=5, ir_tol=1e-10,
-             ir_abs=0.0, flat_start=1, spin_limit=0):
+             ir_abs=0.0, flat_start=1, spin_limit=0, engine=PF_ENGINE_AUTO):
     if max_iter is None:
         max_iter = 200 if method == PF_FDPF else 20
     return pf_run_opts(method, precision, tol, max_iter, ir_max, ir_tol, ir_abs, flat_start,
-                       spin_limit)
+                       spin_limit, engine)
 
 
 def pf_run_to_tol(ctx, opts, vm_dev, va_dev, ncase, stream=None, check=True):

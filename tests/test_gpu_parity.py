@@ -264,3 +264,68 @@ def test_fp32_batched_cases_refined(oracle):
         assert np.max(np.abs(vm[c] - vm0)) <= 1e-8, c
         assert np.max(np.abs(va[c] - va0)) <= 1e-8, c
     g.close()
+
+
+def test_small_angle_rotation_series_vs_cuda_sincos():
+    """The Maclaurin sin/cos used to rotate cached cos/sin by a step agree with
+    the CUDA math library's sincos to within 2 ulp on |x| <= 0.2."""
+    import ctypes as C
+    L = gbpf.load()
+    x = torch.linspace(-0.2, 0.2, 200001, dtype=torch.float64, device=DEV)
+    s, c, sr, cr = (torch.empty_like(x) for _ in range(4))
+    p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    assert L.gbpf_selftest_small_sincos(p(x), p(s), p(c), p(sr), p(cr), C.c_int(x.numel())) == 0
+    ulp_s = torch.abs(s - sr) / torch.clamp(torch.abs(sr), min=1e-300) / 2.0 ** -52
+    ulp_c = torch.abs(c - cr) / torch.abs(cr) / 2.0 ** -52
+    nz = torch.abs(x) > 1e-300
+    assert ulp_s[nz].max().item() <= 2.0
+    assert ulp_c.max().item() <= 2.0
+
+
+@pytest.mark.parametrize("precision", [gbpf.PF_FP64, gbpf.PF_FP32])
+def test_lane_engine_batched_vs_oracle(oracle, precision):
+    """Lockstep lane engine (groups of 32 cases, graph-replayed half-iterations):
+    load and outage cases, partly filled groups, voltages against the oracle."""
+    base = gridgen.config(0)
+    sc = gridgen.scenarios(base, n_load=7, n_outage=6, seed=41)
+    g = _grid(base, sc.ncase, sc.load_scale, sc.outage)
+    vm = torch.zeros((sc.ncase, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, precision, tol=1e-11, max_iter=300,
+                         engine=gbpf.PF_ENGINE_LANES)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+    assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    vm, va = vm.cpu().numpy(), va.cpu().numpy()
+    for c in range(sc.ncase):
+        cc = gridgen.apply_scenario(base, sc, c)
+        rc, vm0, va0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+        assert rc == oracle.OK
+        assert np.max(np.abs(vm[c] - vm0)) <= 1e-8, c
+        assert np.max(np.abs(va[c] - va0)) <= 1e-8, c
+    g.close()
+
+
+def test_lane_engine_10k_batch_sampled(oracle):
+    """64 cases of the 10,000-bus grid (32 load, 32 outage) in FP32 with FP64
+    mismatch and refinement; 6 sampled cases against the oracle, and the same
+    batch on the block-per-case engine."""
+    base = gridgen.config(1)
+    sc = gridgen.scenarios(base, n_load=32, n_outage=32, seed=43)
+    g = _grid(base, sc.ncase, sc.load_scale, sc.outage)
+    out = {}
+    for eng in (gbpf.PF_ENGINE_LANES, gbpf.PF_ENGINE_BLOCK):
+        vm = torch.zeros((sc.ncase, base.n), dtype=torch.float64, device=DEV)
+        va = torch.zeros_like(vm)
+        opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP32, tol=1e-11, max_iter=300, engine=eng)
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+        assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+        out[eng] = (vm.cpu().numpy(), va.cpu().numpy())
+    a, b = out[gbpf.PF_ENGINE_LANES], out[gbpf.PF_ENGINE_BLOCK]
+    assert np.max(np.abs(a[0] - b[0])) <= 1e-8 and np.max(np.abs(a[1] - b[1])) <= 1e-8
+    for c in (0, 5, 31, 32, 40, 63):
+        cc = gridgen.apply_scenario(base, sc, c)
+        rc, vm0, va0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+        assert rc == oracle.OK
+        assert np.max(np.abs(a[0][c] - vm0)) <= 1e-8, c
+        assert np.max(np.abs(a[1][c] - va0)) <= 1e-8, c
+    g.close()
