@@ -255,7 +255,46 @@ __device__ __forceinline__ void piece_rows(const int *h, const unsigned char *ba
     const T *Dv = h[10] >= 0 ? reinterpret_cast<const T *>(base + h[10]) : nullptr;
     const int r0 = h[0], r1 = h[1], p_lo = h[3], i_lo = h[4], v_lo = h[5], d_lo = h[11];
     const int lane = threadIdx.x & 31;
-    if (mode == 0) {
+    if (mode == 4) {
+        // scatter over the tail rows (NB = 1): slot rows [e0/32, e1/32) of the
+        // tail levels r0..r1-1; a lane applies x_i -= l x_j for its own rows i
+        // Within a level the sources are never targets, so a batch of slots
+        // loads its indices, values and source entries first; a lane's slots
+        // are sorted by target, so consecutive updates of one row accumulate
+        // in a register and the row is read and written once per batch.
+        const int k0 = h[2] >> 5, k1 = h[16] >> 5;
+        X *xt = x + h[14];
+        for (int lv = r0; lv < r1; lv++) {
+            const int ka = max(P[lv - p_lo], k0), kb = min(P[lv + 1 - p_lo], k1);
+            for (int k = ka; k < kb; k += 4) {
+                int pk[4];
+                X v[4], xs[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int sl = (k + u) * 32 + lane;
+                    pk[u] = k + u < kb ? I[sl - i_lo] : -1;
+                    v[u] = pk[u] >= 0 ? X(Vv[sl - v_lo]) : X(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) xs[u] = pk[u] >= 0 ? xt[pk[u] >> 16] : X(0);
+                int cur = -1;
+                X acc = X(0);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (pk[u] < 0) continue;
+                    const int tg = pk[u] & 0xffff;
+                    if (tg != cur) {
+                        if (cur >= 0) xt[cur] = acc;
+                        cur = tg;
+                        acc = xt[tg];
+                    }
+                    acc -= v[u] * xs[u];
+                }
+                if (cur >= 0) xt[cur] = acc;
+            }
+            __syncwarp();
+        }
+    } else if (mode == 0 || mode == 5 || mode == 6) {
         for (int r = r0 + first; r < r1; r += stride) {
             Vec<X, NB> acc;
 #pragma unroll
@@ -313,32 +352,58 @@ __device__ __forceinline__ void piece_rows(const int *h, const unsigned char *ba
     }
 }
 
+// Arrays staged for the pieces of one sweep: modes 0-3 read (ptr, idx, val,
+// dinv, lvl_ptr); mode 4 the scatter schedule (ptr4 slot-row offsets, idx4
+// slots, val4 slot values); mode 5 the tail rows' entries below the tail
+// (ptr5, idx5, val5); mode 6 only the inverse diagonal (ptr6: zeros).
+template <class T>
+struct SweepSrc {
+    const int *ptr, *idx;
+    const T *val, *dinv;
+    const int *lvl_ptr;
+    const int *ptr4, *idx4;
+    const T *val4;
+    const int *ptr5, *idx5;
+    const T *val5;
+    const int *ptr6;
+};
+
+template <class T, int NB>
+__device__ __forceinline__ void issue_piece(Ring *R, unsigned char *stages, int st, const Piece &pc,
+                                            const SweepSrc<T> &S) {
+    if (pc.mode == 4)
+        ring_issue<T, NB>(R, stages, st, pc, S.ptr4, S.idx4, S.val4, nullptr, nullptr);
+    else if (pc.mode == 5)
+        ring_issue<T, NB>(R, stages, st, pc, S.ptr5, S.idx5, S.val5, nullptr, nullptr);
+    else if (pc.mode == 6)
+        ring_issue<T, NB>(R, stages, st, pc, S.ptr6, nullptr, nullptr, S.dinv, nullptr);
+    else
+        ring_issue<T, NB>(R, stages, st, pc, S.ptr, S.idx, S.val, S.dinv, S.lvl_ptr);
+}
+
 // One substitution sweep: for every piece in order, every row r of the piece
 // gets x_r -= sum_e val_e x_{idx_e} (NB x NB blocks, optionally transposed,
 // with the inverse diagonal applied first when given).  Pieces of the same
 // level are independent.  Block-wide pieces end with a block barrier that
-// also releases their stage; runs of narrow levels (mode 2) are consumed by
-// warp 0 alone with warp barriers while the other warps wait at the end of
+// also releases their stage; runs of single-warp pieces (modes 2-4) are
+// consumed by warp 0 alone with warp barriers while the other warps wait at the end of
 // the run.  Returns false if a wait gave up (then no copy is left in flight).
 template <class T, class X, int NB, bool TRANS>
 __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces, int np,
-                             const int *ptr, const int *idx, const T *val, const T *dinv,
-                             const int *lvl_ptr, X *x, unsigned spin) {
+                             const SweepSrc<T> &S, X *x, unsigned spin) {
     const unsigned g0 = R->gcount;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     Piece next{};     // thread 0: descriptor of the next piece to issue, loaded ahead
     int issued = 0;   // thread 0: pieces issued so far in this sweep
     if (threadIdx.x == 0) {
         const int pre = np < kStages ? np : kStages;
-        for (int j = 0; j < pre; j++)
-            ring_issue<T, NB>(R, stages, int((g0 + j) % kStages), pieces[j], ptr, idx, val, dinv,
-                              lvl_ptr);
+        for (int j = 0; j < pre; j++) issue_piece<T, NB>(R, stages, int((g0 + j) % kStages), pieces[j], S);
         issued = pre;
         if (kStages < np) next = pieces[kStages];
     }
     auto issue_after = [&](int j) {  // stage of piece j is free: refill it with j + kStages
         if (j + kStages < np) {
-            ring_issue<T, NB>(R, stages, int((g0 + j) % kStages), next, ptr, idx, val, dinv, lvl_ptr);
+            issue_piece<T, NB>(R, stages, int((g0 + j) % kStages), next, S);
             issued = j + kStages + 1;
             if (j + kStages + 1 < np) next = pieces[j + kStages + 1];
         }
@@ -351,7 +416,7 @@ __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces
         if (!mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin)) atomicExch(&R->err, 1);
         const int *h = R->hdr[st];
         const int mode = h[8];
-        if (mode >= 2) {
+        if (mode >= 2 && mode <= 4) {
             const int jr = h[9];
             __syncthreads();  // every warp has read this header before warp 0 refills the stage
             if (warp == 0) {
@@ -374,8 +439,8 @@ __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces
         } else {
             if (!R->err)
                 piece_rows<T, X, NB, TRANS>(h, stages + size_t(st) * kStageBytes, x, mode,
-                                            mode == 0 ? int(threadIdx.x) : warp,
-                                            mode == 0 ? int(blockDim.x) : nwarps);
+                                            mode == 1 ? warp : int(threadIdx.x),
+                                            mode == 1 ? nwarps : int(blockDim.x));
             __syncthreads();
             if (R->err) { ok = false; break; }
             if (threadIdx.x == 0) issue_after(j);
@@ -395,13 +460,37 @@ __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces
     return ok;
 }
 
+// The same sweep over pieces of modes 0-3 only.
+template <class T, class X, int NB, bool TRANS>
+__device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces, int np,
+                             const int *ptr, const int *idx, const T *val, const T *dinv,
+                             const int *lvl_ptr, X *x, unsigned spin) {
+    const SweepSrc<T> S{ptr, idx, val, dinv, lvl_ptr, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, nullptr, nullptr};
+    return staged_sweep<T, X, NB, TRANS>(R, stages, pieces, np, S, x, spin);
+}
+
 // L D L^T x = x in place (level order): forward substitution over the rows
 // of L (levels ascending), then back substitution over the columns of L
 // (levels descending) with the normalisation y = z / d of Eq. 4 fused in as
 // a multiplication by the stored inverse diagonal.
+//
+// With the gathered tail values tv of the instance (and a matrix with a
+// scatter tail), the sweeps run the tail levels as a one-warp scatter: the
+// forward sweep ends with the tail rows' entries below the tail and the
+// forward scatter; the backward sweep starts with the tail rows' inverse
+// diagonal and the backward scatter.
 template <class T, class X>
 __device__ bool block_solve(Ring *R, unsigned char *stages, const DevMat &m, const T *F, X *x,
-                            unsigned spin) {
+                            unsigned spin, const T *tv = nullptr) {
+    if (tv && m.npf2 > 0) {
+        const SweepSrc<T> Sf{m.Fp, m.Fc, F + m.offLr, nullptr, m.lvl_ptr, m.SKf, m.SIf, tv + m.tv_f,
+                             m.PPp, m.PPc, tv + m.tv_p, m.ZP};
+        if (!staged_sweep<T, X, 1, false>(R, stages, m.pf2, m.npf2, Sf, x, spin)) return false;
+        const SweepSrc<T> Sb{m.Cp, m.Cr, F + m.offLc, F + m.offDi, m.lvl_ptr, m.SKb, m.SIb,
+                             tv + m.tv_b, nullptr, nullptr, nullptr, m.ZP};
+        return staged_sweep<T, X, 1, false>(R, stages, m.pb2, m.npb2, Sb, x, spin);
+    }
     if (!staged_sweep<T, X, 1, false>(R, stages, m.pf, m.npf, m.Fp, m.Fc, F + m.offLr, nullptr,
                                       m.lvl_ptr, x, spin))
         return false;

@@ -155,6 +155,147 @@ std::vector<int> min_degree_order(int n, std::vector<std::vector<int>> adj) {
 // ---------------------------------------------------------------- analysis
 
 
+// Scatter tail of one matrix (see DevMat): the schedules, the gathered value
+// layout and the sweeps' piece lists that use them (pf2, pb2).  Without a
+// tail (no narrow level at the top, or more than 32767 tail rows) the lists
+// stay empty and the sweeps use pf, pb.
+template <class MakePieces, class RunEnds>
+pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &set_run_ends) {
+    const int n = H.n;
+    int lt = H.nlev;
+    while (lt > 0 && H.lvl_ptr[lt] - H.lvl_ptr[lt - 1] <= kNarrowRows) lt--;
+    const int t0 = H.lvl_ptr[lt], nt = n - t0;
+    H.pf2.clear();
+    H.pb2.clear();
+    H.t0 = t0;
+    H.nt = 0;
+    H.ntl = 0;
+    if (nt <= 0 || nt > 32767) return PF_OK;  // 16-bit row indices in the slots
+    H.nt = nt;
+    H.ntl = H.nlev - lt;
+    struct Upd {
+        int tgt, src, pos;
+    };
+    auto schedule = [&](bool fwd, std::vector<int> &SK, std::vector<int> &SI, std::vector<int> &spos) {
+        SK.assign(1, 0);
+        SI.clear();
+        spos.clear();
+        std::vector<std::vector<Upd>> lane(32);
+        for (int li = 0; li < H.ntl; li++) {
+            const int l = fwd ? lt + li : H.nlev - 1 - li;
+            for (auto &v : lane) v.clear();
+            for (int j = H.lvl_ptr[l]; j < H.lvl_ptr[l + 1]; j++) {
+                if (fwd) {
+                    for (int p = H.Cp[j]; p < H.Cp[j + 1]; p++) {
+                        const int i = H.Cr[p];
+                        lane[(i - t0) & 31].push_back({i - t0, j - t0, H.offLc + p});
+                    }
+                } else {
+                    for (int q = H.Fp[j]; q < H.Fp[j + 1]; q++) {
+                        const int i = H.Fc[q];
+                        if (i >= t0) lane[(i - t0) & 31].push_back({i - t0, j - t0, H.offLr + q});
+                    }
+                }
+            }
+            size_t K = 0;
+            for (auto &v : lane) {
+                std::sort(v.begin(), v.end(), [](const Upd &a, const Upd &b) {
+                    return a.tgt != b.tgt ? a.tgt < b.tgt : a.src < b.src;
+                });
+                K = std::max(K, v.size());
+            }
+            for (size_t k = 0; k < K; k++)
+                for (int ln = 0; ln < 32; ln++) {
+                    if (k < lane[ln].size()) {
+                        const Upd &u = lane[ln][k];
+                        SI.push_back(u.tgt | (u.src << 16));
+                        spos.push_back(u.pos);
+                    } else {
+                        SI.push_back(-1);
+                        spos.push_back(-1);
+                    }
+                }
+            SK.push_back(SK.back() + int(K));
+        }
+    };
+    std::vector<int> posf, posb;
+    schedule(true, H.SKf, H.SIf, posf);
+    schedule(false, H.SKb, H.SIb, posb);
+    // tail rows' entries in columns below t0 (a prefix of each CSR row)
+    H.PPp.assign(n + 1, 0);
+    H.PPc.clear();
+    std::vector<int> posp;
+    for (int r = 0; r < n; r++) {
+        if (r >= t0)
+            for (int q = H.Fp[r]; q < H.Fp[r + 1] && H.Fc[q] < t0; q++) {
+                H.PPc.push_back(H.Fc[q]);
+                posp.push_back(H.offLr + q);
+            }
+        H.PPp[r + 1] = int(H.PPc.size());
+    }
+    auto pad32 = [](int64_t v) { return int((v + 31) / 32 * 32); };
+    H.tv_f = 0;
+    H.tv_b = pad32(int64_t(posf.size()));
+    H.tv_p = H.tv_b + pad32(int64_t(posb.size()));
+    H.tv_stride = H.tv_p + pad32(int64_t(posp.size()));
+    H.TVsrc.assign(std::max(1, H.tv_stride), -1);
+    std::copy(posf.begin(), posf.end(), H.TVsrc.begin() + H.tv_f);
+    std::copy(posb.begin(), posb.end(), H.TVsrc.begin() + H.tv_b);
+    std::copy(posp.begin(), posp.end(), H.TVsrc.begin() + H.tv_p);
+    const int budget = kPieceBytes - kPieceSlack;
+    // scatter pieces: consecutive slot rows, 4 bytes of index and up to 8 of
+    // value per slot, plus the slot-row offsets of the levels touched
+    auto scatter_pieces = [&](const std::vector<int> &SK, std::vector<Piece> &out) {
+        const int per = (budget - 64) / (32 * 12) - 1;  // slot rows per piece
+        const int nrows = SK.back();
+        int lv = 0;
+        for (int k0 = 0; k0 < nrows;) {
+            const int k1 = std::min(nrows, k0 + per);
+            while (SK[lv + 1] <= k0) lv++;
+            int lv1 = lv;
+            while (lv1 < H.ntl && SK[lv1] < k1) lv1++;
+            if (4 * (lv1 - lv + 8) + 12 * 32 * (k1 - k0) > budget)
+                return fail(ctx, PF_ERR_ARG, "internal: scatter piece exceeds a stage");
+            out.push_back(Piece{lv, lv1, k0 * 32, k1 * 32, 4, 0, t0, 0});
+            k0 = k1;
+        }
+        return PF_OK;
+    };
+    // block-wide pieces over the tail rows: ptr gives the entries of a row
+    auto row_pieces = [&](const std::vector<int> &ptr, int mode, int ebytes, int rbytes,
+                          std::vector<Piece> &out) {
+        int r = t0;
+        while (r < n) {
+            const int r0 = r;
+            int64_t bytes = 16;
+            while (r < n) {
+                const int64_t rb = rbytes + int64_t(ebytes) * (ptr[r + 1] - ptr[r]);
+                if (16 + rb > budget) return fail(ctx, PF_ERR_ARG, "internal: tail row exceeds a stage");
+                if (r > r0 && bytes + rb > budget) break;
+                bytes += rb;
+                r++;
+            }
+            out.push_back(Piece{r0, r, ptr[r0], ptr[r], mode, 0, 0, 0});
+        }
+        return PF_OK;
+    };
+    std::vector<Piece> wide;
+    // forward: wide levels, entries below the tail, scatter over the tail
+    TRY(make_pieces(H.Fp, true, 12, 12, wide, lt));
+    H.pf2 = wide;
+    TRY(row_pieces(H.PPp, 5, 12, 12, H.pf2));
+    TRY(scatter_pieces(H.SKf, H.pf2));
+    // backward: inverse diagonal of the tail rows, scatter, wide levels
+    std::vector<int> zp(n + 1, 0);
+    TRY(row_pieces(zp, 6, 12, 12, H.pb2));
+    TRY(scatter_pieces(H.SKb, H.pb2));
+    TRY(make_pieces(H.Cp, false, 12, 12, wide, lt));
+    H.pb2.insert(H.pb2.end(), wide.begin(), wide.end());
+    set_run_ends(H.pf2);
+    set_run_ends(H.pb2);
+    return PF_OK;
+}
+
 // Device layout of one analysed matrix in level order (see DevMat).
 pf_status build_layout(pf_ctx *ctx, HostMat &H) {
     const int n = H.n;
@@ -248,6 +389,27 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
             }
         }
     }
+    // gather lists of the same updates, grouped by target, in CSR-entry order
+    H.gp.assign(size_t(n) + nnz + 1, 0);
+    for (int c = 0; c < n; c++)
+        for (int q = H.Fp[c]; q < H.Fp[c + 1]; q++) {
+            const int k = H.Fc[q];
+            for (int o = H.uoff[q], p = H.Fpos[q]; p < H.Cp[k + 1]; p++, o++)
+                H.gp[size_t(H.Cp[c]) + c + H.umap[o] + 1]++;
+        }
+    for (size_t g = 0; g + 1 < H.gp.size(); g++) H.gp[g + 1] += H.gp[g];
+    H.gl.assign(std::max<int64_t>(1, H.nupd), int4{0, 0, 0, 0});
+    {
+        std::vector<int> f(H.gp.begin(), H.gp.end() - 1);
+        for (int c = 0; c < n; c++)
+            for (int q = H.Fp[c]; q < H.Fp[c + 1]; q++) {
+                const int k = H.Fc[q];
+                for (int o = H.uoff[q], p = H.Fpos[q]; p < H.Cp[k + 1]; p++, o++)
+                    H.gl[f[size_t(H.Cp[c]) + c + H.umap[o]]++] = int4{p, H.Fpos[q], k, 0};
+            }
+    }
+    H.Cpos.assign(std::max<int64_t>(1, nnz), 0);
+    for (int64_t q = 0; q < nnz; q++) H.Cpos[H.Fpos[q]] = int(q);
     auto pad32 = [](int64_t v) { return int((v + 31) / 32 * 32); };
     H.offDi = pad32(n);
     H.offLc = H.offDi + pad32(n);
@@ -279,7 +441,7 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
     // levels, whose pointers, indices and values fit one stage; ebytes and
     // rbytes are the staged bytes per entry and per row
     auto make_pieces = [&](const std::vector<int> &ptr, bool ascending, int ebytes, int rbytes,
-                           std::vector<Piece> &out) {
+                           std::vector<Piece> &out, int nlev_used) {
         out.clear();
         const int budget = kPieceBytes - kPieceSlack;
         auto row_bytes = [&](int r) { return int64_t(rbytes) + int64_t(ebytes) * (ptr[r + 1] - ptr[r]); };
@@ -312,8 +474,8 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
             return true;
         };
         int li = 0;
-        while (li < H.nlev) {
-            int l = ascending ? li : H.nlev - 1 - li;
+        while (li < nlev_used) {
+            int l = ascending ? li : nlev_used - 1 - li;
             const int lrows = H.lvl_ptr[l + 1] - H.lvl_ptr[l];
             if (lrows <= kNarrowRows) {
                 int64_t bytes = 8 + level_bytes(l);
@@ -325,8 +487,8 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
                 // whole narrow levels, as many consecutive ones as fit
                 int lo = l, hi = l;
                 li++;
-                while (li < H.nlev) {
-                    int l2 = ascending ? li : H.nlev - 1 - li;
+                while (li < nlev_used) {
+                    int l2 = ascending ? li : nlev_used - 1 - li;
                     if (H.lvl_ptr[l2 + 1] - H.lvl_ptr[l2] > kNarrowRows) break;
                     int64_t add = level_bytes(l2);
                     if (bytes + add > budget) break;
@@ -343,12 +505,15 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
                 return fail(ctx, PF_ERR_ARG, "internal: row exceeds a stage");
             li++;
         }
-        // end of every run of single-warp pieces
-        int np = int(out.size());
-        for (int j = np - 1; j >= 0; j--)
-            if (out[j].mode >= 2)
-                out[j].run_end = (j + 1 < np && out[j + 1].mode >= 2) ? out[j + 1].run_end : j + 1;
         return PF_OK;
+    };
+    // end of every run of single-warp pieces (modes 2, 3, 4)
+    auto set_run_ends = [](std::vector<Piece> &out) {
+        auto single = [](int mode) { return mode >= 2 && mode <= 4; };
+        const int np = int(out.size());
+        for (int j = np - 1; j >= 0; j--)
+            if (single(out[j].mode))
+                out[j].run_end = (j + 1 < np && single(out[j + 1].mode)) ? out[j + 1].run_end : j + 1;
     };
     // off-diagonal pattern of A by row, both triangles, fill excluded
     {
@@ -371,13 +536,18 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
             H.Ap[r + 1] = int(H.Aj.size());
         }
     }
-    TRY(make_pieces(H.Fp, true, 12, 12, H.pf));
-    TRY(make_pieces(H.Cp, false, 12, 12, H.pb));
+    TRY(make_pieces(H.Fp, true, 12, 12, H.pf, H.nlev));
+    TRY(make_pieces(H.Cp, false, 12, 12, H.pb, H.nlev));
+    set_run_ends(H.pf);
+    set_run_ends(H.pb);
+    TRY(build_tail(ctx, H, make_pieces, set_run_ends));
     // Newton-Raphson Jacobian on the same pattern: 2 x 2 blocks (36 staged
     // bytes per FP64 block entry and per row), transposed slot sources, and
     // the block value layout [D | Dinv | Lc | Uc | Lr | Ur]
-    TRY(make_pieces(H.Fp, true, 36, 36, H.pfJ));
-    TRY(make_pieces(H.Cp, false, 36, 36, H.pbJ));
+    TRY(make_pieces(H.Fp, true, 36, 36, H.pfJ, H.nlev));
+    TRY(make_pieces(H.Cp, false, 36, 36, H.pbJ, H.nlev));
+    set_run_ends(H.pfJ);
+    set_run_ends(H.pbJ);
     H.srcT.assign(nnz, -1);
     for (int c = 0; c < n; c++)
         for (int p = H.Cp[c]; p < H.Cp[c + 1]; p++) H.srcT[p] = ypos(ctx, H.bus_new[c], H.bus_new[H.Cr[p]]);
@@ -502,6 +672,9 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
     TRY(upload_padded(ctx, &D.Fpos, H.Fpos));
     TRY(upload_padded(ctx, &D.uoff, H.uoff));
     TRY(upload_padded(ctx, &D.umap, H.umap));
+    TRY(upload_padded(ctx, &D.gp, H.gp));
+    TRY(upload(ctx, &D.gl, H.gl.data(), H.gl.size()));
+    TRY(upload_padded(ctx, &D.Cpos, H.Cpos));
     TRY(upload_padded(ctx, &D.src, H.src));
     TRY(upload_padded(ctx, &D.br_slot, H.br_slot));
     TRY(upload_padded(ctx, &D.Ap, H.Ap));
@@ -516,6 +689,27 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
     D.jstride = H.jstride;
     TRY(upload(ctx, &D.pf, H.pf.data(), H.pf.size()));
     TRY(upload(ctx, &D.pb, H.pb.data(), H.pb.size()));
+    D.t0 = H.t0;
+    D.nt = H.nt;
+    D.ntl = H.ntl;
+    D.npf2 = int(H.pf2.size());
+    D.npb2 = int(H.pb2.size());
+    if (H.nt > 0) {
+        TRY(upload(ctx, &D.pf2, H.pf2.data(), H.pf2.size()));
+        TRY(upload(ctx, &D.pb2, H.pb2.data(), H.pb2.size()));
+        TRY(upload_padded(ctx, &D.SKf, H.SKf));
+        TRY(upload_padded(ctx, &D.SIf, H.SIf));
+        TRY(upload_padded(ctx, &D.SKb, H.SKb));
+        TRY(upload_padded(ctx, &D.SIb, H.SIb));
+        TRY(upload_padded(ctx, &D.PPp, H.PPp));
+        TRY(upload_padded(ctx, &D.PPc, H.PPc));
+        TRY(upload_padded(ctx, &D.ZP, std::vector<int>(H.n + 1, 0)));
+        TRY(upload_padded(ctx, &D.TVsrc, H.TVsrc));
+        D.tv_f = H.tv_f;
+        D.tv_b = H.tv_b;
+        D.tv_p = H.tv_p;
+        D.tv_stride = H.tv_stride;
+    }
     return PF_OK;
 }
 
@@ -599,6 +793,20 @@ pf_status ensure_factor_storage(pf_ctx *ctx, int which, int prec) {
     if (prec == PF_FP64 && !w.F64[which]) TRY(dalloc(ctx, &w.F64[which], sz));
     if (prec == PF_FP32 && !w.F32[which]) TRY(dalloc(ctx, &w.F32[which], sz));
     if (!w.fstatus[which][prec]) TRY(dalloc(ctx, &w.fstatus[which][prec], size_t(ctx->dc.ninst)));
+    if (m.npf2 > 0 && !w.TV[which][prec]) {
+        const size_t nt = size_t(ctx->dc.ninst) * size_t(m.tv_stride);
+        if (prec == PF_FP64) TRY(dalloc(ctx, reinterpret_cast<double **>(&w.TV[which][prec]), nt));
+        else TRY(dalloc(ctx, reinterpret_cast<float **>(&w.TV[which][prec]), nt));
+    }
+    if (!w.fdone[which]) {
+        const size_t nd = size_t(ctx->dc.ninst) * size_t(std::max(1, m.n));
+        TRY(dalloc(ctx, &w.fdone[which], nd));
+        TRY(dalloc(ctx, &w.fsync[which], size_t(2)));
+        TRY(dalloc(ctx, &w.famax[which], size_t(ctx->dc.ninst)));
+        cudaError_t e = cudaMemset(w.fdone[which], 0, nd * sizeof(unsigned));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "factor flags");
+        w.fepoch[which] = 0;
+    }
     return PF_OK;
 }
 
@@ -608,6 +816,13 @@ void free_case_storage(pf_ctx *ctx) {
         dfree(ctx, w.A[a]); w.A[a] = nullptr;
         dfree(ctx, w.F64[a]); w.F64[a] = nullptr;
         dfree(ctx, w.F32[a]); w.F32[a] = nullptr;
+        dfree(ctx, w.fdone[a]); w.fdone[a] = nullptr;
+        for (int b = 0; b < 2; b++) {
+            dfree(ctx, w.TV[a][b]);
+            w.TV[a][b] = nullptr;
+        }
+        dfree(ctx, w.fsync[a]); w.fsync[a] = nullptr;
+        dfree(ctx, w.famax[a]); w.famax[a] = nullptr;
         for (int b = 0; b < 2; b++) {
             dfree(ctx, w.fstatus[a][b]);
             w.fstatus[a][b] = nullptr;
@@ -661,10 +876,25 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble launch");
     void *F = prec == PF_FP64 ? (void *)w.F64[which] : (void *)w.F32[which];
-    e = counted(ctx, PF_K_FACTOR, 1, s, [&] {
-        return launch_factor(m, prec, w.A[which], F, ctx->dc.ninst, w.fstatus[which][prec], s);
+    FactorSync fs;
+    fs.done = w.fdone[which];
+    fs.sync = w.fsync[which];
+    fs.amax = w.famax[which];
+    if (++w.fepoch[which] == 0u) {  // wrapped: clear the flags, restart at 1
+        cudaError_t z = cudaMemsetAsync(w.fdone[which], 0,
+                                        size_t(ctx->dc.ninst) * size_t(std::max(1, m.n)) * sizeof(unsigned), s);
+        if (z != cudaSuccess) return cuda_fail(ctx, z, "factor flags");
+        w.fepoch[which] = 1u;
+    }
+    fs.epoch = w.fepoch[which];
+    fs.spin = 0;
+    fs.nsm = ctx->num_sms;
+    e = counted(ctx, PF_K_FACTOR, 2, s, [&] {
+        return launch_factor(m, prec, w.A[which], F, ctx->dc.ninst, w.fstatus[which][prec], fs, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "factor launch");
+    e = launch_tail_values(m, prec, F, w.TV[which][prec], ctx->dc.ninst, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tail values launch");
     w.factored[which][prec] = true;
     return PF_OK;
 }
@@ -1041,8 +1271,8 @@ pf_status pf_solve(pf_ctx *ctx, int32_t which, int32_t precision, int32_t transp
                                          : (const void *)ctx->ws.F32[which];
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = counted(ctx, PF_K_SOLVE, 1, s, [&] {
-        return launch_solve(ctx->dm[which], precision, F, ctx->dc.inst, rhs_inout_dev, ncase,
-                            ctx->ws.vec, ctx->ws.cstatus, ctx->smem_optin, s);
+        return launch_solve(ctx->dm[which], precision, F, ctx->ws.TV[which][precision], ctx->dc.inst,
+                            rhs_inout_dev, ncase, ctx->ws.vec, ctx->ws.cstatus, ctx->smem_optin, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve launch");
     return PF_OK;
@@ -1142,7 +1372,8 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
     const int cl = fdpf_cluster_size(ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin,
                                      std::max(ctx->dm[0].n, ctx->dm[1].n));
     cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
-        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, w.A[0], w.A[1],
+        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, w.TV[0][prec], w.TV[1][prec],
+                           w.A[0], w.A[1],
                            w.fstatus[0][prec], w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef,
                            w.iv, w.vec, w.bmax, w.res, ctx->smem_optin, cl, s);
     });

@@ -23,8 +23,13 @@ constexpr int kPieceSlack = 128;
 // the CSR (CSC) arrays, all in level order.  mode: 0 one thread per row,
 // 1 one warp per row (whole block), 2 warp 0 alone over rows of the narrow
 // levels l0..l1, 3 warp 0 alone over part [e0, e1) of the single row r0 (a
-// row too long for one stage); run_end: for modes 2 and 3, the first piece
-// after the run of single-warp pieces.  Mode 0/1/3 pieces lie in one level.
+// row too long for one stage); run_end: for modes 2, 3 and 4, the first
+// piece after the run of single-warp pieces.  Mode 0/1/3 pieces lie in one
+// level.  The sweeps with a scatter tail add: 4 warp 0 alone over the slot
+// rows [e0/32, e1/32) of the tail levels r0..r1-1 of a scatter schedule
+// (l0 = first tail row); 5 one thread per row over the entries of the tail
+// rows in columns below the tail; 6 one thread per row, inverse diagonal
+// only.
 struct Piece {
     int r0, r1, e0, e1;
     int mode, run_end, l0, l1;
@@ -55,9 +60,33 @@ struct DevMat {
     int *Fpos = nullptr;       // [nnz] CSR entry -> CSC position
     int *uoff = nullptr;       // [nnz+1] CSR entry (c, k) -> start of its update map
     int *umap = nullptr;       // [nupd] target in column c: 0 diagonal, 1 + t = t-th entry
+    // gather form of the same updates: target g = Cp[c] + c + t of column c
+    // (t = 0 diagonal, 1 + t the t-th entry) receives sum over its list
+    // gl[gp[g] .. gp[g+1]) of L[x] * L[y] * D[z] (x, y CSC positions, z column)
+    int *gp = nullptr;         // [n + nnz + 1]
+    int4 *gl = nullptr;        // [nupd] {x: L(i,k), y: L(c,k), z: k, w: 0}
+    int *Cpos = nullptr;       // [nnz] CSC position -> CSR position
     int *src = nullptr;        // [n + nnz] Ybus position of every D and Lc slot, -1 = fill
     int *br_slot = nullptr;    // [3 nbranch] value slots (D f, D t, Lc (f,t)) or -1
     Piece *pf = nullptr, *pb = nullptr;  // forward (levels ascending), backward (descending)
+    // Scatter tail: rows [t0, n) are the longest run of narrow levels at the
+    // top of the elimination tree.  Their substitution runs on one warp as a
+    // right-looking scatter: once x_j is final, x_i -= l x_j is applied to
+    // every tail row i it reaches, each row owned by lane (i - t0) mod 32,
+    // from a schedule of 32-slot rows per level.  SK: slot-row offsets per
+    // tail level in sweep order; SI: (i - t0) | (j - t0) << 16 per slot, -1
+    // empty; a lane's slots of one level are sorted by row.  The values of the slots (forward: L by column,
+    // backward: L by row) and of the tail rows' entries in columns below t0
+    // (PPp/PPc, by row) are gathered per instance after each factorisation
+    // into [tv_f: forward slots | tv_b: backward slots | tv_p: entries below
+    // t0] from the value slots TVsrc (-1: zero).
+    int t0 = 0, nt = 0, ntl = 0;
+    int npf2 = 0, npb2 = 0;
+    Piece *pf2 = nullptr, *pb2 = nullptr;
+    int *SKf = nullptr, *SIf = nullptr, *SKb = nullptr, *SIb = nullptr;
+    int *PPp = nullptr, *PPc = nullptr, *ZP = nullptr;
+    int tv_f = 0, tv_b = 0, tv_p = 0, tv_stride = 0;
+    int *TVsrc = nullptr;
     int *Ap = nullptr, *Aj = nullptr, *Apos = nullptr;  // off-diagonal A (no fill), by row:
                                                        // column and value slot of each entry
     // Newton-Raphson Jacobian (2 x 2 blocks on the same pattern, B' only)
@@ -86,7 +115,8 @@ struct HostMat {
     std::vector<int> new_of_step;  // step -> level order
     std::vector<int> bus_new, local_new, new_of_bus;
     std::vector<int> lvl_ptr;
-    std::vector<int> Cp, Cr, Fp, Fc, Fpos, uoff, umap, src, br_slot;
+    std::vector<int> Cp, Cr, Fp, Fc, Fpos, uoff, umap, src, br_slot, gp, Cpos;
+    std::vector<int4> gl;
     std::vector<int> csc_of_steppos;  // step-numbered CSC position -> level-order CSC position
     std::vector<int> Ap, Aj, Apos;    // off-diagonal pattern of A by row (both triangles, no fill)
     std::vector<Piece> pfJ, pbJ;
@@ -94,6 +124,10 @@ struct HostMat {
     int jD = 0, jDi = 0, jLc = 0, jUc = 0, jLr = 0, jUr = 0, jstride = 0;
     std::vector<Piece> pf, pb;
     int offDi = 0, offLc = 0, offLr = 0, stride = 0;
+    int t0 = 0, nt = 0, ntl = 0;
+    std::vector<Piece> pf2, pb2;
+    std::vector<int> SKf, SIf, SKb, SIb, PPp, PPc, TVsrc;
+    int tv_f = 0, tv_b = 0, tv_p = 0, tv_stride = 0;
 };
 
 // Device arrays of the network and of the case batch.
@@ -150,6 +184,14 @@ struct Workspace {
     int *fstatus[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}; // [mat][prec] per instance
     bool factored[2][2] = {{false, false}, {false, false}};
     int ninst_alloc = 0;
+    // dependency-driven factor: per matrix, column-done flags [ninst][n]
+    // (a column is done when its flag equals the epoch of the current
+    // factorisation), the column counter and abort flag, diagonal maxima
+    unsigned *fdone[2] = {nullptr, nullptr};
+    unsigned *fsync[2] = {nullptr, nullptr};  // [0] next column, [1] abort
+    double *famax[2] = {nullptr, nullptr};    // [ninst]
+    unsigned fepoch[2] = {0u, 0u};
+    void *TV[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mat][prec] tail values
     // per-case scratch
     double *ef = nullptr;     // [ncase][4*nbus] e, f, cos(theta), sin(theta)
     double *vec = nullptr;    // [ncase][3*nbus] rhs, refined FP64 solution, FP32 work vector
@@ -211,16 +253,28 @@ cudaError_t launch_case_spec(const DevNet &dn, const DevCases &dc, const double 
                              cudaStream_t s);
 cudaError_t launch_assemble_slots(const DevNet &dn, const DevCases &dc, const DevMat &m, int which,
                                   double *A, cudaStream_t s);
+struct FactorSync {
+    unsigned *done = nullptr;  // [ninst][n]
+    unsigned *sync = nullptr;  // [0] column counter, [1] abort flag
+    double *amax = nullptr;    // [ninst]
+    unsigned epoch = 0;
+    unsigned spin = 0;
+    int nsm = 0;
+    int mode = 0;              // 0 auto, 1 dependency-driven, 2 block per instance
+};
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
-                          int *fstatus, cudaStream_t s);
-cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const int *inst_of_case,
-                         double *rhs, int ncase, void *gvec, int *status, size_t smem_optin,
-                         cudaStream_t s);
+                          int *fstatus, const FactorSync &fs, cudaStream_t s);
+cudaError_t launch_tail_values(const DevMat &m, int prec, const void *F, void *TV, int ninst,
+                               cudaStream_t s);
+cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const void *TV,
+                         const int *inst_of_case, double *rhs, int ncase, void *gvec, int *status,
+                         size_t smem_optin, cudaStream_t s);
 cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
                             double *dp, double *dq, double *maxmis, double *ef, int ncase,
                             cudaStream_t s);
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
-                        const void *F0, const void *F1, const double *A0, const double *A1,
+                        const void *F0, const void *F1, const void *TV0, const void *TV1,
+                        const double *A0, const double *A1,
                         const int *fstat0, const int *fstat1, const pf_run_opts &o, double *vm,
                         double *va, double *ef, double *iv, double *xg, double *bmax,
                         pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s);

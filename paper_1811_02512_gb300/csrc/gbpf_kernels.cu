@@ -114,10 +114,175 @@ __global__ void k_assemble_slots(DevNet dn, DevCases dc, DevMat m, int which, do
 
 // ------------------------------------------------------------ Section III.B
 
-// Numeric factor A = L D L^T of one instance per block, left-looking, level by
-// level (FactorizeGraphA).  Column c of a level is owned by one warp: it
-// gathers the updates a_ic -= l_ik d_k l_ck from every descendant column k in
-// row c of L (ascending k, so the order of operations is fixed), then
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Diagonal maxima of the assembled matrices (the pivot tolerance), status
+// reset, and reset of the column counter and abort flag of k_factor_dep.
+__global__ void k_factor_prep(DevMat m, const double *A, int *fstatus, FactorSync fs) {
+    __shared__ double red[33];
+    const int inst = blockIdx.x;
+    const double *a = A + (long long)inst * m.stride;
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < m.n; j += blockDim.x) mx = fmax(mx, fabs(a[j]));
+    mx = block_max(mx, red);
+    if (threadIdx.x == 0) {
+        fs.amax[inst] = mx;
+        fstatus[inst] = PF_OK;
+        if (inst == 0) {
+            fs.sync[0] = 0u;
+            fs.sync[1] = 0u;
+        }
+    }
+}
+
+constexpr int kDepThreads = 256;
+constexpr int kDepTargets = 8;   // targets per lane: columns of up to 255 entries
+constexpr int kDepChunk = 512;   // update terms staged per warp and pass
+
+// Numeric factor A = L D L^T (Section III.B, left-looking), driven by the
+// elimination tree's dependencies instead of level barriers, for every
+// instance at once over the whole GPU.  Warps take (column, instance) pairs
+// from a global counter in level order; a warp first waits until every
+// column k of row c of L is done (its flag holds this factorisation's
+// epoch), then evaluates the update terms l_ik d_k l_ck of column c (a
+// contiguous range of the gather lists, grouped by target) with the whole
+// warp into shared memory, and sums each target's terms with a lane per
+// target:
+//   d_c = a_cc - sum_k l_ck^2 d_k,   l_ic = (a_ic - sum_k l_ik d_k l_ck) / d_c.
+// It writes the column to the column- and row-ordered copies of L and
+// publishes its own flag.  Columns are handed out in level order, so every
+// column a warp waits for was taken earlier by a running warp: the waits
+// always end (each is bounded all the same; a wait that gives up raises the
+// abort flag, which ends the others).  The order of operations of every
+// entry is fixed, so results are deterministic.  Factor entries of other
+// columns are read through L2 (__ldcg): other SMs wrote them in this launch.
+template <class T>
+__global__ void __launch_bounds__(kDepThreads)
+    k_factor_dep(DevMat m, const double *A, T *F, int *fstatus, int ninst, FactorSync fs) {
+    __shared__ T terms_all[kDepThreads / 32][kDepChunk];
+    const int lane = threadIdx.x & 31;
+    T *terms = terms_all[threadIdx.x >> 5];
+    const unsigned total = unsigned(m.n) * unsigned(ninst);
+    const unsigned spin = fs.spin ? fs.spin : kDefaultSpin;
+    for (;;) {
+        unsigned idx = 0;
+        if (lane == 0) idx = atomicAdd(fs.sync, 1u);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= total) break;
+        const int c = int(idx / unsigned(ninst)), inst = int(idx % unsigned(ninst));
+        const double *a = A + (long long)inst * m.stride;
+        T *v = F + (long long)inst * m.stride;
+        T *Lc = v + m.offLc;
+        unsigned *done = fs.done + (long long)inst * m.n;
+        bool ok = true;
+        for (int q = m.Fp[c] + lane; q < m.Fp[c + 1] && ok; q += 32) {
+            const unsigned *f = done + m.Fc[q];
+            unsigned it = 0;
+            while (ld_acquire_u32(f) != fs.epoch) {
+                if (++it > spin || *reinterpret_cast<volatile unsigned *>(fs.sync + 1)) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(fs.sync + 1, 1u);
+                atomicCAS(fstatus + inst, PF_OK, PF_ERR_TIMEOUT);
+            }
+            continue;
+        }
+        const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0, tb = c0 + c;
+        int g_lo[kDepTargets], g_hi[kDepTargets];
+        T part[kDepTargets];
+#pragma unroll
+        for (int j = 0; j < kDepTargets; j++) {
+            const int t = lane + 32 * j;
+            g_lo[j] = t <= cnt ? m.gp[tb + t] : 0;
+            g_hi[j] = t <= cnt ? m.gp[tb + t + 1] : 0;
+            part[j] = T(0);
+        }
+        const int gb = m.gp[tb], ge = m.gp[tb + cnt + 1];
+        for (int cb = gb; cb < ge; cb += kDepChunk) {
+            const int ce = min(ge, cb + kDepChunk);
+            // terms of this pass, four per lane in flight
+            for (int g0 = cb + lane; g0 < ce; g0 += 128) {
+                int4 e[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (g0 + 32 * u < ce) e[u] = __ldg(m.gl + g0 + 32 * u);
+                T x[4], y[4], z[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (g0 + 32 * u < ce) {
+                        x[u] = __ldcg(Lc + e[u].x);
+                        y[u] = __ldcg(Lc + e[u].y);
+                        z[u] = __ldcg(v + e[u].z);
+                    }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (g0 + 32 * u < ce) terms[g0 + 32 * u - cb] = x[u] * (y[u] * z[u]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < kDepTargets; j++) {
+                const int lo = max(g_lo[j], cb), hi = min(g_hi[j], ce);
+                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+                int g = lo;
+                for (; g + 4 <= hi; g += 4) {
+                    s0 += terms[g - cb];
+                    s1 += terms[g + 1 - cb];
+                    s2 += terms[g + 2 - cb];
+                    s3 += terms[g + 3 - cb];
+                }
+                for (; g < hi; g++) s0 += terms[g - cb];
+                part[j] += (s0 + s1) + (s2 + s3);
+            }
+            __syncwarp();
+        }
+        T val[kDepTargets];
+#pragma unroll
+        for (int j = 0; j < kDepTargets; j++) {
+            const int t = lane + 32 * j;
+            val[j] = t <= cnt ? T(t == 0 ? a[c] : a[m.offLc + c0 + t - 1]) - part[j] : T(0);
+        }
+        const T d = __shfl_sync(0xffffffffu, val[0], 0);
+        if (lane == 0) {
+            v[c] = d;
+            v[m.offDi + c] = T(1) / d;
+            const double dd = double(d);
+            if (!isfinite(dd)) atomicCAS(fstatus + inst, PF_OK, PF_ERR_NONFINITE);
+            else if (fabs(dd) <= 1e-14 * fs.amax[inst]) atomicCAS(fstatus + inst, PF_OK, PF_ERR_SINGULAR);
+        }
+#pragma unroll
+        for (int j = 0; j < kDepTargets; j++) {
+            const int t = lane + 32 * j;
+            if (t >= 1 && t <= cnt) {
+                const T l = val[j] / d;
+                Lc[c0 + t - 1] = l;
+                v[m.offLr + m.Cpos[c0 + t - 1]] = l;
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_u32(done + c, fs.epoch);
+    }
+}
+
+// Block-per-instance form of the same factor (columns of more than 255
+// entries): level by level, column c of a level owned by one warp, which
+// scatters the updates a_ic -= l_ik d_k l_ck from every descendant column k
+// in row c of L (ascending k, so the order of operations is fixed), then
 // normalises l_ic = a_ic / d_c.  Columns of one level never write the same
 // entry, so no atomics are needed and results are deterministic.  Finally the
 // column-ordered L is copied to the row-ordered Lr used by the forward sweep.
@@ -214,8 +379,8 @@ __global__ void __launch_bounds__(kFactorThreads)
 
 template <class T>
 __global__ void __launch_bounds__(kSolveThreads)
-    k_solve(DevMat m, const T *F, const int *inst_of_case, double *rhs, T *gvec, int use_smem,
-            int *status) {
+    k_solve(DevMat m, const T *F, const T *TV, const int *inst_of_case, double *rhs, T *gvec,
+            int use_smem, int *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Ring R;
     const int c = blockIdx.x;
@@ -228,7 +393,8 @@ __global__ void __launch_bounds__(kSolveThreads)
     ring_init(&R);
     for (int k = threadIdx.x; k < n; k += blockDim.x) x[k] = T(r[m.local[k]]);
     __syncthreads();
-    const bool ok = block_solve<T, T>(&R, stages, m, v, x, kDefaultSpin);
+    const T *tv = TV ? TV + (long long)inst_of_case[c] * m.tv_stride : nullptr;
+    const bool ok = block_solve<T, T>(&R, stages, m, v, x, kDefaultSpin, tv);
     for (int k = threadIdx.x; k < n; k += blockDim.x) r[m.local[k]] = double(x[k]);
     if (threadIdx.x == 0 && !ok) atomicExch(status, PF_ERR_TIMEOUT);
 }
@@ -281,6 +447,7 @@ struct RunArgs {
     DevCases dc;
     DevMat m0, m1;  // B', B''
     const void *F0, *F1;
+    const void *TV0, *TV1;  // gathered tail values per instance (or null)
     const double *A0, *A1;  // FP64 assembled values of B', B'' (refinement residuals)
     const int *fs0, *fs1;
     double tol;
@@ -352,8 +519,8 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
 // (the refined x lives in the second half of the exchange vector).
 template <class T>
 __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T *xs,
-                            const DevMat &m, const T *F, const double *A, int c, double *red,
-                            int &ir_steps) {
+                            const DevMat &m, const T *F, const T *tv, const double *A, int c,
+                            double *red, int &ir_steps) {
     const int nbus = a.dn.nbus;
     double *xg = a.xg + (long long)c * 3 * nbus;
     bool ok = true;
@@ -361,10 +528,10 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
         if (xs) {
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) xs[r] = T(xg[r]);
             __syncthreads();
-            ok = block_solve<T, T>(R, stages, m, F, xs, a.spin);
+            ok = block_solve<T, T>(R, stages, m, F, xs, a.spin, tv);
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) xg[r] = double(xs[r]);
         } else {
-            ok = block_solve<T, double>(R, stages, m, F, xg, a.spin);
+            ok = block_solve<T, double>(R, stages, m, F, xg, a.spin, tv);
         }
     } else {
         double *x64 = xg + nbus;
@@ -376,7 +543,7 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
         }
         bn = block_max(bn, red);
         for (int k = 0;; k++) {
-            ok = block_solve<T, T>(R, stages, m, F, xv, a.spin);
+            ok = block_solve<T, T>(R, stages, m, F, xv, a.spin, tv);
             if (!ok) break;
             for (int r = threadIdx.x; r < m.n; r += blockDim.x)
                 x64[r] = (k == 0 ? 0.0 : x64[r]) + double(xv[r]);
@@ -404,7 +571,7 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
 // With C = 1 every case is one independent block (batches); with C > 1 one
 // case spreads its FP64 mismatch over C SMs (single large cases).
 template <class T, int C>
-__global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
+__global__ void __launch_bounds__(kRunThreads, C == 1 ? 2 : 1) k_fdpf(RunArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[33];
     __shared__ Ring R;
@@ -424,6 +591,8 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
     double *flag = a.bmax + (long long)c * 16 + 15;
     const T *F0 = static_cast<const T *>(a.F0) + (long long)inst * a.m0.stride;
     const T *F1 = static_cast<const T *>(a.F1) + (long long)inst * a.m1.stride;
+    const T *TV0 = a.TV0 ? static_cast<const T *>(a.TV0) + (long long)inst * a.m0.tv_stride : nullptr;
+    const T *TV1 = a.TV1 ? static_cast<const T *>(a.TV1) + (long long)inst * a.m1.tv_stride : nullptr;
     const double *A0 = a.A0 + (long long)inst * a.m0.stride;
     const double *A1 = a.A1 + (long long)inst * a.m1.stride;
     int ir_steps = 0;
@@ -461,7 +630,7 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, A0, c, red, ir_steps);
+                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, TV0, A0, c, red, ir_steps);
                 if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
             }
             cluster_sync<C>();
@@ -489,7 +658,7 @@ __global__ void __launch_bounds__(kRunThreads) k_fdpf(RunArgs a) {
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, A1, c, red, ir_steps);
+                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, TV1, A1, c, red, ir_steps);
                 if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
             }
             cluster_sync<C>();
@@ -575,8 +744,51 @@ cudaError_t launch_assemble_slots(const DevNet &dn, const DevCases &dc, const De
     return cudaGetLastError();
 }
 
+// Values of the scatter-tail schedules and of the tail rows' entries below
+// the tail, gathered from the factor of every instance (zero for empty slots).
+template <class T>
+__global__ void k_tail_values(DevMat m, const T *F, T *TV, int ninst) {
+    const long long total = (long long)ninst * m.tv_stride;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long inst = idx / m.tv_stride;
+        const int sl = int(idx - inst * m.tv_stride);
+        const int src = m.TVsrc[sl];
+        TV[idx] = src >= 0 ? F[inst * m.stride + src] : T(0);
+    }
+}
+
+cudaError_t launch_tail_values(const DevMat &m, int prec, const void *F, void *TV, int ninst,
+                               cudaStream_t s) {
+    if (m.npf2 == 0 || !TV) return cudaSuccess;
+    const long long total = (long long)ninst * m.tv_stride;
+    if (prec == PF_FP64)
+        k_tail_values<double><<<grid_for(total, 256), 256, 0, s>>>(m, static_cast<const double *>(F),
+                                                                   static_cast<double *>(TV), ninst);
+    else
+        k_tail_values<float><<<grid_for(total, 256), 256, 0, s>>>(m, static_cast<const float *>(F),
+                                                                  static_cast<float *>(TV), ninst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
-                          int *fstatus, cudaStream_t s) {
+                          int *fstatus, const FactorSync &fs, cudaStream_t s) {
+    const long long total = (long long)m.n * ninst;
+    const bool dep = fs.mode == 1 || (fs.mode == 0 && ninst < fs.nsm / 2);
+    if (dep && m.max_col + 1 <= 32 * kDepTargets && total < (1ll << 31) && fs.done) {
+        k_factor_prep<<<ninst, 256, 0, s>>>(m, A, fstatus, fs);
+        const int per_sm = 2;  // resident 256-thread blocks per SM (register-limited)
+        long long blocks = (total + kDepThreads / 32 - 1) / (kDepThreads / 32);
+        if (blocks > (long long)fs.nsm * per_sm) blocks = (long long)fs.nsm * per_sm;
+        if (blocks < 1) blocks = 1;
+        if (prec == PF_FP64)
+            k_factor_dep<double><<<int(blocks), kDepThreads, 0, s>>>(m, A, static_cast<double *>(F),
+                                                                      fstatus, ninst, fs);
+        else
+            k_factor_dep<float><<<int(blocks), kDepThreads, 0, s>>>(m, A, static_cast<float *>(F),
+                                                                     fstatus, ninst, fs);
+        return cudaGetLastError();
+    }
     const int threads = kFactorThreads;
     if (prec == PF_FP64) {
         size_t smem = sizeof(double) * size_t(m.max_col + 1) * (threads / 32 + 1);
@@ -592,9 +804,10 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const int *inst_of_case,
-                         double *rhs, int ncase, void *gvec, int *status, size_t smem_optin,
-                         cudaStream_t s) {
+cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const void *TV,
+                         const int *inst_of_case, double *rhs, int ncase, void *gvec, int *status,
+                         size_t smem_optin, cudaStream_t s) {
+    if (m.npf2 == 0) TV = nullptr;
     // The solve vector lives in shared memory after the staging ring when it
     // fits, else in the per-case global scratch gvec ([ncase][2 nbus] doubles).
     const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
@@ -605,12 +818,14 @@ cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const int *in
     if (prec == PF_FP64) {
         cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         k_solve<double><<<ncase, kSolveThreads, smem, s>>>(m, static_cast<const double *>(F),
+                                                            static_cast<const double *>(TV),
                                                             inst_of_case, rhs,
                                                             static_cast<double *>(gvec), use_smem,
                                                             status);
     } else {
         cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         k_solve<float><<<ncase, kSolveThreads, smem, s>>>(m, static_cast<const float *>(F),
+                                                          static_cast<const float *>(TV),
                                                           inst_of_case, rhs,
                                                           static_cast<float *>(gvec), use_smem,
                                                           status);
@@ -670,11 +885,14 @@ int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int n
 }
 
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
-                        const void *F0, const void *F1, const double *A0, const double *A1,
-                        const int *fstat0, const int *fstat1, const pf_run_opts &o, double *vm,
-                        double *va, double *ef, double *iv, double *xg, double *bmax,
-                        pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s) {
+                        const void *F0, const void *F1, const void *TV0, const void *TV1,
+                        const double *A0, const double *A1, const int *fstat0, const int *fstat1,
+                        const pf_run_opts &o, double *vm, double *va, double *ef, double *iv,
+                        double *xg, double *bmax, pf_case_result *res, size_t smem_optin,
+                        int cluster, cudaStream_t s) {
     RunArgs a;
+    a.TV0 = m[0].npf2 > 0 ? TV0 : nullptr;
+    a.TV1 = m[1].npf2 > 0 ? TV1 : nullptr;
     a.iv = iv;
     a.A0 = A0;
     a.A1 = A1;

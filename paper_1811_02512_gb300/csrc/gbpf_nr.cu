@@ -422,7 +422,7 @@ __device__ bool nr_solve(const NrArgs &a, Ring *R, unsigned char *stages, T *xs,
 // Newton-Raphson power flow of one case per cluster of C CTAs: mismatch and
 // Jacobian assembly spread over the cluster, factor and solve in CTA 0.
 template <class T, int C>
-__global__ void __launch_bounds__(512) k_nr(NrArgs a) {
+__global__ void __launch_bounds__(512, C == 1 ? 2 : 1) k_nr(NrArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[33];
     __shared__ Ring R;
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(512) k_nr(NrArgs a) {
 // Newton step, i.e. of an earlier state) refined in FP64 against the exact
 // J(x) assembled here; dJ/dP_i = y_P(i), dJ/dQ_i = y_Q(i) (PQ), 0 elsewhere.
 template <class T, int C>
-__global__ void __launch_bounds__(512) k_adjoint(NrArgs a, int factor_now) {
+__global__ void __launch_bounds__(512, C == 1 ? 2 : 1) k_adjoint(NrArgs a, int factor_now) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[33];
     __shared__ Ring R;
