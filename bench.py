@@ -13,6 +13,10 @@ Workloads (seeded synthetic grids, see paper_1811_02512_gb300/gridgen.py):
   plain10k   one 10,000-bus pruned-Delaunay grid, FP64 (default)
   batch10k   the same topology with 1,024 cases (512 load scenarios, 512
              single-branch outages) in one launch
+  pack256    256 grids of 2,000 to 80,000 buses (log-uniform), each with its
+             own ordering and levels, in one packed launch (pf_pack_run, FP32
+             factor + FP64 refinement); the same grids solved one after the
+             other by the plain FP64 path are reported beside it
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbpf|reference]
 """
@@ -43,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbpf", choices=["gbpf", "reference"])
-    ap.add_argument("--workload", default="plain10k", choices=["plain10k", "batch10k"])
+    ap.add_argument("--workload", default="plain10k", choices=["plain10k", "batch10k", "pack256"])
+    ap.add_argument("--ngrid", type=int, default=256, help="pack256: number of grids (first n)")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
     ap.add_argument("--method", default="fdpf", choices=["fdpf", "nr"])
     ap.add_argument("--engine", default="auto", choices=["auto", "block", "lanes"])
@@ -230,6 +235,159 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ uneven multi-grid batch
+
+def _pack_case(g):
+    from paper_1811_02512_gb300 import gridgen
+    n, seed = gridgen.config4_sizes()[g]
+    return gridgen.with_loading_factor(gridgen.delaunay_raw(n, seed, name=f"multigrid{g}"))
+
+
+def pack_cases(ngrid):
+    """The first ngrid grids of the uneven batch, generated in spawned processes."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(ngrid, os.cpu_count() or 1)) as pool:
+        return pool.map(_pack_case, range(ngrid))
+
+
+def run_pack(args, dev, local, world, rank):
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1811_02512_gb300 import gbpf
+    t0 = time.perf_counter()
+    cases = pack_cases(args.ngrid)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        grids = list(ex.map(gbpf.Grid, cases))
+    analyze_s = time.perf_counter() - t0
+    for g in grids:
+        g.set_cases(1)
+    pk = gbpf.Pack(grids)
+    tot = int(pk.offset[-1])
+    prec_name = args.precision or "fp32"
+    prec = gbpf.PF_FP64 if prec_name == "fp64" else gbpf.PF_FP32
+    opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=TOL, max_iter=200)
+    vm = torch.zeros(tot, dtype=torch.float64, device=dev)
+    va = torch.zeros_like(vm)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(int(2.5 * 129e6) // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        st, res = pk.run(opts, vm, va, stream=stream)
+    torch.cuda.synchronize()
+    for g in grids:
+        gbpf.pf_set_profiling(g.ctx, True)
+        for k in range(7):
+            gbpf.pf_get_profile(g.ctx, k, reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, res = pk.run(opts, vm, va, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    other_ms, launches = 0.0, 0
+    for g in grids:
+        for k in range(7):
+            n, ms = gbpf.pf_get_profile(g.ctx, k, reset=True)
+            other_ms += ms
+            launches += n
+        gbpf.pf_set_profiling(g.ctx, False)
+    launches += args.steps  # the packed iteration launch of each step
+    converged = int(np.sum(res["status"] == gbpf.PF_OK))
+    value = converged * args.steps * world / (total_ms / 1e3)
+    run_ms = max(1e-6, (total_ms - other_ms) / args.steps)
+    # the same grids one after the other by the plain FP64 path
+    seq_opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=TOL, max_iter=200)
+    vms = [torch.zeros((1, g.nbus), dtype=torch.float64, device=dev) for g in grids]
+    vas = [torch.zeros_like(v) for v in vms]
+    for g, v, w in zip(grids, vms, vas):
+        gbpf.pf_run_to_tol(g.ctx, seq_opts, v, w, 1, stream=stream)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    seq_ok = 0
+    for g, v, w in zip(grids, vms, vas):
+        st1, r1 = gbpf.pf_run_to_tol(g.ctx, seq_opts, v, w, 1, stream=stream)
+        seq_ok += int(r1["status"][0] == gbpf.PF_OK)
+    b.record(stream)
+    b.synchronize()
+    seq_ms = a.elapsed_time(b)
+    # end to end: start state from pinned host memory, solution back
+    host_in = torch.zeros((2, tot), dtype=torch.float64).pin_memory()
+    host_out = torch.empty((2, tot), dtype=torch.float64).pin_memory()
+    e2e_opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=TOL, max_iter=200, flat_start=0)
+    pos = 0
+    for g in grids:  # flat start written on the host
+        c = g.case
+        host_in[0, pos:pos + c.n] = torch.from_numpy(np.where(c.btype == 1, 1.0, c.vset))
+        host_in[1, pos:pos + c.n] = torch.from_numpy(np.where(c.btype == 3, c.va, 0.0))
+        pos += c.n
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        vm.copy_(host_in[0], non_blocking=True)
+        va.copy_(host_in[1], non_blocking=True)
+        st, res_e = pk.run(e2e_opts, vm, va, stream=stream)
+        host_out[0].copy_(vm, non_blocking=True)
+        host_out[1].copy_(va, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te0
+    e2e_val = int(np.sum(res_e["status"] == gbpf.PF_OK)) * e2e_steps / e2e_s
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    prec_bytes = 8 if prec == gbpf.PF_FP64 else 4
+    alg = 0.0
+    for k, g in enumerate(grids):
+        per_half = algorithmic_bytes_per_half_iteration(g.info, g.nbus, g.info.nnz_ybus, prec_bytes)
+        alg += per_half * (float(res["iters"][k]) + 1.0)
+    achieved = alg / (run_ms / 1e3) / 1e9
+    sizes = [g.nbus for g in grids]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == gbpf.PF_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": "pack256", "ngrid": len(grids), "nbus_total": tot,
+                       "nbus_min": min(sizes), "nbus_max": max(sizes), "precision": prec_name,
+                       "tol_pu": TOL, "method": "fdpf",
+                       "l2": "flushed between timed steps (2.5x L2 buffer write)",
+                       "generate_s": gen_s, "analyze_s": analyze_s,
+                       "parallelism": "grids-in-blocks"},
+            "converged": converged, "iters_mean": float(np.mean(res["iters"])),
+            "gpu_launches": launches,
+            "sequential_plain_fp64": {"value": seq_ok / (seq_ms / 1e3), "unit": UNIT,
+                                      "ms": seq_ms, "converged": seq_ok},
+            "roofline": {"bound": "hbm", "kernel": "k_fdpf_pack", "achieved": achieved,
+                         "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None,
+                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                         "algorithmic_bytes_per_launch": alg, "kernel_ms_per_launch": run_ms},
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * tot * 8),
+                    "d2h_bytes_per_step": int(2 * tot * 8 + 24 * len(grids))}}
+    if rank == 0:
+        print(json.dumps(line))
+    pk.close()
+    for g in grids:
+        g.close()
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -250,6 +408,11 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_1811_02512_gb300 import gbpf
+    if args.workload == "pack256":
+        run_pack(args, dev, local, world, rank)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     base, ncase, load_scale, outage = make_workload(args.workload, args.ncase)
     prec_name = workload_precision(args.workload, args.precision)

@@ -280,6 +280,44 @@ pf_status pf_mismatch_static(int32_t nbus, const int32_t *rowptr_dev, const int3
 /* Releases the context and all its device memory.  NULL is accepted. */
 void pf_destroy(pf_ctx *ctx);
 
+/* ---------------------------------------------------------------- packs
+ * An uneven multi-grid batch: many independent grids of different sizes,
+ * each with its own ordering, elimination tree and level sets (its own
+ * context), solved by one persistent launch in which the thread blocks take
+ * the grids largest first (the batched serving pattern of the problem
+ * statement applied across grids; the paper solves one grid per call,
+ * Section III).  The pack does not own the contexts. */
+typedef struct pf_pack pf_pack;
+
+/* Creates a pack over grids[0..ngrid).  Every context must have been
+ * analysed; the pack keeps the pointers, so the contexts must outlive it.
+ * PF_ERR_ARG for ngrid < 1, a NULL or repeated context, or a factor column
+ * of more than 255 strict-lower entries (pf_symbolic_info.max_col);
+ * PF_ERR_STATE for a context not analysed.  Synchronous. */
+pf_status pf_pack_create(pf_ctx *const *grids, int32_t ngrid, pf_pack **out);
+
+/* Runs every grid of the pack to opts->tol with the fast decoupled method
+ * (opts->method must be PF_FDPF; precision, tolerance, iteration and
+ * refinement options as for pf_run_to_tol; engine is ignored).  For each
+ * grid it assembles the admittance matrix and B', B'' of its one case
+ * (pf_set_cases with ncase 1, or never called); one dependency-driven launch
+ * factorises every grid's B' and B'' (Section III.B), then one launch
+ * iterates all grids.  vm_dev / va_dev are caller-owned device arrays of
+ * sum(nbus) doubles, the grids' buses concatenated in pack order, with the
+ * start state read when opts->flat_start is 0 and the solution written;
+ * res_host[ngrid] receives each grid's outcome.  Returns PF_OK when every
+ * grid converged, else the first failing grid's status (all results are
+ * still written).  Synchronous with respect to the host; work is issued on
+ * `stream`. */
+pf_status pf_pack_run(pf_pack *pack, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                      pf_case_result *res_host, void *stream);
+
+/* Message of the last failing pack call (never NULL). */
+const char *pf_pack_last_error(const pf_pack *pack);
+
+/* Releases the pack's own device memory (not the contexts).  NULL is accepted. */
+void pf_pack_destroy(pf_pack *pack);
+
 #ifdef __cplusplus
 }
 #endif

@@ -865,9 +865,8 @@ pf_status assemble_ybus(pf_ctx *ctx, cudaStream_t s) {
     return PF_OK;
 }
 
-// Assembles B' or B'' of every instance from the current admittance matrix
-// and factorises them.
-pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
+// Assembles B' or B'' of every instance from the current admittance matrix.
+pf_status assemble_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
     TRY(ensure_factor_storage(ctx, which, prec));
     Workspace &w = ctx->ws;
     const DevMat &m = ctx->dm[which];
@@ -875,6 +874,38 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
         return launch_assemble_slots(ctx->dn, ctx->dc, m, which, w.A[which], s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble launch");
+    return PF_OK;
+}
+
+// The next factorisation of matrix `which` (one instance) as a job of a
+// packed factor launch: advances the matrix's flag epoch.
+pf_status factor_job(pf_ctx *ctx, int which, int prec, FactorJob &J, cudaStream_t s) {
+    Workspace &w = ctx->ws;
+    const DevMat &m = ctx->dm[which];
+    if (++w.fepoch[which] == 0u) {
+        cudaError_t z = cudaMemsetAsync(w.fdone[which], 0,
+                                        size_t(ctx->dc.ninst) * size_t(std::max(1, m.n)) * sizeof(unsigned), s);
+        if (z != cudaSuccess) return cuda_fail(ctx, z, "factor flags");
+        w.fepoch[which] = 1u;
+    }
+    J.m = m;
+    J.A = w.A[which];
+    J.F = prec == PF_FP64 ? (void *)w.F64[which] : (void *)w.F32[which];
+    J.TV = w.TV[which][prec];
+    J.fstatus = w.fstatus[which][prec];
+    J.done = w.fdone[which];
+    J.amax = w.famax[which];
+    J.epoch = w.fepoch[which];
+    return PF_OK;
+}
+
+// Assembles B' or B'' of every instance from the current admittance matrix
+// and factorises them.
+pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
+    TRY(assemble_matrix(ctx, which, prec, s));
+    Workspace &w = ctx->ws;
+    const DevMat &m = ctx->dm[which];
+    cudaError_t e;
     void *F = prec == PF_FP64 ? (void *)w.F64[which] : (void *)w.F32[which];
     FactorSync fs;
     fs.done = w.fdone[which];
@@ -1482,6 +1513,197 @@ pf_status pf_get_ybus(pf_ctx *ctx, int32_t *rowptr, int32_t *col, double *G, dou
         if (e != cudaSuccess) return cuda_fail(ctx, e, "get_ybus");
     }
     return PF_OK;
+}
+
+}  // extern "C"
+
+struct pf_pack {
+    std::vector<pf_ctx *> grids;
+    std::vector<int> order;       // grids by decreasing size
+    std::vector<int64_t> offset;  // first bus of each grid in the concatenated state
+    std::vector<int2> items;      // factor work items (job = 2 grid + matrix, column)
+    int2 *items_dev = nullptr;
+    gbpf::FactorJob *jobs_dev = nullptr;
+    unsigned *fsync = nullptr;
+    void *args = nullptr;
+    int *order_dev = nullptr;
+    unsigned *counter = nullptr;
+    pf_case_result *res = nullptr;
+    int device = 0, num_sms = 0;
+    size_t smem_optin = 0;
+    std::string err;
+};
+
+namespace {
+pf_status pack_fail(pf_pack *pk, pf_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (pk) pk->err = buf;
+    return st;
+}
+}  // namespace
+
+extern "C" {
+
+pf_status pf_pack_create(pf_ctx *const *grids, int32_t ngrid, pf_pack **out) {
+    if (!out) return PF_ERR_ARG;
+    *out = nullptr;
+    if (!grids || ngrid < 1) return PF_ERR_ARG;
+    auto *pk = new (std::nothrow) pf_pack();
+    if (!pk) return PF_ERR_OOM;
+    std::vector<pf_ctx *> seen;
+    int64_t off = 0;
+    for (int g = 0; g < ngrid; g++) {
+        pf_ctx *c = grids[g];
+        if (!c || std::find(seen.begin(), seen.end(), c) != seen.end()) {
+            delete pk;
+            return PF_ERR_ARG;
+        }
+        if (!c->analyzed) {
+            delete pk;
+            return PF_ERR_STATE;
+        }
+        if (c->hm[0].max_col > gbpf::kDepMaxCol || c->hm[1].max_col > gbpf::kDepMaxCol) {
+            delete pk;  // a column longer than the packed factor takes
+            return PF_ERR_ARG;
+        }
+        seen.push_back(c);
+        pk->grids.push_back(c);
+        pk->offset.push_back(off);
+        off += c->nbus;
+    }
+    pk->order.resize(size_t(ngrid));
+    for (int g = 0; g < ngrid; g++) pk->order[g] = g;
+    std::stable_sort(pk->order.begin(), pk->order.end(), [&](int a, int b) {
+        return pk->grids[a]->nbus > pk->grids[b]->nbus;
+    });
+    // factor work items: levels ascending across all matrices, so every
+    // column follows the columns it depends on
+    int maxlev = 0;
+    for (pf_ctx *c : pk->grids)
+        for (int w = 0; w < 2; w++) maxlev = std::max(maxlev, c->hm[w].nlev);
+    for (int l = 0; l < maxlev; l++)
+        for (int g = 0; g < ngrid; g++)
+            for (int w = 0; w < 2; w++) {
+                const gbpf::HostMat &H = pk->grids[g]->hm[w];
+                if (l >= H.nlev) continue;
+                for (int c = H.lvl_ptr[l]; c < H.lvl_ptr[l + 1]; c++) pk->items.push_back(int2{2 * g + w, c});
+            }
+    *out = pk;
+    return PF_OK;
+}
+
+pf_status pf_pack_run(pf_pack *pk, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                      pf_case_result *res_host, void *stream) {
+    if (!pk || !opts || !vm_dev || !va_dev || !res_host) return pack_fail(pk, PF_ERR_ARG, "null pointer");
+    if (opts->method != PF_FDPF) return pack_fail(pk, PF_ERR_ARG, "packs run the fast decoupled method");
+    if (opts->precision != PF_FP64 && opts->precision != PF_FP32)
+        return pack_fail(pk, PF_ERR_ARG, "bad precision");
+    if (!(opts->tol > 0) || opts->max_iter < 1) return pack_fail(pk, PF_ERR_ARG, "bad tol/max_iter");
+    if (opts->precision == PF_FP32 && (opts->ir_max < 0 || opts->ir_max > 100 || !(opts->ir_tol >= 0)))
+        return pack_fail(pk, PF_ERR_ARG, "bad refinement options");
+    const int ngrid = int(pk->grids.size());
+    const int prec = opts->precision;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<PackGrid> pg(static_cast<size_t>(ngrid));
+    std::vector<FactorJob> jobs(static_cast<size_t>(2 * ngrid));
+    for (int g = 0; g < ngrid; g++) {
+        pf_ctx *ctx = pk->grids[g];
+        pf_status st = ensure_cases(ctx);
+        if (st == PF_OK && ctx->dc.ncase != 1) st = fail(ctx, PF_ERR_STATE, "a packed grid has one case");
+        if (st == PF_OK) st = assemble_ybus(ctx, s);
+        if (st == PF_OK) st = assemble_matrix(ctx, PF_MAT_BP, prec, s);
+        if (st == PF_OK) st = assemble_matrix(ctx, PF_MAT_BPP, prec, s);
+        if (st == PF_OK) st = factor_job(ctx, PF_MAT_BP, prec, jobs[2 * g], s);
+        if (st == PF_OK) st = factor_job(ctx, PF_MAT_BPP, prec, jobs[2 * g + 1], s);
+        if (st != PF_OK) return pack_fail(pk, st, "grid %d: %s", g, ctx->err.c_str());
+        Workspace &w = ctx->ws;
+        PackGrid &p = pg[g];
+        p.dn = ctx->dn;
+        p.dc = ctx->dc;
+        p.m[0] = ctx->dm[0];
+        p.m[1] = ctx->dm[1];
+        p.F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
+        p.F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
+        p.TV0 = w.TV[0][prec];
+        p.TV1 = w.TV[1][prec];
+        p.A0 = w.A[0];
+        p.A1 = w.A[1];
+        p.fs0 = w.fstatus[0][prec];
+        p.fs1 = w.fstatus[1][prec];
+        p.vm = vm_dev + pk->offset[g];
+        p.va = va_dev + pk->offset[g];
+        p.ef = w.ef;
+        p.iv = w.iv;
+        p.xg = w.vec;
+        p.bmax = w.bmax;
+        p.res = nullptr;  // set below
+        if (g == 0) {
+            pk->device = ctx->device;
+            pk->num_sms = ctx->num_sms;
+            pk->smem_optin = ctx->smem_optin;
+        } else if (ctx->device != pk->device) {
+            return pack_fail(pk, PF_ERR_ARG, "grid %d is on another device", g);
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!pk->args) {
+        e = cudaMalloc(reinterpret_cast<void **>(&pk->jobs_dev), sizeof(FactorJob) * size_t(2 * ngrid));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&pk->fsync), 2 * sizeof(unsigned));
+        if (e == cudaSuccess)
+            e = cudaMalloc(reinterpret_cast<void **>(&pk->items_dev), sizeof(int2) * std::max<size_t>(1, pk->items.size()));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pk->items_dev, pk->items.data(), sizeof(int2) * pk->items.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&pk->args, run_args_bytes() * size_t(ngrid));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&pk->order_dev), sizeof(int) * size_t(ngrid));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&pk->counter), sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&pk->res), sizeof(pf_case_result) * size_t(ngrid));
+        if (e != cudaSuccess)
+            return pack_fail(pk, e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA, "pack scratch: %s",
+                             cudaGetErrorString(e));
+    }
+    for (int g = 0; g < ngrid; g++) pg[g].res = pk->res + g;
+    // every grid's B' and B'' in one factor launch
+    e = cudaMemcpyAsync(pk->jobs_dev, jobs.data(), sizeof(FactorJob) * jobs.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // jobs is released on return
+    if (e == cudaSuccess)
+        e = launch_factor_jobs(pk->jobs_dev, 2 * ngrid, pk->items_dev, unsigned(pk->items.size()), pk->fsync,
+                               prec, pk->num_sms, s);
+    if (e != cudaSuccess)
+        return pack_fail(pk, e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA, "pack factor: %s",
+                         cudaGetErrorString(e));
+    for (pf_ctx *ctx : pk->grids)
+        for (int w = 0; w < 2; w++) ctx->ws.factored[w][prec] = true;
+    e = launch_pack(pg.data(), ngrid, prec, *opts, pk->order.data(), pk->args, pk->order_dev, pk->counter,
+                    pk->smem_optin, pk->num_sms, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res_host, pk->res, sizeof(pf_case_result) * size_t(ngrid), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return pack_fail(pk, e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA, "pack run: %s",
+                         cudaGetErrorString(e));
+    for (int g = 0; g < ngrid; g++)
+        if (res_host[g].status != PF_OK)
+            return pack_fail(pk, pf_status(res_host[g].status), "grid %d: status %d after %d iterations", g,
+                             res_host[g].status, res_host[g].iters);
+    return PF_OK;
+}
+
+const char *pf_pack_last_error(const pf_pack *pk) { return pk ? pk->err.c_str() : "null pack"; }
+
+void pf_pack_destroy(pf_pack *pk) {
+    if (!pk) return;
+    cudaFree(pk->args);
+    cudaFree(pk->jobs_dev);
+    cudaFree(pk->items_dev);
+    cudaFree(pk->fsync);
+    cudaFree(pk->order_dev);
+    cudaFree(pk->counter);
+    cudaFree(pk->res);
+    delete pk;
 }
 
 void pf_destroy(pf_ctx *ctx) {

@@ -264,6 +264,25 @@ struct FactorSync {
 };
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
                           int *fstatus, const FactorSync &fs, cudaStream_t s);
+// Longest column (strict-lower entries) the dependency-driven factor takes.
+constexpr int kDepMaxCol = 255;
+// One matrix (single instance) of a packed factorisation.
+struct FactorJob {
+    DevMat m;
+    const double *A;
+    void *F;
+    void *TV;
+    int *fstatus;
+    unsigned *done;
+    double *amax;
+    unsigned epoch;
+};
+// Factorises the matrices jobs_dev[0..njob) in one dependency-driven launch
+// over the work items (job, column) of items_dev (every column after the
+// columns it depends on), then gathers their tail values.  sync_dev: the
+// column counter and abort flag.
+cudaError_t launch_factor_jobs(const FactorJob *jobs_dev, int njob, const int2 *items_dev,
+                               unsigned nitems, unsigned *sync_dev, int prec, int nsm, cudaStream_t s);
 cudaError_t launch_tail_values(const DevMat &m, int prec, const void *F, void *TV, int ninst,
                                cudaStream_t s);
 cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const void *TV,
@@ -279,6 +298,27 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         double *va, double *ef, double *iv, double *xg, double *bmax,
                         pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s);
 int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int nmax);
+
+// One grid of a pack (uneven multi-grid batch): its device network, case,
+// layout, factors and per-case scratch, with vm/va inside the pack's
+// concatenated state vectors and res inside the pack's result array.
+struct PackGrid {
+    DevNet dn;
+    DevCases dc;
+    DevMat m[2];
+    const void *F0, *F1, *TV0, *TV1;
+    const double *A0, *A1;
+    const int *fs0, *fs1;
+    double *vm, *va, *ef, *iv, *xg, *bmax;
+    pf_case_result *res;
+};
+size_t run_args_bytes();
+// Runs every grid of a pack to tolerance in one persistent launch (grids
+// taken largest first, order_host); args_dev/order_dev/counter_dev are
+// device scratch of ngrid run arguments, ngrid ints and one counter.
+cudaError_t launch_pack(const PackGrid *grids, int ngrid, int prec, const pf_run_opts &o,
+                        const int *order_host, void *args_dev, int *order_dev, unsigned *counter_dev,
+                        size_t smem_optin, int nsm, cudaStream_t s);
 
 // One launch of the Newton-Raphson kernel (adjoint = false) or of the
 // adjoint kernel (adjoint = true).

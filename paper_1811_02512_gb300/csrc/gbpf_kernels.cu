@@ -20,6 +20,8 @@
 
 #include "gbpf_device.cuh"
 
+#include <vector>
+
 namespace gbpf {
 
 namespace {
@@ -145,6 +147,7 @@ __global__ void k_factor_prep(DevMat m, const double *A, int *fstatus, FactorSyn
 
 constexpr int kDepThreads = 256;
 constexpr int kDepTargets = 8;   // targets per lane: columns of up to 255 entries
+static_assert(32 * kDepTargets == kDepMaxCol + 1, "targets per lane cover the longest column");
 constexpr int kDepChunk = 512;   // update terms staged per warp and pass
 
 // Numeric factor A = L D L^T (Section III.B, left-looking), driven by the
@@ -164,6 +167,105 @@ constexpr int kDepChunk = 512;   // update terms staged per warp and pass
 // abort flag, which ends the others).  The order of operations of every
 // entry is fixed, so results are deterministic.  Factor entries of other
 // columns are read through L2 (__ldcg): other SMs wrote them in this launch.
+// Column c of one instance (a: assembled values, v: factor values, done:
+// column flags).  Returns false when a wait gave up (the caller raises the
+// abort flag).
+template <class T>
+__device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, T *v, unsigned *done,
+                                              int *fstat, double amax, unsigned epoch, int c,
+                                              T *terms, unsigned spin, const unsigned *abort) {
+    const int lane = threadIdx.x & 31;
+    T *Lc = v + m.offLc;
+    bool ok = true;
+    for (int q = m.Fp[c] + lane; q < m.Fp[c + 1] && ok; q += 32) {
+        const unsigned *f = done + m.Fc[q];
+        unsigned it = 0;
+        while (ld_acquire_u32(f) != epoch) {
+            if (++it > spin || *reinterpret_cast<const volatile unsigned *>(abort)) {
+                ok = false;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0, tb = c0 + c;
+    int g_lo[kDepTargets], g_hi[kDepTargets];
+    T part[kDepTargets];
+#pragma unroll
+    for (int j = 0; j < kDepTargets; j++) {
+        const int t = lane + 32 * j;
+        g_lo[j] = t <= cnt ? m.gp[tb + t] : 0;
+        g_hi[j] = t <= cnt ? m.gp[tb + t + 1] : 0;
+        part[j] = T(0);
+    }
+    const int gb = m.gp[tb], ge = m.gp[tb + cnt + 1];
+    for (int cb = gb; cb < ge; cb += kDepChunk) {
+        const int ce = min(ge, cb + kDepChunk);
+        // terms of this pass, four per lane in flight
+        for (int g0 = cb + lane; g0 < ce; g0 += 128) {
+            int4 e[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (g0 + 32 * u < ce) e[u] = __ldg(m.gl + g0 + 32 * u);
+            T x[4], y[4], z[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (g0 + 32 * u < ce) {
+                    x[u] = __ldcg(Lc + e[u].x);
+                    y[u] = __ldcg(Lc + e[u].y);
+                    z[u] = __ldcg(v + e[u].z);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (g0 + 32 * u < ce) terms[g0 + 32 * u - cb] = x[u] * (y[u] * z[u]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kDepTargets; j++) {
+            const int lo = max(g_lo[j], cb), hi = min(g_hi[j], ce);
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            int g = lo;
+            for (; g + 4 <= hi; g += 4) {
+                s0 += terms[g - cb];
+                s1 += terms[g + 1 - cb];
+                s2 += terms[g + 2 - cb];
+                s3 += terms[g + 3 - cb];
+            }
+            for (; g < hi; g++) s0 += terms[g - cb];
+            part[j] += (s0 + s1) + (s2 + s3);
+        }
+        __syncwarp();
+    }
+    T val[kDepTargets];
+#pragma unroll
+    for (int j = 0; j < kDepTargets; j++) {
+        const int t = lane + 32 * j;
+        val[j] = t <= cnt ? T(t == 0 ? a[c] : a[m.offLc + c0 + t - 1]) - part[j] : T(0);
+    }
+    const T d = __shfl_sync(0xffffffffu, val[0], 0);
+    if (lane == 0) {
+        v[c] = d;
+        v[m.offDi + c] = T(1) / d;
+        const double dd = double(d);
+        if (!isfinite(dd)) atomicCAS(fstat, PF_OK, PF_ERR_NONFINITE);
+        else if (fabs(dd) <= 1e-14 * amax) atomicCAS(fstat, PF_OK, PF_ERR_SINGULAR);
+    }
+#pragma unroll
+    for (int j = 0; j < kDepTargets; j++) {
+        const int t = lane + 32 * j;
+        if (t >= 1 && t <= cnt) {
+            const T l = val[j] / d;
+            Lc[c0 + t - 1] = l;
+            v[m.offLr + m.Cpos[c0 + t - 1]] = l;
+        }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release_u32(done + c, epoch);
+    return true;
+}
+
 template <class T>
 __global__ void __launch_bounds__(kDepThreads)
     k_factor_dep(DevMat m, const double *A, T *F, int *fstatus, int ninst, FactorSync fs) {
@@ -178,104 +280,71 @@ __global__ void __launch_bounds__(kDepThreads)
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= total) break;
         const int c = int(idx / unsigned(ninst)), inst = int(idx % unsigned(ninst));
-        const double *a = A + (long long)inst * m.stride;
-        T *v = F + (long long)inst * m.stride;
-        T *Lc = v + m.offLc;
-        unsigned *done = fs.done + (long long)inst * m.n;
-        bool ok = true;
-        for (int q = m.Fp[c] + lane; q < m.Fp[c + 1] && ok; q += 32) {
-            const unsigned *f = done + m.Fc[q];
-            unsigned it = 0;
-            while (ld_acquire_u32(f) != fs.epoch) {
-                if (++it > spin || *reinterpret_cast<volatile unsigned *>(fs.sync + 1)) {
-                    ok = false;
-                    break;
-                }
-                __nanosleep(32);
-            }
+        if (!factor_column<T>(m, A + (long long)inst * m.stride, F + (long long)inst * m.stride,
+                              fs.done + (long long)inst * m.n, fstatus + inst, fs.amax[inst], fs.epoch,
+                              c, terms, spin, fs.sync + 1) &&
+            lane == 0) {
+            atomicExch(fs.sync + 1, 1u);
+            atomicCAS(fstatus + inst, PF_OK, PF_ERR_TIMEOUT);
         }
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) {
-            if (lane == 0) {
-                atomicExch(fs.sync + 1, 1u);
-                atomicCAS(fstatus + inst, PF_OK, PF_ERR_TIMEOUT);
-            }
-            continue;
+    }
+}
+
+// Diagonal maxima and status reset of the matrices of a pack (block per job);
+// block 0 also resets the pack's column counter and abort flag.
+__global__ void k_factor_prep_jobs(const FactorJob *jobs, unsigned *sync) {
+    __shared__ double red[33];
+    const FactorJob &J = jobs[blockIdx.x];
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < J.m.n; j += blockDim.x) mx = fmax(mx, fabs(J.A[j]));
+    mx = block_max(mx, red);
+    if (threadIdx.x == 0) {
+        *J.amax = mx;
+        *J.fstatus = PF_OK;
+        if (blockIdx.x == 0) {
+            sync[0] = 0u;
+            sync[1] = 0u;
         }
-        const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0, tb = c0 + c;
-        int g_lo[kDepTargets], g_hi[kDepTargets];
-        T part[kDepTargets];
-#pragma unroll
-        for (int j = 0; j < kDepTargets; j++) {
-            const int t = lane + 32 * j;
-            g_lo[j] = t <= cnt ? m.gp[tb + t] : 0;
-            g_hi[j] = t <= cnt ? m.gp[tb + t + 1] : 0;
-            part[j] = T(0);
+    }
+}
+
+// The dependency-driven factor over the matrices of a pack: work items
+// (job, column) in an order where every column comes after the columns it
+// depends on (levels ascending across all jobs).
+template <class T>
+__global__ void __launch_bounds__(kDepThreads)
+    k_factor_dep_jobs(const FactorJob *jobs, const int2 *items, unsigned nitems, unsigned *sync,
+                      unsigned spin) {
+    __shared__ T terms_all[kDepThreads / 32][kDepChunk];
+    const int lane = threadIdx.x & 31;
+    T *terms = terms_all[threadIdx.x >> 5];
+    if (!spin) spin = kDefaultSpin;
+    for (;;) {
+        unsigned idx = 0;
+        if (lane == 0) idx = atomicAdd(sync, 1u);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= nitems) break;
+        const int2 it = items[idx];
+        const FactorJob &J = jobs[it.x];
+        if (!factor_column<T>(J.m, J.A, static_cast<T *>(J.F), J.done, J.fstatus, *J.amax, J.epoch, it.y,
+                              terms, spin, sync + 1) &&
+            lane == 0) {
+            atomicExch(sync + 1, 1u);
+            atomicCAS(J.fstatus, PF_OK, PF_ERR_TIMEOUT);
         }
-        const int gb = m.gp[tb], ge = m.gp[tb + cnt + 1];
-        for (int cb = gb; cb < ge; cb += kDepChunk) {
-            const int ce = min(ge, cb + kDepChunk);
-            // terms of this pass, four per lane in flight
-            for (int g0 = cb + lane; g0 < ce; g0 += 128) {
-                int4 e[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (g0 + 32 * u < ce) e[u] = __ldg(m.gl + g0 + 32 * u);
-                T x[4], y[4], z[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (g0 + 32 * u < ce) {
-                        x[u] = __ldcg(Lc + e[u].x);
-                        y[u] = __ldcg(Lc + e[u].y);
-                        z[u] = __ldcg(v + e[u].z);
-                    }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (g0 + 32 * u < ce) terms[g0 + 32 * u - cb] = x[u] * (y[u] * z[u]);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < kDepTargets; j++) {
-                const int lo = max(g_lo[j], cb), hi = min(g_hi[j], ce);
-                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-                int g = lo;
-                for (; g + 4 <= hi; g += 4) {
-                    s0 += terms[g - cb];
-                    s1 += terms[g + 1 - cb];
-                    s2 += terms[g + 2 - cb];
-                    s3 += terms[g + 3 - cb];
-                }
-                for (; g < hi; g++) s0 += terms[g - cb];
-                part[j] += (s0 + s1) + (s2 + s3);
-            }
-            __syncwarp();
-        }
-        T val[kDepTargets];
-#pragma unroll
-        for (int j = 0; j < kDepTargets; j++) {
-            const int t = lane + 32 * j;
-            val[j] = t <= cnt ? T(t == 0 ? a[c] : a[m.offLc + c0 + t - 1]) - part[j] : T(0);
-        }
-        const T d = __shfl_sync(0xffffffffu, val[0], 0);
-        if (lane == 0) {
-            v[c] = d;
-            v[m.offDi + c] = T(1) / d;
-            const double dd = double(d);
-            if (!isfinite(dd)) atomicCAS(fstatus + inst, PF_OK, PF_ERR_NONFINITE);
-            else if (fabs(dd) <= 1e-14 * fs.amax[inst]) atomicCAS(fstatus + inst, PF_OK, PF_ERR_SINGULAR);
-        }
-#pragma unroll
-        for (int j = 0; j < kDepTargets; j++) {
-            const int t = lane + 32 * j;
-            if (t >= 1 && t <= cnt) {
-                const T l = val[j] / d;
-                Lc[c0 + t - 1] = l;
-                v[m.offLr + m.Cpos[c0 + t - 1]] = l;
-            }
-        }
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_release_u32(done + c, fs.epoch);
+    }
+}
+
+// Tail values of the matrices of a pack (block-strided per job).
+template <class T>
+__global__ void k_tail_values_jobs(const FactorJob *jobs) {
+    const FactorJob &J = jobs[blockIdx.y];
+    if (J.m.npf2 == 0 || !J.TV) return;
+    const T *F = static_cast<const T *>(J.F);
+    T *TV = static_cast<T *>(J.TV);
+    for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl < J.m.tv_stride; sl += gridDim.x * blockDim.x) {
+        const int src = J.m.TVsrc[sl];
+        TV[sl] = src >= 0 ? F[src] : T(0);
     }
 }
 
@@ -571,17 +640,14 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
 // With C = 1 every case is one independent block (batches); with C > 1 one
 // case spreads its FP64 mismatch over C SMs (single large cases).
 template <class T, int C>
-__global__ void __launch_bounds__(kRunThreads, C == 1 ? 2 : 1) k_fdpf(RunArgs a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double red[33];
-    __shared__ Ring R;
+__device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char *smem_raw,
+                                          double *red, Ring &R, bool init_ring) {
     const DevNet &dn = a.dn;
     const int nbus = dn.nbus;
-    const int c = blockIdx.x / C;
     const int rank = C == 1 ? 0 : int(cluster_rank());
     unsigned char *stages = smem_raw;
     T *xs = a.use_smem ? reinterpret_cast<T *>(smem_raw + kStages * kStageBytes) : nullptr;
-    ring_init(&R);
+    if (init_ring) ring_init(&R);
     const int inst = a.dc.inst[c];
     double *vm = a.vm + (long long)c * nbus;
     double *va = a.va + (long long)c * nbus;
@@ -687,6 +753,55 @@ __global__ void __launch_bounds__(kRunThreads, C == 1 ? 2 : 1) k_fdpf(RunArgs a)
     cluster_sync<C>();
 }
 
+template <class T, int C>
+__global__ void __launch_bounds__(kRunThreads, C == 1 ? 2 : 1) k_fdpf(RunArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[33];
+    __shared__ Ring R;
+    fdpf_case<T, C>(a, int(blockIdx.x) / C, smem_raw, red, R, true);
+}
+
+// Uneven multi-grid batch: one persistent launch over the grids of a pack,
+// each grid with its own network, symbolic layout and factors (args[g]).
+// Blocks take grids from a counter in the order given by order[] (largest
+// first); a grid's solve vector is in shared memory when it fits the
+// launch's reservation (args[g].use_smem), else in its global scratch.
+template <class T>
+__global__ void __launch_bounds__(kRunThreads, 1)
+    k_fdpf_pack(const RunArgs *args, const int *order, int ngrid, unsigned *counter) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[33];
+    __shared__ Ring R;
+    __shared__ int next;
+    // the staging ring is initialised once and its phases run on across the
+    // grids; after a wait that gave up (ring error) the block runs no more
+    // grids and reports those it takes as timed out
+    ring_init(&R);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned q = atomicAdd(counter, 1u);
+            next = q < unsigned(ngrid) ? order[q] : -1;
+        }
+        __syncthreads();
+        const int g = next;
+        const bool broken = R.err != 0;
+        __syncthreads();
+        if (g < 0) break;
+        if (broken) {
+            if (threadIdx.x == 0) {
+                args[g].res[0].status = PF_ERR_TIMEOUT;
+                args[g].res[0].iters = 0;
+                args[g].res[0].ir_steps = 0;
+                args[g].res[0].pad = 0;
+                args[g].res[0].max_mismatch = INFINITY;
+            }
+            continue;
+        }
+        fdpf_case<T, 1>(args[g], 0, smem_raw, red, R, false);
+        __syncthreads();
+    }
+}
+
 int grid_for(long long total, int threads) {
     long long b = (total + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -771,11 +886,27 @@ cudaError_t launch_tail_values(const DevMat &m, int prec, const void *F, void *T
     return cudaGetLastError();
 }
 
+cudaError_t launch_factor_jobs(const FactorJob *jobs_dev, int njob, const int2 *items_dev,
+                               unsigned nitems, unsigned *sync_dev, int prec, int nsm, cudaStream_t s) {
+    k_factor_prep_jobs<<<njob, 256, 0, s>>>(jobs_dev, sync_dev);
+    long long blocks = (nitems + kDepThreads / 32 - 1) / (kDepThreads / 32);
+    if (blocks > (long long)nsm * 2) blocks = (long long)nsm * 2;
+    if (blocks < 1) blocks = 1;
+    if (prec == PF_FP64) {
+        k_factor_dep_jobs<double><<<int(blocks), kDepThreads, 0, s>>>(jobs_dev, items_dev, nitems, sync_dev, 0u);
+        k_tail_values_jobs<double><<<dim3(8, unsigned(njob)), 256, 0, s>>>(jobs_dev);
+    } else {
+        k_factor_dep_jobs<float><<<int(blocks), kDepThreads, 0, s>>>(jobs_dev, items_dev, nitems, sync_dev, 0u);
+        k_tail_values_jobs<float><<<dim3(8, unsigned(njob)), 256, 0, s>>>(jobs_dev);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
                           int *fstatus, const FactorSync &fs, cudaStream_t s) {
     const long long total = (long long)m.n * ninst;
     const bool dep = fs.mode == 1 || (fs.mode == 0 && ninst < fs.nsm / 2);
-    if (dep && m.max_col + 1 <= 32 * kDepTargets && total < (1ll << 31) && fs.done) {
+    if (dep && m.max_col <= kDepMaxCol && total < (1ll << 31) && fs.done) {
         k_factor_prep<<<ninst, 256, 0, s>>>(m, A, fstatus, fs);
         const int per_sm = 2;  // resident 256-thread blocks per SM (register-limited)
         long long blocks = (total + kDepThreads / 32 - 1) / (kDepThreads / 32);
@@ -848,6 +979,91 @@ cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *
 // Cluster size of the power-flow kernel: a case spreads its nodal work over
 // 16 (or 8) SMs when the batch is too small to fill the GPU with one block per
 // case and such clusters can be resident; otherwise one block per case.
+cudaError_t launch_fdpf_pack(const RunArgs *args_dev, const int *order_dev, int ngrid,
+                             unsigned *counter_dev, int prec, size_t smem, int nsm, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counter_dev, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int blocks = ngrid < nsm ? ngrid : nsm;
+    if (prec == PF_FP64) {
+        e = cudaFuncSetAttribute(k_fdpf_pack<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_fdpf_pack<double><<<blocks, kRunThreads, smem, s>>>(args_dev, order_dev, ngrid, counter_dev);
+    } else {
+        e = cudaFuncSetAttribute(k_fdpf_pack<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_fdpf_pack<float><<<blocks, kRunThreads, smem, s>>>(args_dev, order_dev, ngrid, counter_dev);
+    }
+    return cudaGetLastError();
+}
+
+// Fills the run arguments of one grid of a pack (the single-case form of
+// launch_fdpf's arguments); use_smem is decided by the caller.
+void fill_run_args(RunArgs &a, const DevNet &dn, const DevCases &dc, const DevMat *m, const void *F0,
+                   const void *F1, const void *TV0, const void *TV1, const double *A0,
+                   const double *A1, const int *fstat0, const int *fstat1, const pf_run_opts &o,
+                   double *vm, double *va, double *ef, double *iv, double *xg, double *bmax,
+                   pf_case_result *res) {
+    a.TV0 = m[0].npf2 > 0 ? TV0 : nullptr;
+    a.TV1 = m[1].npf2 > 0 ? TV1 : nullptr;
+    a.iv = iv;
+    a.A0 = A0;
+    a.A1 = A1;
+    a.ir_max = o.ir_max;
+    a.ir_tol = o.ir_tol;
+    a.ir_abs = o.ir_abs > 0 ? o.ir_abs : 0.01 * o.tol;
+    a.dn = dn;
+    a.dc = dc;
+    a.m0 = m[0];
+    a.m1 = m[1];
+    a.F0 = F0;
+    a.F1 = F1;
+    a.fs0 = fstat0;
+    a.fs1 = fstat1;
+    a.tol = o.tol;
+    a.max_iter = o.max_iter;
+    a.flat = o.flat_start;
+    a.spin = o.spin_limit > 0 ? unsigned(o.spin_limit) : kDefaultSpin;
+    a.vm = vm;
+    a.va = va;
+    a.ef = ef;
+    a.xg = xg;
+    a.bmax = bmax;
+    a.res = res;
+    a.use_smem = 0;
+}
+
+size_t run_args_bytes() { return sizeof(RunArgs); }
+
+cudaError_t launch_pack(const PackGrid *grids, int ngrid, int prec, const pf_run_opts &o,
+                        const int *order_host, void *args_dev, int *order_dev, unsigned *counter_dev,
+                        size_t smem_optin, int nsm, cudaStream_t s) {
+    // the launch reserves shared memory for the largest grid whose solve
+    // vector fits; larger grids keep theirs in global scratch
+    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
+    const size_t ring = size_t(kStages) * kStageBytes;
+    int ns = 0;
+    for (int g = 0; g < ngrid; g++) {
+        const int nm = grids[g].m[0].n > grids[g].m[1].n ? grids[g].m[0].n : grids[g].m[1].n;
+        if (ring + elt * size_t(nm) + 2048 <= smem_optin && nm > ns) ns = nm;
+    }
+    std::vector<RunArgs> A(static_cast<size_t>(ngrid));
+    for (int g = 0; g < ngrid; g++) {
+        const PackGrid &p = grids[g];
+        fill_run_args(A[g], p.dn, p.dc, p.m, p.F0, p.F1, p.TV0, p.TV1, p.A0, p.A1, p.fs0, p.fs1, o,
+                      p.vm, p.va, p.ef, p.iv, p.xg, p.bmax, p.res);
+        const int nm = p.m[0].n > p.m[1].n ? p.m[0].n : p.m[1].n;
+        A[g].use_smem = nm <= ns;
+    }
+    cudaError_t e = cudaMemcpyAsync(args_dev, A.data(), sizeof(RunArgs) * size_t(ngrid),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(order_dev, order_host, sizeof(int) * size_t(ngrid), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // A is released on return
+    if (e != cudaSuccess) return e;
+    return launch_fdpf_pack(static_cast<const RunArgs *>(args_dev), order_dev, ngrid, counter_dev, prec,
+                            ring + elt * size_t(ns), nsm, s);
+}
+
 int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int nmax) {
     const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
     size_t smem = size_t(kStages) * kStageBytes + elt * size_t(nmax);

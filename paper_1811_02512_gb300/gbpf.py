@@ -100,6 +100,14 @@ def load():
         L.pf_last_error.restype = C.c_char_p
         L.pf_destroy.argtypes = [_P]
         L.pf_destroy.restype = None
+        L.pf_pack_create.argtypes = [_P, C.c_int32, C.POINTER(_P)]
+        L.pf_pack_create.restype = S
+        L.pf_pack_run.argtypes = [_P, C.POINTER(pf_run_opts), _P, _P, _P, _P]
+        L.pf_pack_run.restype = S
+        L.pf_pack_last_error.argtypes = [_P]
+        L.pf_pack_last_error.restype = C.c_char_p
+        L.pf_pack_destroy.argtypes = [_P]
+        L.pf_pack_destroy.restype = None
         for name in ("pf_create", "pf_analyze", "pf_get_symbolic", "pf_set_cases", "pf_factor",
                      "pf_get_factor", "pf_solve", "pf_mismatch", "pf_run_to_tol", "pf_get_ybus",
                      "pf_set_profiling", "pf_get_profile"):
@@ -291,6 +299,45 @@ def pf_destroy(ctx):
 
 
 # ----------------------------------------------------------------- convenience
+
+class Pack:
+    """An uneven multi-grid batch over analysed ``Grid`` objects (which it
+    does not own): ``run`` solves every grid in one persistent launch."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        arr = (_P * len(self.grids))(*[g.ctx for g in self.grids])
+        h = _P()
+        st = load().pf_pack_create(arr, len(self.grids), C.byref(h))
+        if st != PF_OK:
+            raise PFError(st, "pf_pack_create")
+        self.h = h
+        self.nbus = [g.nbus for g in self.grids]
+        self.offset = np.concatenate([[0], np.cumsum(self.nbus)]).astype(np.int64)
+
+    def run(self, opts, vm_dev, va_dev, stream=None, check=True):
+        """vm_dev/va_dev: device float64 vectors of sum(nbus), grids in pack order."""
+        res = np.zeros(len(self.grids), dtype=CASE_RESULT_DTYPE)
+        st = load().pf_pack_run(self.h, C.byref(opts), _ptr(vm_dev), _ptr(va_dev), _ptr(res),
+                                _stream(stream))
+        if check and st not in (PF_OK, PF_ERR_NOT_CONVERGED, PF_ERR_SINGULAR, PF_ERR_NONFINITE):
+            raise PFError(st, "pf_pack_run: " + load().pf_pack_last_error(self.h).decode())
+        return st, res
+
+    def last_error(self):
+        return load().pf_pack_last_error(self.h).decode()
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pf_pack_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class Grid:
     """A context for one grid: ``Grid(case)`` runs pf_create and pf_analyze."""

@@ -112,6 +112,17 @@ class Case:
         c.lam = self.lam * lam
         return c
 
+    def scaled_network(self, lam: float) -> "Case":
+        """``scaled`` plus the other sources of flow at a flat start scaled
+        towards the flat profile: line charging b -> lam b, off-nominal taps
+        t -> 1 + lam (t - 1), PV and slack set-points v -> 1 + lam (v - 1)."""
+        c = self.scaled(lam)
+        c.b = c.b * lam
+        c.tap = np.where(c.tap != 0.0, 1.0 + lam * (c.tap - 1.0), c.tap)
+        gen = c.btype != PQ
+        c.vset = np.where(gen, 1.0 + lam * (c.vset - 1.0), c.vset)
+        return c
+
 
 # --------------------------------------------------------------------------- topology
 
@@ -312,12 +323,19 @@ def loading_key(case: Case) -> str:
     return f"{case.name}:{case.seed}:{case.n}:{case.m}"
 
 
+def network_scaled(name: str) -> bool:
+    """Grids of the uneven multi-grid batch take their loading factor on the
+    whole network (Case.scaled_network); the others on the injections only."""
+    return name.startswith("multigrid")
+
+
 def with_loading_factor(raw: Case, table=None) -> Case:
     table = load_loading_factors() if table is None else table
     key = loading_key(raw)
     if key not in table:
         raise KeyError(f"no stored loading factor for {key}; run oracle/find_loading_factors.py")
-    return raw.scaled(float(table[key]))
+    lam = float(table[key])
+    return raw.scaled_network(lam) if network_scaled(raw.name) else raw.scaled(lam)
 
 
 # --------------------------------------------------------------------------- named workloads
