@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--ncase", type=int, default=1024,
                     help="batch10k: number of cases (half load scenarios, half outages)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip pf_autotune (untimed) before the warm-up")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     return ap.parse_args()
 
@@ -434,6 +436,11 @@ def main():
     def step():
         return gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase, stream=stream)
 
+    tuning = None
+    if not args.no_autotune and args.engine == "auto":
+        t0 = time.perf_counter()
+        tuning = gbpf.pf_autotune(g.ctx, opts, vm, va, reps=2 if ncase == 1 else 1, stream=stream)
+        tuning["tune_s"] = time.perf_counter() - t0
     for _ in range(max(3, args.warmup)):
         st, res = step()
     torch.cuda.synchronize()
@@ -525,6 +532,7 @@ def main():
                        "method": args.method, "engine": args.engine,
                        "l2": "flushed between timed steps (2.5x L2 buffer write)",
                        "loading_factor": base.lam, "analyze_ms": analyze_ms,
+                       "tuning": tuning,
                        "parallelism": "replicas" if ncase == 1 else "cases-in-blocks"},
             "converged": converged, "ncase": ncase,
             "iters_mean": float(np.mean(iters)), "gpu_launches": launches,

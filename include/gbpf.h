@@ -114,6 +114,26 @@ typedef struct {
  * BLOCK; LANES falls back to BLOCK where not even one case fits. */
 enum { PF_ENGINE_AUTO = 0, PF_ENGINE_BLOCK = 1, PF_ENGINE_LANES = 2 };
 
+/* Kernel mappings of a context, chosen by pf_autotune (or set directly with
+ * pf_set_tuning; 0 in a field = the library's default choice):
+ *   engine   PF_ENGINE_BLOCK or PF_ENGINE_LANES, used by FDPF runs whose
+ *            options ask for PF_ENGINE_AUTO;
+ *   cluster  thread blocks per case of a single-case FDPF run (1, 8, 16;
+ *            capped at what fits the GPU);
+ *   factor   1: dependency-driven factor over all SMs, 2: one thread block
+ *            per instance (level by level);
+ *   tail     1: narrow top of the elimination tree substituted as a one-warp
+ *            scatter, 2: level by level (warp per narrow level).
+ * ms is the time of one run of the chosen mapping as measured by
+ * pf_autotune (0 when set directly). */
+typedef struct {
+    int32_t engine;
+    int32_t cluster;
+    int32_t factor;
+    int32_t tail;
+    double ms;
+} pf_tuning;
+
 /* Per-case outcome of pf_run_to_tol. */
 typedef struct {
     int32_t status;      /* pf_status of this case */
@@ -240,6 +260,23 @@ pf_status pf_adjoint(pf_ctx *ctx, int32_t precision, const double *vm_dev, const
  * dJ/dV_k for every bus.  Asynchronous. */
 pf_status pf_objective(pf_ctx *ctx, const double *vm_dev, const double *va_dev, double *J_dev,
                        double *gva_dev, double *gvm_dev, void *stream);
+
+/* Project autotuner: runs pf_run_to_tol with opts (engine AUTO) under every
+ * applicable mapping of pf_tuning -- engines for FDPF batches, cluster sizes
+ * for single cases, the two factor forms, the two tail forms -- `reps` times
+ * each after one untimed run, times them with CUDA events on `stream`, and
+ * keeps the fastest mapping whose cases all converged; it becomes the
+ * context's tuning (used by later runs) and is written to *out.  vm_dev,
+ * va_dev as for pf_run_to_tol (overwritten).  PF_ERR_ARG for reps < 1 or bad
+ * options; the status of pf_run_to_tol when no mapping converges.
+ * Synchronous. */
+pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                      int32_t reps, pf_tuning *out, void *stream);
+
+/* Reads or replaces the context's tuning.  PF_ERR_ARG for a field out of
+ * range.  Synchronous, host only. */
+pf_status pf_get_tuning(const pf_ctx *ctx, pf_tuning *out);
+pf_status pf_set_tuning(pf_ctx *ctx, const pf_tuning *tuning);
 
 /* Message of the last failing call on this context (never NULL). */
 const char *pf_last_error(const pf_ctx *ctx);

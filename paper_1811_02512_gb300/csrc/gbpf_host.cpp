@@ -920,6 +920,7 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
     fs.epoch = w.fepoch[which];
     fs.spin = 0;
     fs.nsm = ctx->num_sms;
+    fs.mode = ctx->tune.factor;
     e = counted(ctx, PF_K_FACTOR, 2, s, [&] {
         return launch_factor(m, prec, w.A[which], F, ctx->dc.ninst, w.fstatus[which][prec], fs, s);
     });
@@ -1302,7 +1303,8 @@ pf_status pf_solve(pf_ctx *ctx, int32_t which, int32_t precision, int32_t transp
                                          : (const void *)ctx->ws.F32[which];
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = counted(ctx, PF_K_SOLVE, 1, s, [&] {
-        return launch_solve(ctx->dm[which], precision, F, ctx->ws.TV[which][precision], ctx->dc.inst,
+        return launch_solve(ctx->dm[which], precision, F,
+                            ctx->tune.tail != 2 ? ctx->ws.TV[which][precision] : nullptr, ctx->dc.inst,
                             rhs_inout_dev, ncase, ctx->ws.vec, ctx->ws.cstatus, ctx->smem_optin, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve launch");
@@ -1367,7 +1369,8 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
     const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
     const int nmax = std::max(ctx->dm[0].n, ctx->dm[1].n);
     const bool lanes_ok = opts->method == PF_FDPF && lane_width(nmax, prec, ctx->smem_optin) > 0;
-    const int engine = opts->engine == PF_ENGINE_LANES && lanes_ok ? PF_ENGINE_LANES : PF_ENGINE_BLOCK;
+    const int want = opts->engine != PF_ENGINE_AUTO ? opts->engine : ctx->tune.engine;
+    const int engine = want == PF_ENGINE_LANES && lanes_ok ? PF_ENGINE_LANES : PF_ENGINE_BLOCK;
     if (engine == PF_ENGINE_LANES) {
         TRY(ensure_lanes(ctx, prec));
         LaneRun r;
@@ -1400,10 +1403,13 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
                             c, res_host[c].status, res_host[c].iters);
         return PF_OK;
     }
-    const int cl = fdpf_cluster_size(ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin,
-                                     std::max(ctx->dm[0].n, ctx->dm[1].n));
+    int cl = fdpf_cluster_size(ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin,
+                               std::max(ctx->dm[0].n, ctx->dm[1].n));
+    if (ctx->tune.cluster > 0 && ctx->tune.cluster < cl) cl = ctx->tune.cluster < 8 ? 1 : 8;
+    const bool tail = ctx->tune.tail != 2;
     cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
-        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, w.TV[0][prec], w.TV[1][prec],
+        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, tail ? w.TV[0][prec] : nullptr,
+                           tail ? w.TV[1][prec] : nullptr,
                            w.A[0], w.A[1],
                            w.fstatus[0][prec], w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef,
                            w.iv, w.vec, w.bmax, w.res, ctx->smem_optin, cl, s);
@@ -1512,6 +1518,99 @@ pf_status pf_get_ybus(pf_ctx *ctx, int32_t *rowptr, int32_t *col, double *G, dou
             e = cudaMemcpy(B, ctx->dn.B, sizeof(double) * ctx->dn.nnz, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "get_ybus");
     }
+    return PF_OK;
+}
+
+pf_status pf_get_tuning(const pf_ctx *ctx, pf_tuning *out) {
+    if (!ctx || !out) return PF_ERR_ARG;
+    *out = ctx->tune;
+    return PF_OK;
+}
+
+pf_status pf_set_tuning(pf_ctx *ctx, const pf_tuning *t) {
+    if (!ctx || !t) return fail(ctx, PF_ERR_ARG, "null pointer");
+    if (t->engine < 0 || t->engine > PF_ENGINE_LANES || t->factor < 0 || t->factor > 2 || t->tail < 0 ||
+        t->tail > 2 || (t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16))
+        return fail(ctx, PF_ERR_ARG, "tuning field out of range");
+    ctx->tune = *t;
+    ctx->tune.ms = t->ms;
+    return PF_OK;
+}
+
+pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                      int32_t reps, pf_tuning *out, void *stream) {
+    if (!ctx || !opts || !vm_dev || !va_dev || !out) return fail(ctx, PF_ERR_ARG, "null pointer");
+    if (reps < 1 || reps > 1000) return fail(ctx, PF_ERR_ARG, "reps out of range");
+    if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    TRY(ensure_cases(ctx));
+    TRY(ensure_device(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    pf_run_opts o = *opts;
+    o.engine = PF_ENGINE_AUTO;
+    const int ncase = ctx->dc.ncase;
+    const int prec = o.precision;
+    // candidate mappings
+    std::vector<pf_tuning> cand;
+    std::vector<int> engines{PF_ENGINE_BLOCK};
+    const int nmax = std::max(ctx->dm[0].n, ctx->dm[1].n);
+    if (o.method == PF_FDPF && ncase >= 32 && lane_width(nmax, prec, ctx->smem_optin) > 0)
+        engines.push_back(PF_ENGINE_LANES);
+    std::vector<int> clusters{0};
+    if (o.method == PF_FDPF) {
+        const int cmax = fdpf_cluster_size(ncase, ctx->num_sms, prec, ctx->smem_optin, nmax);
+        clusters.clear();
+        for (int c : {1, 8, 16})
+            if (c <= cmax) clusters.push_back(c);
+    }
+    std::vector<int> factors{2};
+    if (std::max(ctx->hm[0].max_col, ctx->hm[1].max_col) <= kDepMaxCol) factors.push_back(1);
+    std::vector<int> tails{2};
+    if (o.method == PF_FDPF && (ctx->dm[0].npf2 > 0 || ctx->dm[1].npf2 > 0)) tails.push_back(1);
+    for (int e : engines)
+        for (int c : (e == PF_ENGINE_LANES ? std::vector<int>{0} : clusters))
+            for (int f : factors)
+                for (int t : (e == PF_ENGINE_LANES ? std::vector<int>{0} : tails))
+                    cand.push_back(pf_tuning{e, c, f, t, 0.0});
+    std::vector<pf_case_result> res(static_cast<size_t>(ncase));
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return fail(ctx, PF_ERR_CUDA, "event creation");
+    }
+    const pf_tuning saved = ctx->tune;
+    pf_tuning best{0, 0, 0, 0, -1.0};
+    pf_status last = PF_OK;
+    for (const pf_tuning &t : cand) {
+        ctx->tune = t;
+        pf_status st = pf_run_to_tol(ctx, &o, vm_dev, va_dev, res.data(), stream);  // untimed
+        if (st != PF_OK) {
+            last = st;
+            continue;
+        }
+        cudaEventRecord(a, s);
+        for (int r = 0; r < reps && st == PF_OK; r++) st = pf_run_to_tol(ctx, &o, vm_dev, va_dev, res.data(), stream);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (st != PF_OK) {
+            last = st;
+            continue;
+        }
+        const double per = double(ms) / reps;
+        if (best.ms < 0 || per < best.ms) {
+            best = t;
+            best.ms = per;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (best.ms < 0) {
+        ctx->tune = saved;
+        return fail(ctx, last == PF_OK ? PF_ERR_NOT_CONVERGED : last, "no mapping converged");
+    }
+    ctx->tune = best;
+    *out = best;
     return PF_OK;
 }
 
@@ -1628,8 +1727,8 @@ pf_status pf_pack_run(pf_pack *pk, const pf_run_opts *opts, double *vm_dev, doub
         p.m[1] = ctx->dm[1];
         p.F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
         p.F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
-        p.TV0 = w.TV[0][prec];
-        p.TV1 = w.TV[1][prec];
+        p.TV0 = ctx->tune.tail != 2 ? w.TV[0][prec] : nullptr;
+        p.TV1 = ctx->tune.tail != 2 ? w.TV[1][prec] : nullptr;
         p.A0 = w.A[0];
         p.A1 = w.A[1];
         p.fs0 = w.fstatus[0][prec];

@@ -242,6 +242,7 @@ struct pf_ctx {
     size_t smem_optin = 0;
     std::string err;
     std::vector<void *> allocations;  // everything owned by the context
+    pf_tuning tune = {0, 0, 0, 0, 0.0};  // kernel mappings (pf_autotune / pf_set_tuning)
 };
 
 namespace gbpf {

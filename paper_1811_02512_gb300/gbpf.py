@@ -100,6 +100,11 @@ def load():
         L.pf_last_error.restype = C.c_char_p
         L.pf_destroy.argtypes = [_P]
         L.pf_destroy.restype = None
+        L.pf_autotune.argtypes = [_P, C.POINTER(pf_run_opts), _P, _P, C.c_int32, _P, _P]
+        L.pf_get_tuning.argtypes = [_P, _P]
+        L.pf_set_tuning.argtypes = [_P, _P]
+        for nm in ("pf_autotune", "pf_get_tuning", "pf_set_tuning"):
+            getattr(L, nm).restype = S
         L.pf_pack_create.argtypes = [_P, C.c_int32, C.POINTER(_P)]
         L.pf_pack_create.restype = S
         L.pf_pack_run.argtypes = [_P, C.POINTER(pf_run_opts), _P, _P, _P, _P]
@@ -299,6 +304,31 @@ def pf_destroy(ctx):
 
 
 # ----------------------------------------------------------------- convenience
+
+class pf_tuning(C.Structure):
+    _fields_ = [("engine", C.c_int32), ("cluster", C.c_int32), ("factor", C.c_int32),
+                ("tail", C.c_int32), ("ms", C.c_double)]
+
+
+def pf_autotune(ctx, opts, vm_dev, va_dev, reps=3, stream=None):
+    """Times the applicable kernel mappings on this context's problem and keeps
+    the fastest converging one; returns it as a dict."""
+    t = pf_tuning()
+    _check(ctx, load().pf_autotune(ctx, C.byref(opts), _ptr(vm_dev), _ptr(va_dev), int(reps),
+                                   C.byref(t), _stream(stream)), "pf_autotune")
+    return {k: getattr(t, k) for k, _ in pf_tuning._fields_}
+
+
+def pf_get_tuning(ctx):
+    t = pf_tuning()
+    _check(ctx, load().pf_get_tuning(ctx, C.byref(t)), "pf_get_tuning")
+    return {k: getattr(t, k) for k, _ in pf_tuning._fields_}
+
+
+def pf_set_tuning(ctx, engine=0, cluster=0, factor=0, tail=0):
+    t = pf_tuning(engine, cluster, factor, tail, 0.0)
+    _check(ctx, load().pf_set_tuning(ctx, C.byref(t)), "pf_set_tuning")
+
 
 class Pack:
     """An uneven multi-grid batch over analysed ``Grid`` objects (which it

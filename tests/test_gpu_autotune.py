@@ -1,0 +1,76 @@
+"""Project autotuner (pf_autotune) and explicit kernel mappings (pf_set_tuning).
+
+Every mapping the tuner may choose -- cluster size of a single case, the
+dependency-driven or block-per-instance factor, the scatter or level-by-level
+narrow tail, the block or lane engine of a batch -- must reach the oracle's
+solution (1e-8 p.u./rad, both sides run tight); the tuner must return one of
+them with a positive time, and leave it set on the context.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1811_02512_gb300 import gbpf, gridgen  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_02512_gb300 import build
+    build.build()
+    gbpf.load()
+
+
+def test_every_single_case_mapping_matches_oracle(oracle):
+    case = gridgen.config(1)
+    rc, vm0, va0, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
+    assert rc == oracle.OK
+    g = gbpf.Grid(case)
+    g.set_cases(1)
+    vm = torch.zeros((1, case.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    for prec, cl, fac, tail in itertools.product([gbpf.PF_FP64, gbpf.PF_FP32], [1, 8, 16], [1, 2], [1, 2]):
+        gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, cluster=cl, factor=fac, tail=tail)
+        opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=1e-11, max_iter=300)
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, 1)
+        assert st == gbpf.PF_OK, (prec, cl, fac, tail, gbpf.pf_last_error(g.ctx))
+        assert np.max(np.abs(vm.cpu().numpy()[0] - vm0)) <= 1e-8, (prec, cl, fac, tail)
+        assert np.max(np.abs(va.cpu().numpy()[0] - va0)) <= 1e-8, (prec, cl, fac, tail)
+    g.close()
+
+
+def test_autotune_single_and_batch(oracle):
+    base = gridgen.config(1)
+    g = gbpf.Grid(base)
+    g.set_cases(1)
+    vm = torch.zeros((1, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-8, max_iter=200)
+    t = gbpf.pf_autotune(g.ctx, opts, vm, va, reps=2)
+    assert t["ms"] > 0 and t["cluster"] in (1, 8, 16) and t["factor"] in (1, 2) and t["tail"] in (1, 2)
+    assert gbpf.pf_get_tuning(g.ctx) == t
+    g.close()
+    sc = gridgen.scenarios(base, n_load=32, n_outage=32, seed=5)
+    g = gbpf.Grid(base)
+    g.set_cases(sc.ncase, sc.load_scale, sc.outage)
+    vm = torch.zeros((sc.ncase, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP32, tol=1e-11, max_iter=300)
+    t = gbpf.pf_autotune(g.ctx, opts, vm, va, reps=1)
+    assert t["ms"] > 0 and t["engine"] in (gbpf.PF_ENGINE_BLOCK, gbpf.PF_ENGINE_LANES)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+    assert st == gbpf.PF_OK
+    v, a = vm.cpu().numpy(), va.cpu().numpy()
+    for c in (0, 31, 32, 63):
+        cc = gridgen.apply_scenario(base, sc, c)
+        rc, vm0, va0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+        assert rc == oracle.OK
+        assert np.max(np.abs(v[c] - vm0)) <= 1e-8 and np.max(np.abs(a[c] - va0)) <= 1e-8
+    g.close()

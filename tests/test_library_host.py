@@ -102,3 +102,32 @@ def test_device_calls_fail_cleanly_without_gpu(lib):
         g.set_cases(1)
     assert e.value.status in (gbpf.PF_ERR_CUDA, gbpf.PF_ERR_OOM)
     g.close()
+
+
+def test_tuning_fields_validated(lib):
+    case = gridgen.config_raw(0)
+    ctx = gbpf.pf_create(*_tables(case))
+    gbpf.pf_analyze(ctx)
+    assert gbpf.pf_get_tuning(ctx) == {"engine": 0, "cluster": 0, "factor": 0, "tail": 0, "ms": 0.0}
+    gbpf.pf_set_tuning(ctx, engine=gbpf.PF_ENGINE_LANES, cluster=8, factor=1, tail=2)
+    t = gbpf.pf_get_tuning(ctx)
+    assert (t["engine"], t["cluster"], t["factor"], t["tail"]) == (gbpf.PF_ENGINE_LANES, 8, 1, 2)
+    for bad in ({"cluster": 3}, {"factor": 3}, {"tail": -1}, {"engine": 7}):
+        with pytest.raises(gbpf.PFError) as e:
+            gbpf.pf_set_tuning(ctx, **bad)
+        assert e.value.status == gbpf.PF_ERR_ARG
+    gbpf.pf_destroy(ctx)
+
+
+def test_pack_create_validates(lib):
+    case = gridgen.config_raw(0)
+    ctx = gbpf.pf_create(*_tables(case))
+    arr = (C.c_void_p * 2)(ctx, ctx)
+    h = C.c_void_p()
+    assert lib.pf_pack_create(arr, 2, C.byref(h)) == gbpf.PF_ERR_STATE  # not analysed
+    gbpf.pf_analyze(ctx)
+    assert lib.pf_pack_create(arr, 2, C.byref(h)) == gbpf.PF_ERR_ARG  # repeated
+    assert lib.pf_pack_create(arr, 0, C.byref(h)) == gbpf.PF_ERR_ARG
+    assert lib.pf_pack_create(arr, 1, C.byref(h)) == gbpf.PF_OK
+    lib.pf_pack_destroy(h)
+    gbpf.pf_destroy(ctx)
