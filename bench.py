@@ -160,6 +160,29 @@ def algorithmic_bytes_per_half_iteration(info, nbus, nnz_y, prec_bytes):
     return mismatch + solve
 
 
+def measured_traffic(workload, prec_name, ncase):
+    """DRAM bytes per launch of the iteration kernel from the committed ncu
+    summary of the same kernel and workload (scaled by cases when the capture
+    ran fewer cases), or None when there is no such capture."""
+    files = {("plain10k", "fp64"): "k_fdpf_plain10k_fp64.md",
+             ("batch10k", "fp32"): "k_fdpf_batch128_fp32.md"}
+    name = files.get((workload, prec_name))
+    if not name:
+        return None
+    vals = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as fh:
+            for ln in fh:
+                if "=" in ln and ln.split("=")[0].strip() in ("traffic_bytes_per_launch", "traffic_cases"):
+                    k, v = ln.split("=")
+                    vals[k.strip()] = float(v)
+    except OSError:
+        return None
+    if "traffic_bytes_per_launch" not in vals:
+        return None
+    return vals["traffic_bytes_per_launch"] * (ncase / vals.get("traffic_cases", ncase))
+
+
 # ------------------------------------------------------------------ oracle baseline
 
 def _oracle_job(args):
@@ -517,7 +540,8 @@ def main():
     alg_bytes = per_half * half_iters  # per launch (one launch per step)
     achieved = alg_bytes / (run_ms / max(run_n, 1) / 1e3) / 1e9 if run_ms > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": "k_fdpf", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": measured_traffic(args.workload, prec_name, ncase) if method == gbpf.PF_FDPF else None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_ms_per_launch": run_ms / max(run_n, 1)}
