@@ -214,7 +214,7 @@ def cpu_baseline(workload, sample_s, ncase):
     O.build()
     cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
-    per = max(1, int(sample_s / 0.06 / 2))
+    per = max(1, int(sample_s / 0.03))  # more than the budget; the deadline stops it
     jobs = []
     for w in range(cores):
         if workload == "plain10k":

@@ -451,7 +451,9 @@ __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces
         // drain: at most the last kStages issued pieces can still be in flight
         for (int q = (issued > kStages ? issued - kStages : 0); q < issued; q++) {
             const unsigned gq = g0 + unsigned(q);
-            mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, spin);
+            // the caller's limit may be short; the drain always waits long
+            // enough for a copy to land (a copy must not outlive the block)
+            mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, spin > kDefaultSpin ? spin : kDefaultSpin);
         }
     }
     __syncthreads();

@@ -817,6 +817,7 @@ void free_case_storage(pf_ctx *ctx) {
         dfree(ctx, w.F64[a]); w.F64[a] = nullptr;
         dfree(ctx, w.F32[a]); w.F32[a] = nullptr;
         dfree(ctx, w.fdone[a]); w.fdone[a] = nullptr;
+
         for (int b = 0; b < 2; b++) {
             dfree(ctx, w.TV[a][b]);
             w.TV[a][b] = nullptr;
@@ -901,7 +902,7 @@ pf_status factor_job(pf_ctx *ctx, int which, int prec, FactorJob &J, cudaStream_
 
 // Assembles B' or B'' of every instance from the current admittance matrix
 // and factorises them.
-pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
+pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int blocks_per_sm = 2) {
     TRY(assemble_matrix(ctx, which, prec, s));
     Workspace &w = ctx->ws;
     const DevMat &m = ctx->dm[which];
@@ -921,6 +922,7 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
     fs.spin = 0;
     fs.nsm = ctx->num_sms;
     fs.mode = ctx->tune.factor;
+    fs.blocks_per_sm = blocks_per_sm;
     e = counted(ctx, PF_K_FACTOR, 2, s, [&] {
         return launch_factor(m, prec, w.A[which], F, ctx->dc.ninst, w.fstatus[which][prec], fs, s);
     });
@@ -928,6 +930,36 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
     e = launch_tail_values(m, prec, F, w.TV[which][prec], ctx->dc.ninst, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tail values launch");
     w.factored[which][prec] = true;
+    return PF_OK;
+}
+
+// B' and B'' of every instance.  With the dependency-driven factor (few
+// instances) the two factorisations are independent chains of dependent
+// columns: B'' runs on a second stream beside B', each launch capped at one
+// block per SM so both are resident at once.
+pf_status factor_both(pf_ctx *ctx, int prec, cudaStream_t s) {
+    Workspace &w = ctx->ws;
+    const int ninst = ctx->dc.ninst;
+    const bool dep = ctx->tune.factor == 1 || (ctx->tune.factor == 0 && ninst < ctx->num_sms / 2);
+    if (!dep) {
+        TRY(factor_matrix(ctx, PF_MAT_BP, prec, s));
+        TRY(factor_matrix(ctx, PF_MAT_BPP, prec, s));
+        return PF_OK;
+    }
+    if (!w.side) {
+        if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming) != cudaSuccess)
+            return fail(ctx, PF_ERR_CUDA, "side stream");
+    }
+    cudaError_t e = cudaEventRecord(w.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(w.side, w.fork, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fork");
+    TRY(factor_matrix(ctx, PF_MAT_BPP, prec, w.side, 1));
+    TRY(factor_matrix(ctx, PF_MAT_BP, prec, s, 1));
+    e = cudaEventRecord(w.join, w.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "join");
     return PF_OK;
 }
 
@@ -1362,8 +1394,7 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
                             c, res_host[c].status, res_host[c].iters);
         return PF_OK;
     }
-    TRY(factor_matrix(ctx, PF_MAT_BP, prec, s));
-    TRY(factor_matrix(ctx, PF_MAT_BPP, prec, s));
+    TRY(factor_both(ctx, prec, s));
     Workspace &w = ctx->ws;
     const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
     const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
@@ -1807,6 +1838,12 @@ void pf_pack_destroy(pf_pack *pk) {
 
 void pf_destroy(pf_ctx *ctx) {
     if (!ctx) return;
+    if (ctx->ws.side) {
+        cudaStreamSynchronize(ctx->ws.side);
+        cudaStreamDestroy(ctx->ws.side);
+        cudaEventDestroy(ctx->ws.fork);
+        cudaEventDestroy(ctx->ws.join);
+    }
     for (auto &k : ctx->kstat) {
         for (auto &pr : k.pending) {
             cudaEventDestroy(pr.first);

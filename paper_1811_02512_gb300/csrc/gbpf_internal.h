@@ -176,6 +176,8 @@ struct LaneSet {
     int prec = -1;
 };
 
+struct FactorJob;
+
 struct Workspace {
     // factor storage per matrix and precision: [ninst][stride]
     double *A[2] = {nullptr, nullptr};       // assembled values (FP64), per instance
@@ -192,6 +194,9 @@ struct Workspace {
     double *famax[2] = {nullptr, nullptr};    // [ninst]
     unsigned fepoch[2] = {0u, 0u};
     void *TV[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mat][prec] tail values
+    // second stream for the B'' factorisation beside B' (fork/join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     // per-case scratch
     double *ef = nullptr;     // [ncase][4*nbus] e, f, cos(theta), sin(theta)
     double *vec = nullptr;    // [ncase][3*nbus] rhs, refined FP64 solution, FP32 work vector
@@ -262,6 +267,7 @@ struct FactorSync {
     unsigned spin = 0;
     int nsm = 0;
     int mode = 0;              // 0 auto, 1 dependency-driven, 2 block per instance
+    int blocks_per_sm = 2;     // dependency-driven grid: blocks per SM
 };
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
                           int *fstatus, const FactorSync &fs, cudaStream_t s);

@@ -126,6 +126,19 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Waits until *f == epoch (acquire), polling at most `spin` times with a
+// short sleep; gives up early when *abort is raised.  Returns whether the
+// flag was seen.
+__device__ __forceinline__ bool wait_flag(const unsigned *f, unsigned epoch, unsigned spin,
+                                          const unsigned *abort) {
+    unsigned it = 0;
+    while (ld_acquire_u32(f) != epoch) {
+        if (++it > spin || *reinterpret_cast<const volatile unsigned *>(abort)) return false;
+        __nanosleep(32);
+    }
+    return true;
+}
+
 // Diagonal maxima of the assembled matrices (the pivot tolerance), status
 // reset, and reset of the column counter and abort flag of k_factor_dep.
 __global__ void k_factor_prep(DevMat m, const double *A, int *fstatus, FactorSync fs) {
@@ -177,17 +190,8 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
     const int lane = threadIdx.x & 31;
     T *Lc = v + m.offLc;
     bool ok = true;
-    for (int q = m.Fp[c] + lane; q < m.Fp[c + 1] && ok; q += 32) {
-        const unsigned *f = done + m.Fc[q];
-        unsigned it = 0;
-        while (ld_acquire_u32(f) != epoch) {
-            if (++it > spin || *reinterpret_cast<const volatile unsigned *>(abort)) {
-                ok = false;
-                break;
-            }
-            __nanosleep(32);
-        }
-    }
+    for (int q = m.Fp[c] + lane; q < m.Fp[c + 1] && ok; q += 32)
+        ok = wait_flag(done + m.Fc[q], epoch, spin, abort);
     if (!__all_sync(0xffffffffu, ok)) return false;
     const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0, tb = c0 + c;
     int g_lo[kDepTargets], g_hi[kDepTargets];
@@ -908,7 +912,7 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
     const bool dep = fs.mode == 1 || (fs.mode == 0 && ninst < fs.nsm / 2);
     if (dep && m.max_col <= kDepMaxCol && total < (1ll << 31) && fs.done) {
         k_factor_prep<<<ninst, 256, 0, s>>>(m, A, fstatus, fs);
-        const int per_sm = 2;  // resident 256-thread blocks per SM (register-limited)
+        const int per_sm = fs.blocks_per_sm > 0 && fs.blocks_per_sm < 2 ? fs.blocks_per_sm : 2;  // resident blocks per SM (registers)
         long long blocks = (total + kDepThreads / 32 - 1) / (kDepThreads / 32);
         if (blocks > (long long)fs.nsm * per_sm) blocks = (long long)fs.nsm * per_sm;
         if (blocks < 1) blocks = 1;
@@ -1163,6 +1167,47 @@ __global__ void k_ref_sincos(const double *x, double *s, double *c, int n) {
     if (i < n) sincos(x[i], s + i, c + i);
 }
 }  // namespace
+
+// Self-test hook of the bounded waits: an mbarrier on which nothing arrives
+// and a done flag that nothing sets must both give up after their limit and
+// report it (out[0], out[1] = 1 when the wait gave up), with the cycles spent
+// (out[2], out[3]).
+namespace {
+__global__ void k_selftest_waits(long long *out, unsigned limit, unsigned *flag, unsigned *abort) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        gbpf::mbar_init(&bar, 1);
+        gbpf::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t0 = clock64();
+        const bool got = gbpf::mbar_wait_bounded(&bar, 0u, limit);
+        out[0] = got ? 0 : 1;
+        out[2] = clock64() - t0;
+        t0 = clock64();
+        const bool seen = gbpf::wait_flag(flag, 1u, limit, abort);
+        out[1] = seen ? 0 : 1;
+        out[3] = clock64() - t0;
+    }
+}
+}  // namespace
+
+extern "C" int gbpf_selftest_waits(unsigned limit, long long *out_host) {
+    long long *out = nullptr;
+    unsigned *flags = nullptr;
+    if (cudaMalloc(&out, 4 * sizeof(long long)) != cudaSuccess) return 1;
+    if (cudaMalloc(&flags, 2 * sizeof(unsigned)) != cudaSuccess) {
+        cudaFree(out);
+        return 1;
+    }
+    cudaMemset(flags, 0, 2 * sizeof(unsigned));
+    k_selftest_waits<<<1, 32>>>(out, limit, flags, flags + 1);
+    cudaError_t e = cudaMemcpy(out_host, out, 4 * sizeof(long long), cudaMemcpyDeviceToHost);
+    cudaFree(out);
+    cudaFree(flags);
+    return e == cudaSuccess ? 0 : 1;
+}
 
 extern "C" int gbpf_selftest_small_sincos(const double *x_dev, double *s_dev, double *c_dev,
                                           double *s_ref_dev, double *c_ref_dev, int n) {

@@ -11,6 +11,8 @@ Tolerances:
     a tight mismatch (the power-flow solution is only defined to
     ||J^-1|| * tol by a tolerance-based stop).
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -213,6 +215,40 @@ def test_iteration_limit_reported():
     assert st == gbpf.PF_ERR_NOT_CONVERGED
     assert res[0]["status"] == gbpf.PF_ERR_NOT_CONVERGED and res[0]["iters"] == 2
     g.close()
+
+
+@pytest.mark.parametrize("ncase", [1, 4])
+def test_wait_limit_reports_timeout_and_context_survives(oracle, ncase):
+    """A one-poll limit on every wait of the staged sweeps: a wait that gives
+    up makes the kernel drain its copies and report PF_ERR_TIMEOUT; a poll
+    usually suffices (mbarrier try_wait suspends until the phase completes or a
+    hardware time limit), so the run may also converge.  Either way the next
+    run with the default limit is correct."""
+    case = gridgen.config(1)
+    g = _grid(case, ncase)
+    vm = torch.zeros((ncase, case.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-8, max_iter=200, spin_limit=1)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase, check=False)
+    assert st in (gbpf.PF_OK, gbpf.PF_ERR_TIMEOUT)
+    assert all(s in (gbpf.PF_OK, gbpf.PF_ERR_TIMEOUT) for s in res["status"])
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-11, max_iter=300)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+    assert st == gbpf.PF_OK
+    rc, vm0, va0, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
+    assert np.max(np.abs(vm.cpu().numpy()[0] - vm0)) <= 1e-8
+    g.close()
+
+
+def test_waits_that_never_complete_give_up():
+    """The bounded-wait primitives of the sweeps (mbarrier) and of the
+    dependency-driven factor (done flag) on a barrier nothing arrives on and
+    a flag nothing sets: both give up after their limit and say so."""
+    L = gbpf.load()
+    out = (C.c_longlong * 4)()
+    assert L.gbpf_selftest_waits(C.c_uint(20000), out) == 0
+    assert out[0] == 1 and out[1] == 1
+    assert 0 < out[2] < 2_000_000_000 and 0 < out[3] < 2_000_000_000
 
 
 def test_no_pq_bus_empty_bpp(oracle):
