@@ -233,6 +233,25 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
             }
         H.PPp[r + 1] = int(H.PPc.size());
     }
+    // tail factor: per target of the tail columns its A slot, column and the
+    // first gather term from a tail column (terms are in CSR order, k ascending)
+    H.ft_g0 = H.Cp[t0] + t0;
+    H.ft_e0 = H.Cp[t0];
+    H.ft_ng = (n + int(H.Lp[n])) - H.ft_g0;
+    H.ft_ne = int(H.Lp[n]) - H.ft_e0;
+    H.tapos.assign(std::max(1, H.ft_ng), 0);
+    H.tcol.assign(std::max(1, H.ft_ng), 0);
+    H.gsplit.assign(std::max(1, H.ft_ng), 0);
+    for (int c = t0; c < n; c++)
+        for (int t = 0; t <= H.Cp[c + 1] - H.Cp[c]; t++) {
+            const int g = H.Cp[c] + c + t;
+            const int k = g - H.ft_g0;
+            H.tapos[k] = t == 0 ? c : H.offLc + H.Cp[c] + t - 1;
+            H.tcol[k] = c;
+            int q = H.gp[g];
+            while (q < H.gp[g + 1] && H.gl[q].z < t0) q++;
+            H.gsplit[k] = q;
+        }
     auto pad32 = [](int64_t v) { return int((v + 31) / 32 * 32); };
     H.tv_f = 0;
     H.tv_b = pad32(int64_t(posf.size()));
@@ -709,6 +728,13 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
         D.tv_b = H.tv_b;
         D.tv_p = H.tv_p;
         D.tv_stride = H.tv_stride;
+        TRY(upload_padded(ctx, &D.tapos, H.tapos));
+        TRY(upload_padded(ctx, &D.tcol, H.tcol));
+        TRY(upload_padded(ctx, &D.gsplit, H.gsplit));
+        D.ft_ng = H.ft_ng;
+        D.ft_ne = H.ft_ne;
+        D.ft_g0 = H.ft_g0;
+        D.ft_e0 = H.ft_e0;
     }
     return PF_OK;
 }
@@ -923,6 +949,8 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int bl
     fs.nsm = ctx->num_sms;
     fs.mode = ctx->tune.factor;
     fs.blocks_per_sm = blocks_per_sm;
+    fs.tail = ctx->tune.tail != 2;
+    fs.smem_optin = ctx->smem_optin;
     e = counted(ctx, PF_K_FACTOR, 2, s, [&] {
         return launch_factor(m, prec, w.A[which], F, ctx->dc.ninst, w.fstatus[which][prec], fs, s);
     });

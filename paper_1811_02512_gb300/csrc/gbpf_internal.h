@@ -87,6 +87,13 @@ struct DevMat {
     int *PPp = nullptr, *PPc = nullptr, *ZP = nullptr;
     int tv_f = 0, tv_b = 0, tv_p = 0, tv_stride = 0;
     int *TVsrc = nullptr;
+    // Tail factor: the columns [t0, n) factorised by one block in shared
+    // memory, level by level.  Its gather targets are g0 + [0, ng) (g0 =
+    // Cp[t0] + t0), its L entries Lc[e0 + [0, ne)) (e0 = Cp[t0]); per target
+    // the A-value slot (tapos), its column (tcol) and the first of its gather
+    // terms whose column k is in the tail (gsplit; earlier terms have k < t0).
+    int ft_ng = 0, ft_ne = 0, ft_g0 = 0, ft_e0 = 0;
+    int *tapos = nullptr, *tcol = nullptr, *gsplit = nullptr;
     int *Ap = nullptr, *Aj = nullptr, *Apos = nullptr;  // off-diagonal A (no fill), by row:
                                                        // column and value slot of each entry
     // Newton-Raphson Jacobian (2 x 2 blocks on the same pattern, B' only)
@@ -128,6 +135,8 @@ struct HostMat {
     std::vector<Piece> pf2, pb2;
     std::vector<int> SKf, SIf, SKb, SIb, PPp, PPc, TVsrc;
     int tv_f = 0, tv_b = 0, tv_p = 0, tv_stride = 0;
+    int ft_ng = 0, ft_ne = 0, ft_g0 = 0, ft_e0 = 0;
+    std::vector<int> tapos, tcol, gsplit;
 };
 
 // Device arrays of the network and of the case batch.
@@ -268,6 +277,8 @@ struct FactorSync {
     int nsm = 0;
     int mode = 0;              // 0 auto, 1 dependency-driven, 2 block per instance
     int blocks_per_sm = 2;     // dependency-driven grid: blocks per SM
+    bool tail = true;          // factor the narrow top in one block (k_factor_tail) when it fits
+    size_t smem_optin = 0;
 };
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
                           int *fstatus, const FactorSync &fs, cudaStream_t s);

@@ -272,11 +272,11 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
 
 template <class T>
 __global__ void __launch_bounds__(kDepThreads)
-    k_factor_dep(DevMat m, const double *A, T *F, int *fstatus, int ninst, FactorSync fs) {
+    k_factor_dep(DevMat m, const double *A, T *F, int *fstatus, int ninst, FactorSync fs, int ncols) {
     __shared__ T terms_all[kDepThreads / 32][kDepChunk];
     const int lane = threadIdx.x & 31;
     T *terms = terms_all[threadIdx.x >> 5];
-    const unsigned total = unsigned(m.n) * unsigned(ninst);
+    const unsigned total = unsigned(ncols) * unsigned(ninst);
     const unsigned spin = fs.spin ? fs.spin : kDefaultSpin;
     for (;;) {
         unsigned idx = 0;
@@ -291,6 +291,83 @@ __global__ void __launch_bounds__(kDepThreads)
             atomicExch(fs.sync + 1, 1u);
             atomicCAS(fstatus + inst, PF_OK, PF_ERR_TIMEOUT);
         }
+    }
+}
+
+// The columns [t0, n) of one instance per block (the narrow top of the
+// elimination tree), after k_factor_dep has finished the columns below t0.
+// Shared memory holds the tail's L entries, D and one partial value per
+// gather target.  First every target subtracts, in parallel, its update
+// terms from columns below the tail (read from the factor in global
+// memory); then level by level each target subtracts the terms from tail
+// columns (shared memory), the diagonals are published, and the entries are
+// divided by them.  The order of operations of every entry is fixed.
+template <class T>
+__global__ void __launch_bounds__(kFactorThreads)
+    k_factor_tail(DevMat m, const double *A, T *F, int *fstatus, const double *amaxv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int inst = blockIdx.x;
+    const double *a = A + (long long)inst * m.stride;
+    T *v = F + (long long)inst * m.stride;
+    const T *Lc = v + m.offLc;
+    T *Lt = reinterpret_cast<T *>(smem_raw);
+    T *Dt = Lt + m.ft_ne;
+    T *part = Dt + m.nt;
+    const int t0 = m.t0, e0 = m.ft_e0, g0 = m.ft_g0;
+    for (int k = threadIdx.x; k < m.ft_ng; k += blockDim.x) {
+        const int g = g0 + k;
+        T s0 = T(0), s1 = T(0);
+        int q = m.gp[g];
+        const int qe = m.gsplit[k];
+        for (; q + 2 <= qe; q += 2) {
+            const int4 e = m.gl[q], f = m.gl[q + 1];
+            s0 += Lc[e.x] * (Lc[e.y] * v[e.z]);
+            s1 += Lc[f.x] * (Lc[f.y] * v[f.z]);
+        }
+        if (q < qe) {
+            const int4 e = m.gl[q];
+            s0 += Lc[e.x] * (Lc[e.y] * v[e.z]);
+        }
+        part[k] = T(a[m.tapos[k]]) - (s0 + s1);
+    }
+    __syncthreads();
+    int bad = PF_OK;
+    const double tol = 1e-14 * amaxv[inst];
+    for (int l = m.nlev - m.ntl; l < m.nlev; l++) {
+        const int cb = m.lvl_ptr[l], ce = m.lvl_ptr[l + 1];
+        const int kb = m.Cp[cb] + cb - g0, ke = m.Cp[ce] + ce - g0;
+        for (int k = kb + int(threadIdx.x); k < ke; k += blockDim.x) {
+            T s = T(0);
+            for (int q = m.gsplit[k]; q < m.gp[g0 + k + 1]; q++) {
+                const int4 e = m.gl[q];
+                s += Lt[e.x - e0] * (Lt[e.y - e0] * Dt[e.z - t0]);
+            }
+            part[k] -= s;
+        }
+        __syncthreads();
+        for (int c = cb + int(threadIdx.x); c < ce; c += blockDim.x) {
+            const T d = part[m.Cp[c] + c - g0];
+            Dt[c - t0] = d;
+            const double dd = double(d);
+            if (!isfinite(dd)) bad = PF_ERR_NONFINITE;
+            else if (fabs(dd) <= tol && bad == PF_OK) bad = PF_ERR_SINGULAR;
+        }
+        __syncthreads();
+        for (int k = kb + int(threadIdx.x); k < ke; k += blockDim.x) {
+            const int c = m.tcol[k];
+            const int t = k - (m.Cp[c] + c - g0);
+            if (t > 0) Lt[m.Cp[c] + t - 1 - e0] = part[k] / Dt[c - t0];
+        }
+        __syncthreads();
+    }
+    if (bad != PF_OK) atomicCAS(fstatus + inst, PF_OK, bad);
+    for (int c = t0 + int(threadIdx.x); c < m.n; c += blockDim.x) {
+        v[c] = Dt[c - t0];
+        v[m.offDi + c] = T(1) / Dt[c - t0];
+    }
+    for (int e = threadIdx.x; e < m.ft_ne; e += blockDim.x) {
+        v[m.offLc + e0 + e] = Lt[e];
+        v[m.offLr + m.Cpos[e0 + e]] = Lt[e];
     }
 }
 
@@ -912,17 +989,37 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
     const bool dep = fs.mode == 1 || (fs.mode == 0 && ninst < fs.nsm / 2);
     if (dep && m.max_col <= kDepMaxCol && total < (1ll << 31) && fs.done) {
         k_factor_prep<<<ninst, 256, 0, s>>>(m, A, fstatus, fs);
+        const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
+        const size_t tsmem = elt * (size_t(m.ft_ne) + size_t(m.nt) + size_t(m.ft_ng));
+        const bool tail = fs.tail && m.ft_ng > 0 && tsmem + 1024 <= fs.smem_optin;
+        const int ncols = tail ? m.t0 : m.n;
         const int per_sm = fs.blocks_per_sm > 0 && fs.blocks_per_sm < 2 ? fs.blocks_per_sm : 2;  // resident blocks per SM (registers)
-        long long blocks = (total + kDepThreads / 32 - 1) / (kDepThreads / 32);
+        long long blocks = ((long long)ncols * ninst + kDepThreads / 32 - 1) / (kDepThreads / 32);
         if (blocks > (long long)fs.nsm * per_sm) blocks = (long long)fs.nsm * per_sm;
         if (blocks < 1) blocks = 1;
-        if (prec == PF_FP64)
-            k_factor_dep<double><<<int(blocks), kDepThreads, 0, s>>>(m, A, static_cast<double *>(F),
-                                                                      fstatus, ninst, fs);
-        else
-            k_factor_dep<float><<<int(blocks), kDepThreads, 0, s>>>(m, A, static_cast<float *>(F),
-                                                                     fstatus, ninst, fs);
-        return cudaGetLastError();
+        cudaError_t e = cudaSuccess;
+        if (prec == PF_FP64) {
+            if (ncols > 0)
+                k_factor_dep<double><<<int(blocks), kDepThreads, 0, s>>>(m, A, static_cast<double *>(F),
+                                                                          fstatus, ninst, fs, ncols);
+            if (tail) {
+                e = cudaFuncSetAttribute(k_factor_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
+                if (e == cudaSuccess)
+                    k_factor_tail<double><<<ninst, kFactorThreads, tsmem, s>>>(m, A, static_cast<double *>(F),
+                                                                               fstatus, fs.amax);
+            }
+        } else {
+            if (ncols > 0)
+                k_factor_dep<float><<<int(blocks), kDepThreads, 0, s>>>(m, A, static_cast<float *>(F),
+                                                                         fstatus, ninst, fs, ncols);
+            if (tail) {
+                e = cudaFuncSetAttribute(k_factor_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
+                if (e == cudaSuccess)
+                    k_factor_tail<float><<<ninst, kFactorThreads, tsmem, s>>>(m, A, static_cast<float *>(F),
+                                                                              fstatus, fs.amax);
+            }
+        }
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     const int threads = kFactorThreads;
     if (prec == PF_FP64) {
