@@ -252,6 +252,26 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
             while (q < H.gp[g + 1] && H.gl[q].z < t0) q++;
             H.gsplit[k] = q;
         }
+    // the tail terms, packed with 16-bit positions (the tail factor is only
+    // used when the tail has fewer than 65,536 entries)
+    H.tptr.assign(size_t(std::max(1, H.ft_ng)) + 1, 0);
+    H.tterm.clear();
+    H.ft_tmax = 0;
+    if (H.ft_ne < 65536) {
+        for (int k = 0; k < H.ft_ng; k++) {
+            for (int q = H.gsplit[k]; q < H.gp[H.ft_g0 + k + 1]; q++) {
+                const int4 e = H.gl[q];
+                H.tterm.push_back(int2{(e.x - H.ft_e0) | ((e.y - H.ft_e0) << 16), e.z - t0});
+            }
+            H.tptr[k + 1] = int(H.tterm.size());
+        }
+        if (H.tterm.empty()) H.tterm.push_back(int2{0, 0});
+        for (int l = H.nlev - H.ntl; l < H.nlev; l++) {
+            const int kb = H.Cp[H.lvl_ptr[l]] + H.lvl_ptr[l] - H.ft_g0;
+            const int ke = H.Cp[H.lvl_ptr[l + 1]] + H.lvl_ptr[l + 1] - H.ft_g0;
+            H.ft_tmax = std::max(H.ft_tmax, H.tptr[ke] - H.tptr[kb]);
+        }
+    }
     auto pad32 = [](int64_t v) { return int((v + 31) / 32 * 32); };
     H.tv_f = 0;
     H.tv_b = pad32(int64_t(posf.size()));
@@ -731,6 +751,10 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
         TRY(upload_padded(ctx, &D.tapos, H.tapos));
         TRY(upload_padded(ctx, &D.tcol, H.tcol));
         TRY(upload_padded(ctx, &D.gsplit, H.gsplit));
+        TRY(upload_padded(ctx, &D.tptr, H.tptr));
+        if (H.tterm.empty()) return fail(ctx, PF_ERR_ARG, "internal: tail terms");
+        TRY(upload(ctx, &D.tterm, H.tterm.data(), H.tterm.size()));
+        D.ft_tmax = H.ft_ne < 65536 ? H.ft_tmax : -1;
         D.ft_ng = H.ft_ng;
         D.ft_ne = H.ft_ne;
         D.ft_g0 = H.ft_g0;

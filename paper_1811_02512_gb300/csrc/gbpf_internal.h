@@ -94,6 +94,11 @@ struct DevMat {
     // terms whose column k is in the tail (gsplit; earlier terms have k < t0).
     int ft_ng = 0, ft_ne = 0, ft_g0 = 0, ft_e0 = 0;
     int *tapos = nullptr, *tcol = nullptr, *gsplit = nullptr;
+    // the tail terms alone, packed {(x - e0) | (y - e0) << 16, k - t0}, by
+    // target (tptr[ng + 1]); ft_tmax = most terms of one tail level
+    int2 *tterm = nullptr;
+    int *tptr = nullptr;
+    int ft_tmax = 0;
     int *Ap = nullptr, *Aj = nullptr, *Apos = nullptr;  // off-diagonal A (no fill), by row:
                                                        // column and value slot of each entry
     // Newton-Raphson Jacobian (2 x 2 blocks on the same pattern, B' only)
@@ -136,7 +141,9 @@ struct HostMat {
     std::vector<int> SKf, SIf, SKb, SIb, PPp, PPc, TVsrc;
     int tv_f = 0, tv_b = 0, tv_p = 0, tv_stride = 0;
     int ft_ng = 0, ft_ne = 0, ft_g0 = 0, ft_e0 = 0;
-    std::vector<int> tapos, tcol, gsplit;
+    std::vector<int> tapos, tcol, gsplit, tptr;
+    std::vector<int2> tterm;
+    int ft_tmax = 0;
 };
 
 // Device arrays of the network and of the case batch.

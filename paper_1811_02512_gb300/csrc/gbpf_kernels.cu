@@ -296,24 +296,30 @@ __global__ void __launch_bounds__(kDepThreads)
 
 // The columns [t0, n) of one instance per block (the narrow top of the
 // elimination tree), after k_factor_dep has finished the columns below t0.
-// Shared memory holds the tail's L entries, D and one partial value per
-// gather target.  First every target subtracts, in parallel, its update
-// terms from columns below the tail (read from the factor in global
-// memory); then level by level each target subtracts the terms from tail
-// columns (shared memory), the diagonals are published, and the entries are
-// divided by them.  The order of operations of every entry is fixed.
+// Shared memory holds the tail's L entries, D, one partial value per gather
+// target and two buffers of packed tail terms.  First every target
+// subtracts, in parallel, its update terms from columns below the tail (read
+// from the factor in global memory); then level by level each target
+// subtracts its terms from tail columns (shared memory; the level's terms
+// were staged while the previous level was computed), the diagonals are
+// published, and the entries are divided by them.  The order of operations
+// of every entry is fixed.
 template <class T>
 __global__ void __launch_bounds__(kFactorThreads)
     k_factor_tail(DevMat m, const double *A, T *F, int *fstatus, const double *amaxv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int R = 4;  // terms per thread prefetched into registers
     const int inst = blockIdx.x;
     const double *a = A + (long long)inst * m.stride;
     T *v = F + (long long)inst * m.stride;
     const T *Lc = v + m.offLc;
-    T *Lt = reinterpret_cast<T *>(smem_raw);
+    const int tmax = m.ft_tmax;
+    int2 *tbuf = reinterpret_cast<int2 *>(smem_raw);
+    T *Lt = reinterpret_cast<T *>(smem_raw + sizeof(int2) * 2 * size_t(tmax));
     T *Dt = Lt + m.ft_ne;
     T *part = Dt + m.nt;
     const int t0 = m.t0, e0 = m.ft_e0, g0 = m.ft_g0;
+    const int l0 = m.nlev - m.ntl;
     for (int k = threadIdx.x; k < m.ft_ng; k += blockDim.x) {
         const int g = g0 + k;
         T s0 = T(0), s1 = T(0);
@@ -330,20 +336,53 @@ __global__ void __launch_bounds__(kFactorThreads)
         }
         part[k] = T(a[m.tapos[k]]) - (s0 + s1);
     }
+    auto kfirst = [&](int l) { return m.Cp[m.lvl_ptr[l]] + m.lvl_ptr[l] - g0; };
+    {
+        const int tb = m.tptr[kfirst(l0)], te = m.tptr[kfirst(l0 + 1)];
+        for (int i = threadIdx.x; i < te - tb; i += blockDim.x) tbuf[i] = m.tterm[tb + i];
+    }
     __syncthreads();
     int bad = PF_OK;
     const double tol = 1e-14 * amaxv[inst];
-    for (int l = m.nlev - m.ntl; l < m.nlev; l++) {
+    for (int l = l0; l < m.nlev; l++) {
+        const int cur = (l - l0) & 1;
+        const int2 *buf = tbuf + cur * tmax;
+        int2 *nbuf = tbuf + (cur ^ 1) * tmax;
         const int cb = m.lvl_ptr[l], ce = m.lvl_ptr[l + 1];
-        const int kb = m.Cp[cb] + cb - g0, ke = m.Cp[ce] + ce - g0;
-        for (int k = kb + int(threadIdx.x); k < ke; k += blockDim.x) {
-            T s = T(0);
-            for (int q = m.gsplit[k]; q < m.gp[g0 + k + 1]; q++) {
-                const int4 e = m.gl[q];
-                s += Lt[e.x - e0] * (Lt[e.y - e0] * Dt[e.z - t0]);
-            }
-            part[k] -= s;
+        const int kb = kfirst(l), ke = kfirst(l + 1);
+        const int tb = m.tptr[kb];
+        const bool more = l + 1 < m.nlev;
+        const int ntb = more ? m.tptr[ke] : 0, nte = more ? m.tptr[kfirst(l + 2)] : 0;
+        int2 pre[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int i = int(threadIdx.x) + r * int(blockDim.x);
+            if (i < nte - ntb) pre[r] = m.tterm[ntb + i];
         }
+        for (int k = kb + int(threadIdx.x); k < ke; k += blockDim.x) {
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            int q = m.tptr[k] - tb;
+            const int qe = m.tptr[k + 1] - tb;
+            auto term = [&](int2 u) {
+                const unsigned w = unsigned(u.x);
+                return Lt[w & 0xffffu] * (Lt[w >> 16] * Dt[u.y]);
+            };
+            for (; q + 4 <= qe; q += 4) {
+                s0 += term(buf[q]);
+                s1 += term(buf[q + 1]);
+                s2 += term(buf[q + 2]);
+                s3 += term(buf[q + 3]);
+            }
+            for (; q < qe; q++) s0 += term(buf[q]);
+            part[k] -= (s0 + s1) + (s2 + s3);
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int i = int(threadIdx.x) + r * int(blockDim.x);
+            if (i < nte - ntb) nbuf[i] = pre[r];
+        }
+        for (int i = int(threadIdx.x) + R * int(blockDim.x); i < nte - ntb; i += blockDim.x)
+            nbuf[i] = m.tterm[ntb + i];
         __syncthreads();
         for (int c = cb + int(threadIdx.x); c < ce; c += blockDim.x) {
             const T d = part[m.Cp[c] + c - g0];
@@ -990,8 +1029,9 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
     if (dep && m.max_col <= kDepMaxCol && total < (1ll << 31) && fs.done) {
         k_factor_prep<<<ninst, 256, 0, s>>>(m, A, fstatus, fs);
         const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
-        const size_t tsmem = elt * (size_t(m.ft_ne) + size_t(m.nt) + size_t(m.ft_ng));
-        const bool tail = fs.tail && m.ft_ng > 0 && tsmem + 1024 <= fs.smem_optin;
+        const size_t tsmem = elt * (size_t(m.ft_ne) + size_t(m.nt) + size_t(m.ft_ng)) +
+                             sizeof(int2) * 2 * size_t(m.ft_tmax > 0 ? m.ft_tmax : 0);
+        const bool tail = fs.tail && m.ft_ng > 0 && m.ft_tmax >= 0 && tsmem + 1024 <= fs.smem_optin;
         const int ncols = tail ? m.t0 : m.n;
         const int per_sm = fs.blocks_per_sm > 0 && fs.blocks_per_sm < 2 ? fs.blocks_per_sm : 2;  // resident blocks per SM (registers)
         long long blocks = ((long long)ncols * ninst + kDepThreads / 32 - 1) / (kDepThreads / 32);
