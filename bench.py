@@ -13,6 +13,11 @@ Workloads (seeded synthetic grids, see paper_1811_02512_gb300/gridgen.py):
   plain10k   one 10,000-bus pruned-Delaunay grid, FP64 (default)
   batch10k   the same topology with 1,024 cases (512 load scenarios, 512
              single-branch outages) in one launch
+  plain120   the 120-bus grid, FP64 (the small single-case configuration)
+  adjoint20k one 20,000-bus grid: Newton-Raphson to tolerance, the objective
+             sum (V - 1)^2 + losses and its adjoint gradient w.r.t. every P/Q
+             injection (reusing the Newton factors), FP64; a step is 1 PF + 1
+             gradient
   pack256    256 grids of 2,000 to 80,000 buses (log-uniform), each with its
              own ordering and levels, in one packed launch (pf_pack_run, FP32
              factor + FP64 refinement); the same grids solved one after the
@@ -47,7 +52,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbpf", choices=["gbpf", "reference"])
-    ap.add_argument("--workload", default="plain10k", choices=["plain10k", "batch10k", "pack256"])
+    ap.add_argument("--workload", default="plain10k",
+                    choices=["plain10k", "batch10k", "plain120", "adjoint20k", "pack256"])
     ap.add_argument("--ngrid", type=int, default=256, help="pack256: number of grids (first n)")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
     ap.add_argument("--method", default="fdpf", choices=["fdpf", "nr"])
@@ -72,6 +78,8 @@ def dist_env():
 
 def make_workload(name, ncase=1024):
     from paper_1811_02512_gb300 import gridgen
+    if name == "plain120":
+        return gridgen.config(0), 1, None, None
     base = gridgen.config(1)
     if name == "plain10k":
         return base, 1, None, None
@@ -82,7 +90,7 @@ def make_workload(name, ncase=1024):
 def workload_precision(name, override):
     if override:
         return override
-    return "fp64" if name == "plain10k" else "fp32"
+    return "fp32" if name in ("batch10k", "pack256") else "fp64"
 
 
 # ------------------------------------------------------------------ clocks
@@ -189,8 +197,8 @@ def _oracle_job(args):
     import numpy as np  # noqa: F401
     from oracle import oracle as O
     from paper_1811_02512_gb300 import gridgen
-    case_ids, deadline = args
-    base = gridgen.config(1)
+    case_ids, deadline, workload = args
+    base = gridgen.config(0 if workload == "plain120" else 1)
     sc = None
     if case_ids is not None and any(c is not None for c in case_ids):
         sc = gridgen.scenarios(base, n_load=512, n_outage=512)
@@ -214,10 +222,10 @@ def cpu_baseline(workload, sample_s, ncase):
     O.build()
     cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
-    per = max(1, int(sample_s / 0.03))  # more than the budget; the deadline stops it
+    per = max(1, int(sample_s / 0.0005))  # more than the budget; the deadline stops it
     jobs = []
     for w in range(cores):
-        if workload == "plain10k":
+        if workload in ("plain10k", "plain120"):
             ids = [None] * per
         else:
             ids = [(w + cores * k) % ncase for k in range(per)]
@@ -225,11 +233,11 @@ def cpu_baseline(workload, sample_s, ncase):
     t0 = time.perf_counter()
     deadline = time.perf_counter() + sample_s
     with ctx.Pool(cores) as pool:
-        out = pool.map(_oracle_job, [(j, deadline) for j in jobs])
+        out = pool.map(_oracle_job, [(j, deadline, workload) for j in jobs])
     wall = time.perf_counter() - t0
     solved = sum(o[0] for o in out)
     return {"value": solved / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{solved} {'10k-bus' if workload == 'plain10k' else 'batch10k'} cases "
+            "sample": f"{solved} {dict(plain10k='10k-bus', plain120='120-bus').get(workload, 'batch10k')} cases "
                       f"(FP64 FDPF incl. ordering/symbolic/factor) across {cores} processes "
                       f"in {wall:.1f} s"}
 
@@ -260,6 +268,24 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def aggregate_ranks(total_ms, solves_local, world, device):
+    """Whole-job throughput of a weak-scaling run: every rank solved
+    solves_local cases; the job time is the slowest rank's (max over ranks,
+    the only collective).  Returns (max ms, total solves, solves/s)."""
+    import torch
+    t = torch.tensor([total_ms, float(solves_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms, solves = float(tmax.item()), float(tsum.item())
+    else:
+        solves = float(solves_local)
+    return total_ms, solves, solves / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------------ uneven multi-grid batch
 
 def _pack_case(g):
@@ -274,6 +300,95 @@ def pack_cases(ngrid):
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(ngrid, os.cpu_count() or 1)) as pool:
         return pool.map(_pack_case, range(ngrid))
+
+
+def run_adjoint(args, dev, local, world, rank):
+    """adjoint20k: per step Newton-Raphson from flat start to tolerance, the
+    objective and the adjoint gradient (all through the C ABI)."""
+    import torch
+    from paper_1811_02512_gb300 import gbpf, gridgen
+    case = gridgen.config(3)
+    t0 = time.perf_counter()
+    g = gbpf.Grid(case)
+    analyze_ms = (time.perf_counter() - t0) * 1e3
+    g.set_cases(1)
+    prec_name = args.precision or "fp64"
+    prec = gbpf.PF_FP64 if prec_name == "fp64" else gbpf.PF_FP32
+    opts = gbpf.run_opts(gbpf.PF_NR, prec, tol=TOL, max_iter=20)
+    vm = torch.zeros((1, case.n), dtype=torch.float64, device=dev)
+    va = torch.zeros_like(vm)
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    gva, gvm = torch.zeros_like(vm), torch.zeros_like(vm)
+    dP, dQ = torch.zeros_like(vm), torch.zeros_like(vm)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(int(2.5 * 129e6) // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, 1, stream=stream)
+        gbpf.pf_objective(g.ctx, vm, va, J, gva, gvm, stream=stream)
+        gbpf.pf_adjoint(g.ctx, prec, vm, va, gva, gvm, dP, dQ, 1, stream=stream)
+        return st, res
+
+    for _ in range(max(3, args.warmup)):
+        st, res = step()
+    torch.cuda.synchronize()
+    gbpf.pf_set_profiling(g.ctx, True)
+    for k in range(7):
+        gbpf.pf_get_profile(g.ctx, k, reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms = 0.0
+    ok = 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, res = step()
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+        ok += int(res["status"][0] == gbpf.PF_OK)
+    clk = clocks.stop()
+    prof, launches = {}, 0
+    for k, nm in enumerate(gbpf.KERNEL_KINDS):
+        n, ms = gbpf.pf_get_profile(g.ctx, k, reset=True)
+        prof[nm] = ms
+        launches += n
+    gbpf.pf_set_profiling(g.ctx, False)
+    total_ms, _, value = aggregate_ranks(total_ms, ok, world, dev)
+    # end to end: specified injections from pinned host memory, gradient back
+    psp = torch.from_numpy((case.pg - case.pd)[None].copy()).pin_memory()
+    qsp = torch.from_numpy((-case.qd)[None].copy()).pin_memory()
+    psp_d, qsp_d = torch.empty_like(vm), torch.empty_like(vm)
+    out = torch.empty((2, case.n), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        psp_d.copy_(psp, non_blocking=True)
+        qsp_d.copy_(qsp, non_blocking=True)
+        gbpf.pf_set_injections(g.ctx, psp_d, qsp_d, stream=stream)
+        st, res = step()
+        out[0].copy_(dP[0], non_blocking=True)
+        out[1].copy_(dQ[0], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_val = e2e_steps / (time.perf_counter() - te0)
+    line = {"metric": METRIC, "value": value, "unit": "(PF + gradient)/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == gbpf.PF_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": "adjoint20k", "nbus": case.n, "nbranch": case.m,
+                       "precision": prec_name, "tol_pu": TOL, "method": "nr+adjoint",
+                       "l2": "flushed between timed steps (2.5x L2 buffer write)",
+                       "loading_factor": case.lam, "analyze_ms": analyze_ms},
+            "converged": ok, "iters": int(res["iters"][0]), "gpu_launches": launches,
+            "kernel_ms": prof, "roofline": None, "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": "(PF + gradient)/s",
+                    "h2d_bytes_per_step": int(2 * 8 * case.n), "d2h_bytes_per_step": int(2 * 8 * case.n)}}
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
 
 
 def run_pack(args, dev, local, world, rank):
@@ -329,7 +444,7 @@ def run_pack(args, dev, local, world, rank):
         gbpf.pf_set_profiling(g.ctx, False)
     launches += args.steps  # the packed iteration launch of each step
     converged = int(np.sum(res["status"] == gbpf.PF_OK))
-    value = converged * args.steps * world / (total_ms / 1e3)
+    total_ms, _, value = aggregate_ranks(total_ms, converged * args.steps, world, dev)
     run_ms = max(1e-6, (total_ms - other_ms) / args.steps)
     # the same grids one after the other by the plain FP64 path
     seq_opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=TOL, max_iter=200)
@@ -433,8 +548,8 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_1811_02512_gb300 import gbpf
-    if args.workload == "pack256":
-        run_pack(args, dev, local, world, rank)
+    if args.workload in ("pack256", "adjoint20k"):
+        (run_pack if args.workload == "pack256" else run_adjoint)(args, dev, local, world, rank)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -500,12 +615,7 @@ def main():
         launches += n
     gbpf.pf_set_profiling(g.ctx, False)
 
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    solves = converged * args.steps * world
-    value = solves / (total_ms / 1e3)
+    total_ms, solves, value = aggregate_ranks(total_ms, converged * args.steps, world, dev)
 
     # end to end through the C ABI with host buffers: per step copy the case
     # inputs (load scales, outages) from pinned host memory, run, copy V back
