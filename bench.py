@@ -16,7 +16,8 @@ Workloads (seeded synthetic grids, see paper_1811_02512_gb300/gridgen.py):
   plain120   the 120-bus grid, FP64 (the small single-case configuration)
   adjoint20k one 20,000-bus grid: Newton-Raphson to tolerance, the objective
              sum (V - 1)^2 + losses and its adjoint gradient w.r.t. every P/Q
-             injection (reusing the Newton factors), FP64; a step is 1 PF + 1
+             injection (reusing the Newton factors); FP32 factors with FP64
+             mismatch and FP64-refined solves by default; a step is 1 PF + 1
              gradient
   pack256    256 grids of 2,000 to 80,000 buses (log-uniform), each with its
              own ordering and levels, in one packed launch (pf_pack_run, FP32
@@ -90,7 +91,7 @@ def make_workload(name, ncase=1024):
 def workload_precision(name, override):
     if override:
         return override
-    return "fp32" if name in ("batch10k", "pack256") else "fp64"
+    return "fp32" if name in ("batch10k", "pack256", "adjoint20k") else "fp64"
 
 
 # ------------------------------------------------------------------ clocks
@@ -312,7 +313,7 @@ def run_adjoint(args, dev, local, world, rank):
     g = gbpf.Grid(case)
     analyze_ms = (time.perf_counter() - t0) * 1e3
     g.set_cases(1)
-    prec_name = args.precision or "fp64"
+    prec_name = workload_precision("adjoint20k", args.precision)
     prec = gbpf.PF_FP64 if prec_name == "fp64" else gbpf.PF_FP32
     opts = gbpf.run_opts(gbpf.PF_NR, prec, tol=TOL, max_iter=20)
     vm = torch.zeros((1, case.n), dtype=torch.float64, device=dev)

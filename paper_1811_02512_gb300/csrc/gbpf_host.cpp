@@ -1099,6 +1099,14 @@ pf_status ensure_nr_storage(pf_ctx *ctx, int prec) {
         }
     }
     if (!w.jfstat[prec]) TRY(dalloc(ctx, &w.jfstat[prec], size_t(ctx->dc.ncase)));
+    if (!w.jdone) {
+        const size_t nd = size_t(ctx->dc.ncase) * size_t(std::max(1, m.n));
+        TRY(dalloc(ctx, &w.jdone, nd));
+        TRY(dalloc(ctx, &w.jsync, size_t(2) * size_t(ctx->dc.ncase)));
+        cudaError_t e = cudaMemset(w.jdone, 0, nd * sizeof(unsigned));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "jacobian flags");
+        w.jepoch = 0;
+    }
     return PF_OK;
 }
 
@@ -1118,7 +1126,22 @@ NrLaunch nr_launch(pf_ctx *ctx, int prec) {
     L.res = w.res;
     L.smem_optin = ctx->smem_optin;
     L.cluster = nr_cluster_size(L.m, ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin);
+    L.jdone = w.jdone;
+    L.jsync = w.jsync;
     return L;
+}
+
+// Epochs for the Jacobian factorisations of one NR or adjoint launch (at
+// most `count`); the flags are cleared when the counter would wrap.
+unsigned nr_epochs(pf_ctx *ctx, unsigned count, cudaStream_t s) {
+    Workspace &w = ctx->ws;
+    if (w.jepoch > 0xF0000000u) {
+        cudaMemsetAsync(w.jdone, 0, size_t(ctx->dc.ncase) * size_t(std::max(1, ctx->dm[0].n)) * sizeof(unsigned), s);
+        w.jepoch = 0;
+    }
+    const unsigned e0 = w.jepoch;
+    w.jepoch += count;
+    return e0;
 }
 
 }  // namespace
@@ -1433,6 +1456,7 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
         L.o = *opts;
         L.vm = vm_dev;
         L.va = va_dev;
+        L.epoch0 = nr_epochs(ctx, unsigned(opts->max_iter) + 2u, s);
         cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] { return launch_nr(L, s); });
         if (e != cudaSuccess) return cuda_fail(ctx, e, "nr launch");
         ctx->ws.jfactored[prec] = true;
@@ -1533,6 +1557,7 @@ pf_status pf_adjoint(pf_ctx *ctx, int32_t precision, const double *vm_dev, const
     L.dJdQ = dJdQ_dev;
     L.adjoint = true;
     L.factor_now = ctx->ws.jfactored[precision] ? 0 : 1;
+    L.epoch0 = nr_epochs(ctx, 2u, s);
     cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] { return launch_nr(L, s); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     ctx->ws.jfactored[precision] = true;

@@ -228,6 +228,9 @@ struct Workspace {
     int *jfstat[2] = {nullptr, nullptr};
     bool jfactored[2] = {false, false};
     double *xg6 = nullptr;    // [ncase][6*nbus] Newton right-hand side, refined x, FP32 work
+    unsigned *jdone = nullptr;   // [ncase][n] Jacobian column done flags (epochs)
+    unsigned *jsync = nullptr;   // [ncase][2]
+    unsigned jepoch = 0;         // last epoch handed to a launch
     LaneSet lanes;
 };
 
@@ -364,6 +367,9 @@ struct NrLaunch {
     int cluster = 1;
     bool adjoint = false;
     int factor_now = 0;
+    unsigned *jdone = nullptr;  // [ncase][n] column done flags of the Jacobian factor
+    unsigned *jsync = nullptr;  // [ncase][2] column counter, abort flag
+    unsigned epoch0 = 0;        // factorisation k of this launch publishes epoch0 + k
 };
 cudaError_t launch_nr(const NrLaunch &L, cudaStream_t s);
 int nr_cluster_size(const DevMat &m, int ncase, int num_sms, int prec, size_t smem_optin);

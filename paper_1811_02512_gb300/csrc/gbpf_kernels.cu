@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kDepThreads)
 template <class T>
 __global__ void __launch_bounds__(kFactorThreads)
     k_factor_tail(DevMat m, const double *A, T *F, int *fstatus, const double *amaxv) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int R = 4;  // terms per thread prefetched into registers
     const int inst = blockIdx.x;
     const double *a = A + (long long)inst * m.stride;

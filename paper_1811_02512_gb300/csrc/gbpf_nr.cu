@@ -6,8 +6,8 @@
 // and levels).  The V unknown of a PV bus is pinned by an identity row and
 // column, which keeps the block pattern equal to the bus graph.  The
 // Jacobian is factorised without pivoting as J = L D U (unit block-lower L,
-// unit block-upper U, 2 x 2 block diagonal D), level by level with the same
-// left-looking update lists as the scalar LDL^T, and solved with the
+// unit block-upper U, 2 x 2 block diagonal D), column by column in level
+// order with the same gather lists as the scalar LDL^T, and solved with the
 // TMA-staged sweeps: J x = b uses L by rows and U by columns; J^T y = g uses
 // U^T by rows and L^T by columns with the same factors (the adjoint).
 #include "gbpf_device.cuh"
@@ -15,6 +15,8 @@
 namespace gbpf {
 
 namespace {
+
+constexpr int kNrChunkMax = 128;  // update terms staged per warp and pass in the block factor (at most)
 
 // ------------------------------------------------------------ 2 x 2 blocks
 
@@ -25,6 +27,12 @@ struct B2 {
 
 template <class T>
 __device__ __forceinline__ B2<T> ld2(const T *p) { return B2<T>{p[0], p[1], p[2], p[3]}; }
+
+// A block written by another SM during this launch: read through L2.
+template <class T>
+__device__ __forceinline__ B2<T> ldcg2(const T *p) {
+    return B2<T>{__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3)};
+}
 
 template <class T>
 __device__ __forceinline__ void st2(T *p, const B2<T> &m) {
@@ -109,6 +117,10 @@ struct NrArgs {
     const double *gva, *gvm;    // adjoint right-hand side per bus
     double *dJdP, *dJdQ;        // adjoint outputs per bus
     int use_smem;
+    unsigned *jdone;   // [ncase][n] column done flags
+    unsigned *jsync;   // [ncase][2] column counter, abort flag
+    unsigned epoch0;   // factorisation k of this launch publishes epoch0 + k
+    int fchunk;        // update terms staged per warp and pass (fits the shared memory)
 };
 
 // Rectangular voltages of the CTA's bus slice.
@@ -200,137 +212,159 @@ __device__ void nr_assemble(const NrArgs &a, int c, int s0, int s1) {
     }
 }
 
-// Block LDU factor of one Jacobian by one block (Section III.B with 2 x 2
-// blocks): left-looking, level by level; wide levels one warp per column,
-// narrow levels one column at a time with the warps' partial sums reduced in
-// warp order.  Column c gathers, from every descendant k in row c of L,
-//   A_ic -= L_ik (D_k U_kc)   (i >= c, the diagonal when i = c)
-//   A_ci -= (L_ck D_k) U_ki   (i > c)
-// then D_c = A_cc, L_ic = A_ic D_c^-1, U_ci = D_c^-1 A_ci.  The pivot check
-// is on det(D_c) against the largest diagonal-block entry.  Returns status.
-template <class T>
-__device__ int block_factor(const DevMat &m, const double *Aj, T *F, unsigned char *scratch,
-                            double *red) {
-    __shared__ int bad;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int sa = 8 * (m.max_col + 1);  // per-warp accumulator: L blocks then U blocks
-    T *accw = reinterpret_cast<T *>(scratch) + warp * sa;
-    T *fin = reinterpret_cast<T *>(scratch) + nwarps * sa;
+// Block LDU factor of the Jacobian of case c (Section III.B with 2 x 2
+// blocks, no pivoting; the pivot check is on det(D_c) against the largest
+// diagonal-block entry) by all C blocks of its cluster, driven by the
+// elimination tree's dependencies: every warp of the cluster takes
+// columns in level order from a counter, waits until the columns of row c of
+// L are done (their flags hold `epoch`), then computes each target block of
+// column c with a lane per target from the gather lists of the pattern
+// (Section III.B, 2 x 2 blocks),
+//   A_ic - sum_k L_ik (D_k U_kc),  A_ci - sum_k (L_ck D_k) U_ki,
+// publishes D_c, D_c^-1, L_ic = A_ic D_c^-1, U_ci = D_c^-1 A_ci (by column
+// and by row) and its own flag.  Every wait is bounded; one that gives up
+// raises the case's abort flag.  Cluster-uniform status.
+template <class T, int C>
+__device__ int cluster_block_factor(const NrArgs &a, int c, int rank, T *F, const double *Aj,
+                                    unsigned char *scratch, double *red, unsigned epoch) {
+    const DevMat &m = a.m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int chunk = a.fchunk;
+    const int sa = 8 * (m.max_col + 1) + 8 * chunk;
+    T *accL = reinterpret_cast<T *>(scratch) + warp * sa;
+    T *accU = accL + 4 * (m.max_col + 1);
+    T *termL = accU + 4 * (m.max_col + 1);
+    T *termU = termL + 4 * chunk;
     T *D = F + m.jD, *Di = F + m.jDi, *Lc = F + m.jLc, *Uc = F + m.jUc;
-    if (threadIdx.x == 0) bad = PF_OK;
+    T *Lr = F + m.jLr, *Ur = F + m.jUr;
+    unsigned *done = a.jdone + (long long)c * m.n;
+    unsigned *ctr = a.jsync + 2LL * c, *abort_flag = ctr + 1;
+    // pivot tolerance: largest diagonal-block entry over the cluster
+    const int nd = 4 * m.n, slice = (nd + C - 1) / C;
     double amax = 0.0;
-    for (int j = threadIdx.x; j < 4 * m.n; j += blockDim.x) amax = fmax(amax, fabs(Aj[m.jD + j]));
+    for (int j = rank * slice + int(threadIdx.x); j < min(nd, (rank + 1) * slice); j += blockDim.x)
+        amax = fmax(amax, fabs(Aj[m.jD + j]));
     amax = block_max(amax, red);
+    if (threadIdx.x == 0) {
+        a.bmax[(long long)c * 16 + rank] = amax;
+        if (rank == 0) {
+            *ctr = 0u;
+            *abort_flag = 0u;
+            a.fstat[c] = PF_OK;
+        }
+    }
+    cluster_sync<C>();
+    amax = 0.0;
+    for (int r = 0; r < C; r++) amax = fmax(amax, a.bmax[(long long)c * 16 + r]);
     const double piv = 1e-14 * amax * amax;
-    auto finalize = [&](int c, const T *accL, const T *accU, int cnt, int first, int step) {
+    for (;;) {
+        unsigned col = 0;
+        if (lane == 0) col = atomicAdd(ctr, 1u);
+        col = __shfl_sync(0xffffffffu, col, 0);
+        if (col >= unsigned(m.n)) break;
+        const int cc = int(col);
+        bool ok = true;
+        for (int q = m.Fp[cc] + lane; q < m.Fp[cc + 1] && ok; q += 32) {
+            const unsigned *f = done + m.Fc[q];
+            unsigned it = 0;
+            unsigned v;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+                if (v == epoch) break;
+                if (++it > a.spin || *reinterpret_cast<volatile unsigned *>(abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicExch(abort_flag, 1u);
+                atomicCAS(a.fstat + c, PF_OK, PF_ERR_TIMEOUT);
+            }
+            continue;
+        }
+        const int c0 = m.Cp[cc], cnt = m.Cp[cc + 1] - c0, tb = c0 + cc;
+        for (int t = lane; t <= cnt; t += 32) {
+            const double *src = t == 0 ? Aj + m.jD + 4 * cc : Aj + m.jLc + 4 * (c0 + t - 1);
+            st2(accL + 4 * t, B2<T>{T(src[0]), T(src[1]), T(src[2]), T(src[3])});
+            if (t > 0) {
+                const double *us = Aj + m.jUc + 4 * (c0 + t - 1);
+                st2(accU + 4 * t, B2<T>{T(us[0]), T(us[1]), T(us[2]), T(us[3])});
+            }
+        }
+        // the column's update terms, a chunk at a time: evaluated with the
+        // whole warp (a lane per term) into shared memory, then summed per
+        // target with a lane per target in list order
+        const int gb = m.gp[tb], ge = m.gp[tb + cnt + 1];
+        for (int cb = gb; cb < ge; cb += chunk) {
+            const int ce = min(ge, cb + chunk);
+            // four terms per lane in flight: their indices, then their blocks
+            for (int g0 = cb + lane; g0 < ce; g0 += 128) {
+                int4 e[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (g0 + 32 * u < ce) e[u] = __ldg(m.gl + g0 + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int g = g0 + 32 * u;
+                    if (g >= ce) continue;
+                    const B2<T> Lx = ldcg2(Lc + 4 * e[u].x), Dk = ldcg2(D + 4 * e[u].z);
+                    const B2<T> Uy = ldcg2(Uc + 4 * e[u].y), Ly = ldcg2(Lc + 4 * e[u].y);
+                    const B2<T> Ux = ldcg2(Uc + 4 * e[u].x);
+                    st2(termL + 4 * (g - cb), mul2(Lx, mul2(Dk, Uy)));
+                    st2(termU + 4 * (g - cb), mul2(mul2(Ly, Dk), Ux));
+                }
+            }
+            __syncwarp();
+            for (int t = lane; t <= cnt; t += 32) {
+                const int lo = max(m.gp[tb + t], cb), hi = min(m.gp[tb + t + 1], ce);
+                if (lo >= hi) continue;
+                B2<T> sl{T(0), T(0), T(0), T(0)}, su{T(0), T(0), T(0), T(0)};
+                for (int g = lo; g < hi; g++) {
+                    const B2<T> a2 = ld2(termL + 4 * (g - cb)), b2 = ld2(termU + 4 * (g - cb));
+                    sl.a += a2.a; sl.b += a2.b; sl.c += a2.c; sl.d += a2.d;
+                    su.a += b2.a; su.b += b2.b; su.c += b2.c; su.d += b2.d;
+                }
+                T *al = accL + 4 * t;
+                al[0] -= sl.a; al[1] -= sl.b; al[2] -= sl.c; al[3] -= sl.d;
+                if (t > 0) {
+                    T *au = accU + 4 * t;
+                    au[0] -= su.a; au[1] -= su.b; au[2] -= su.c; au[3] -= su.d;
+                }
+            }
+            __syncwarp();
+        }
         const B2<T> Dc = ld2(accL);
         const T det = Dc.a * Dc.d - Dc.b * Dc.c;
         const B2<T> inv{Dc.d / det, -Dc.b / det, -Dc.c / det, Dc.a / det};
-        if (first == 0) {
-            st2(D + 4 * c, Dc);
-            st2(Di + 4 * c, inv);
+        if (lane == 0) {
+            st2(D + 4 * cc, Dc);
+            st2(Di + 4 * cc, inv);
             const double dd = double(det);
             if (!isfinite(dd) || !isfinite(double(Dc.a)) || !isfinite(double(Dc.d)))
-                atomicCAS(&bad, PF_OK, PF_ERR_NONFINITE);
+                atomicCAS(a.fstat + c, PF_OK, PF_ERR_NONFINITE);
             else if (fabs(dd) <= piv)
-                atomicCAS(&bad, PF_OK, PF_ERR_SINGULAR);
+                atomicCAS(a.fstat + c, PF_OK, PF_ERR_SINGULAR);
         }
-        const int c0 = m.Cp[c];
-        for (int t = first; t < cnt; t += step) {
-            st2(Lc + 4 * (c0 + t), mul2(ld2(accL + 4 * (1 + t)), inv));
-            st2(Uc + 4 * (c0 + t), mul2(inv, ld2(accU + 4 * (1 + t))));
+        for (int t = lane; t < cnt; t += 32) {
+            const B2<T> L = mul2(ld2(accL + 4 * (1 + t)), inv);
+            const B2<T> U = mul2(inv, ld2(accU + 4 * (1 + t)));
+            st2(Lc + 4 * (c0 + t), L);
+            st2(Uc + 4 * (c0 + t), U);
+            const int q = m.Cpos[c0 + t];
+            st2(Lr + 4 * q, L);
+            st2(Ur + 4 * q, U);
         }
-    };
-    for (int lev = 0; lev < m.nlev; lev++) {
-        const int cb = m.lvl_ptr[lev], c1 = m.lvl_ptr[lev + 1];
-        if (c1 - cb > kNarrowRows) {
-            for (int c = cb + warp; c < c1; c += nwarps) {
-                const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0;
-                T *accL = accw, *accU = accw + 4 * (m.max_col + 1);
-                for (int t = lane; t <= cnt; t += 32) {
-                    const double *src = t == 0 ? Aj + m.jD + 4 * c : Aj + m.jLc + 4 * (c0 + t - 1);
-                    for (int q = 0; q < 4; q++) accL[4 * t + q] = T(src[q]);
-                    if (t > 0)
-                        for (int q = 0; q < 4; q++) accU[4 * t + q] = T(Aj[m.jUc + 4 * (c0 + t - 1) + q]);
-                }
-                __syncwarp();
-                for (int q = m.Fp[c]; q < m.Fp[c + 1]; q++) {
-                    const int k = m.Fc[q], pkc = m.Fpos[q];
-                    const B2<T> Dk = ld2(D + 4 * k);
-                    const B2<T> M1 = mul2(Dk, ld2(Uc + 4 * pkc));   // D_k U_kc
-                    const B2<T> M2 = mul2(ld2(Lc + 4 * pkc), Dk);   // L_ck D_k
-                    const int len = m.Cp[k + 1] - pkc, o = m.uoff[q];
-                    for (int t = lane; t < len; t += 32) {
-                        const int tg = m.umap[o + t];
-                        const B2<T> lo = mul2(ld2(Lc + 4 * (pkc + t)), M1);
-                        T *al = accL + 4 * tg;
-                        al[0] -= lo.a; al[1] -= lo.b; al[2] -= lo.c; al[3] -= lo.d;
-                        if (t > 0) {
-                            const B2<T> up = mul2(M2, ld2(Uc + 4 * (pkc + t)));
-                            T *au = accU + 4 * tg;
-                            au[0] -= up.a; au[1] -= up.b; au[2] -= up.c; au[3] -= up.d;
-                        }
-                    }
-                    __syncwarp();
-                }
-                finalize(c, accL, accU, cnt, lane, 32);
-                __syncwarp();
-            }
-        } else {
-            for (int c = cb; c < c1; c++) {
-                const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0;
-                T *accL = accw, *accU = accw + 4 * (m.max_col + 1);
-                for (int t = lane; t < 8 * (cnt + 1); t += 32) accw[t < 4 * (cnt + 1) ? t : 4 * (m.max_col + 1) + t - 4 * (cnt + 1)] = T(0);
-                __syncwarp();
-                for (int q = m.Fp[c] + warp; q < m.Fp[c + 1]; q += nwarps) {
-                    const int k = m.Fc[q], pkc = m.Fpos[q];
-                    const B2<T> Dk = ld2(D + 4 * k);
-                    const B2<T> M1 = mul2(Dk, ld2(Uc + 4 * pkc));
-                    const B2<T> M2 = mul2(ld2(Lc + 4 * pkc), Dk);
-                    const int len = m.Cp[k + 1] - pkc, o = m.uoff[q];
-                    for (int t = lane; t < len; t += 32) {
-                        const int tg = m.umap[o + t];
-                        const B2<T> lo = mul2(ld2(Lc + 4 * (pkc + t)), M1);
-                        T *al = accL + 4 * tg;
-                        al[0] += lo.a; al[1] += lo.b; al[2] += lo.c; al[3] += lo.d;
-                        if (t > 0) {
-                            const B2<T> up = mul2(M2, ld2(Uc + 4 * (pkc + t)));
-                            T *au = accU + 4 * tg;
-                            au[0] += up.a; au[1] += up.b; au[2] += up.c; au[3] += up.d;
-                        }
-                    }
-                    __syncwarp();
-                }
-                __syncthreads();
-                // reduce the warps' partial sums in warp order into fin (L then U)
-                T *finL = fin, *finU = fin + 4 * (m.max_col + 1);
-                for (int t = threadIdx.x; t < 4 * (cnt + 1); t += blockDim.x) {
-                    const int blk = t >> 2, q4 = t & 3;
-                    double sl = blk == 0 ? Aj[m.jD + 4 * c + q4] : Aj[m.jLc + 4 * (c0 + blk - 1) + q4];
-                    double su = blk == 0 ? 0.0 : Aj[m.jUc + 4 * (c0 + blk - 1) + q4];
-                    T vl = T(sl), vu = T(su);
-                    for (int w = 0; w < nwarps; w++) {
-                        vl -= reinterpret_cast<T *>(scratch)[w * sa + t];
-                        vu -= reinterpret_cast<T *>(scratch)[w * sa + 4 * (m.max_col + 1) + t];
-                    }
-                    finL[t] = vl;
-                    finU[t] = vu;
-                }
-                __syncthreads();
-                finalize(c, finL, finU, cnt, int(threadIdx.x), int(blockDim.x));
-                __syncthreads();
-            }
-        }
-        __syncthreads();
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(done + cc), "r"(epoch) : "memory");
     }
-    // row-ordered copies for the forward sweeps
-    T *Lr = F + m.jLr, *Ur = F + m.jUr;
-    for (int q = threadIdx.x; q < m.nnz; q += blockDim.x) {
-        st2(Lr + 4 * q, ld2(Lc + 4 * m.Fpos[q]));
-        st2(Ur + 4 * q, ld2(Uc + 4 * m.Fpos[q]));
-    }
-    __syncthreads();
-    return bad;
+    cluster_sync<C>();
+    const int st = *reinterpret_cast<volatile int *>(a.fstat + c);
+    cluster_sync<C>();
+    return st;
 }
 
 // J x = x (TRANS = false) or J^T x = x (TRANS = true) with the block factors.
@@ -419,8 +453,8 @@ __device__ bool nr_solve(const NrArgs &a, Ring *R, unsigned char *stages, T *xs,
     return ok;
 }
 
-// Newton-Raphson power flow of one case per cluster of C CTAs: mismatch and
-// Jacobian assembly spread over the cluster, factor and solve in CTA 0.
+// Newton-Raphson power flow of one case per cluster of C CTAs: mismatch,
+// Jacobian assembly and factor spread over the cluster, solve in CTA 0.
 template <class T, int C>
 __global__ void __launch_bounds__(512, C == 1 ? 2 : 1) k_nr(NrArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -466,8 +500,8 @@ __global__ void __launch_bounds__(512, C == 1 ? 2 : 1) k_nr(NrArgs a) {
         if (it >= a.max_iter) break;
         nr_assemble(a, c, s0, s1);
         cluster_sync<C>();
+        const int fs = cluster_block_factor<T, C>(a, c, rank, F, A, scratch, red, a.epoch0 + unsigned(it) + 1u);
         if (rank == 0) {
-            const int fs = block_factor<T>(m, A, F, scratch, red);
             bool ok = fs == PF_OK;
             if (ok) ok = nr_solve<T, false>(a, &R, stages, xs, F, A, c, red, ir_steps, false);
             if (threadIdx.x == 0) {
@@ -536,9 +570,10 @@ __global__ void __launch_bounds__(512, C == 1 ? 2 : 1) k_adjoint(NrArgs a, int f
     cluster_sync<C>();
     nr_assemble(a, c, s0, s1);
     cluster_sync<C>();
+    int fsn = PF_OK;
+    if (factor_now) fsn = cluster_block_factor<T, C>(a, c, rank, F, A, scratch, red, a.epoch0 + 1u);
     if (rank == 0) {
-        int fs = factor_now ? PF_OK : a.fstat[c];
-        if (factor_now) fs = block_factor<T>(m, A, F, scratch, red);
+        int fs = factor_now ? fsn : a.fstat[c];
         int irs = 0;
         bool ok = fs == PF_OK;
         if (ok) ok = nr_solve<T, true>(a, &R, stages, xs, F, A, c, red, irs, true);
@@ -658,10 +693,23 @@ cudaError_t launch_cluster(void (*kernel)(Args...), size_t smem, cudaStream_t s,
 
 // ------------------------------------------------------------ launchers
 
+// Update terms staged per warp by the block factor: the most (up to
+// kNrChunkMax, at least 32) that fit beside the ring and the accumulators.
+int nr_chunk(const DevMat &m, int prec, size_t smem_optin) {
+    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
+    const size_t ring = size_t(kStages) * kStageBytes;
+    const size_t room = smem_optin > ring + 4096 ? smem_optin - ring - 4096 : 0;
+    const long long per_warp = (long long)(room / (512 / 32) / elt) - 8LL * (m.max_col + 1);
+    long long ch = per_warp / 8;
+    if (ch > kNrChunkMax) ch = kNrChunkMax;
+    if (ch < 32) ch = 32;
+    return int(ch);
+}
+
 size_t nr_smem(const DevMat &m, int prec, size_t smem_optin, int *use_smem) {
     const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
     const size_t ring = size_t(kStages) * kStageBytes;
-    const size_t fac = elt * size_t(8 * (m.max_col + 1)) * (512 / 32 + 1);
+    const size_t fac = elt * size_t(8 * (m.max_col + 1) + 8 * nr_chunk(m, prec, smem_optin)) * (512 / 32);
     const size_t vec = elt * size_t(2 * m.n);
     size_t smem = ring + (fac > vec ? fac : vec);
     *use_smem = smem + 2048 <= smem_optin;
@@ -729,6 +777,10 @@ cudaError_t launch_nr(const NrLaunch &L, cudaStream_t s) {
     a.gvm = L.gvm;
     a.dJdP = L.dJdP;
     a.dJdQ = L.dJdQ;
+    a.jdone = L.jdone;
+    a.jsync = L.jsync;
+    a.epoch0 = L.epoch0;
+    a.fchunk = nr_chunk(L.m, L.prec, L.smem_optin);
     int use = 0;
     const size_t smem = nr_smem(L.m, L.prec, L.smem_optin, &use);
     a.use_smem = use;
