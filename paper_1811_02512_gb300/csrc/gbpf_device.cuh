@@ -80,6 +80,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Barrier among the first `nthreads` threads of the block (named barrier 1).
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
 // Bulk copy global -> this CTA's shared memory, completion counted on `bar`.
 // Both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void tma_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -131,7 +140,8 @@ __device__ __forceinline__ void cluster_sync() {
 // Shared-memory ring of kStages stages; each stage holds one piece: row
 // pointers, indices and values of a run of rows of one level.
 struct Ring {
-    uint64_t bar[kStages];
+    uint64_t bar[kStages];   // full: the stage's copies have landed
+    uint64_t ebar[kStages];  // empty: the consumers are done with the stage
     int hdr[kStages][20]; // r0, r1, e0, p_lo, i_lo, v_lo, idx off, val off, mode, run_end,
                           // diag off (-1: none), d_lo, level-pointer off, lp_lo, l0, l1, e1
     int err;              // set when a wait gave up
@@ -140,7 +150,10 @@ struct Ring {
 
 __device__ void ring_init(Ring *R) {
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; s++) mbar_init(&R->bar[s], 1);
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&R->bar[s], 1);
+            mbar_init(&R->ebar[s], 1);
+        }
         R->err = 0;
         R->gcount = 0;
         fence_mbar_init();
@@ -384,80 +397,106 @@ __device__ __forceinline__ void issue_piece(Ring *R, unsigned char *stages, int 
 // One substitution sweep: for every piece in order, every row r of the piece
 // gets x_r -= sum_e val_e x_{idx_e} (NB x NB blocks, optionally transposed,
 // with the inverse diagonal applied first when given).  Pieces of the same
-// level are independent.  Block-wide pieces end with a block barrier that
-// also releases their stage; runs of single-warp pieces (modes 2-4) are
-// consumed by warp 0 alone with warp barriers while the other warps wait at the end of
-// the run.  Returns false if a wait gave up (then no copy is left in flight).
+// level are independent.  The last warp of the block is the producer: it
+// issues each piece's copies into the ring as soon as the consumers have
+// released the stage's previous piece (an "empty" mbarrier per stage), so
+// issuing is off the consumers' critical path.  The other warps consume:
+// block-wide pieces end with a barrier among the consumers, after which the
+// stage is released; runs of single-warp pieces (modes 2-4) are consumed by
+// warp 0 alone, releasing each stage as it goes, while the other consumers
+// wait at the end of the run.  Returns false if a wait gave up (then no copy
+// is left in flight).
 template <class T, class X, int NB, bool TRANS>
 __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces, int np,
                              const SweepSrc<T> &S, X *x, unsigned spin) {
     const unsigned g0 = R->gcount;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    Piece next{};     // thread 0: descriptor of the next piece to issue, loaded ahead
-    int issued = 0;   // thread 0: pieces issued so far in this sweep
-    if (threadIdx.x == 0) {
-        const int pre = np < kStages ? np : kStages;
-        for (int j = 0; j < pre; j++) issue_piece<T, NB>(R, stages, int((g0 + j) % kStages), pieces[j], S);
-        issued = pre;
-        if (kStages < np) next = pieces[kStages];
-    }
-    auto issue_after = [&](int j) {  // stage of piece j is free: refill it with j + kStages
-        if (j + kStages < np) {
-            issue_piece<T, NB>(R, stages, int((g0 + j) % kStages), next, S);
-            issued = j + kStages + 1;
-            if (j + kStages + 1 < np) next = pieces[j + kStages + 1];
-        }
-    };
+    const int ncw = nwarps - 1, nct = ncw * 32;  // consumer warps / threads
+    volatile int *err = &R->err;
     bool ok = true;
-    int j = 0;
-    while (j < np) {
-        const unsigned g = g0 + unsigned(j);
-        const int st = int(g % kStages);
-        if (!mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin)) atomicExch(&R->err, 1);
-        const int *h = R->hdr[st];
-        const int mode = h[8];
-        if (mode >= 2 && mode <= 4) {
-            const int jr = h[9];
-            __syncthreads();  // every warp has read this header before warp 0 refills the stage
-            if (warp == 0) {
-                for (int jj = j; jj < jr; jj++) {
-                    const unsigned gg = g0 + unsigned(jj);
-                    const int s2 = int(gg % kStages);
-                    if (jj > j && !mbar_wait_bounded(&R->bar[s2], (gg / kStages) & 1u, spin))
+    if (warp == ncw) {
+        // producer: piece j goes into stage (g0 + j) mod kStages once the
+        // consumers have released that stage's previous piece
+        if (lane == 0) {
+            int issued = 0;
+            const unsigned long_spin = spin > kDefaultSpin ? spin : kDefaultSpin;
+            for (int j = 0; j < np; j++) {
+                const unsigned g = g0 + unsigned(j);
+                const int st = int(g % kStages);
+                if (g >= unsigned(kStages)) {
+                    bool got = false;
+                    for (unsigned it = 0; it < spin && !*err; it++)
+                        if (mbar_try_wait(&R->ebar[st], ((g / kStages) & 1u) ^ 1u)) {
+                            got = true;
+                            break;
+                        }
+                    if (!got) {
                         atomicExch(&R->err, 1);
-                    __syncwarp();
-                    if (R->err) break;
-                    piece_rows<T, X, NB, TRANS>(R->hdr[s2], stages + size_t(s2) * kStageBytes, x,
-                                                R->hdr[s2][8], 0, 1);
-                    __syncwarp();
-                    if (lane == 0) issue_after(jj);
+                        break;
+                    }
+                }
+                if (*err) break;
+                issue_piece<T, NB>(R, stages, st, pieces[j], S);
+                issued = j + 1;
+            }
+            if (*err) {
+                // drain: the last issued piece of every stage may still be in
+                // flight; a copy must not outlive the block
+                for (int q = (issued > kStages ? issued - kStages : 0); q < issued; q++) {
+                    const unsigned gq = g0 + unsigned(q);
+                    mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, long_spin);
                 }
             }
-            __syncthreads();
-            if (R->err) { ok = false; break; }
-            j = jr;
-        } else {
-            if (!R->err)
-                piece_rows<T, X, NB, TRANS>(h, stages + size_t(st) * kStageBytes, x, mode,
-                                            mode == 1 ? warp : int(threadIdx.x),
-                                            mode == 1 ? nwarps : int(blockDim.x));
-            __syncthreads();
-            if (R->err) { ok = false; break; }
-            if (threadIdx.x == 0) issue_after(j);
-            j++;
         }
-    }
-    if (!ok && threadIdx.x == 0) {
-        // drain: at most the last kStages issued pieces can still be in flight
-        for (int q = (issued > kStages ? issued - kStages : 0); q < issued; q++) {
-            const unsigned gq = g0 + unsigned(q);
-            // the caller's limit may be short; the drain always waits long
-            // enough for a copy to land (a copy must not outlive the block)
-            mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, spin > kDefaultSpin ? spin : kDefaultSpin);
+        __syncwarp();
+    } else {
+        int j = 0;
+        while (j < np) {
+            const unsigned g = g0 + unsigned(j);
+            const int st = int(g % kStages);
+            if (!mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin)) atomicExch(&R->err, 1);
+            const int *h = R->hdr[st];
+            const int mode = h[8];
+            if (mode >= 2 && mode <= 4) {
+                const int jr = h[9];
+                consumer_sync(nct);  // every consumer has read this header before the stage is released
+                if (warp == 0) {
+                    for (int jj = j; jj < jr; jj++) {
+                        const unsigned gg = g0 + unsigned(jj);
+                        const int s2 = int(gg % kStages);
+                        if (jj > j && !mbar_wait_bounded(&R->bar[s2], (gg / kStages) & 1u, spin))
+                            atomicExch(&R->err, 1);
+                        __syncwarp();
+                        if (*err) break;
+                        piece_rows<T, X, NB, TRANS>(R->hdr[s2], stages + size_t(s2) * kStageBytes, x,
+                                                    R->hdr[s2][8], 0, 1);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&R->ebar[s2]);
+                    }
+                }
+                consumer_sync(nct);
+                if (*err) {
+                    ok = false;
+                    break;
+                }
+                j = jr;
+            } else {
+                if (!*err)
+                    piece_rows<T, X, NB, TRANS>(h, stages + size_t(st) * kStageBytes, x, mode,
+                                                mode == 1 ? warp : int(threadIdx.x), mode == 1 ? ncw : nct);
+                consumer_sync(nct);
+                if (*err) {
+                    ok = false;
+                    break;
+                }
+                if (threadIdx.x == 0) mbar_arrive(&R->ebar[st]);
+                j++;
+            }
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) R->gcount = g0 + unsigned(np);
+    ok = R->err == 0;
     __syncthreads();
     return ok;
 }
