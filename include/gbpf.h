@@ -102,6 +102,11 @@ typedef struct {
     int32_t flat_start; /* 1: theta = slack angle / 0, V = 1 (PQ) or vset; 0: use vm/va */
     int32_t spin_limit; /* bound on every device-side wait (0 = library default) */
     int32_t engine;     /* PF_ENGINE_AUTO, PF_ENGINE_BLOCK or PF_ENGINE_LANES (FDPF only) */
+    int32_t fallback;   /* FDPF only: 1 = cases the fast decoupled iteration leaves
+                           unconverged (PF_ERR_NOT_CONVERGED, PF_ERR_NONFINITE) are
+                           re-run by Newton-Raphson from a flat start in the same
+                           call (at most 30 Newton steps, same precision and
+                           tolerance); their results then report method PF_NR */
 } pf_run_opts;
 
 /* Engines of pf_run_to_tol.  BLOCK: one thread block (or, for a few large
@@ -139,7 +144,7 @@ typedef struct {
     int32_t status;      /* pf_status of this case */
     int32_t iters;       /* NR steps, or FDPF half-iterations */
     int32_t ir_steps;    /* refinement corrections taken (PF_FP32) */
-    int32_t pad;
+    int32_t method;      /* method that produced the result: PF_FDPF or PF_NR */
     double max_mismatch; /* last max |mismatch| evaluated */
 } pf_case_result;
 
@@ -260,6 +265,20 @@ pf_status pf_adjoint(pf_ctx *ctx, int32_t precision, const double *vm_dev, const
  * dJ/dV_k for every bus.  Asynchronous. */
 pf_status pf_objective(pf_ctx *ctx, const double *vm_dev, const double *va_dev, double *J_dev,
                        double *gva_dev, double *gvm_dev, void *stream);
+
+/* Branch flows and losses after a solve (the per-branch split of the nodal
+ * injections of Section II.A; the losses are the second term of the adjoint
+ * objective).  For case c and branch k (pf_create's order),
+ * flows_dev[(c * nbranch + k) * 4 + {0, 1, 2, 3}] = (P_f, Q_f, P_t, Q_t): the
+ * complex power entering the branch at its from and at its to end, with the
+ * pi model of the admittance matrix (tap on the from side).  The case's
+ * outaged branch and out-of-service branches carry zero.  loss_dev[c] = the
+ * sum over branches of P_f + P_t plus the shunt consumption sum gs V^2 (the
+ * total active loss).  vm_dev / va_dev: [ncase][nbus] device states (as
+ * written by pf_run_to_tol).  PF_ERR_ARG for a NULL pointer or ncase outside
+ * 1 .. the cases set.  Asynchronous on `stream`. */
+pf_status pf_branch_flows(pf_ctx *ctx, const double *vm_dev, const double *va_dev, int32_t ncase,
+                          double *flows_dev, double *loss_dev, void *stream);
 
 /* Project autotuner: runs pf_run_to_tol with opts (engine AUTO) under every
  * applicable mapping of pf_tuning -- engines for FDPF batches, cluster sizes

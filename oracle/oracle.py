@@ -378,6 +378,34 @@ def adjoint(case, vm, va):
     return dP, dQ, J.value
 
 
+def branch_flows(case, vm, va):
+    """Flows of every branch at the state (vm, va): the complex power entering
+    the branch at its from end, S_f = V_f conj(I_f), and at its to end, S_t =
+    V_t conj(I_t), with the pi model of the admittance matrix (Section III.A:
+    series y = 1/(r + jx), charging jb/2 at each end, the tap t on the from
+    side): I_f = (y + jb/2)/t^2 V_f - y/t V_t, I_t = -y/t V_f + (y + jb/2) V_t.
+    Out-of-service branches carry nothing.  Returns (Pf, Qf, Pt, Qt, loss)
+    with loss = sum of Pf + Pt over branches plus the shunt consumption
+    sum gs V^2 (the total active loss)."""
+    V = vm * np.exp(1j * va)
+    m = case.m
+    Pf = np.zeros(m); Qf = np.zeros(m); Pt = np.zeros(m); Qt = np.zeros(m)
+    for k in range(m):
+        if not case.status[k]:
+            continue
+        y = 1.0 / complex(case.r[k], case.x[k])
+        t = case.tap[k] if case.tap[k] != 0 else 1.0
+        ysh = 0.5j * case.b[k]
+        vf, vt = V[case.f[k]], V[case.t[k]]
+        i_f = (y + ysh) / (t * t) * vf - y / t * vt
+        i_t = -y / t * vf + (y + ysh) * vt
+        sf = vf * np.conj(i_f)
+        st = vt * np.conj(i_t)
+        Pf[k], Qf[k], Pt[k], Qt[k] = sf.real, sf.imag, st.real, st.imag
+    loss = float(np.sum(Pf + Pt) + np.sum(case.gs * vm ** 2))
+    return Pf, Qf, Pt, Qt, loss
+
+
 def objective(case, vm, va):
     rowptr, col, G, B = ybus(case)
     P, _ = injections(rowptr, col, G, B, vm, va)

@@ -108,7 +108,7 @@ __global__ void k_lane_store(LaneArgs a, double *vm, double *va, pf_case_result 
             res[c].status = L.status[lane];
             res[c].iters = L.iters[lane];
             res[c].ir_steps = L.irs[lane];
-            res[c].pad = 0;
+            res[c].method = PF_FDPF;
             res[c].max_mismatch = L.lastmis[lane];
         }
     }

@@ -1435,8 +1435,70 @@ pf_status pf_mismatch(pf_ctx *ctx, const double *vm_dev, const double *va_dev, d
     return PF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                   pf_case_result *res_host, void *stream);
+
+// FDPF -> NR fallback: the cases left unconverged by the fast decoupled
+// iteration restart from a flat start under Newton-Raphson; the others keep
+// their results (their NR run stops at step 0, already within tolerance).
+pf_status nr_fallback(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                      pf_case_result *res_host, void *stream) {
+    const int ncase = ctx->dc.ncase;
+    std::vector<int> mask(static_cast<size_t>(ncase), 0);
+    bool any = false;
+    for (int c = 0; c < ncase; c++)
+        if (res_host[c].status == PF_ERR_NOT_CONVERGED || res_host[c].status == PF_ERR_NONFINITE) {
+            mask[c] = 1;
+            any = true;
+        }
+    if (!any) return PF_OK;
+    Workspace &w = ctx->ws;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!w.fbmask) TRY(dalloc(ctx, &w.fbmask, size_t(ncase)));
+    cudaError_t e = cudaMemcpyAsync(w.fbmask, mask.data(), sizeof(int) * size_t(ncase), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_reset_flat(ctx->dn, ncase, w.fbmask, vm_dev, va_dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // mask is released on return
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fallback reset");
+    pf_run_opts o = *opts;
+    o.method = PF_NR;
+    o.max_iter = 30;
+    o.flat_start = 0;
+    o.fallback = 0;
+    std::vector<pf_case_result> nr(static_cast<size_t>(ncase));
+    const pf_status st = run_once(ctx, &o, vm_dev, va_dev, nr.data(), stream);
+    if (st != PF_OK && st != PF_ERR_NOT_CONVERGED && st != PF_ERR_NONFINITE && st != PF_ERR_SINGULAR &&
+        st != PF_ERR_TIMEOUT)
+        return st;
+    for (int c = 0; c < ncase; c++)
+        if (mask[c]) res_host[c] = nr[size_t(c)];
+    return PF_OK;
+}
+}  // namespace
+
+extern "C" {
+
 pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
                         pf_case_result *res_host, void *stream) {
+    pf_status st = run_once(ctx, opts, vm_dev, va_dev, res_host, stream);
+    if (!opts || opts->method != PF_FDPF || !opts->fallback) return st;
+    if (st != PF_ERR_NOT_CONVERGED && st != PF_ERR_NONFINITE && st != PF_ERR_SINGULAR && st != PF_ERR_TIMEOUT)
+        return st;  // converged, or no per-case results to fall back from
+    TRY(nr_fallback(ctx, opts, vm_dev, va_dev, res_host, stream));
+    for (int c = 0; c < ctx->dc.ncase; c++)
+        if (res_host[c].status != PF_OK)
+            return fail(ctx, pf_status(res_host[c].status), "case %d: status %d after %d iterations (%s)", c,
+                        res_host[c].status, res_host[c].iters, res_host[c].method == PF_NR ? "NR" : "FDPF");
+    return PF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
+                   pf_case_result *res_host, void *stream) {
     if (!ctx || !opts || !vm_dev || !va_dev || !res_host) return fail(ctx, PF_ERR_ARG, "null pointer");
     if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
     if (opts->method != PF_FDPF && opts->method != PF_NR)
@@ -1533,6 +1595,10 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
     return PF_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
 pf_status pf_adjoint(pf_ctx *ctx, int32_t precision, const double *vm_dev, const double *va_dev,
                      const double *gva_dev, const double *gvm_dev, double *dJdP_dev,
                      double *dJdQ_dev, pf_case_result *res_host, void *stream) {
@@ -1626,6 +1692,19 @@ pf_status pf_get_ybus(pf_ctx *ctx, int32_t *rowptr, int32_t *col, double *G, dou
             e = cudaMemcpy(B, ctx->dn.B, sizeof(double) * ctx->dn.nnz, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "get_ybus");
     }
+    return PF_OK;
+}
+
+pf_status pf_branch_flows(pf_ctx *ctx, const double *vm_dev, const double *va_dev, int32_t ncase,
+                          double *flows_dev, double *loss_dev, void *stream) {
+    if (!ctx || !vm_dev || !va_dev || !flows_dev || !loss_dev) return fail(ctx, PF_ERR_ARG, "null pointer");
+    TRY(ensure_cases(ctx));
+    if (ncase < 1 || ncase > ctx->dc.ncase) return fail(ctx, PF_ERR_ARG, "ncase out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = counted(ctx, PF_K_MISMATCH, 2, s, [&] {
+        return launch_branch_flows(ctx->dn, ctx->dc, vm_dev, va_dev, ncase, flows_dev, loss_dev, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "branch flows launch");
     return PF_OK;
 }
 

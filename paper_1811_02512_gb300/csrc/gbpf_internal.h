@@ -231,6 +231,7 @@ struct Workspace {
     unsigned *jdone = nullptr;   // [ncase][n] Jacobian column done flags (epochs)
     unsigned *jsync = nullptr;   // [ncase][2]
     unsigned jepoch = 0;         // last epoch handed to a launch
+    int *fbmask = nullptr;       // [ncase] cases re-run by the NR fallback
     LaneSet lanes;
 };
 
@@ -278,6 +279,10 @@ cudaError_t launch_case_spec(const DevNet &dn, const DevCases &dc, const double 
                              cudaStream_t s);
 cudaError_t launch_assemble_slots(const DevNet &dn, const DevCases &dc, const DevMat &m, int which,
                                   double *A, cudaStream_t s);
+cudaError_t launch_branch_flows(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
+                                int ncase, double *flows, double *loss, cudaStream_t s);
+cudaError_t launch_reset_flat(const DevNet &dn, int ncase, const int *mask, double *vm, double *va,
+                              cudaStream_t s);
 struct FactorSync {
     unsigned *done = nullptr;  // [ninst][n]
     unsigned *sync = nullptr;  // [0] column counter, [1] abort flag

@@ -564,6 +564,80 @@ __global__ void __launch_bounds__(kFactorThreads)
     if (threadIdx.x == 0) fstatus[inst] = bad;
 }
 
+// ------------------------------------------------------------ branch flows
+
+// Flows of branch k in case c: S_f = V_f conj(I_f), S_t = V_t conj(I_t) with
+// the pi model (series y = 1/(r + jx), charging jb/2 at each end, tap t on
+// the from side); zero for the case's outage and out-of-service branches.
+__global__ void k_branch_flows(DevNet dn, DevCases dc, const double *vm, const double *va, int ncase,
+                               double *flows) {
+    const long long total = (long long)ncase * dn.nbr;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = int(idx / dn.nbr), k = int(idx - (long long)c * dn.nbr);
+        double *o = flows + idx * 4;
+        if (!dn.bstatus[k] || dc.outage[c] == k) {
+            o[0] = o[1] = o[2] = o[3] = 0.0;
+            continue;
+        }
+        const int f = dn.bf[k], t = dn.bt[k];
+        const double *vmc = vm + (long long)c * dn.nbus, *vac = va + (long long)c * dn.nbus;
+        double sf, cf, st, ct;
+        sincos(vac[f], &sf, &cf);
+        sincos(vac[t], &st, &ct);
+        const double ef = vmc[f] * cf, ff = vmc[f] * sf, et = vmc[t] * ct, ft = vmc[t] * st;
+        const double r = dn.br[k], x = dn.bx[k], den = r * r + x * x;
+        const double g = r / den, b = -x / den, bc = 0.5 * dn.bb[k];
+        const double tap = dn.btap[k] != 0.0 ? dn.btap[k] : 1.0;
+        // I_f = ((g + j(b + bc)) / t^2) V_f - ((g + jb) / t) V_t
+        const double gff = g / (tap * tap), bff = (b + bc) / (tap * tap), gft = -g / tap, bft = -b / tap;
+        const double ifr = gff * ef - bff * ff + gft * et - bft * ft;
+        const double ifi = gff * ff + bff * ef + gft * ft + bft * et;
+        // I_t = -((g + jb) / t) V_f + (g + j(b + bc)) V_t
+        const double itr = gft * ef - bft * ff + g * et - (b + bc) * ft;
+        const double iti = gft * ff + bft * ef + g * ft + (b + bc) * et;
+        o[0] = ef * ifr + ff * ifi;
+        o[1] = ff * ifr - ef * ifi;
+        o[2] = et * itr + ft * iti;
+        o[3] = ft * itr - et * iti;
+    }
+}
+
+// Flat start (V = 1 at PQ buses, set-point elsewhere; angle 0 but the
+// slack's) for the cases with mask[c] != 0, the others untouched.
+__global__ void k_reset_flat(DevNet dn, int ncase, const int *mask, double *vm, double *va) {
+    const long long total = (long long)ncase * dn.nbus;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = int(idx / dn.nbus), i = int(idx - (long long)c * dn.nbus);
+        if (!mask[c]) continue;
+        const int t = dn.btype[i];
+        vm[idx] = t == PF_BUS_PQ ? 1.0 : dn.vset[i];
+        va[idx] = t == PF_BUS_SLACK ? dn.va0[i] : 0.0;
+    }
+}
+
+// Total active loss of case c (block per case, fixed summation order).
+__global__ void k_case_loss(DevNet dn, const double *vm, const double *flows, double *loss) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < dn.nbr; k += blockDim.x) {
+        const double *o = flows + ((long long)c * dn.nbr + k) * 4;
+        s += o[0] + o[2];
+    }
+    const double *vmc = vm + (long long)c * dn.nbus;
+    for (int i = threadIdx.x; i < dn.nbus; i += blockDim.x) s += dn.gs[i] * vmc[i] * vmc[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) loss[c] = w;
+    }
+}
+
 // ------------------------------------------------------------ Section III.C
 
 template <class T>
@@ -867,7 +941,7 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
         a.res[c].status = status;
         a.res[c].iters = iters;
         a.res[c].ir_steps = ir_steps;
-        a.res[c].pad = 0;
+        a.res[c].method = PF_FDPF;
         a.res[c].max_mismatch = mis;
     }
     cluster_sync<C>();
@@ -912,7 +986,7 @@ __global__ void __launch_bounds__(kRunThreads, 1)
                 args[g].res[0].status = PF_ERR_TIMEOUT;
                 args[g].res[0].iters = 0;
                 args[g].res[0].ir_steps = 0;
-                args[g].res[0].pad = 0;
+                args[g].res[0].method = PF_FDPF;
                 args[g].res[0].max_mismatch = INFINITY;
             }
             continue;
@@ -969,6 +1043,20 @@ cudaError_t launch_ybus(const DevNet &dn, cudaStream_t s) {
 cudaError_t launch_case_spec(const DevNet &dn, const DevCases &dc, const double *ls,
                              cudaStream_t s) {
     k_case_spec<<<grid_for((long long)dc.ncase * dn.nbus, 256), 256, 0, s>>>(dn, dc, ls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_flat(const DevNet &dn, int ncase, const int *mask, double *vm, double *va,
+                              cudaStream_t s) {
+    k_reset_flat<<<grid_for((long long)ncase * dn.nbus, 256), 256, 0, s>>>(dn, ncase, mask, vm, va);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_branch_flows(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
+                                int ncase, double *flows, double *loss, cudaStream_t s) {
+    const long long total = (long long)ncase * dn.nbr;
+    k_branch_flows<<<grid_for(total, 256), 256, 0, s>>>(dn, dc, vm, va, ncase, flows);
+    k_case_loss<<<ncase, 256, 0, s>>>(dn, vm, flows, loss);
     return cudaGetLastError();
 }
 

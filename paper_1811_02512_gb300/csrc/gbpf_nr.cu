@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(512, C == 1 ? 2 : 1) k_nr(NrArgs a) {
         a.res[c].status = status;
         a.res[c].iters = iters;
         a.res[c].ir_steps = ir_steps;
-        a.res[c].pad = 0;
+        a.res[c].method = PF_NR;
         a.res[c].max_mismatch = mis;
     }
     cluster_sync<C>();

@@ -51,18 +51,18 @@ class pf_run_opts(C.Structure):
     _fields_ = [("method", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("max_iter", C.c_int32), ("ir_max", C.c_int32), ("ir_tol", C.c_double),
                 ("ir_abs", C.c_double), ("flat_start", C.c_int32), ("spin_limit", C.c_int32),
-                ("engine", C.c_int32)]
+                ("engine", C.c_int32), ("fallback", C.c_int32)]
 
 
 class pf_case_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("ir_steps", C.c_int32),
-                ("pad", C.c_int32), ("max_mismatch", C.c_double)]
+                ("method", C.c_int32), ("max_mismatch", C.c_double)]
 
 
 assert C.sizeof(pf_bus) == gridgen.BUS_DTYPE.itemsize
 assert C.sizeof(pf_branch) == gridgen.BRANCH_DTYPE.itemsize
 CASE_RESULT_DTYPE = np.dtype([("status", "<i4"), ("iters", "<i4"), ("ir_steps", "<i4"),
-                              ("pad", "<i4"), ("max_mismatch", "<f8")], align=True)
+                              ("method", "<i4"), ("max_mismatch", "<f8")], align=True)
 
 _lib = None
 _P = C.c_void_p
@@ -100,6 +100,8 @@ def load():
         L.pf_last_error.restype = C.c_char_p
         L.pf_destroy.argtypes = [_P]
         L.pf_destroy.restype = None
+        L.pf_branch_flows.argtypes = [_P, _P, _P, C.c_int32, _P, _P, _P]
+        L.pf_branch_flows.restype = S
         L.pf_autotune.argtypes = [_P, C.POINTER(pf_run_opts), _P, _P, C.c_int32, _P, _P]
         L.pf_get_tuning.argtypes = [_P, _P]
         L.pf_set_tuning.argtypes = [_P, _P]
@@ -222,11 +224,11 @@ PF_ENGINE_AUTO, PF_ENGINE_BLOCK, PF_ENGINE_LANES = 0, 1, 2
 
 
 def run_opts(method=PF_FDPF, precision=PF_FP64, tol=1e-8, max_iter=None, ir_max=5, ir_tol=1e-10,
-             ir_abs=0.0, flat_start=1, spin_limit=0, engine=PF_ENGINE_AUTO):
+             ir_abs=0.0, flat_start=1, spin_limit=0, engine=PF_ENGINE_AUTO, fallback=0):
     if max_iter is None:
         max_iter = 200 if method == PF_FDPF else 20
     return pf_run_opts(method, precision, tol, max_iter, ir_max, ir_tol, ir_abs, flat_start,
-                       spin_limit, engine)
+                       spin_limit, engine, fallback)
 
 
 def pf_run_to_tol(ctx, opts, vm_dev, va_dev, ncase, stream=None, check=True):
@@ -304,6 +306,12 @@ def pf_destroy(ctx):
 
 
 # ----------------------------------------------------------------- convenience
+
+def pf_branch_flows(ctx, vm_dev, va_dev, ncase, flows_dev, loss_dev, stream=None):
+    """flows_dev [ncase, nbranch, 4] (P_f, Q_f, P_t, Q_t), loss_dev [ncase]."""
+    _check(ctx, load().pf_branch_flows(ctx, _ptr(vm_dev), _ptr(va_dev), int(ncase), _ptr(flows_dev),
+                                       _ptr(loss_dev), _stream(stream)), "pf_branch_flows")
+
 
 class pf_tuning(C.Structure):
     _fields_ = [("engine", C.c_int32), ("cluster", C.c_int32), ("factor", C.c_int32),

@@ -365,3 +365,73 @@ def test_lane_engine_10k_batch_sampled(oracle):
         assert np.max(np.abs(a[0][c] - vm0)) <= 1e-8, c
         assert np.max(np.abs(a[1][c] - va0)) <= 1e-8, c
     g.close()
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_branch_flows_vs_oracle(oracle, cfg):
+    """Branch flows and total losses of solved cases (one load scenario, one
+    single-branch outage) against the oracle's definition at the same
+    voltages, element by element."""
+    base = CASES[cfg]()
+    sc = gridgen.scenarios(base, n_load=1, n_outage=1, seed=3)
+    g = _grid(base, sc.ncase, sc.load_scale, sc.outage)
+    st, res, vm, va = _run(g, sc.ncase, tol=1e-10, max_iter=300)
+    assert st == gbpf.PF_OK
+    vm_d = torch.tensor(vm, device=DEV)
+    va_d = torch.tensor(va, device=DEV)
+    flows = torch.zeros((sc.ncase, base.m, 4), dtype=torch.float64, device=DEV)
+    loss = torch.zeros(sc.ncase, dtype=torch.float64, device=DEV)
+    gbpf.pf_branch_flows(g.ctx, vm_d, va_d, sc.ncase, flows, loss)
+    torch.cuda.synchronize()
+    fl, ls = flows.cpu().numpy(), loss.cpu().numpy()
+    for c in range(sc.ncase):
+        cc = gridgen.apply_scenario(base, sc, c)
+        Pf, Qf, Pt, Qt, l0 = oracle.branch_flows(cc, vm[c], va[c])
+        ref = np.stack([Pf, Qf, Pt, Qt], axis=1)
+        scale = max(1.0, np.max(np.abs(ref)))
+        assert np.max(np.abs(fl[c] - ref)) <= 1e-12 * scale
+        assert abs(ls[c] - l0) <= 1e-11 * max(1.0, abs(l0))
+        if sc.outage[c] >= 0:
+            assert np.all(fl[c, sc.outage[c]] == 0.0)
+    g.close()
+
+
+def _high_rx(base, seed=0):
+    """The 120-bus grid with r/x about 2: the XB fast decoupled iteration
+    stalls there while Newton-Raphson converges (checked on the oracle)."""
+    rng = np.random.default_rng(seed)
+    c = base.copy()
+    c.x = c.r * rng.uniform(0.5, 1.5, c.m) * 0.5
+    return c
+
+
+def test_fdpf_nr_fallback(oracle):
+    """Without the fallback the stalled case reports PF_ERR_NOT_CONVERGED; with
+    it the case is re-run by Newton-Raphson and matches the oracle's NR; a
+    grid FDPF solves keeps its FDPF result."""
+    case = _high_rx(gridgen.config(0))
+    rf, *_ = oracle.power_flow(case, oracle.FDPF, tol=1e-8, max_iter=60)
+    rn, vm0, va0, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
+    assert rf == oracle.ERR_NOT_CONVERGED and rn == oracle.OK
+    g = _grid(case, 2)
+    vm = torch.zeros((2, case.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-11, max_iter=60)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, 2)
+    assert st == gbpf.PF_ERR_NOT_CONVERGED and res[0]["method"] == gbpf.PF_FDPF
+    for prec in (gbpf.PF_FP64, gbpf.PF_FP32):
+        opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=1e-11, max_iter=60, fallback=1)
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, 2)
+        assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+        assert all(res["method"] == gbpf.PF_NR) and all(res["status"] == gbpf.PF_OK)
+        for c in range(2):
+            assert np.max(np.abs(vm.cpu().numpy()[c] - vm0)) <= 1e-8
+            assert np.max(np.abs(va.cpu().numpy()[c] - va0)) <= 1e-8
+    g.close()
+    g = _grid(gridgen.config(0), 1)
+    st, res, _, _ = _run(g, 1)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-8, max_iter=200, fallback=1)
+    vm = torch.zeros((1, g.nbus), dtype=torch.float64, device=DEV)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, torch.zeros_like(vm), 1)
+    assert st == gbpf.PF_OK and res[0]["method"] == gbpf.PF_FDPF
+    g.close()

@@ -160,6 +160,31 @@ def test_energy_conservation_any_voltage(oracle, seed):
     assert abs(Q.sum() - ql) < 1e-12 * max(1.0, abs(ql)) * case.n
 
 
+@pytest.mark.parametrize("seed", [4, 5])
+def test_branch_flows_kirchhoff_and_losses(oracle, seed):
+    """Branch flows at an arbitrary state: at every bus the injection from the
+    admittance matrix equals the flows entering its branches plus its shunt
+    consumption (Kirchhoff's current law, per bus: pins every branch's value,
+    not only a sum), and the total loss equals the physical-model consumption
+    of the series elements, charging and shunts."""
+    case = random_grid(15, seed)
+    case.status[2] = 0
+    rng = np.random.default_rng(seed)
+    vm = rng.uniform(0.9, 1.1, case.n)
+    va = rng.uniform(-0.3, 0.3, case.n)
+    rowptr, col, G, B = oracle.ybus(case)
+    P, Q = oracle.injections(rowptr, col, G, B, vm, va)
+    Pf, Qf, Pt, Qt, loss = oracle.branch_flows(case, vm, va)
+    assert Pf[2] == Qf[2] == Pt[2] == Qt[2] == 0.0
+    Pb = case.gs * vm ** 2
+    Qb = -case.bs * vm ** 2
+    np.add.at(Pb, case.f, Pf); np.add.at(Pb, case.t, Pt)
+    np.add.at(Qb, case.f, Qf); np.add.at(Qb, case.t, Qt)
+    assert np.max(np.abs(Pb - P)) < 1e-12 and np.max(np.abs(Qb - Q)) < 1e-12
+    pl, _ = branch_losses(case, vm, va)
+    assert abs(loss - pl) < 1e-12 * max(1.0, abs(pl))
+
+
 def test_out_of_service_branch_keeps_slot(oracle):
     case = random_grid(10, 4, taps=False, shunts=False)
     rowptr, col, G, B = oracle.ybus(case)
