@@ -170,6 +170,20 @@ pf_status pf_analyze(pf_ctx *ctx, pf_symbolic_info *info);
 pf_status pf_get_symbolic(const pf_ctx *ctx, int32_t which, int32_t *perm, int32_t *parent,
                           int32_t *level, int64_t *Lp, int32_t *Li);
 
+/* Elimination tree and level sets of a filled pattern on the GPU (Section
+ * II.B: FormEliminationTree and the leaf-peeling partition of Table I), for
+ * workloads whose topology changes: from the strict-lower pattern of L by
+ * column, Lp_dev[n + 1] (int64) and Li_dev[Lp[n]] (int32 rows; caller-owned
+ * device arrays, e.g. pf_get_symbolic's uploaded), it writes parent_dev[j] =
+ * the smallest row i > j of column j (-1 for a root), level_dev[j] = 1 for a
+ * leaf, else 1 + the largest level of j's children, and nlev_dev[0] = the
+ * number of levels -- the same numbers as pf_get_symbolic's.  scratch_dev:
+ * 3 n int32 of caller-owned device memory.  PF_ERR_ARG for n < 1 or a NULL
+ * pointer, PF_ERR_CUDA for a failed launch.  Asynchronous on `stream`. */
+pf_status pf_etree_levels_device(int32_t n, const int64_t *Lp_dev, const int32_t *Li_dev,
+                                 int32_t *parent_dev, int32_t *level_dev, int32_t *nlev_dev,
+                                 int32_t *scratch_dev, void *stream);
+
 /* Defines a batch of ncase >= 1 cases sharing the topology.  load_scale
  * [ncase][nbus] (host, NULL = all 1) multiplies pd and qd of every PQ bus of
  * a case; outage[ncase] (host, NULL = none) names a branch taken out of

@@ -100,6 +100,8 @@ def load():
         L.pf_last_error.restype = C.c_char_p
         L.pf_destroy.argtypes = [_P]
         L.pf_destroy.restype = None
+        L.pf_etree_levels_device.argtypes = [C.c_int32, _P, _P, _P, _P, _P, _P, _P]
+        L.pf_etree_levels_device.restype = S
         L.pf_branch_flows.argtypes = [_P, _P, _P, C.c_int32, _P, _P, _P]
         L.pf_branch_flows.restype = S
         L.pf_autotune.argtypes = [_P, C.POINTER(pf_run_opts), _P, _P, C.c_int32, _P, _P]
@@ -306,6 +308,15 @@ def pf_destroy(ctx):
 
 
 # ----------------------------------------------------------------- convenience
+
+def pf_etree_levels_device(n, Lp_dev, Li_dev, parent_dev, level_dev, nlev_dev, scratch_dev,
+                           stream=None):
+    st = load().pf_etree_levels_device(int(n), _ptr(Lp_dev), _ptr(Li_dev), _ptr(parent_dev),
+                                       _ptr(level_dev), _ptr(nlev_dev), _ptr(scratch_dev),
+                                       _stream(stream))
+    if st != PF_OK:
+        raise PFError(st, "pf_etree_levels_device")
+
 
 def pf_branch_flows(ctx, vm_dev, va_dev, ncase, flows_dev, loss_dev, stream=None):
     """flows_dev [ncase, nbranch, 4] (P_f, Q_f, P_t, Q_t), loss_dev [ncase]."""
