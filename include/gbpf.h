@@ -128,7 +128,12 @@ enum { PF_ENGINE_AUTO = 0, PF_ENGINE_BLOCK = 1, PF_ENGINE_LANES = 2 };
  *   factor   1: dependency-driven factor over all SMs, 2: one thread block
  *            per instance (level by level);
  *   tail     1: narrow top of the elimination tree substituted as a one-warp
- *            scatter, 2: level by level (warp per narrow level).
+ *            scatter, 2: level by level (warp per narrow level);
+ *   outage   1: every single-branch outage case has its own B'/B'' factors,
+ *            2: outage cases reuse the base factors with a low-rank
+ *            (Woodbury) correction of each solve by the outaged branch's
+ *            share (block engine; FP32 runs still refine against each
+ *            case's exact matrix in FP64).
  * ms is the time of one run of the chosen mapping as measured by
  * pf_autotune (0 when set directly). */
 typedef struct {
@@ -136,6 +141,7 @@ typedef struct {
     int32_t cluster;
     int32_t factor;
     int32_t tail;
+    int32_t outage;
     double ms;
 } pf_tuning;
 

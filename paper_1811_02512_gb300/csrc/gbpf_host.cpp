@@ -867,6 +867,11 @@ void free_case_storage(pf_ctx *ctx) {
         dfree(ctx, w.F64[a]); w.F64[a] = nullptr;
         dfree(ctx, w.F32[a]); w.F32[a] = nullptr;
         dfree(ctx, w.fdone[a]); w.fdone[a] = nullptr;
+        dfree(ctx, w.LK[a]); w.LK[a] = nullptr;
+        for (int b = 0; b < 2; b++) {
+            dfree(ctx, w.LZ[a][b]); w.LZ[a][b] = nullptr;
+            dfree(ctx, w.Lscr[a][b]); w.Lscr[a][b] = nullptr;
+        }
 
         for (int b = 0; b < 2; b++) {
             dfree(ctx, w.TV[a][b]);
@@ -952,7 +957,9 @@ pf_status factor_job(pf_ctx *ctx, int which, int prec, FactorJob &J, cudaStream_
 
 // Assembles B' or B'' of every instance from the current admittance matrix
 // and factorises them.
-pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int blocks_per_sm = 2) {
+pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int blocks_per_sm = 2,
+                        int ninst_f = -1) {
+    const int nf = ninst_f > 0 ? ninst_f : ctx->dc.ninst;  // instances factorised (the first nf)
     TRY(assemble_matrix(ctx, which, prec, s));
     Workspace &w = ctx->ws;
     const DevMat &m = ctx->dm[which];
@@ -976,12 +983,50 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int bl
     fs.tail = ctx->tune.tail != 2;
     fs.smem_optin = ctx->smem_optin;
     e = counted(ctx, PF_K_FACTOR, 2, s, [&] {
-        return launch_factor(m, prec, w.A[which], F, ctx->dc.ninst, w.fstatus[which][prec], fs, s);
+        return launch_factor(m, prec, w.A[which], F, nf, w.fstatus[which][prec], fs, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "factor launch");
-    e = launch_tail_values(m, prec, F, w.TV[which][prec], ctx->dc.ninst, s);
+    e = launch_tail_values(m, prec, F, w.TV[which][prec], nf, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tail values launch");
     w.factored[which][prec] = true;
+    return PF_OK;
+}
+
+// Low-rank outages: Z and K of every outage instance of both matrices from
+// the base factors (after factor_both with lowrank).
+pf_status prepare_lowrank(pf_ctx *ctx, int prec, cudaStream_t s) {
+    Workspace &w = ctx->ws;
+    const int ninst = ctx->dc.ninst;
+    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
+    for (int m = 0; m < 2; m++) {
+        const DevMat &D = ctx->dm[m];
+        if (!w.LZ[m][prec]) {
+            const size_t nz = size_t(ninst) * 2 * size_t(std::max(1, D.n));
+            const size_t ns = size_t(2 * (ninst - 1)) * size_t(std::max(1, D.n));
+            if (prec == PF_FP64) {
+                double *z = nullptr, *g = nullptr;
+                TRY(dalloc(ctx, &z, nz));
+                TRY(dalloc(ctx, &g, ns));
+                w.LZ[m][prec] = z;
+                w.Lscr[m][prec] = g;
+            } else {
+                float *z = nullptr, *g = nullptr;
+                TRY(dalloc(ctx, &z, nz));
+                TRY(dalloc(ctx, &g, ns));
+                w.LZ[m][prec] = z;
+                w.Lscr[m][prec] = g;
+            }
+            (void)elt;
+        }
+        if (!w.LK[m]) TRY(dalloc(ctx, &w.LK[m], size_t(4) * size_t(ninst)));
+        const void *F = prec == PF_FP64 ? (const void *)w.F64[m] : (const void *)w.F32[m];
+        const void *TV = ctx->tune.tail != 2 ? w.TV[m][prec] : nullptr;
+        cudaError_t e = counted(ctx, PF_K_SOLVE, 2, s, [&] {
+            return launch_lowrank(D, ctx->dn, ctx->dc, m, prec, F, TV, w.LZ[m][prec], w.LK[m],
+                                  w.Lscr[m][prec], w.fstatus[m][prec], ctx->smem_optin, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "low-rank outages");
+    }
     return PF_OK;
 }
 
@@ -989,13 +1034,13 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int bl
 // instances) the two factorisations are independent chains of dependent
 // columns: B'' runs on a second stream beside B', each launch capped at one
 // block per SM so both are resident at once.
-pf_status factor_both(pf_ctx *ctx, int prec, cudaStream_t s) {
+pf_status factor_both(pf_ctx *ctx, int prec, cudaStream_t s, bool lowrank) {
     Workspace &w = ctx->ws;
-    const int ninst = ctx->dc.ninst;
+    const int ninst = lowrank ? 1 : ctx->dc.ninst;
     const bool dep = ctx->tune.factor == 1 || (ctx->tune.factor == 0 && ninst < ctx->num_sms / 2);
     if (!dep) {
-        TRY(factor_matrix(ctx, PF_MAT_BP, prec, s));
-        TRY(factor_matrix(ctx, PF_MAT_BPP, prec, s));
+        TRY(factor_matrix(ctx, PF_MAT_BP, prec, s, 2, ninst));
+        TRY(factor_matrix(ctx, PF_MAT_BPP, prec, s, 2, ninst));
         return PF_OK;
     }
     if (!w.side) {
@@ -1007,8 +1052,8 @@ pf_status factor_both(pf_ctx *ctx, int prec, cudaStream_t s) {
     cudaError_t e = cudaEventRecord(w.fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(w.side, w.fork, 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fork");
-    TRY(factor_matrix(ctx, PF_MAT_BPP, prec, w.side, 1));
-    TRY(factor_matrix(ctx, PF_MAT_BP, prec, s, 1));
+    TRY(factor_matrix(ctx, PF_MAT_BPP, prec, w.side, 1, ninst));
+    TRY(factor_matrix(ctx, PF_MAT_BP, prec, s, 1, ninst));
     e = cudaEventRecord(w.join, w.side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join, 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "join");
@@ -1532,14 +1577,21 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
                             c, res_host[c].status, res_host[c].iters);
         return PF_OK;
     }
-    TRY(factor_both(ctx, prec, s));
     Workspace &w = ctx->ws;
-    const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
-    const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
     const int nmax = std::max(ctx->dm[0].n, ctx->dm[1].n);
     const bool lanes_ok = opts->method == PF_FDPF && lane_width(nmax, prec, ctx->smem_optin) > 0;
     const int want = opts->engine != PF_ENGINE_AUTO ? opts->engine : ctx->tune.engine;
     const int engine = want == PF_ENGINE_LANES && lanes_ok ? PF_ENGINE_LANES : PF_ENGINE_BLOCK;
+    const bool lowrank = engine == PF_ENGINE_BLOCK && ctx->tune.outage == 2 && ctx->dc.ninst > 1;
+    TRY(factor_both(ctx, prec, s, lowrank));
+    if (lowrank) {
+        TRY(prepare_lowrank(ctx, prec, s));
+        // the outage instances' own factors were not computed: pf_solve and
+        // pf_get_factor need pf_factor first
+        w.factored[0][prec] = w.factored[1][prec] = false;
+    }
+    const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
+    const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
     if (engine == PF_ENGINE_LANES) {
         TRY(ensure_lanes(ctx, prec));
         LaneRun r;
@@ -1581,7 +1633,9 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
                            tail ? w.TV[1][prec] : nullptr,
                            w.A[0], w.A[1],
                            w.fstatus[0][prec], w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef,
-                           w.iv, w.vec, w.bmax, w.res, ctx->smem_optin, cl, s);
+                           w.iv, w.vec, w.bmax, w.res, ctx->smem_optin, cl, s,
+                           lowrank ? w.LZ[0][prec] : nullptr, lowrank ? w.LZ[1][prec] : nullptr,
+                           lowrank ? w.LK[0] : nullptr, lowrank ? w.LK[1] : nullptr);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
     e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,
@@ -1717,7 +1771,8 @@ pf_status pf_get_tuning(const pf_ctx *ctx, pf_tuning *out) {
 pf_status pf_set_tuning(pf_ctx *ctx, const pf_tuning *t) {
     if (!ctx || !t) return fail(ctx, PF_ERR_ARG, "null pointer");
     if (t->engine < 0 || t->engine > PF_ENGINE_LANES || t->factor < 0 || t->factor > 2 || t->tail < 0 ||
-        t->tail > 2 || (t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16))
+        t->tail > 2 || t->outage < 0 || t->outage > 2 ||
+        (t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16))
         return fail(ctx, PF_ERR_ARG, "tuning field out of range");
     ctx->tune = *t;
     ctx->tune.ms = t->ms;
@@ -1753,11 +1808,14 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     if (std::max(ctx->hm[0].max_col, ctx->hm[1].max_col) <= kDepMaxCol) factors.push_back(1);
     std::vector<int> tails{2};
     if (o.method == PF_FDPF && (ctx->dm[0].npf2 > 0 || ctx->dm[1].npf2 > 0)) tails.push_back(1);
+    std::vector<int> outages{1};
+    if (o.method == PF_FDPF && ctx->dc.ninst > 1) outages.push_back(2);
     for (int e : engines)
         for (int c : (e == PF_ENGINE_LANES ? std::vector<int>{0} : clusters))
             for (int f : factors)
                 for (int t : (e == PF_ENGINE_LANES ? std::vector<int>{0} : tails))
-                    cand.push_back(pf_tuning{e, c, f, t, 0.0});
+                    for (int u : (e == PF_ENGINE_LANES ? std::vector<int>{1} : outages))
+                        cand.push_back(pf_tuning{e, c, f, t, u, 0.0});
     std::vector<pf_case_result> res(static_cast<size_t>(ncase));
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
@@ -1765,7 +1823,7 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
         return fail(ctx, PF_ERR_CUDA, "event creation");
     }
     const pf_tuning saved = ctx->tune;
-    pf_tuning best{0, 0, 0, 0, -1.0};
+    pf_tuning best{0, 0, 0, 0, 0, -1.0};
     pf_status last = PF_OK;
     for (const pf_tuning &t : cand) {
         ctx->tune = t;

@@ -210,6 +210,11 @@ struct Workspace {
     double *famax[2] = {nullptr, nullptr};    // [ninst]
     unsigned fepoch[2] = {0u, 0u};
     void *TV[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mat][prec] tail values
+    // low-rank outages, per matrix: Z [ninst][2][n] of the factor type (per
+    // precision), K [ninst][4], solve scratch
+    void *LZ[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    double *LK[2] = {nullptr, nullptr};
+    void *Lscr[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     // second stream for the B'' factorisation beside B' (fork/join events)
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -267,7 +272,7 @@ struct pf_ctx {
     size_t smem_optin = 0;
     std::string err;
     std::vector<void *> allocations;  // everything owned by the context
-    pf_tuning tune = {0, 0, 0, 0, 0.0};  // kernel mappings (pf_autotune / pf_set_tuning)
+    pf_tuning tune = {0, 0, 0, 0, 0, 0.0};  // kernel mappings (pf_autotune / pf_set_tuning)
 };
 
 namespace gbpf {
@@ -329,7 +334,15 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         const double *A0, const double *A1,
                         const int *fstat0, const int *fstat1, const pf_run_opts &o, double *vm,
                         double *va, double *ef, double *iv, double *xg, double *bmax,
-                        pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s);
+                        pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s,
+                        const void *Z0 = nullptr, const void *Z1 = nullptr, const double *K0 = nullptr,
+                        const double *K1 = nullptr);
+// Z = A^-1 U and K = (I - S U^T Z)^-1 S of every outage instance of matrix
+// `which` from the base factor F (instance 0): the low-rank form of the
+// outage cases.  gvec: [2 (ninst - 1)][n] scratch of the factor type.
+cudaError_t launch_lowrank(const DevMat &m, const DevNet &dn, const DevCases &dc, int which, int prec,
+                           const void *F, const void *TV, void *Z, double *Kd, void *gvec, int *status,
+                           size_t smem_optin, cudaStream_t s);
 int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int nmax);
 
 // One grid of a pack (uneven multi-grid batch): its device network, case,

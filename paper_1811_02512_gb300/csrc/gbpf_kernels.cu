@@ -662,6 +662,67 @@ __global__ void __launch_bounds__(kSolveThreads)
     if (threadIdx.x == 0 && !ok) atomicExch(status, PF_ERR_TIMEOUT);
 }
 
+// ------------------------------------------------------------ low-rank outages
+
+// Z = A^-1 U for the outage instances (instance inst >= 1, column col of U =
+// the unit vector of the outaged branch's bus p = br_slot[3 e + col], zero
+// when that bus is not in the matrix): one block per (instance, column),
+// solving with the base factor (instance 0).
+template <class T>
+__global__ void __launch_bounds__(kSolveThreads)
+    k_lowrank_z(DevMat m, DevNet dn, DevCases dc, const T *F, const T *TV, T *Z, T *gvec, int use_smem,
+                int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ Ring R;
+    const int inst = 1 + int(blockIdx.x) / 2, col = int(blockIdx.x) % 2;
+    const int e = dc.inst_outage[inst];
+    const int p = (e >= 0 && dn.bstatus[e]) ? m.br_slot[3 * e + col] : -1;
+    T *z = Z + ((long long)inst * 2 + col) * m.n;
+    if (p < 0) {
+        for (int k = threadIdx.x; k < m.n; k += blockDim.x) z[k] = T(0);
+        return;
+    }
+    T *x = use_smem ? reinterpret_cast<T *>(smem_raw + kStages * kStageBytes) : gvec + (long long)blockIdx.x * m.n;
+    ring_init(&R);
+    for (int k = threadIdx.x; k < m.n; k += blockDim.x) x[k] = T(k == p ? 1 : 0);
+    __syncthreads();
+    const bool ok = block_solve<T, T>(&R, smem_raw, m, F, x, kDefaultSpin, TV);
+    for (int k = threadIdx.x; k < m.n; k += blockDim.x) z[k] = x[k];
+    if (threadIdx.x == 0 && !ok) atomicExch(status, PF_ERR_TIMEOUT);
+}
+
+// K = (I - S U^T Z)^-1 S of every outage instance (S the branch's share of
+// the matrix on its two buses), in FP64; K = 0 when the branch is already
+// out of service.
+template <class T>
+__global__ void k_lowrank_k(DevMat m, DevNet dn, DevCases dc, int which, const T *Z, double *Kout) {
+    for (int inst = 1 + blockIdx.x * blockDim.x + threadIdx.x; inst < dc.ninst; inst += gridDim.x * blockDim.x) {
+        double *Kq = Kout + 4LL * inst;
+        const int e = dc.inst_outage[inst];
+        if (e < 0 || !dn.bstatus[e]) {
+            Kq[0] = Kq[1] = Kq[2] = Kq[3] = 0.0;
+            continue;
+        }
+        const int p0 = m.br_slot[3 * e], p1 = m.br_slot[3 * e + 1], sl = m.br_slot[3 * e + 2];
+        const double s00 = p0 >= 0 ? branch_slot_value(dn, m, which, e, p0) : 0.0;
+        const double s11 = p1 >= 0 ? branch_slot_value(dn, m, which, e, p1) : 0.0;
+        const double s01 = sl >= 0 ? branch_slot_value(dn, m, which, e, sl) : 0.0;
+        const T *z0 = Z + (long long)inst * 2 * m.n, *z1 = z0 + m.n;
+        // W = U^T Z (W_ij = Z_j at bus p_i)
+        const double w00 = p0 >= 0 ? double(z0[p0]) : 0.0, w01 = p0 >= 0 ? double(z1[p0]) : 0.0;
+        const double w10 = p1 >= 0 ? double(z0[p1]) : 0.0, w11 = p1 >= 0 ? double(z1[p1]) : 0.0;
+        // N = I - S W
+        const double n00 = 1.0 - (s00 * w00 + s01 * w10), n01 = -(s00 * w01 + s01 * w11);
+        const double n10 = -(s01 * w00 + s11 * w10), n11 = 1.0 - (s01 * w01 + s11 * w11);
+        const double det = n00 * n11 - n01 * n10;
+        const double i00 = n11 / det, i01 = -n01 / det, i10 = -n10 / det, i11 = n00 / det;
+        Kq[0] = i00 * s00 + i01 * s01;
+        Kq[1] = i00 * s01 + i01 * s11;
+        Kq[2] = i10 * s00 + i11 * s01;
+        Kq[3] = i10 * s01 + i11 * s11;
+    }
+}
+
 // ------------------------------------------------------------ Section II.A
 
 __global__ void k_polar_to_rect(int nbus, int ncase, const double *vm, const double *va,
@@ -711,6 +772,10 @@ struct RunArgs {
     DevMat m0, m1;  // B', B''
     const void *F0, *F1;
     const void *TV0, *TV1;  // gathered tail values per instance (or null)
+    // low-rank outages: outage cases solve with the base factor (instance 0)
+    // and the correction x += Z K (x[p0], x[p1]) of their instance (or null)
+    const void *Z0, *Z1;     // [ninst][2][n] T
+    const double *K0, *K1;   // [ninst][4]
     const double *A0, *A1;  // FP64 assembled values of B', B'' (refinement residuals)
     const int *fs0, *fs1;
     double tol;
@@ -774,6 +839,34 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
     return m;
 }
 
+// Low-rank outage correction of one case's solve (Woodbury): the outage
+// takes the branch's share U S U^T out of the base matrix A (U the unit
+// columns of the branch's two buses p0, p1 in level order, absent ones
+// skipped), so (A - U S U^T)^-1 b = y + Z K (U^T y) with y = A^-1 b, Z =
+// A^-1 U and K = (I - S U^T Z)^-1 S, both computed once per factorisation.
+template <class T>
+struct LowRank {
+    const T *Z = nullptr;     // [2][n] columns A^-1 e_p0, A^-1 e_p1 (null: no correction)
+    const double *K = nullptr;
+    int p0 = -1, p1 = -1;
+};
+
+template <class T, class X>
+__device__ void lowrank_correct(const LowRank<T> &lr, X *x, int n, double *red) {
+    if (!lr.Z) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double y0 = lr.p0 >= 0 ? double(x[lr.p0]) : 0.0, y1 = lr.p1 >= 0 ? double(x[lr.p1]) : 0.0;
+        red[0] = lr.K[0] * y0 + lr.K[1] * y1;
+        red[1] = lr.K[2] * y0 + lr.K[3] * y1;
+    }
+    __syncthreads();
+    const double s0 = red[0], s1 = red[1];
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+        x[r] = X(double(x[r]) + double(lr.Z[r]) * s0 + double(lr.Z[n + r]) * s1);
+    __syncthreads();
+}
+
 // Solves one matrix of case c in the cluster's CTA 0 (the others wait at the
 // following cluster barrier): the exchange vector is staged into shared
 // memory, solved with the TMA-staged sweeps and written back.  With an FP32
@@ -783,7 +876,7 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
 template <class T>
 __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T *xs,
                             const DevMat &m, const T *F, const T *tv, const double *A, int c,
-                            double *red, int &ir_steps) {
+                            double *red, int &ir_steps, const LowRank<T> &lr) {
     const int nbus = a.dn.nbus;
     double *xg = a.xg + (long long)c * 3 * nbus;
     bool ok = true;
@@ -792,9 +885,11 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) xs[r] = T(xg[r]);
             __syncthreads();
             ok = block_solve<T, T>(R, stages, m, F, xs, a.spin, tv);
+            if (ok) lowrank_correct<T, T>(lr, xs, m.n, red);
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) xg[r] = double(xs[r]);
         } else {
             ok = block_solve<T, double>(R, stages, m, F, xg, a.spin, tv);
+            if (ok) lowrank_correct<T, double>(lr, xg, m.n, red);
         }
     } else {
         double *x64 = xg + nbus;
@@ -808,6 +903,7 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
         for (int k = 0;; k++) {
             ok = block_solve<T, T>(R, stages, m, F, xv, a.spin, tv);
             if (!ok) break;
+            lowrank_correct<T, T>(lr, xv, m.n, red);
             for (int r = threadIdx.x; r < m.n; r += blockDim.x)
                 x64[r] = (k == 0 ? 0.0 : x64[r]) + double(xv[r]);
             __syncthreads();
@@ -849,18 +945,32 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
     double *sn = cs + nbus;
     const double *xg = a.xg + (long long)c * 3 * nbus;
     double *flag = a.bmax + (long long)c * 16 + 15;
-    const T *F0 = static_cast<const T *>(a.F0) + (long long)inst * a.m0.stride;
-    const T *F1 = static_cast<const T *>(a.F1) + (long long)inst * a.m1.stride;
-    const T *TV0 = a.TV0 ? static_cast<const T *>(a.TV0) + (long long)inst * a.m0.tv_stride : nullptr;
-    const T *TV1 = a.TV1 ? static_cast<const T *>(a.TV1) + (long long)inst * a.m1.tv_stride : nullptr;
+    const bool lowrank = a.Z0 != nullptr && inst > 0;
+    const int finst = lowrank ? 0 : inst;  // the instance whose factor the solves use
+    const T *F0 = static_cast<const T *>(a.F0) + (long long)finst * a.m0.stride;
+    const T *F1 = static_cast<const T *>(a.F1) + (long long)finst * a.m1.stride;
+    const T *TV0 = a.TV0 ? static_cast<const T *>(a.TV0) + (long long)finst * a.m0.tv_stride : nullptr;
+    const T *TV1 = a.TV1 ? static_cast<const T *>(a.TV1) + (long long)finst * a.m1.tv_stride : nullptr;
+    LowRank<T> lr0, lr1;
+    if (lowrank) {
+        const int e = a.dc.inst_outage[inst];
+        lr0.Z = static_cast<const T *>(a.Z0) + (long long)inst * 2 * a.m0.n;
+        lr0.K = a.K0 + 4LL * inst;
+        lr0.p0 = a.m0.br_slot[3 * e];
+        lr0.p1 = a.m0.br_slot[3 * e + 1];
+        lr1.Z = static_cast<const T *>(a.Z1) + (long long)inst * 2 * a.m1.n;
+        lr1.K = a.K1 + 4LL * inst;
+        lr1.p0 = a.m1.br_slot[3 * e];
+        lr1.p1 = a.m1.br_slot[3 * e + 1];
+    }
     const double *A0 = a.A0 + (long long)inst * a.m0.stride;
     const double *A1 = a.A1 + (long long)inst * a.m1.stride;
     int ir_steps = 0;
     const int slice = (nbus + C - 1) / C;
     const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
     int status = PF_ERR_NOT_CONVERGED;
-    if (a.fs0[inst] != PF_OK) status = a.fs0[inst];
-    else if (a.fs1[inst] != PF_OK) status = a.fs1[inst];
+    if (a.fs0[finst] != PF_OK) status = a.fs0[finst];
+    else if (a.fs1[finst] != PF_OK) status = a.fs1[finst];
     int iters = 0;
     double mis = INFINITY;
     double *iv = a.iv + (long long)c * nbus;
@@ -890,7 +1000,7 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, TV0, A0, c, red, ir_steps);
+                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, TV0, A0, c, red, ir_steps, lr0);
                 if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
             }
             cluster_sync<C>();
@@ -918,7 +1028,7 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, TV1, A1, c, red, ir_steps);
+                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, TV1, A1, c, red, ir_steps, lr1);
                 if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
             }
             cluster_sync<C>();
@@ -1043,6 +1153,38 @@ cudaError_t launch_ybus(const DevNet &dn, cudaStream_t s) {
 cudaError_t launch_case_spec(const DevNet &dn, const DevCases &dc, const double *ls,
                              cudaStream_t s) {
     k_case_spec<<<grid_for((long long)dc.ncase * dn.nbus, 256), 256, 0, s>>>(dn, dc, ls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lowrank(const DevMat &m, const DevNet &dn, const DevCases &dc, int which, int prec,
+                           const void *F, const void *TV, void *Z, double *Kd, void *gvec, int *status,
+                           size_t smem_optin, cudaStream_t s) {
+    if (dc.ninst < 2) return cudaSuccess;
+    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
+    const size_t ring = size_t(kStages) * kStageBytes;
+    size_t smem = ring + elt * size_t(m.n);
+    const int use_smem = smem + 2048 <= smem_optin;
+    if (!use_smem) smem = ring;
+    if (m.npf2 == 0) TV = nullptr;
+    const int blocks = 2 * (dc.ninst - 1);
+    cudaError_t e;
+    if (prec == PF_FP64) {
+        e = cudaFuncSetAttribute(k_lowrank_z<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_lowrank_z<double><<<blocks, kSolveThreads, smem, s>>>(m, dn, dc, static_cast<const double *>(F),
+                                                                static_cast<const double *>(TV),
+                                                                static_cast<double *>(Z),
+                                                                static_cast<double *>(gvec), use_smem, status);
+        k_lowrank_k<double><<<(dc.ninst + 127) / 128, 128, 0, s>>>(m, dn, dc, which, static_cast<const double *>(Z), Kd);
+    } else {
+        e = cudaFuncSetAttribute(k_lowrank_z<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_lowrank_z<float><<<blocks, kSolveThreads, smem, s>>>(m, dn, dc, static_cast<const float *>(F),
+                                                               static_cast<const float *>(TV),
+                                                               static_cast<float *>(Z),
+                                                               static_cast<float *>(gvec), use_smem, status);
+        k_lowrank_k<float><<<(dc.ninst + 127) / 128, 128, 0, s>>>(m, dn, dc, which, static_cast<const float *>(Z), Kd);
+    }
     return cudaGetLastError();
 }
 
@@ -1234,6 +1376,8 @@ void fill_run_args(RunArgs &a, const DevNet &dn, const DevCases &dc, const DevMa
                    pf_case_result *res) {
     a.TV0 = m[0].npf2 > 0 ? TV0 : nullptr;
     a.TV1 = m[1].npf2 > 0 ? TV1 : nullptr;
+    a.Z0 = a.Z1 = nullptr;
+    a.K0 = a.K1 = nullptr;
     a.iv = iv;
     a.A0 = A0;
     a.A1 = A1;
@@ -1334,8 +1478,13 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         const double *A0, const double *A1, const int *fstat0, const int *fstat1,
                         const pf_run_opts &o, double *vm, double *va, double *ef, double *iv,
                         double *xg, double *bmax, pf_case_result *res, size_t smem_optin,
-                        int cluster, cudaStream_t s) {
+                        int cluster, cudaStream_t s, const void *Z0, const void *Z1, const double *K0,
+                        const double *K1) {
     RunArgs a;
+    a.Z0 = Z0;
+    a.Z1 = Z1;
+    a.K0 = K0;
+    a.K1 = K1;
     a.TV0 = m[0].npf2 > 0 ? TV0 : nullptr;
     a.TV1 = m[1].npf2 > 0 ? TV1 : nullptr;
     a.iv = iv;

@@ -326,7 +326,7 @@ def pf_branch_flows(ctx, vm_dev, va_dev, ncase, flows_dev, loss_dev, stream=None
 
 class pf_tuning(C.Structure):
     _fields_ = [("engine", C.c_int32), ("cluster", C.c_int32), ("factor", C.c_int32),
-                ("tail", C.c_int32), ("ms", C.c_double)]
+                ("tail", C.c_int32), ("outage", C.c_int32), ("ms", C.c_double)]
 
 
 def pf_autotune(ctx, opts, vm_dev, va_dev, reps=3, stream=None):
@@ -344,8 +344,8 @@ def pf_get_tuning(ctx):
     return {k: getattr(t, k) for k, _ in pf_tuning._fields_}
 
 
-def pf_set_tuning(ctx, engine=0, cluster=0, factor=0, tail=0):
-    t = pf_tuning(engine, cluster, factor, tail, 0.0)
+def pf_set_tuning(ctx, engine=0, cluster=0, factor=0, tail=0, outage=0):
+    t = pf_tuning(engine, cluster, factor, tail, outage, 0.0)
     _check(ctx, load().pf_set_tuning(ctx, C.byref(t)), "pf_set_tuning")
 
 

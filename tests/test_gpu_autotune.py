@@ -74,3 +74,31 @@ def test_autotune_single_and_batch(oracle):
         assert rc == oracle.OK
         assert np.max(np.abs(v[c] - vm0)) <= 1e-8 and np.max(np.abs(a[c] - va0)) <= 1e-8
     g.close()
+
+
+@pytest.mark.parametrize("precision", [gbpf.PF_FP64, gbpf.PF_FP32])
+def test_low_rank_outages_match_oracle(oracle, precision):
+    """Outage cases solved with the base factors and the low-rank (Woodbury)
+    correction of every solve reach the oracle's solution of each outaged
+    grid, as the per-case factors do."""
+    base = gridgen.config(1)
+    sc = gridgen.scenarios(base, n_load=2, n_outage=14, seed=9)
+    g = gbpf.Grid(base)
+    g.set_cases(sc.ncase, sc.load_scale, sc.outage)
+    vm = torch.zeros((sc.ncase, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, precision, tol=1e-11, max_iter=300)
+    out = {}
+    for outage in (1, 2):
+        gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, outage=outage)
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+        assert st == gbpf.PF_OK, (outage, gbpf.pf_last_error(g.ctx))
+        out[outage] = (vm.cpu().numpy().copy(), va.cpu().numpy().copy())
+    for c in (0, 2, 7, 15):
+        cc = gridgen.apply_scenario(base, sc, c)
+        rc, vm0, va0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+        assert rc == oracle.OK
+        for outage in (1, 2):
+            assert np.max(np.abs(out[outage][0][c] - vm0)) <= 1e-8, (outage, c)
+            assert np.max(np.abs(out[outage][1][c] - va0)) <= 1e-8, (outage, c)
+    g.close()
