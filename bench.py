@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip pf_autotune (untimed) before the warm-up")
+    ap.add_argument("--mapping", default=None,
+                    help="engine,cluster,factor,tail,outage: set this kernel mapping instead of tuning")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     return ap.parse_args()
 
@@ -576,7 +578,11 @@ def main():
         return gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase, stream=stream)
 
     tuning = None
-    if not args.no_autotune and args.engine == "auto":
+    if args.mapping:
+        e_, c_, f_, t_, o_ = (int(v) for v in args.mapping.split(","))
+        gbpf.pf_set_tuning(g.ctx, engine=e_, cluster=c_, factor=f_, tail=t_, outage=o_)
+        tuning = gbpf.pf_get_tuning(g.ctx)
+    elif not args.no_autotune and args.engine == "auto":
         t0 = time.perf_counter()
         tuning = gbpf.pf_autotune(g.ctx, opts, vm, va, reps=2 if ncase == 1 else 1, stream=stream)
         tuning["tune_s"] = time.perf_counter() - t0
