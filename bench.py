@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--ncase", type=int, default=1024,
                     help="batch10k: number of cases (half load scenarios, half outages)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="plain10k: skip the batched FP32+IR measurement reported beside it")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip pf_autotune (untimed) before the warm-up")
     ap.add_argument("--mapping", default=None,
@@ -269,6 +271,24 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def batched_line(args):
+    """The metric's other half -- the same grid as 1,024 load/outage cases in
+    one launch, FP32 factor + FP64 refinement -- measured by this script's
+    batch10k workload in a child process; its main figures."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "batch10k", "--steps", "5",
+           "--warmup", str(max(3, args.warmup)), "--no-cpu-baseline"]
+    try:
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=900, check=True).stdout
+        d = json.loads([ln for ln in out.splitlines() if ln.startswith("{")][-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as exc:
+        return {"unavailable": str(exc)[:200]}
+    keep = ("value", "unit", "ms_per_step", "dtype", "converged", "gpu_launches", "roofline", "e2e",
+            "clocks")
+    r = {k: d.get(k) for k in keep}
+    r["config"] = d.get("config")
+    return r
 
 
 def aggregate_ranks(total_ms, solves_local, world, device):
@@ -684,6 +704,8 @@ def main():
                     "d2h_bytes_per_step": int(d2h)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_s, ncase)
+    if rank == 0 and world == 1 and args.workload == "plain10k" and not args.no_batched:
+        line["batched_fp32_ir"] = batched_line(args)
     if rank == 0:
         print(json.dumps(line))
     g.close()
