@@ -252,6 +252,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if args.workload not in ("plain10k", "plain120", "batch10k"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the fast decoupled "
+                          "workloads (plain10k, plain120, batch10k); " + args.workload + " has none"}))
+        return
     from paper_1811_02512_gb300 import gridgen  # noqa: F401
     base, ncase, _, _ = make_workload(args.workload)
     for _ in range(args.warmup):

@@ -435,3 +435,21 @@ def test_fdpf_nr_fallback(oracle):
     st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, torch.zeros_like(vm), 1)
     assert st == gbpf.PF_OK and res[0]["method"] == gbpf.PF_FDPF
     g.close()
+
+
+@pytest.mark.parametrize("precision", [gbpf.PF_FP64, gbpf.PF_FP32])
+def test_largest_grid_single_case(oracle, precision):
+    """The largest grid of the uneven multi-grid set (79,035 buses: its FP64
+    solve vector does not fit shared memory, its factor columns are the
+    longest) as a single case, against the oracle's Newton-Raphson."""
+    sizes = gridgen.config4_sizes()
+    g_ = int(np.argmax([n for n, _ in sizes]))
+    n, seed = sizes[g_]
+    case = gridgen.with_loading_factor(gridgen.delaunay_raw(n, seed, name=f"multigrid{g_}"))
+    rc, vm0, va0, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
+    assert rc == oracle.OK
+    g = _grid(case)
+    st, res, vm, va = _run(g, 1, precision=precision, tol=1e-11, max_iter=300)
+    assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    assert np.max(np.abs(vm[0] - vm0)) <= 1e-8 and np.max(np.abs(va[0] - va0)) <= 1e-8
+    g.close()
