@@ -253,8 +253,8 @@ __device__ __forceinline__ void row_finish(const Vec<X, NB> &acc, const T *Dv, i
     for (int i = 0; i < NB; i++) x[size_t(r) * NB + i] = out[i];
 }
 
-// Rows of one staged piece.  mode 0: thread per row; mode 1: warp per row
-// over all warps; mode 2: the calling warp alone walks the narrow levels
+// Rows of one staged piece.  mode 0: thread per row; mode 1: groups of 8
+// lanes per row over all warps; mode 2: the calling warp alone walks the narrow levels
 // l0..l1 of the piece (ascending forward, descending when the piece carries
 // the diagonal, i.e. in the back substitution), split into groups of 32/R
 // lanes for the R rows of each level.  Entries of a row are spread over the
@@ -329,14 +329,20 @@ __device__ __forceinline__ void piece_rows(const int *h, const unsigned char *ba
         if (lane == 0)
             row_finish<T, X, NB, TRANS>(acc, e0 == P[r0 - p_lo] ? Dv : nullptr, d_lo, x, r0);
     } else if (mode == 1) {
-        for (int r = r0 + first; r < r1; r += stride) {
+        // groups of 8 lanes per row, four rows per warp and round: the rows
+        // of these levels are short, so a three-step reduction suffices
+        constexpr int G = 8;
+        const int grp = lane / G, gl = lane % G;
+        for (int rb = r0 + first * (32 / G); rb < r1; rb += stride * (32 / G)) {
+            const int r = rb + grp;
             Vec<X, NB> acc;
 #pragma unroll
             for (int i = 0; i < NB; i++) acc.v[i] = X(0);
-            row_partial<T, X, NB, TRANS>(acc, P, I, Vv, x, r, p_lo, i_lo, v_lo, lane, 32);
+            if (r < r1) row_partial<T, X, NB, TRANS>(acc, P, I, Vv, x, r, p_lo, i_lo, v_lo, gl, G);
+            for (int o = G >> 1; o > 0; o >>= 1)
 #pragma unroll
-            for (int i = 0; i < NB; i++) acc.v[i] = warp_sum(acc.v[i]);
-            if (lane == 0) row_finish<T, X, NB, TRANS>(acc, Dv, d_lo, x, r);
+                for (int i = 0; i < NB; i++) acc.v[i] += __shfl_xor_sync(0xffffffffu, acc.v[i], o);
+            if (r < r1 && gl == 0) row_finish<T, X, NB, TRANS>(acc, Dv, d_lo, x, r);
         }
     } else {
         const int *LP = reinterpret_cast<const int *>(base + h[12]) - h[13];

@@ -21,7 +21,7 @@ constexpr int kPieceSlack = 128;
 
 // One staged piece: rows (columns) [r0, r1) whose entries are [e0, e1) of
 // the CSR (CSC) arrays, all in level order.  mode: 0 one thread per row,
-// 1 one warp per row (whole block), 2 warp 0 alone over rows of the narrow
+// 1 groups of 8 lanes per row (whole block), 2 warp 0 alone over rows of the narrow
 // levels l0..l1, 3 warp 0 alone over part [e0, e1) of the single row r0 (a
 // row too long for one stage); run_end: for modes 2, 3 and 4, the first
 // piece after the run of single-warp pieces.  Mode 0/1/3 pieces lie in one
