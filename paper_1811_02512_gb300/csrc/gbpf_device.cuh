@@ -307,7 +307,7 @@ __device__ __forceinline__ void piece_rows(const int *h, const unsigned char *ba
             }
             __syncwarp();
         }
-    } else if (mode == 0 || mode == 5 || mode == 6) {
+    } else if (mode == 0 || mode == 6) {
         for (int r = r0 + first; r < r1; r += stride) {
             Vec<X, NB> acc;
 #pragma unroll
@@ -328,10 +328,11 @@ __device__ __forceinline__ void piece_rows(const int *h, const unsigned char *ba
         for (int i = 0; i < NB; i++) acc.v[i] = warp_sum(acc.v[i]);
         if (lane == 0)
             row_finish<T, X, NB, TRANS>(acc, e0 == P[r0 - p_lo] ? Dv : nullptr, d_lo, x, r0);
-    } else if (mode == 1) {
-        // groups of 8 lanes per row, four rows per warp and round: the rows
-        // of these levels are short, so a three-step reduction suffices
-        constexpr int G = 8;
+    } else if (mode == 1 || mode == 5) {
+        // groups of G lanes per row, 32 / G rows per warp and round: the rows
+        // of these pieces are short (mode 1, G = 8) or of moderate length
+        // (mode 5, G = 4), so a two- or three-step reduction suffices
+        const int G = mode == 1 ? 8 : 4;
         const int grp = lane / G, gl = lane % G;
         for (int rb = r0 + first * (32 / G); rb < r1; rb += stride * (32 / G)) {
             const int r = rb + grp;
@@ -489,7 +490,8 @@ __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces
             } else {
                 if (!*err)
                     piece_rows<T, X, NB, TRANS>(h, stages + size_t(st) * kStageBytes, x, mode,
-                                                mode == 1 ? warp : int(threadIdx.x), mode == 1 ? ncw : nct);
+                                                (mode == 1 || mode == 5) ? warp : int(threadIdx.x),
+                                                (mode == 1 || mode == 5) ? ncw : nct);
                 consumer_sync(nct);
                 if (*err) {
                     ok = false;

@@ -27,7 +27,7 @@ constexpr int kPieceSlack = 128;
 // piece after the run of single-warp pieces.  Mode 0/1/3 pieces lie in one
 // level.  The sweeps with a scatter tail add: 4 warp 0 alone over the slot
 // rows [e0/32, e1/32) of the tail levels r0..r1-1 of a scatter schedule
-// (l0 = first tail row); 5 one thread per row over the entries of the tail
+// (l0 = first tail row); 5 groups of 4 lanes per row over the entries of the tail
 // rows in columns below the tail; 6 one thread per row, inverse diagonal
 // only.
 struct Piece {
