@@ -650,15 +650,17 @@ def main():
 
     # end to end through the C ABI with host buffers: per step copy the case
     # inputs (load scales, outages) from pinned host memory, run, copy V back
-    ls_host = None if load_scale is None else torch.from_numpy(load_scale).pin_memory()
+    # (a single case uploads its load profile too: all ones, the base loading)
+    ls_np = load_scale if load_scale is not None else np.ones((ncase, base.n))
+    ls_host = torch.from_numpy(np.ascontiguousarray(ls_np, dtype=np.float64)).pin_memory()
     out_host = torch.empty((2, ncase, base.n), dtype=torch.float64).pin_memory()
-    h2d = (0 if load_scale is None else load_scale.nbytes) + (0 if outage is None else outage.nbytes)
+    h2d = ls_host.numel() * 8 + (0 if outage is None else outage.nbytes)
     d2h = out_host.numel() * 8 + ncase * 24
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     te0 = time.perf_counter()
     for _ in range(e2e_steps):
-        g.set_cases(ncase, None if ls_host is None else ls_host.numpy(), outage)
+        g.set_cases(ncase, ls_host.numpy(), outage)
         st, res_e = step()
         out_host[0].copy_(vm, non_blocking=True)
         out_host[1].copy_(va, non_blocking=True)
