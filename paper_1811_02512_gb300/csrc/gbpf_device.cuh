@@ -48,6 +48,39 @@ __device__ double block_max(double v, double *red) {
 
 __device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
 
+// |x| as its IEEE-754 bit pattern: non-negative doubles order like their bit
+// patterns read as unsigned integers, with every NaN above infinity, so a
+// running maximum of these keys is the NaN-winning maximum of |x| and runs
+// on the integer pipe instead of the (slow) FP64 one.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+
+// Block-wide maximum of abs_key values; every thread receives the result.
+// `red` is a 33-entry shared array.  Contains two __syncthreads.
+__device__ unsigned long long block_max_key(unsigned long long v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long *r = reinterpret_cast<unsigned long long *>(red);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    if (lane == 0) r[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = (lane < int(blockDim.x >> 5)) ? r[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, w, o);
+            w = u > w ? u : w;
+        }
+        if (lane == 0) r[32] = w;
+    }
+    __syncthreads();
+    return r[32];
+}
+
 // Atomic maximum of a non-negative double through its bit pattern (IEEE order
 // of non-negative doubles equals integer order; NaN patterns sort above Inf).
 __device__ void atomic_max_nonneg(double *addr, double v) {
@@ -572,12 +605,13 @@ __device__ __forceinline__ void small_sincos(double x, double *s, double *c) {
     *c = 1.0 + x2 * u;
 }
 
-// Injection at bus i of one case: I_i = sum_k Y_ik V_k on the base admittance
+// Current at bus i of one case: I_i = sum_k Y_ik V_k on the base admittance
 // matrix, minus the terms of the case's outaged branch (if any) at its end
-// buses; returns S_i = V_i conj(I_i) as (P, Q).
-__device__ __forceinline__ void bus_injection(const DevNet &dn, int i, int outage,
-                                              const double *e, const double *f, double &P,
-                                              double &Q) {
+// buses; returns (Re I_i, Im I_i).  The injection is S_i = V_i conj(I_i):
+// P_i = e_i Re I_i + f_i Im I_i, Q_i = f_i Re I_i - e_i Im I_i.
+__device__ __forceinline__ void bus_current(const DevNet &dn, int i, int outage,
+                                            const double *e, const double *f, double &ir_out,
+                                            double &ii_out) {
     double ir = 0.0, ii = 0.0;
     for (int p = dn.rowptr[i]; p < dn.rowptr[i + 1]; p++) {
         const int k = dn.col[p];
@@ -602,6 +636,16 @@ __device__ __forceinline__ void bus_injection(const DevNet &dn, int i, int outag
         ir -= gs * e[i] - bs * f[i] + gm * e[o] - bm * f[o];
         ii -= gs * f[i] + bs * e[i] + gm * f[o] + bm * e[o];
     }
+    ir_out = ir;
+    ii_out = ii;
+}
+
+// Injection at bus i of one case, S_i = V_i conj(I_i) as (P, Q).
+__device__ __forceinline__ void bus_injection(const DevNet &dn, int i, int outage,
+                                              const double *e, const double *f, double &P,
+                                              double &Q) {
+    double ir, ii;
+    bus_current(dn, i, outage, e, f, ir, ii);
     P = e[i] * ir + f[i] * ii;
     Q = f[i] * ir - e[i] * ii;
 }

@@ -795,11 +795,17 @@ struct RunArgs {
 
 // One half-iteration's mismatch for case c on the C CTAs of its cluster: each
 // CTA owns a slice of buses, forms e + jf from V and the cached cos/sin of
-// theta, then (after a cluster barrier) the injections of its rows and writes
+// theta, then (after a cluster barrier) the currents of its rows and writes
 // dP/V (which = 0, B' unknowns) or dQ/V (which = 1, B'' unknowns) into the
-// exchange vector in level order.  Returns the case maximum (cluster-uniform).
+// exchange vector in level order.  Returns the case maximum (cluster-uniform)
+// of |dP| over non-slack and |dQ| over PQ buses when `full`, else of the
+// half-iteration's own part only (|dP| or |dQ|): a lower bound of the full
+// maximum, so a partial maximum above the tolerance already decides "not
+// converged" and only one at or below it needs the full check.  Skipping the
+// other part saves FP64 work, which bounds batches on this part.
 template <int C>
-__device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which, double *red) {
+__device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which, double *red,
+                                   bool full) {
     const DevNet &dn = a.dn;
     const int nbus = dn.nbus;
     const int slice = (nbus + C - 1) / C;
@@ -817,22 +823,24 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
     const int outage = a.dc.outage[c];
     const int *nob = which == 0 ? a.m0.new_of_bus : a.m1.new_of_bus;
     double *xg = a.xg + (long long)c * 3 * nbus;
-    double mx = 0.0;
+    const bool wantP = full || which == 0, wantQ = full || which == 1;
+    unsigned long long mx = 0;
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        double P, Q;
-        bus_injection(dn, i, outage, e, f, P, Q);
+        double ir, ii;
+        bus_current(dn, i, outage, e, f, ir, ii);
         const int t = dn.btype[i];
         const long long idx = (long long)c * nbus + i;
-        const double dP = (t != PF_BUS_SLACK) ? a.dc.Psp[idx] - P : 0.0;
-        const double dQ = (t == PF_BUS_PQ) ? a.dc.Qsp[idx] - Q : 0.0;
-        double l = fmax(fabs(dP), fabs(dQ));
-        if (dP != dP || dQ != dQ) l = __longlong_as_double(0x7ff8000000000000ll);
-        mx = nan_max(mx, l);
+        double dP = 0.0, dQ = 0.0;
+        if (wantP && t != PF_BUS_SLACK) dP = a.dc.Psp[idx] - (e[i] * ir + f[i] * ii);
+        if (wantQ && t == PF_BUS_PQ) dQ = a.dc.Qsp[idx] - (f[i] * ir - e[i] * ii);
+        const unsigned long long kp = abs_key(dP), kq = abs_key(dQ);
+        mx = kp > mx ? kp : mx;
+        mx = kq > mx ? kq : mx;
         const int k = nob[i];
         if (k >= 0) xg[k] = (which == 0 ? dP : dQ) * a.iv[(long long)c * nbus + i];
     }
-    mx = block_max(mx, red);
-    if (threadIdx.x == 0) a.bmax[(long long)c * 16 + rank] = mx;
+    mx = block_max_key(mx, red);
+    if (threadIdx.x == 0) a.bmax[(long long)c * 16 + rank] = __longlong_as_double(static_cast<long long>(mx));
     cluster_sync<C>();
     double m = 0.0;
     for (int r = 0; r < C; r++) m = nan_max(m, a.bmax[(long long)c * 16 + r]);
@@ -894,12 +902,13 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
     } else {
         double *x64 = xg + nbus;
         T *xv = xs ? xs : reinterpret_cast<T *>(x64 + m.n);  // FP32 work vector
-        double bn = 0.0;
+        unsigned long long bk = 0;
         for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
             xv[r] = T(xg[r]);
-            bn = fmax(bn, fabs(xg[r]));
+            const unsigned long long k = abs_key(xg[r]);
+            bk = k > bk ? k : bk;
         }
-        bn = block_max(bn, red);
+        const double bn = __longlong_as_double(static_cast<long long>(block_max_key(bk, red)));
         for (int k = 0;; k++) {
             ok = block_solve<T, T>(R, stages, m, F, xv, a.spin, tv);
             if (!ok) break;
@@ -908,14 +917,15 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
                 x64[r] = (k == 0 ? 0.0 : x64[r]) + double(xv[r]);
             __syncthreads();
             if (k >= a.ir_max) break;
-            double rn = 0.0;
+            unsigned long long rk = 0;
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
                 double s = xg[r] - A[r] * x64[r];
                 for (int e = m.Ap[r]; e < m.Ap[r + 1]; e++) s -= A[m.Apos[e]] * x64[m.Aj[e]];
                 xv[r] = T(s);
-                rn = nan_max(rn, fabs(s));
+                const unsigned long long k = abs_key(s);
+                rk = k > rk ? k : rk;
             }
-            rn = block_max(rn, red);
+            const double rn = __longlong_as_double(static_cast<long long>(block_max_key(rk, red)));
             if (!(rn > a.ir_tol * bn) || !(rn > a.ir_abs)) break;
             ir_steps++;
         }
@@ -985,18 +995,21 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
     }
     cluster_sync<C>();
     // cos/sin of the angles are rotated by each step (small_sincos) rather than
-    // re-evaluated; before a convergence decision they are recomputed exactly
-    // and the mismatch re-checked, so the decision is taken at the exact state
+    // re-evaluated, and each half-iteration evaluates only its own part of the
+    // mismatch; before a convergence decision the cos/sin are recomputed
+    // exactly and the full mismatch re-checked, so the decision is taken on
+    // both parts at the exact state
     bool rotated = false;
     auto exact_check = [&](int which) {
-        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) sincos(va[i], &sn[i], &cs[i]);
+        if (rotated)
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) sincos(va[i], &sn[i], &cs[i]);
         rotated = false;
-        return cluster_mismatch<C>(a, c, rank, which, red);
+        return cluster_mismatch<C>(a, c, rank, which, red, true);
     };
     if (status == PF_ERR_NOT_CONVERGED) {
         for (int it = 0; it < a.max_iter; it++) {
-            mis = cluster_mismatch<C>(a, c, rank, 0, red);
-            if (mis <= a.tol && rotated) mis = exact_check(0);
+            mis = cluster_mismatch<C>(a, c, rank, 0, red, false);
+            if (mis <= a.tol) mis = exact_check(0);
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
@@ -1023,8 +1036,8 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
             }
             rotated = true;
             iters++;
-            mis = cluster_mismatch<C>(a, c, rank, 1, red);
-            if (mis <= a.tol && rotated) mis = exact_check(1);
+            mis = cluster_mismatch<C>(a, c, rank, 1, red, false);
+            if (mis <= a.tol) mis = exact_check(1);
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
