@@ -272,6 +272,28 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
             H.ft_tmax = std::max(H.ft_tmax, H.tptr[ke] - H.tptr[kb]);
         }
     }
+    // level table and per-target descriptors of the tail factor, so that its
+    // level loop needs no dependent global loads
+    H.tlev.assign(size_t(2) * size_t(std::max(1, H.ntl)), int4{0, 0, 0, 0});
+    H.tinfo.assign(size_t(std::max(1, H.ft_ng)), int4{0, 0, 0, 0});
+    H.ft_kmax = 0;
+    if (H.ft_ne < 65536) {
+        for (int li = 0; li < H.ntl; li++) {
+            const int l = H.nlev - H.ntl + li;
+            const int cb = H.lvl_ptr[l], ce = H.lvl_ptr[l + 1];
+            const int kb = H.Cp[cb] + cb - H.ft_g0, ke = H.Cp[ce] + ce - H.ft_g0;
+            const int tb = H.tptr[kb], te = H.tptr[ke];
+            H.tlev[2 * li] = int4{kb, ke, tb, te};
+            H.tlev[2 * li + 1] = int4{cb - t0, ce - t0, 0, 0};
+            H.ft_kmax = std::max(H.ft_kmax, ke - kb);
+            for (int k = kb; k < ke; k++) {
+                const int c = H.tcol[k];
+                const int t = k - (H.Cp[c] + c - H.ft_g0);
+                H.tinfo[k] = int4{H.tptr[k] - tb, H.tptr[k + 1] - tb,
+                                  t > 0 ? H.Cp[c] + t - 1 - H.ft_e0 : -1, c - t0};
+            }
+        }
+    }
     auto pad32 = [](int64_t v) { return int((v + 31) / 32 * 32); };
     H.tv_f = 0;
     H.tv_b = pad32(int64_t(posf.size()));
@@ -754,6 +776,9 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
         TRY(upload_padded(ctx, &D.tptr, H.tptr));
         if (H.tterm.empty()) return fail(ctx, PF_ERR_ARG, "internal: tail terms");
         TRY(upload(ctx, &D.tterm, H.tterm.data(), H.tterm.size()));
+        TRY(upload(ctx, &D.tlev, H.tlev.data(), H.tlev.size()));
+        TRY(upload(ctx, &D.tinfo, H.tinfo.data(), H.tinfo.size()));
+        D.ft_kmax = H.ft_kmax;
         D.ft_tmax = H.ft_ne < 65536 ? H.ft_tmax : -1;
         D.ft_ng = H.ft_ng;
         D.ft_ne = H.ft_ne;

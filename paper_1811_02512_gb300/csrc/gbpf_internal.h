@@ -99,6 +99,13 @@ struct DevMat {
     int2 *tterm = nullptr;
     int *tptr = nullptr;
     int ft_tmax = 0;
+    // per tail level li: tlev[2 li] = {first target, end target, first term,
+    // end term}, tlev[2 li + 1] = {first column - t0, end column - t0, 0, 0};
+    // per target: tinfo = {first term, end term (both relative to its level's
+    // first), L entry - e0 (-1 for the diagonal), column - t0}; ft_kmax = most
+    // targets of one tail level
+    int4 *tlev = nullptr, *tinfo = nullptr;
+    int ft_kmax = 0;
     int *Ap = nullptr, *Aj = nullptr, *Apos = nullptr;  // off-diagonal A (no fill), by row:
                                                        // column and value slot of each entry
     // Newton-Raphson Jacobian (2 x 2 blocks on the same pattern, B' only)
@@ -144,6 +151,8 @@ struct HostMat {
     std::vector<int> tapos, tcol, gsplit, tptr;
     std::vector<int2> tterm;
     int ft_tmax = 0;
+    std::vector<int4> tlev, tinfo;
+    int ft_kmax = 0;
 };
 
 // Device arrays of the network and of the case batch.

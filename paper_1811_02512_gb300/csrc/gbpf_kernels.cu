@@ -296,117 +296,144 @@ __global__ void __launch_bounds__(kDepThreads)
 
 // The columns [t0, n) of one instance per block (the narrow top of the
 // elimination tree), after k_factor_dep has finished the columns below t0.
-// Shared memory holds the tail's L entries, D, one partial value per gather
-// target and two buffers of packed tail terms.  First every target
-// subtracts, in parallel, its update terms from columns below the tail (read
-// from the factor in global memory); then level by level each target
-// subtracts its terms from tail columns (shared memory; the level's terms
-// were staged while the previous level was computed), the diagonals are
-// published, and the entries are divided by them.  The order of operations
-// of every entry is fixed.
+// Shared memory holds the tail's entries, D and 1/D, one partial value per
+// gather target, the level table and, double-buffered, the packed terms and
+// target descriptors of one level.  First every target subtracts, in
+// parallel, its update terms from columns below the tail (read from the
+// factor in global memory); then level by level each target subtracts its
+// terms from tail columns (the level's terms and descriptors were staged
+// while the previous level was computed).  Within the tail the entries are
+// kept unnormalised, U(i,c) = L(i,c) D(c), so that an update term
+// L(i,k) D(k) L(c,k) is U(i,k) (U(c,k) / D(k)) and a level needs no
+// division pass before the next one: one block barrier per level.  L = U / D
+// is formed once at the end.  The order of operations of every entry is
+// fixed.
 template <class T>
 __global__ void __launch_bounds__(kFactorThreads)
     k_factor_tail(DevMat m, const double *A, T *F, int *fstatus, const double *amaxv) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int R = 4;  // terms per thread prefetched into registers
     const int inst = blockIdx.x;
+    const int bd = int(blockDim.x), tid = int(threadIdx.x);
     const double *a = A + (long long)inst * m.stride;
     T *v = F + (long long)inst * m.stride;
     const T *Lc = v + m.offLc;
-    const int tmax = m.ft_tmax;
-    int2 *tbuf = reinterpret_cast<int2 *>(smem_raw);
-    T *Lt = reinterpret_cast<T *>(smem_raw + sizeof(int2) * 2 * size_t(tmax));
-    T *Dt = Lt + m.ft_ne;
-    T *part = Dt + m.nt;
-    const int t0 = m.t0, e0 = m.ft_e0, g0 = m.ft_g0;
-    const int l0 = m.nlev - m.ntl;
-    for (int k = threadIdx.x; k < m.ft_ng; k += blockDim.x) {
+    const int tmax = m.ft_tmax, kmax = m.ft_kmax, ntl = m.ntl;
+    int4 *lev = reinterpret_cast<int4 *>(smem_raw);  // [2 ntl]
+    int4 *tib = lev + 2 * ntl;                        // [2][kmax]
+    int2 *tbuf = reinterpret_cast<int2 *>(tib + 2 * kmax);  // [2][tmax]
+    T *Ut = reinterpret_cast<T *>(tbuf + 2 * tmax);
+    T *Dt = Ut + m.ft_ne;
+    T *Di = Dt + m.nt;
+    T *part = Di + m.nt;
+    const int g0 = m.ft_g0;
+    for (int i = tid; i < 2 * ntl; i += bd) lev[i] = m.tlev[i];
+    for (int k = tid; k < m.ft_ng; k += bd) {
         const int g = g0 + k;
-        T s0 = T(0), s1 = T(0);
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
         int q = m.gp[g];
         const int qe = m.gsplit[k];
-        for (; q + 2 <= qe; q += 2) {
-            const int4 e = m.gl[q], f = m.gl[q + 1];
+        for (; q + 4 <= qe; q += 4) {
+            const int4 e = m.gl[q], f = m.gl[q + 1], h = m.gl[q + 2], u = m.gl[q + 3];
             s0 += Lc[e.x] * (Lc[e.y] * v[e.z]);
             s1 += Lc[f.x] * (Lc[f.y] * v[f.z]);
+            s2 += Lc[h.x] * (Lc[h.y] * v[h.z]);
+            s3 += Lc[u.x] * (Lc[u.y] * v[u.z]);
         }
-        if (q < qe) {
+        for (; q < qe; q++) {
             const int4 e = m.gl[q];
             s0 += Lc[e.x] * (Lc[e.y] * v[e.z]);
         }
-        part[k] = T(a[m.tapos[k]]) - (s0 + s1);
+        part[k] = T(a[m.tapos[k]]) - ((s0 + s1) + (s2 + s3));
     }
-    auto kfirst = [&](int l) { return m.Cp[m.lvl_ptr[l]] + m.lvl_ptr[l] - g0; };
     {
-        const int tb = m.tptr[kfirst(l0)], te = m.tptr[kfirst(l0 + 1)];
-        for (int i = threadIdx.x; i < te - tb; i += blockDim.x) tbuf[i] = m.tterm[tb + i];
+        const int4 L0 = m.tlev[0];
+        for (int i = tid; i < L0.w - L0.z; i += bd) tbuf[i] = m.tterm[L0.z + i];
+        for (int i = tid; i < L0.y - L0.x; i += bd) tib[i] = m.tinfo[L0.x + i];
     }
     __syncthreads();
     int bad = PF_OK;
     const double tol = 1e-14 * amaxv[inst];
-    for (int l = l0; l < m.nlev; l++) {
-        const int cur = (l - l0) & 1;
+    for (int li = 0; li < ntl; li++) {
+        const int cur = li & 1;
         const int2 *buf = tbuf + cur * tmax;
         int2 *nbuf = tbuf + (cur ^ 1) * tmax;
-        const int cb = m.lvl_ptr[l], ce = m.lvl_ptr[l + 1];
-        const int kb = kfirst(l), ke = kfirst(l + 1);
-        const int tb = m.tptr[kb];
-        const bool more = l + 1 < m.nlev;
-        const int ntb = more ? m.tptr[ke] : 0, nte = more ? m.tptr[kfirst(l + 2)] : 0;
+        const int4 *ti = tib + cur * kmax;
+        int4 *nti = tib + (cur ^ 1) * kmax;
+        const int4 L = lev[2 * li];
+        const int4 N = li + 1 < ntl ? lev[2 * li + 2] : make_int4(0, 0, 0, 0);
         int2 pre[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int i = int(threadIdx.x) + r * int(blockDim.x);
-            if (i < nte - ntb) pre[r] = m.tterm[ntb + i];
+            const int i = tid + r * bd;
+            if (i < N.w - N.z) pre[r] = m.tterm[N.z + i];
         }
-        for (int k = kb + int(threadIdx.x); k < ke; k += blockDim.x) {
+        const bool hp = tid < N.y - N.x;
+        int4 pti = make_int4(0, 0, 0, 0);
+        if (hp) pti = m.tinfo[N.x + tid];
+        // G lanes per target (G the largest power of two <= 32 with G times
+        // the level's targets <= the block): the few targets of the top
+        // levels, whose diagonals gather the most terms, split their sums
+        // over up to a warp and reduce them with shuffles
+        const int nk = L.y - L.x;
+        int G = 32;
+        while (G > 1 && G * nk > bd) G >>= 1;
+        const int gl = tid & (G - 1), ngr = bd / G;
+        for (int jb = 0; jb < nk; jb += ngr) {  // uniform trip count: shuffles stay convergent
+            const int j = jb + tid / G;
+            const bool act = j < nk;
+            const int4 info = act ? ti[j] : make_int4(0, 0, 0, 0);
             T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-            int q = m.tptr[k] - tb;
-            const int qe = m.tptr[k + 1] - tb;
+            int q = info.x + gl;
+            const int qe = info.y;
             auto term = [&](int2 u) {
                 const unsigned w = unsigned(u.x);
-                return Lt[w & 0xffffu] * (Lt[w >> 16] * Dt[u.y]);
+                return Ut[w & 0xffffu] * (Ut[w >> 16] * Di[u.y]);
             };
-            for (; q + 4 <= qe; q += 4) {
+            for (; q + 3 * G < qe; q += 4 * G) {
                 s0 += term(buf[q]);
-                s1 += term(buf[q + 1]);
-                s2 += term(buf[q + 2]);
-                s3 += term(buf[q + 3]);
+                s1 += term(buf[q + G]);
+                s2 += term(buf[q + 2 * G]);
+                s3 += term(buf[q + 3 * G]);
             }
-            for (; q < qe; q++) s0 += term(buf[q]);
-            part[k] -= (s0 + s1) + (s2 + s3);
+            for (; q < qe; q += G) s0 += term(buf[q]);
+            T sum = (s0 + s1) + (s2 + s3);
+            for (int o = G >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (!act || gl != 0) continue;
+            const T val = part[L.x + j] - sum;
+            if (info.z >= 0) {
+                Ut[info.z] = val;
+            } else {
+                Dt[info.w] = val;
+                Di[info.w] = T(1) / val;
+                const double dd = double(val);
+                if (!isfinite(dd)) bad = PF_ERR_NONFINITE;
+                else if (fabs(dd) <= tol && bad == PF_OK) bad = PF_ERR_SINGULAR;
+            }
         }
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int i = int(threadIdx.x) + r * int(blockDim.x);
-            if (i < nte - ntb) nbuf[i] = pre[r];
+            const int i = tid + r * bd;
+            if (i < N.w - N.z) nbuf[i] = pre[r];
         }
-        for (int i = int(threadIdx.x) + R * int(blockDim.x); i < nte - ntb; i += blockDim.x)
-            nbuf[i] = m.tterm[ntb + i];
-        __syncthreads();
-        for (int c = cb + int(threadIdx.x); c < ce; c += blockDim.x) {
-            const T d = part[m.Cp[c] + c - g0];
-            Dt[c - t0] = d;
-            const double dd = double(d);
-            if (!isfinite(dd)) bad = PF_ERR_NONFINITE;
-            else if (fabs(dd) <= tol && bad == PF_OK) bad = PF_ERR_SINGULAR;
-        }
-        __syncthreads();
-        for (int k = kb + int(threadIdx.x); k < ke; k += blockDim.x) {
-            const int c = m.tcol[k];
-            const int t = k - (m.Cp[c] + c - g0);
-            if (t > 0) Lt[m.Cp[c] + t - 1 - e0] = part[k] / Dt[c - t0];
-        }
+        for (int i = tid + R * bd; i < N.w - N.z; i += bd) nbuf[i] = m.tterm[N.z + i];
+        if (hp) nti[tid] = pti;
+        for (int i = tid + bd; i < N.y - N.x; i += bd) nti[i] = m.tinfo[N.x + i];
         __syncthreads();
     }
     if (bad != PF_OK) atomicCAS(fstatus + inst, PF_OK, bad);
-    for (int c = t0 + int(threadIdx.x); c < m.n; c += blockDim.x) {
+    const int t0 = m.t0, e0 = m.ft_e0;
+    for (int c = t0 + tid; c < m.n; c += bd) {
         v[c] = Dt[c - t0];
-        v[m.offDi + c] = T(1) / Dt[c - t0];
+        v[m.offDi + c] = Di[c - t0];
     }
-    for (int e = threadIdx.x; e < m.ft_ne; e += blockDim.x) {
-        v[m.offLc + e0 + e] = Lt[e];
-        v[m.offLr + m.Cpos[e0 + e]] = Lt[e];
+    for (int k = tid; k < m.ft_ng; k += bd) {
+        const int4 info = m.tinfo[k];
+        if (info.z >= 0) {
+            const T l = Ut[info.z] / Dt[info.w];
+            v[m.offLc + e0 + info.z] = l;
+            v[m.offLr + m.Cpos[e0 + info.z]] = l;
+        }
     }
 }
 
@@ -1272,8 +1299,9 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
     if (dep && m.max_col <= kDepMaxCol && total < (1ll << 31) && fs.done) {
         k_factor_prep<<<ninst, 256, 0, s>>>(m, A, fstatus, fs);
         const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
-        const size_t tsmem = elt * (size_t(m.ft_ne) + size_t(m.nt) + size_t(m.ft_ng)) +
-                             sizeof(int2) * 2 * size_t(m.ft_tmax > 0 ? m.ft_tmax : 0);
+        const size_t tsmem = elt * (size_t(m.ft_ne) + 2 * size_t(m.nt) + size_t(m.ft_ng)) +
+                             sizeof(int2) * 2 * size_t(m.ft_tmax > 0 ? m.ft_tmax : 0) +
+                             sizeof(int4) * 2 * (size_t(m.ft_kmax) + size_t(m.ntl));
         const bool tail = fs.tail && m.ft_ng > 0 && m.ft_tmax >= 0 && tsmem + 1024 <= fs.smem_optin;
         const int ncols = tail ? m.t0 : m.n;
         const int per_sm = fs.blocks_per_sm > 0 && fs.blocks_per_sm < 2 ? fs.blocks_per_sm : 2;  // resident blocks per SM (registers)
