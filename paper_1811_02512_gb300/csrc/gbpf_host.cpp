@@ -2095,4 +2095,31 @@ void pf_destroy(pf_ctx *ctx) {
     delete ctx;
 }
 
+// Test hook (host only, no GPU needed): the tail-factor tables of matrix
+// `which` (0 = B', 1 = B'') as built by pf_analyze.  sizes[8] receives {n,
+// t0, ntl, ng, ne, kmax, tmax, number of tail terms}; tlev (4 ints per
+// entry, 2 ntl entries) and tinfo (4 ints per target, ng targets) are copied
+// when cap_lev >= 2 ntl and cap_tgt >= ng.  Returns 0, or -1 for a bad
+// argument or a matrix that has not been analysed.
+int gbpf_debug_tail_tables(const pf_ctx *ctx, int which, int *sizes, int *tlev, int cap_lev,
+                           int *tinfo, int cap_tgt) {
+    if (!ctx || !sizes || which < 0 || which > 1) return -1;
+    const gbpf::HostMat &H = ctx->hm[which];
+    if (H.lvl_ptr.empty()) return -1;
+    const int ntail = H.tptr.empty() ? 0 : H.tptr.back();
+    const int v[8] = {H.n, H.t0, H.ntl, H.ft_ng, H.ft_ne, H.ft_kmax, H.ft_tmax, ntail};
+    for (int i = 0; i < 8; i++) sizes[i] = v[i];
+    if (tlev && cap_lev >= 2 * H.ntl)
+        for (int i = 0; i < 2 * H.ntl; i++) {
+            const int4 e = H.tlev[size_t(i)];
+            tlev[4 * i] = e.x, tlev[4 * i + 1] = e.y, tlev[4 * i + 2] = e.z, tlev[4 * i + 3] = e.w;
+        }
+    if (tinfo && cap_tgt >= H.ft_ng)
+        for (int i = 0; i < H.ft_ng; i++) {
+            const int4 e = H.tinfo[size_t(i)];
+            tinfo[4 * i] = e.x, tinfo[4 * i + 1] = e.y, tinfo[4 * i + 2] = e.z, tinfo[4 * i + 3] = e.w;
+        }
+    return 0;
+}
+
 }  // extern "C"

@@ -82,6 +82,88 @@ def test_symbolic_small_random_grids(lib, oracle, seed):
     g.close()
 
 
+def _tail_tables(lib, g, which):
+    f = lib.gbpf_debug_tail_tables
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+    sizes = np.zeros(8, np.int32)
+    assert f(g.ctx, which, sizes.ctypes.data, None, 0, None, 0) == 0
+    n, t0, ntl, ng, ne, kmax, tmax, nterm = (int(x) for x in sizes)
+    tlev = np.zeros((max(1, 2 * ntl), 4), np.int32)
+    tinfo = np.zeros((max(1, ng), 4), np.int32)
+    assert f(g.ctx, which, sizes.ctypes.data, tlev.ctypes.data, 2 * ntl, tinfo.ctypes.data, ng) == 0
+    return (dict(n=n, t0=t0, ntl=ntl, ng=ng, ne=ne, kmax=kmax, tmax=tmax, nterm=nterm),
+            tlev[:2 * ntl], tinfo[:ng])
+
+
+def _oracle_tail_levels(oracle, case, name, narrow=16):
+    """Per level of the narrow top of the elimination tree (the run of
+    top levels with at most `narrow` columns), from the oracle's own
+    symbolic analysis: (columns, targets = entries + diagonals of its
+    columns, update terms L(i,k) L(c,k) D(k) with k also in the top run)."""
+    an = oracle.analyze(case, name)
+    Lp, Li, lev, nl = an["Lp"], an["Li"], an["level"], an["nlevels"]
+    n = lev.shape[0]
+    cnt = np.bincount(lev, minlength=nl + 1)
+    lt = nl
+    while lt >= 1 and cnt[lt] <= narrow:
+        lt -= 1
+    cols = [set(Li[Lp[j]:Lp[j + 1]].tolist()) for j in range(n)]
+    rows = [[] for _ in range(n)]
+    for j in range(n):
+        for i in Li[Lp[j]:Lp[j + 1]]:
+            rows[i].append(j)
+    out = []
+    for L in range(lt + 1, nl + 1):
+        cs = np.nonzero(lev == L)[0]
+        ntgt = sum(len(cols[c]) + 1 for c in cs)
+        nterm = sum(1 + len(cols[c] & cols[k]) for c in cs for k in rows[c] if lev[k] > lt)
+        out.append((len(cs), ntgt, nterm))
+    return out
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_tail_factor_tables_vs_oracle(lib, oracle, cfg):
+    """The tail factor's level table and target descriptors, built by
+    pf_analyze on the host, against counts taken from the oracle's symbolic
+    analysis (numbering-independent per level), plus the structural
+    invariants the kernel relies on: levels, terms and columns tile their
+    ranges, every tail L entry has exactly one target, every tail column
+    exactly one diagonal target inside its own level."""
+    case = gridgen.config_raw(cfg)
+    g = gbpf.Grid(case)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        sz, tlev, tinfo = _tail_tables(lib, g, which)
+        ref = _oracle_tail_levels(oracle, case, name)
+        assert sz["ntl"] == len(ref) > 0
+        nt = sum(r[0] for r in ref)
+        assert sz["n"] - sz["t0"] == nt
+        assert sz["ng"] == sum(r[1] for r in ref) and sz["ne"] == sz["ng"] - nt
+        assert sz["nterm"] == sum(r[2] for r in ref)
+        assert sz["kmax"] == max(r[1] for r in ref) and sz["tmax"] == max(r[2] for r in ref)
+        seen_diag = np.zeros(nt, np.int32)
+        seen_entry = np.zeros(sz["ne"], np.int32)
+        for li, (ncol, ntgt, nterm) in enumerate(ref):
+            kb, ke, tb, te = tlev[2 * li]
+            cb, ce = tlev[2 * li + 1][:2]
+            assert (ke - kb, te - tb, ce - cb) == (ntgt, nterm, ncol), li
+            if li + 1 < len(ref):
+                assert tlev[2 * li + 2][0] == ke and tlev[2 * li + 2][2] == te
+                assert tlev[2 * li + 3][0] == ce
+            info = tinfo[kb:ke]
+            assert info[0, 0] == 0 and info[-1, 1] == te - tb
+            assert np.array_equal(info[1:, 0], info[:-1, 1]) and np.all(info[:, 1] >= info[:, 0])
+            assert np.all((info[:, 3] >= cb) & (info[:, 3] < ce))
+            d = info[info[:, 2] < 0]
+            assert np.all(d[:, 2] == -1) and d.shape[0] == ncol
+            np.add.at(seen_diag, d[:, 3], 1)
+            np.add.at(seen_entry, info[info[:, 2] >= 0, 2], 1)
+        assert tlev[0][0] == 0 and tlev[0][2] == 0 and tlev[1][0] == 0
+        assert tlev[-2][1] == sz["ng"] and tlev[-2][3] == sz["nterm"] and tlev[-1][1] == nt
+        assert np.all(seen_diag == 1) and np.all(seen_entry == 1)
+    g.close()
+
+
 def test_outage_keeps_pattern(lib):
     case = gridgen.config_raw(0)
     c2 = case.copy()
