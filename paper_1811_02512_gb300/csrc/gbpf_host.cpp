@@ -771,7 +771,6 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
         D.tv_p = H.tv_p;
         D.tv_stride = H.tv_stride;
         TRY(upload_padded(ctx, &D.tapos, H.tapos));
-        TRY(upload_padded(ctx, &D.tcol, H.tcol));
         TRY(upload_padded(ctx, &D.gsplit, H.gsplit));
         TRY(upload_padded(ctx, &D.tptr, H.tptr));
         if (H.tterm.empty()) return fail(ctx, PF_ERR_ARG, "internal: tail terms");

@@ -90,10 +90,10 @@ struct DevMat {
     // Tail factor: the columns [t0, n) factorised by one block in shared
     // memory, level by level.  Its gather targets are g0 + [0, ng) (g0 =
     // Cp[t0] + t0), its L entries Lc[e0 + [0, ne)) (e0 = Cp[t0]); per target
-    // the A-value slot (tapos), its column (tcol) and the first of its gather
-    // terms whose column k is in the tail (gsplit; earlier terms have k < t0).
+    // the A-value slot (tapos) and the first of its gather terms whose column
+    // k is in the tail (gsplit; earlier terms have k < t0).
     int ft_ng = 0, ft_ne = 0, ft_g0 = 0, ft_e0 = 0;
-    int *tapos = nullptr, *tcol = nullptr, *gsplit = nullptr;
+    int *tapos = nullptr, *gsplit = nullptr;
     // the tail terms alone, packed {(x - e0) | (y - e0) << 16, k - t0}, by
     // target (tptr[ng + 1]); ft_tmax = most terms of one tail level
     int2 *tterm = nullptr;
