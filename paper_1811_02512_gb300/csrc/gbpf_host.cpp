@@ -772,7 +772,6 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
         D.tv_stride = H.tv_stride;
         TRY(upload_padded(ctx, &D.tapos, H.tapos));
         TRY(upload_padded(ctx, &D.gsplit, H.gsplit));
-        TRY(upload_padded(ctx, &D.tptr, H.tptr));
         if (H.tterm.empty()) return fail(ctx, PF_ERR_ARG, "internal: tail terms");
         TRY(upload(ctx, &D.tterm, H.tterm.data(), H.tterm.size()));
         TRY(upload(ctx, &D.tlev, H.tlev.data(), H.tlev.size()));

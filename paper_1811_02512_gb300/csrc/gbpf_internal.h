@@ -95,9 +95,8 @@ struct DevMat {
     int ft_ng = 0, ft_ne = 0, ft_g0 = 0, ft_e0 = 0;
     int *tapos = nullptr, *gsplit = nullptr;
     // the tail terms alone, packed {(x - e0) | (y - e0) << 16, k - t0}, by
-    // target (tptr[ng + 1]); ft_tmax = most terms of one tail level
+    // target; ft_tmax = most terms of one tail level
     int2 *tterm = nullptr;
-    int *tptr = nullptr;
     int ft_tmax = 0;
     // per tail level li: tlev[2 li] = {first target, end target, first term,
     // end term}, tlev[2 li + 1] = {first column - t0, end column - t0, 0, 0};
