@@ -82,6 +82,34 @@ def test_symbolic_small_random_grids(lib, oracle, seed):
     g.close()
 
 
+@pytest.mark.parametrize("which_case", ["cfg0", "cfg1", "small0", "small1", "small2"])
+def test_symbolic_sizes_vs_oracle_pattern(lib, oracle, which_case):
+    """pf_analyze's sizes against the oracle's filled pattern: strict-lower
+    nonzeros, the longest column, and the scalar updates of one numeric
+    factor -- for every target (i, c) of L (the diagonal included), one per
+    column k < c with L(c,k) and L(i,k) nonzero -- which sizes the factor's
+    gather lists."""
+    if which_case.startswith("cfg"):
+        case = gridgen.config_raw(int(which_case[3:]))
+    else:
+        s = int(which_case[5:])
+        case = gridgen.small_raw(12 + 9 * s, 500 + s)
+    g = gbpf.Grid(case)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        an = oracle.analyze(case, name)
+        Lp, Li = an["Lp"], an["Li"]
+        n = Lp.shape[0] - 1
+        cols = [set(Li[Lp[j]:Lp[j + 1]].tolist()) for j in range(n)]
+        rows = [[] for _ in range(n)]
+        for j in range(n):
+            for i in Li[Lp[j]:Lp[j + 1]]:
+                rows[i].append(j)
+        assert g.info.nnz_l[which] == Lp[-1]
+        assert g.info.max_col[which] == (int(np.max(np.diff(Lp))) if n else 0)
+        assert g.info.nupdates[which] == sum(1 + len(cols[c] & cols[k]) for c in range(n) for k in rows[c])
+    g.close()
+
+
 def _tail_tables(lib, g, which):
     f = lib.gbpf_debug_tail_tables
     f.restype = C.c_int
