@@ -2120,4 +2120,24 @@ int gbpf_debug_tail_tables(const pf_ctx *ctx, int which, int *sizes, int *tlev, 
     return 0;
 }
 
+// Test hook (host only, no GPU needed): the scatter-tail schedules of matrix
+// `which` as built by pf_analyze.  sizes[6] receives {t0, ntl, len(SKf),
+// len(SIf), len(SKb), len(SIb)}; the four arrays are copied when cap (ints
+// per array) covers them.  Returns 0, or -1 for a bad argument or a matrix
+// that has not been analysed.
+int gbpf_debug_scatter_schedules(const pf_ctx *ctx, int which, int *sizes, int *SKf, int *SIf,
+                                 int *SKb, int *SIb, int cap) {
+    if (!ctx || !sizes || which < 0 || which > 1) return -1;
+    const gbpf::HostMat &H = ctx->hm[which];
+    if (H.lvl_ptr.empty()) return -1;
+    const int v[6] = {H.t0, H.ntl, int(H.SKf.size()), int(H.SIf.size()), int(H.SKb.size()),
+                      int(H.SIb.size())};
+    for (int i = 0; i < 6; i++) sizes[i] = v[i];
+    const std::vector<int> *src[4] = {&H.SKf, &H.SIf, &H.SKb, &H.SIb};
+    int *dst[4] = {SKf, SIf, SKb, SIb};
+    for (int a = 0; a < 4; a++)
+        if (dst[a] && cap >= int(src[a]->size())) std::copy(src[a]->begin(), src[a]->end(), dst[a]);
+    return 0;
+}
+
 }  // extern "C"

@@ -192,6 +192,75 @@ def test_tail_factor_tables_vs_oracle(lib, oracle, cfg):
     g.close()
 
 
+def _scatter_schedules(lib, g, which):
+    f = lib.gbpf_debug_scatter_schedules
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    sizes = np.zeros(6, np.int32)
+    assert f(g.ctx, which, sizes.ctypes.data, None, None, None, None, 0) == 0
+    t0, ntl, nkf, nif, nkb, nib = (int(x) for x in sizes)
+    cap = max(1, nkf, nif, nkb, nib)
+    arrs = [np.zeros(cap, np.int32) for _ in range(4)]
+    assert f(g.ctx, which, sizes.ctypes.data, *[a.ctypes.data for a in arrs], cap) == 0
+    SKf, SIf, SKb, SIb = arrs[0][:nkf], arrs[1][:nif], arrs[2][:nkb], arrs[3][:nib]
+    return t0, ntl, SKf, SIf, SKb, SIb
+
+
+def _oracle_scatter_counts(oracle, case, name, narrow=16):
+    """Per level of the narrow top run (bottom first): the forward updates
+    (strict-lower entries of the level's columns) and the backward updates
+    (strict-lower entries of the level's rows that lie in the top run)."""
+    an = oracle.analyze(case, name)
+    Lp, Li, lev, nl = an["Lp"], an["Li"], an["level"], an["nlevels"]
+    n = lev.shape[0]
+    cnt = np.bincount(lev, minlength=nl + 1)
+    lt = nl
+    while lt >= 1 and cnt[lt] <= narrow:
+        lt -= 1
+    rowcnt = np.zeros(n, np.int64)
+    for j in range(n):
+        for i in Li[Lp[j]:Lp[j + 1]]:
+            if lev[j] > lt:
+                rowcnt[i] += 1
+    out = []
+    for L in range(lt + 1, nl + 1):
+        cs = np.nonzero(lev == L)[0]
+        out.append((int(sum(Lp[c + 1] - Lp[c] for c in cs)), int(rowcnt[cs].sum())))
+    return out
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_scatter_tail_schedules_vs_oracle(lib, oracle, cfg):
+    """The one-warp scatter schedules of the narrow top (forward and back
+    substitution): per level, one slot per update, in the lane that owns the
+    target row (row - t0 = lane mod 32), sources inside the level, targets
+    below (forward) or above (backward) them, no update twice, and as many
+    updates as the oracle's pattern has for that level."""
+    case = gridgen.config_raw(cfg)
+    g = gbpf.Grid(case)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        t0, ntl, SKf, SIf, SKb, SIb = _scatter_schedules(lib, g, which)
+        _, tlev, _ = _tail_tables(lib, g, which)
+        ref = _oracle_scatter_counts(oracle, case, name)
+        assert ntl == len(ref) > 0
+        for SK, SI, fwd in ((SKf, SIf, True), (SKb, SIb, False)):
+            assert SK.shape[0] == ntl + 1 and SK[0] == 0 and SI.shape[0] == 32 * SK[-1]
+            for li in range(ntl):
+                lv = li if fwd else ntl - 1 - li  # the backward sweep walks the levels top down
+                cb, ce = tlev[2 * lv + 1][:2]
+                slots = SI[32 * SK[li]:32 * SK[li + 1]]
+                lanes = np.arange(slots.shape[0]) % 32
+                used = slots >= 0
+                tgt, src = slots[used] & 0xFFFF, slots[used] >> 16
+                assert np.all(slots[~used] == -1)
+                assert np.all(tgt % 32 == lanes[used])
+                assert np.all((src >= cb) & (src < ce))
+                assert np.all(tgt > src) if fwd else np.all(tgt < src)
+                assert np.unique(tgt * 65536 + src).shape[0] == tgt.shape[0]
+                assert tgt.shape[0] == ref[lv][0 if fwd else 1], (name, fwd, li)
+    g.close()
+
+
 def test_outage_keeps_pattern(lib):
     case = gridgen.config_raw(0)
     c2 = case.copy()
