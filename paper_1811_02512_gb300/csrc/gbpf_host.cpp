@@ -2140,4 +2140,25 @@ int gbpf_debug_scatter_schedules(const pf_ctx *ctx, int which, int *sizes, int *
     return 0;
 }
 
+// Test hook (host only, no GPU needed): a piece list of matrix `which`
+// (list 0 = forward sweep, 1 = backward sweep, 2 / 3 = the same with a
+// scatter tail) as 8 ints per piece {r0, r1, e0, e1, mode, run_end, l0, l1};
+// *count receives the number of pieces, copied when cap >= 8 * count.
+// Returns 0, or -1 for a bad argument or a matrix that has not been analysed.
+int gbpf_debug_pieces(const pf_ctx *ctx, int which, int list, int *count, int *out, int cap) {
+    if (!ctx || !count || which < 0 || which > 1 || list < 0 || list > 3) return -1;
+    const gbpf::HostMat &H = ctx->hm[which];
+    if (H.lvl_ptr.empty()) return -1;
+    const std::vector<gbpf::Piece> *L[4] = {&H.pf, &H.pb, &H.pf2, &H.pb2};
+    const std::vector<gbpf::Piece> &P = *L[list];
+    *count = int(P.size());
+    if (out && cap >= 8 * int(P.size()))
+        for (size_t i = 0; i < P.size(); i++) {
+            const gbpf::Piece &q = P[i];
+            const int v[8] = {q.r0, q.r1, q.e0, q.e1, q.mode, q.run_end, q.l0, q.l1};
+            std::copy(v, v + 8, out + 8 * i);
+        }
+    return 0;
+}
+
 }  // extern "C"

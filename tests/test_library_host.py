@@ -261,6 +261,74 @@ def test_scatter_tail_schedules_vs_oracle(lib, oracle, cfg):
     g.close()
 
 
+def _pieces(lib, g, which, lst):
+    f = lib.gbpf_debug_pieces
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]
+    cnt = C.c_int(0)
+    assert f(g.ctx, which, lst, C.byref(cnt), None, 0) == 0
+    out = np.zeros(max(1, 8 * cnt.value), np.int32)
+    assert f(g.ctx, which, lst, C.byref(cnt), out.ctypes.data, out.shape[0]) == 0
+    return out[:8 * cnt.value].reshape(-1, 8)
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 3])
+def test_sweep_pieces_tile_levels(lib, oracle, cfg):
+    """The staged sweeps' piece lists (forward over CSR rows in ascending
+    levels, backward over CSC columns in descending levels): levels in sweep
+    order, every row in exactly one piece (or one run of partial-row pieces
+    with contiguous entry ranges), pieces of modes 0/1/3 inside one level,
+    mode 2 only over narrow levels, per-level entry counts equal to the
+    oracle's pattern, and run_end marking the end of each single-warp run."""
+    case = gridgen.config_raw(cfg)
+    g = gbpf.Grid(case)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        an = oracle.analyze(case, name)
+        Lp, Li, lev, nl = an["Lp"], an["Li"], an["level"], an["nlevels"]
+        n = lev.shape[0]
+        sizes = np.bincount(lev, minlength=nl + 1)[1:]
+        lvl_ptr = np.concatenate([[0], np.cumsum(sizes)])
+        colcnt = np.diff(Lp)
+        rowcnt = np.bincount(Li, minlength=n) if Li.shape[0] else np.zeros(n, np.int64)
+        for lst, fwd in ((0, True), (1, False)):
+            per_lev = np.bincount(lev - 1, weights=rowcnt if fwd else colcnt, minlength=nl)
+            P = _pieces(lib, g, which, lst)
+            covered = np.zeros(n, np.int32)
+            got = np.zeros(nl, np.int64)
+            last_l = -1 if fwd else nl
+            for k, (r0, r1, e0, e1, mode, run_end, l0, l1) in enumerate(P):
+                assert mode in (0, 1, 2, 3) and e1 >= e0 and r1 > r0
+                if mode == 2:
+                    assert r0 == lvl_ptr[l0] and r1 == lvl_ptr[l1 + 1]
+                    assert np.all(sizes[l0:l1 + 1] <= 16)
+                else:
+                    assert l0 == l1 and lvl_ptr[l0] <= r0 < r1 <= lvl_ptr[l0 + 1]
+                assert (l0 >= last_l) if fwd else (l1 <= last_l)
+                last_l = l1 if fwd else l0
+                got[l0] += e1 - e0  # a mode-2 piece's entries are summed over its levels below
+                if mode == 2:
+                    got[l0] -= e1 - e0
+                    assert e1 - e0 == per_lev[l0:l1 + 1].sum()
+                    got[l0:l1 + 1] += per_lev[l0:l1 + 1].astype(np.int64)
+                if mode == 3:
+                    assert r1 == r0 + 1
+                    first = not (k > 0 and P[k - 1][4] == 3 and P[k - 1][0] == r0)
+                    if not first:
+                        assert e0 == P[k - 1][3]
+                    covered[r0] += 1 if first else 0
+                else:
+                    covered[r0:r1] += 1
+                single = 2 <= mode <= 4
+                if single:
+                    nxt = k + 1
+                    while nxt < P.shape[0] and 2 <= P[nxt][4] <= 4:
+                        nxt += 1
+                    assert run_end == nxt
+            assert np.all(covered == 1)
+            assert np.array_equal(got, per_lev.astype(np.int64)), (name, fwd)
+    g.close()
+
+
 def test_outage_keeps_pattern(lib):
     case = gridgen.config_raw(0)
     c2 = case.copy()
