@@ -329,6 +329,64 @@ def test_sweep_pieces_tile_levels(lib, oracle, cfg):
     g.close()
 
 
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_sweep_pieces_with_scatter_tail(lib, oracle, cfg):
+    """The sweeps used when the narrow top runs as a scatter tail.  Forward:
+    pieces over the levels below the tail (rows [0, t0) once, ascending),
+    then block-wide pieces over the tail rows' entries in columns below the
+    tail (their count from the oracle's pattern), then scatter pieces tiling
+    the forward schedule.  Backward: pieces over the tail rows (inverse
+    diagonal), scatter pieces tiling the backward schedule, then the levels
+    below the tail, descending."""
+    case = gridgen.config_raw(cfg)
+    g = gbpf.Grid(case)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        an = oracle.analyze(case, name)
+        Lp, Li, lev, nl = an["Lp"], an["Li"], an["level"], an["nlevels"]
+        n = lev.shape[0]
+        t0, ntl, SKf, _, SKb, _ = _scatter_schedules(lib, g, which)
+        lt = nl - ntl  # levels 1..lt (oracle numbering) lie below the tail
+        cols = np.repeat(np.arange(n), np.diff(Lp))
+        below = int(np.sum((lev[Li] > lt) & (lev[cols] <= lt)))  # tail rows' entries left of t0
+        for lst, fwd in ((2, True), (3, False)):
+            P = _pieces(lib, g, which, lst)
+            modes = P[:, 4]
+            wide = np.isin(modes, (0, 1, 2, 3))
+            if fwd:
+                order = [(0, 1, 2, 3), (5,), (4,)]
+            else:
+                order = [(6,), (4,), (0, 1, 2, 3)]
+            groups = []
+            for ms in order:
+                k = 0 if not groups else groups[-1][1]
+                e = k
+                while e < P.shape[0] and P[e][4] in ms:
+                    e += 1
+                groups.append((k, e))
+            assert groups[-1][1] == P.shape[0], (name, fwd)
+            covered = np.zeros(n, np.int32)
+            for r0, r1 in P[wide][:, :2]:
+                if r1 > r0:
+                    covered[r0:r1] += 1
+            for (r0, r1, _e0, _e1, mode, *_r) in P[wide]:
+                if mode == 3:
+                    covered[r0] -= 1
+            for k in np.nonzero(wide & (modes == 3))[0]:
+                if not (k > 0 and P[k - 1][4] == 3 and P[k - 1][0] == P[k][0]):
+                    covered[P[k][0]] += 1
+            assert np.all(covered[:t0] == 1) and np.all(covered[t0:] == 0)
+            k0, k1 = groups[1] if fwd else groups[0]
+            rows = P[k0:k1]
+            assert rows[0][0] == t0 and rows[-1][1] == n and np.array_equal(rows[1:, 0], rows[:-1, 1])
+            if fwd:
+                assert int(np.sum(rows[:, 3] - rows[:, 2])) == below
+            k0, k1 = groups[2] if fwd else groups[1]
+            sc = P[k0:k1]
+            SK = SKf if fwd else SKb
+            assert sc[0][2] == 0 and sc[-1][3] == 32 * SK[-1] and np.array_equal(sc[1:, 2], sc[:-1, 3])
+    g.close()
+
+
 def test_outage_keeps_pattern(lib):
     case = gridgen.config_raw(0)
     c2 = case.copy()
