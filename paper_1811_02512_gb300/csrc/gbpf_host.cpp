@@ -2161,4 +2161,31 @@ int gbpf_debug_pieces(const pf_ctx *ctx, int which, int list, int *count, int *o
     return 0;
 }
 
+// Test hook (host only, no GPU needed): the level-order CSC pattern of L and
+// the gather lists of the dependency-driven factor of matrix `which`.
+// sizes[3] receives {n, nnz (strict lower), number of gather terms}; Cp (n + 1),
+// Cr (nnz), gp (n + nnz + 1) and gl (4 ints per term) are copied when cap (ints
+// per array) covers them.  Returns 0, or -1 for a bad argument or a matrix
+// that has not been analysed.
+int gbpf_debug_gather(const pf_ctx *ctx, int which, long long *sizes, int *Cp, int *Cr, int *gp,
+                      int *gl, long long cap) {
+    if (!ctx || !sizes || which < 0 || which > 1) return -1;
+    const gbpf::HostMat &H = ctx->hm[which];
+    if (H.lvl_ptr.empty() || H.Cp.empty()) return -1;
+    const long long nnz = H.Cp.back();
+    const long long nterm = H.gp.empty() ? 0 : H.gp.back();
+    sizes[0] = H.n;
+    sizes[1] = nnz;
+    sizes[2] = nterm;
+    if (Cp && cap >= (long long)H.Cp.size()) std::copy(H.Cp.begin(), H.Cp.end(), Cp);
+    if (Cr && cap >= nnz) std::copy(H.Cr.begin(), H.Cr.begin() + nnz, Cr);
+    if (gp && cap >= (long long)H.gp.size()) std::copy(H.gp.begin(), H.gp.end(), gp);
+    if (gl && cap >= 4 * nterm)
+        for (long long q = 0; q < nterm; q++) {
+            const int4 e = H.gl[size_t(q)];
+            gl[4 * q] = e.x, gl[4 * q + 1] = e.y, gl[4 * q + 2] = e.z, gl[4 * q + 3] = e.w;
+        }
+    return 0;
+}
+
 }  // extern "C"

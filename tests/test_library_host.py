@@ -387,6 +387,72 @@ def test_sweep_pieces_with_scatter_tail(lib, oracle, cfg):
     g.close()
 
 
+def _gather(lib, g, which):
+    f = lib.gbpf_debug_gather
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                  C.c_longlong]
+    sizes = np.zeros(3, np.int64)
+    assert f(g.ctx, which, sizes.ctypes.data, None, None, None, None, 0) == 0
+    n, nnz, nterm = (int(x) for x in sizes)
+    Cp = np.zeros(n + 1, np.int32)
+    Cr = np.zeros(max(1, nnz), np.int32)
+    gp = np.zeros(n + nnz + 1, np.int32)
+    gl = np.zeros((max(1, nterm), 4), np.int32)
+    cap = max(n + nnz + 1, 4 * nterm)
+    assert f(g.ctx, which, sizes.ctypes.data, Cp.ctypes.data, Cr.ctypes.data, gp.ctypes.data,
+             gl.ctypes.data, cap) == 0
+    return n, nnz, Cp, Cr[:nnz], gp, gl[:nterm]
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_factor_gather_lists(lib, oracle, cfg):
+    """The dependency-driven factor's gather lists: for every target (i, c)
+    of L in level order (the diagonal first), one term per column k < c with
+    L(c,k) and L(i,k) nonzero -- both positions inside column k, one in row i
+    and one in row c, no k twice, none missing -- and per level as many terms
+    as the oracle's pattern gives."""
+    case = gridgen.config_raw(cfg)
+    g = gbpf.Grid(case)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        n, nnz, Cp, Cr, gp, gl = _gather(lib, g, which)
+        assert g.info.nupdates[which] == gl.shape[0] == gp[-1]
+        tcol = np.repeat(np.arange(n), np.diff(Cp) + 1)
+        toff = np.arange(n + nnz) - (Cp[tcol] + tcol)
+        trow = tcol.copy()
+        off = toff > 0
+        trow[off] = Cr[Cp[tcol[off]] + toff[off] - 1]
+        tt = np.repeat(np.arange(n + nnz), np.diff(gp))
+        x, y, z = gl[:, 0], gl[:, 1], gl[:, 2]
+        pcol = np.repeat(np.arange(n), np.diff(Cp))
+        assert np.all(pcol[x] == z) and np.all(pcol[y] == z)
+        assert np.all(Cr[y] == tcol[tt]) and np.all(Cr[x] == trow[tt])
+        assert np.all(z < tcol[tt])
+        assert np.unique(tt.astype(np.int64) * n + z).shape[0] == tt.shape[0]
+        rowset = [set() for _ in range(n)]
+        for k in range(n):
+            for i in Cr[Cp[k]:Cp[k + 1]]:
+                rowset[i].add(k)
+        want = np.array([len(rowset[c]) if i == c else len(rowset[c] & rowset[i])
+                         for i, c in zip(trow, tcol)])
+        assert np.array_equal(np.diff(gp), want)
+        an = oracle.analyze(case, name)
+        Lp, Li, lev, nl = an["Lp"], an["Li"], an["level"], an["nlevels"]
+        cols = [set(Li[Lp[j]:Lp[j + 1]].tolist()) for j in range(n)]
+        rows = [[] for _ in range(n)]
+        for j in range(n):
+            for i in Li[Lp[j]:Lp[j + 1]]:
+                rows[i].append(j)
+        ref = np.zeros(nl, np.int64)
+        for c in range(n):
+            ref[lev[c] - 1] += sum(1 + len(cols[c] & cols[k]) for k in rows[c])
+        lvl_ptr = np.concatenate([[0], np.cumsum(np.bincount(lev, minlength=nl + 1)[1:])])
+        got = np.array([gp[Cp[lvl_ptr[l + 1]] + lvl_ptr[l + 1]] - gp[Cp[lvl_ptr[l]] + lvl_ptr[l]]
+                        for l in range(nl)])
+        assert np.array_equal(got, ref)
+    g.close()
+
+
 def test_outage_keeps_pattern(lib):
     case = gridgen.config_raw(0)
     c2 = case.copy()
