@@ -2188,4 +2188,33 @@ int gbpf_debug_gather(const pf_ctx *ctx, int which, long long *sizes, int *Cp, i
     return 0;
 }
 
+// Test hook (host only, no GPU needed): the CSR copy of L's pattern and its
+// maps to the CSC one, and the off-diagonal pattern of A used by residuals,
+// of matrix `which`.  sizes[4] receives {n, nnz, offLc, entries of A's
+// pattern}; Fp (n + 1), Fc, Fpos, Cpos (nnz each), Ap (n + 1), Aj and Apos
+// are copied when cap (ints per array) covers them.  Returns 0, or -1 for a
+// bad argument or a matrix that has not been analysed.
+int gbpf_debug_csr(const pf_ctx *ctx, int which, int *sizes, int *Fp, int *Fc, int *Fpos, int *Cpos,
+                   int *Ap, int *Aj, int *Apos, int cap) {
+    if (!ctx || !sizes || which < 0 || which > 1) return -1;
+    const gbpf::HostMat &H = ctx->hm[which];
+    if (H.lvl_ptr.empty() || H.Cp.empty()) return -1;
+    const int nnz = H.Cp.back(), na = int(H.Aj.size());
+    sizes[0] = H.n;
+    sizes[1] = nnz;
+    sizes[2] = H.offLc;
+    sizes[3] = na;
+    auto put = [&](const std::vector<int> &v, int count, int *dst) {
+        if (dst && cap >= count) std::copy(v.begin(), v.begin() + count, dst);
+    };
+    put(H.Fp, H.n + 1, Fp);
+    put(H.Fc, nnz, Fc);
+    put(H.Fpos, nnz, Fpos);
+    put(H.Cpos, nnz, Cpos);
+    put(H.Ap, H.n + 1, Ap);
+    put(H.Aj, na, Aj);
+    put(H.Apos, na, Apos);
+    return 0;
+}
+
 }  // extern "C"

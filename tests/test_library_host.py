@@ -453,6 +453,52 @@ def test_factor_gather_lists(lib, oracle, cfg):
     g.close()
 
 
+def _csr(lib, g, which):
+    f = lib.gbpf_debug_csr
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_void_p] + [C.c_void_p] * 7 + [C.c_int]
+    sizes = np.zeros(4, np.int32)
+    assert f(g.ctx, which, sizes.ctypes.data, *([None] * 7), 0) == 0
+    n, nnz, offLc, na = (int(x) for x in sizes)
+    arrs = [np.zeros(max(1, k), np.int32) for k in (n + 1, nnz, nnz, nnz, n + 1, na, na)]
+    cap = max(n + 1, nnz, na)
+    assert f(g.ctx, which, sizes.ctypes.data, *[a.ctypes.data for a in arrs], cap) == 0
+    Fp, Fc, Fpos, Cpos, Ap, Aj, Apos = arrs
+    return offLc, Fp, Fc[:nnz], Fpos[:nnz], Cpos[:nnz], Ap, Aj[:na], Apos[:na]
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_csr_maps_and_residual_pattern(lib, oracle, cfg):
+    """The CSR copy of L's pattern (strict lower, ascending columns) maps one
+    to one onto the CSC pattern (Fpos, with Cpos its inverse), and the
+    off-diagonal pattern of A used by the FP64 residuals is symmetric, points
+    at the L slot of each entry, and has the degree sequence of the oracle's
+    bus graph of the matrix."""
+    case = gridgen.config_raw(cfg)
+    g = gbpf.Grid(case)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        n, nnz, Cp, Cr, _, _ = _gather(lib, g, which)
+        offLc, Fp, Fc, Fpos, Cpos, Ap, Aj, Apos = _csr(lib, g, which)
+        pcol = np.repeat(np.arange(n), np.diff(Cp))
+        rowF = np.repeat(np.arange(n), np.diff(Fp))
+        assert Fp[-1] == nnz and np.all(Fc < rowF)
+        same = rowF[1:] == rowF[:-1]
+        assert np.all(Fc[1:][same] > Fc[:-1][same])
+        assert np.all(pcol[Fpos] == Fc) and np.all(Cr[Fpos] == rowF)
+        assert np.array_equal(np.sort(Fpos), np.arange(nnz)) and np.all(Cpos[Fpos] == np.arange(nnz))
+        rowA = np.repeat(np.arange(n), np.diff(Ap))
+        pa = Apos - offLc
+        assert np.all(Aj != rowA)
+        assert np.all(pcol[pa] == np.minimum(rowA, Aj)) and np.all(Cr[pa] == np.maximum(rowA, Aj))
+        sa = rowA[1:] == rowA[:-1]
+        assert np.all(Aj[1:][sa] > Aj[:-1][sa])
+        fwd = set(zip(rowA.tolist(), Aj.tolist()))
+        assert fwd == set(zip(Aj.tolist(), rowA.tolist()))
+        _, ogp, _ = oracle.local_graph(case, name)
+        assert np.array_equal(np.sort(np.diff(Ap)), np.sort(np.diff(ogp)))
+    g.close()
+
+
 def test_outage_keeps_pattern(lib):
     case = gridgen.config_raw(0)
     c2 = case.copy()
