@@ -296,15 +296,24 @@ __device__ __forceinline__ void lane_piece(const int *h, const unsigned char *ba
     }
 }
 
-// One substitution sweep for a solve group (same ring protocol as the
-// single-case sweep: block-wide pieces end with a block barrier that
-// releases their stage; runs of single-warp pieces are consumed by warp 0).
+// One substitution sweep for a solve group.  Thread 0 issues the copies:
+// the first kStages pieces up front, then piece j + kStages once piece j
+// has been consumed.  Block-wide pieces end with a block barrier that
+// releases their stage; runs of single-warp pieces are consumed by warp 0,
+// which issues the refills as it goes, while the other warps wait for the
+// piece after the run.  Giving up is collective, as in staged_sweep: every
+// thread waits (bounded) for the next piece and peeks at its control words,
+// then one __syncthreads_or decides for all whether anyone's wait gave up;
+// a header is acted on only after that vote, and a run ends with a vote of
+// its own before the next piece is waited for.  After the sweep, if anything
+// gave up, thread 0 waits for every copy that may still be in flight.
 template <class T, int W>
 __device__ bool lane_sweep(Ring *R, unsigned char *stages, const Piece *pieces, int np,
                            const int *ptr, const int *idx, const T *val, const T *dinv,
                            const int *lvl_ptr, T *x, const T *lfv, const T *lfd, unsigned spin) {
     const unsigned g0 = R->gcount;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *err = &R->err;
     int issued = 0;
     Piece next{};
     if (threadIdx.x == 0) {
@@ -321,51 +330,71 @@ __device__ bool lane_sweep(Ring *R, unsigned char *stages, const Piece *pieces, 
             if (j + kStages + 1 < np) next = pieces[j + kStages + 1];
         }
     };
-    bool ok = true;
-    int j = 0;
-    while (j < np) {
-        const unsigned g = g0 + unsigned(j);
+    auto wait_peek = [&](int jx, int &mode, int &run_end) {
+        const unsigned g = g0 + unsigned(jx);
         const int st = int(g % kStages);
-        if (!mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin)) atomicExch(&R->err, 1);
-        const int *h = R->hdr[st];
-        const int mode = h[8];
-        if (mode >= 2) {
-            const int jr = h[9];
-            __syncthreads();  // every warp has read this header before warp 0 refills the stage
+        const bool got = mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin, err);
+        if (got) {
+            mode = R->hdr[st][8];
+            run_end = R->hdr[st][9];
+        }
+        return got;
+    };
+    int mode = 0, run_end = 0;
+    bool stop = np > 0 ? __syncthreads_or(!wait_peek(0, mode, run_end) || *err != 0) != 0 : false;
+    int j = 0;
+    while (!stop && j < np) {
+        const int st = int((g0 + unsigned(j)) % kStages);
+        const bool run = mode >= 2;
+        const int jn = run ? run_end : j + 1;
+        bool fail = false;
+        if (run) {
             if (warp == 0) {
-                for (int jj = j; jj < jr; jj++) {
+                for (int jj = j; jj < jn; jj++) {
                     const unsigned gg = g0 + unsigned(jj);
                     const int s2 = int(gg % kStages);
-                    if (jj > j && !mbar_wait_bounded(&R->bar[s2], (gg / kStages) & 1u, spin))
-                        atomicExch(&R->err, 1);
-                    __syncwarp();
-                    if (R->err) break;
+                    if (jj > j) {
+                        const bool got = mbar_wait_bounded(&R->bar[s2], (gg / kStages) & 1u, spin, err);
+                        if (__any_sync(0xffffffffu, !got || *err != 0)) {
+                            fail = true;
+                            break;
+                        }
+                    }
                     lane_piece<T, W>(R->hdr[s2], stages + size_t(s2) * kStageBytes, x, lfv, lfd,
                                      R->hdr[s2][8]);
                     __syncwarp();
                     if (lane == 0) issue_after(jj);
                 }
+                if (fail && lane == 0) atomicExch(&R->err, 1);
             }
-            __syncthreads();
-            if (R->err) { ok = false; break; }
-            j = jr;
+            // the others wait for warp 0 before waiting for the piece after
+            // the run (its stage's previous phase must be complete first)
+            if (__syncthreads_or(fail || *err != 0)) {
+                stop = true;
+                break;
+            }
         } else {
-            if (!R->err) lane_piece<T, W>(h, stages + size_t(st) * kStageBytes, x, lfv, lfd, mode);
-            __syncthreads();
-            if (R->err) { ok = false; break; }
-            if (threadIdx.x == 0) issue_after(j);
-            j++;
+            lane_piece<T, W>(R->hdr[st], stages + size_t(st) * kStageBytes, x, lfv, lfd, mode);
         }
+        int nmode = 0, nrun = 0;
+        const bool got = jn < np ? wait_peek(jn, nmode, nrun) : true;
+        stop = __syncthreads_or(!got || *err != 0) != 0;
+        if (!run && !stop && threadIdx.x == 0) issue_after(j);
+        mode = nmode;
+        run_end = nrun;
+        j = jn;
     }
+    if (stop && threadIdx.x == 0) atomicExch(&R->err, 1);
+    __syncthreads();
+    const bool ok = R->err == 0;
     if (!ok && threadIdx.x == 0) {
+        // the caller's limit may be short; the drain always waits long
+        // enough for a copy to land (a copy must not outlive the block)
         for (int q = (issued > kStages ? issued - kStages : 0); q < issued; q++) {
             const unsigned gq = g0 + unsigned(q);
-            // the caller's limit may be short; the drain always waits long
-            // enough for a copy to land (a copy must not outlive the block)
             mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, spin > kDefaultSpin ? spin : kDefaultSpin);
         }
     }
-    __syncthreads();
     if (threadIdx.x == 0) R->gcount = g0 + unsigned(np);
     __syncthreads();
     return ok;

@@ -117,9 +117,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Barrier among the first `nthreads` threads of the block (named barrier 1).
-__device__ __forceinline__ void consumer_sync(int nthreads) {
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+// Barrier among the first `nthreads` threads of the block (named barrier 1)
+// that ORs `pred` over them: every participant receives the same result, so
+// a decision taken on it is uniform over the participants.
+__device__ __forceinline__ bool consumer_vote_any(int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " barrier.cta.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(uint32_t(pred)), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 // Bulk copy global -> this CTA's shared memory, completion counted on `bar`.
@@ -142,10 +151,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for phase `parity` of `bar`, giving up after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned limit) {
-    for (unsigned i = 0; i < limit; i++)
+// Waits for phase `parity` of `bar`, giving up after `limit` polls, or
+// earlier once *stop (optional) is non-zero.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned limit,
+                                                  const volatile int *stop = nullptr) {
+    for (unsigned i = 0; i < limit; i++) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (stop && *stop) return false;
+    }
     return false;
 }
 
@@ -179,6 +192,12 @@ struct Ring {
                           // diag off (-1: none), d_lo, level-pointer off, lp_lo, l0, l1, e1
     int err;              // set when a wait gave up
     unsigned gcount;      // pieces consumed so far (phase bookkeeping)
+    // Self-test hooks of the give-up path (-1 = off; only the sweep self-test
+    // sets them), in pieces counted since ring_init: the producer issues no
+    // piece from number `stall_at` on, as if its copies never landed, and the
+    // consumers do not release the stage of piece number `hold_at`, as if they
+    // never finished with it.  Either makes a bounded wait of a sweep run out.
+    int stall_at, hold_at;
 };
 
 __device__ void ring_init(Ring *R) {
@@ -189,6 +208,8 @@ __device__ void ring_init(Ring *R) {
         }
         R->err = 0;
         R->gcount = 0;
+        R->stall_at = -1;
+        R->hold_at = -1;
         fence_mbar_init();
     }
     __syncthreads();
@@ -441,11 +462,26 @@ __device__ __forceinline__ void issue_piece(Ring *R, unsigned char *stages, int 
 // issues each piece's copies into the ring as soon as the consumers have
 // released the stage's previous piece (an "empty" mbarrier per stage), so
 // issuing is off the consumers' critical path.  The other warps consume:
-// block-wide pieces end with a barrier among the consumers, after which the
-// stage is released; runs of single-warp pieces (modes 2-4) are consumed by
-// warp 0 alone, releasing each stage as it goes, while the other consumers
-// wait at the end of the run.  Returns false if a wait gave up (then no copy
-// is left in flight).
+// a block-wide piece is computed by all of them; a run of single-warp
+// pieces (modes 2-4) is consumed by warp 0 alone, which releases each stage
+// as it goes, while the other consumers go on to wait for the piece after
+// the run.
+//
+// Giving up is collective.  Before each piece every consumer waits (bounded)
+// for the piece's copies and reads the two header words that steer the
+// control flow (mode, run end); then all consumers vote at one named barrier
+// (consumer_vote_any) on whether anyone's wait gave up or the error flag is
+// set.  On "stop" all of them leave at that same barrier, so none is left
+// waiting at a later one, and a header is acted on only after the vote has
+// confirmed that every consumer saw its copies land.  The vote is also the
+// barrier after which a block-wide piece's stage is released.  Warp 0's
+// decisions inside a run are taken by __any_sync over its lanes, and a run
+// ends with a vote of its own before anyone waits for the next piece: a
+// parity wait is only sound once the stage's previous phase (the piece four
+// before) has completed, which only warp 0 has seen for the run's pieces.  After the
+// sweep, if anything gave up, the producer waits for every copy it issued
+// that may still be in flight (a copy must not outlive the block).  Returns
+// false if a wait gave up (the same value in every thread).
 template <class T, class X, int NB, bool TRANS>
 __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces, int np,
                              const SweepSrc<T> &S, X *x, unsigned spin) {
@@ -453,91 +489,104 @@ __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int ncw = nwarps - 1, nct = ncw * 32;  // consumer warps / threads
     volatile int *err = &R->err;
-    bool ok = true;
+    int issued = 0;  // producer lane 0: pieces whose copies were issued
     if (warp == ncw) {
         // producer: piece j goes into stage (g0 + j) mod kStages once the
         // consumers have released that stage's previous piece
         if (lane == 0) {
-            int issued = 0;
-            const unsigned long_spin = spin > kDefaultSpin ? spin : kDefaultSpin;
+            const int stall = R->stall_at;
             for (int j = 0; j < np; j++) {
                 const unsigned g = g0 + unsigned(j);
+                if (stall >= 0 && g >= unsigned(stall)) break;  // self-test: these copies never come
                 const int st = int(g % kStages);
-                if (g >= unsigned(kStages)) {
-                    bool got = false;
-                    for (unsigned it = 0; it < spin && !*err; it++)
-                        if (mbar_try_wait(&R->ebar[st], ((g / kStages) & 1u) ^ 1u)) {
-                            got = true;
-                            break;
-                        }
-                    if (!got) {
-                        atomicExch(&R->err, 1);
-                        break;
-                    }
+                if (g >= unsigned(kStages) &&
+                    !mbar_wait_bounded(&R->ebar[st], ((g / kStages) & 1u) ^ 1u, spin, err)) {
+                    atomicExch(&R->err, 1);
+                    break;
                 }
                 if (*err) break;
                 issue_piece<T, NB>(R, stages, st, pieces[j], S);
                 issued = j + 1;
             }
-            if (*err) {
-                // drain: the last issued piece of every stage may still be in
-                // flight; a copy must not outlive the block
-                for (int q = (issued > kStages ? issued - kStages : 0); q < issued; q++) {
-                    const unsigned gq = g0 + unsigned(q);
-                    mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, long_spin);
-                }
-            }
         }
         __syncwarp();
     } else {
-        int j = 0;
-        while (j < np) {
-            const unsigned g = g0 + unsigned(j);
+        const int hold = R->hold_at;
+        // wait for piece jx and peek at its control words (valid only when
+        // the wait succeeded; used only after a vote confirmed that)
+        auto wait_peek = [&](int jx, int &mode, int &run_end) {
+            const unsigned g = g0 + unsigned(jx);
             const int st = int(g % kStages);
-            if (!mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin)) atomicExch(&R->err, 1);
-            const int *h = R->hdr[st];
-            const int mode = h[8];
-            if (mode >= 2 && mode <= 4) {
-                const int jr = h[9];
-                consumer_sync(nct);  // every consumer has read this header before the stage is released
+            const bool got = mbar_wait_bounded(&R->bar[st], (g / kStages) & 1u, spin, err);
+            if (got) {
+                mode = R->hdr[st][8];
+                run_end = R->hdr[st][9];
+            }
+            return got;
+        };
+        int mode = 0, run_end = 0;
+        bool stop = np > 0 ? consumer_vote_any(nct, !wait_peek(0, mode, run_end) || *err != 0) : false;
+        int j = 0;
+        while (!stop && j < np) {
+            const int st = int((g0 + unsigned(j)) % kStages);
+            const bool run = mode >= 2 && mode <= 4;
+            const int jn = run ? run_end : j + 1;
+            bool fail = false;
+            if (run) {
                 if (warp == 0) {
-                    for (int jj = j; jj < jr; jj++) {
+                    for (int jj = j; jj < jn; jj++) {
                         const unsigned gg = g0 + unsigned(jj);
                         const int s2 = int(gg % kStages);
-                        if (jj > j && !mbar_wait_bounded(&R->bar[s2], (gg / kStages) & 1u, spin))
-                            atomicExch(&R->err, 1);
-                        __syncwarp();
-                        if (*err) break;
+                        if (jj > j) {
+                            const bool got = mbar_wait_bounded(&R->bar[s2], (gg / kStages) & 1u, spin, err);
+                            if (__any_sync(0xffffffffu, !got || *err != 0)) {
+                                fail = true;
+                                break;
+                            }
+                        }
                         piece_rows<T, X, NB, TRANS>(R->hdr[s2], stages + size_t(s2) * kStageBytes, x,
                                                     R->hdr[s2][8], 0, 1);
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(&R->ebar[s2]);
+                        if (lane == 0 && int(gg) != hold) mbar_arrive(&R->ebar[s2]);
                     }
+                    if (fail && lane == 0) atomicExch(&R->err, 1);
                 }
-                consumer_sync(nct);
-                if (*err) {
-                    ok = false;
+                // the other consumers wait here for warp 0: only once the run's
+                // pieces have landed may they wait for the piece after it (the
+                // stage's previous phase must be complete, or the parity wait
+                // could succeed on it)
+                if (consumer_vote_any(nct, fail || *err != 0)) {
+                    stop = true;
                     break;
                 }
-                j = jr;
             } else {
-                if (!*err)
-                    piece_rows<T, X, NB, TRANS>(h, stages + size_t(st) * kStageBytes, x, mode,
-                                                (mode == 1 || mode == 5) ? warp : int(threadIdx.x),
-                                                (mode == 1 || mode == 5) ? ncw : nct);
-                consumer_sync(nct);
-                if (*err) {
-                    ok = false;
-                    break;
-                }
-                if (threadIdx.x == 0) mbar_arrive(&R->ebar[st]);
-                j++;
+                piece_rows<T, X, NB, TRANS>(R->hdr[st], stages + size_t(st) * kStageBytes, x, mode,
+                                            (mode == 1 || mode == 5) ? warp : int(threadIdx.x),
+                                            (mode == 1 || mode == 5) ? ncw : nct);
             }
+            int nmode = 0, nrun = 0;
+            const bool got = jn < np ? wait_peek(jn, nmode, nrun) : true;
+            stop = consumer_vote_any(nct, !got || *err != 0);
+            // every consumer is done with a block-wide piece: release its stage
+            if (!run && !stop && threadIdx.x == 0 && int(g0 + unsigned(j)) != hold)
+                mbar_arrive(&R->ebar[st]);
+            mode = nmode;
+            run_end = nrun;
+            j = jn;
         }
+        if (stop && threadIdx.x == 0) atomicExch(&R->err, 1);
     }
     __syncthreads();
+    const bool ok = R->err == 0;
+    if (!ok && warp == ncw && lane == 0) {
+        // drain: the last issued piece of every stage may still be in flight
+        const unsigned long_spin = spin > kDefaultSpin ? spin : kDefaultSpin;
+        for (int q = (issued > kStages ? issued - kStages : 0); q < issued; q++) {
+            const unsigned gq = g0 + unsigned(q);
+            mbar_wait_bounded(&R->bar[gq % kStages], (gq / kStages) & 1u, long_spin);
+        }
+    }
     if (threadIdx.x == 0) R->gcount = g0 + unsigned(np);
-    ok = R->err == 0;
     __syncthreads();
     return ok;
 }

@@ -2188,6 +2188,30 @@ int gbpf_debug_gather(const pf_ctx *ctx, int which, long long *sizes, int *Cp, i
     return 0;
 }
 
+// Test hook of the substitution sweeps' give-up path (needs a GPU): one
+// solve of matrix `which` in place on rhs_dev (n doubles, local order) with
+// instance 0 of its last factor of precision `prec`, in which the producer
+// issues no piece from index stall_at of a sweep on (-1: off) or the
+// consumers never release the stage of piece hold_at (-1: off), every wait
+// bounded by `spin` polls.  *status_host receives PF_OK when the solve
+// completed or PF_ERR_TIMEOUT when it gave up.  Synchronous.  Returns 0, or
+// -1 for a bad argument, a matrix not factorised in that precision or a
+// vector that does not fit shared memory, -2 when a CUDA call failed.
+int gbpf_selftest_sweep(pf_ctx *ctx, int which, int prec, int stall_at, int hold_at, unsigned spin,
+                        double *rhs_dev, int *status_host) {
+    if (!ctx || which < 0 || which > 1 || (prec != PF_FP64 && prec != PF_FP32) || !rhs_dev ||
+        !status_host || spin == 0)
+        return -1;
+    if (!ctx->ws.factored[which][prec]) return -1;
+    const void *F = prec == PF_FP64 ? (const void *)ctx->ws.F64[which] : (const void *)ctx->ws.F32[which];
+    int *st = ctx->ws.cstatus;
+    cudaError_t e = launch_selftest_sweep(ctx->dm[which], prec, F, ctx->ws.TV[which][prec], rhs_dev, stall_at,
+                                          hold_at, spin, st, ctx->smem_optin, nullptr);
+    if (e == cudaErrorInvalidValue) return -1;
+    if (e == cudaSuccess) e = cudaMemcpy(status_host, st, sizeof(int), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? 0 : -2;
+}
+
 // Test hook (host only, no GPU needed): the CSR copy of L's pattern and its
 // maps to the CSC one, and the off-diagonal pattern of A used by residuals,
 // of matrix `which`.  sizes[4] receives {n, nnz, offLc, entries of A's

@@ -334,6 +334,11 @@ cudaError_t launch_tail_values(const DevMat &m, int prec, const void *F, void *T
 cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const void *TV,
                          const int *inst_of_case, double *rhs, int ncase, void *gvec, int *status,
                          size_t smem_optin, cudaStream_t s);
+// Self-test of the sweeps' give-up path (one block, instance 0 of F; the
+// solve vector must fit shared memory): see k_selftest_sweep.
+cudaError_t launch_selftest_sweep(const DevMat &m, int prec, const void *F, const void *TV, double *rhs,
+                                  int stall_at, int hold_at, unsigned spin, int *status,
+                                  size_t smem_optin, cudaStream_t s);
 cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
                             double *dp, double *dq, double *maxmis, double *ef, int ncase,
                             cudaStream_t s);

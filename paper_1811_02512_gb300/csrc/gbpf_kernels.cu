@@ -689,6 +689,30 @@ __global__ void __launch_bounds__(kSolveThreads)
     if (threadIdx.x == 0 && !ok) atomicExch(status, PF_ERR_TIMEOUT);
 }
 
+// Self-test of the sweeps' give-up path: k_solve's solve of one right-hand
+// side with instance 0's factor, with the ring's self-test hooks set (the
+// producer issues no piece from stall_at on, or the consumers keep the stage
+// of piece hold_at), so that a bounded wait of a sweep runs out.  *status:
+// PF_ERR_TIMEOUT when the solve gave up, PF_OK when it completed.
+template <class T>
+__global__ void __launch_bounds__(kSolveThreads)
+    k_selftest_sweep(DevMat m, const T *F, const T *TV, double *rhs, int stall_at, int hold_at,
+                     unsigned spin, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ Ring R;
+    T *x = reinterpret_cast<T *>(smem_raw + kStages * kStageBytes);
+    ring_init(&R);
+    if (threadIdx.x == 0) {
+        R.stall_at = stall_at;
+        R.hold_at = hold_at;
+    }
+    for (int k = threadIdx.x; k < m.n; k += blockDim.x) x[k] = T(rhs[m.local[k]]);
+    __syncthreads();
+    const bool ok = block_solve<T, T>(&R, smem_raw, m, F, x, spin, TV);
+    for (int k = threadIdx.x; k < m.n; k += blockDim.x) rhs[m.local[k]] = double(x[k]);
+    if (threadIdx.x == 0) *status = ok ? PF_OK : PF_ERR_TIMEOUT;
+}
+
 // ------------------------------------------------------------ low-rank outages
 
 // Z = A^-1 U for the outage instances (instance inst >= 1, column col of U =
@@ -1372,6 +1396,30 @@ cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const void *T
                                                           inst_of_case, rhs,
                                                           static_cast<float *>(gvec), use_smem,
                                                           status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_sweep(const DevMat &m, int prec, const void *F, const void *TV, double *rhs,
+                                  int stall_at, int hold_at, unsigned spin, int *status,
+                                  size_t smem_optin, cudaStream_t s) {
+    if (m.npf2 == 0) TV = nullptr;
+    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
+    const size_t smem = size_t(kStages) * kStageBytes + elt * size_t(m.n);
+    if (smem + 2048 > smem_optin) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (prec == PF_FP64) {
+        e = cudaFuncSetAttribute(k_selftest_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_selftest_sweep<double><<<1, kSolveThreads, smem, s>>>(m, static_cast<const double *>(F),
+                                                                static_cast<const double *>(TV), rhs,
+                                                                stall_at, hold_at, spin, status);
+    } else {
+        e = cudaFuncSetAttribute(k_selftest_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_selftest_sweep<float><<<1, kSolveThreads, smem, s>>>(m, static_cast<const float *>(F),
+                                                               static_cast<const float *>(TV), rhs,
+                                                               stall_at, hold_at, spin, status);
     }
     return cudaGetLastError();
 }

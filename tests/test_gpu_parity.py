@@ -217,26 +217,72 @@ def test_iteration_limit_reported():
     g.close()
 
 
-@pytest.mark.parametrize("ncase", [1, 4])
-def test_wait_limit_reports_timeout_and_context_survives(oracle, ncase):
-    """A one-poll limit on every wait of the staged sweeps: a wait that gives
-    up makes the kernel drain its copies and report PF_ERR_TIMEOUT; a poll
-    usually suffices (mbarrier try_wait suspends until the phase completes or a
-    hardware time limit), so the run may also converge.  Either way the next
-    run with the default limit is correct."""
+def _pieces(g, which, lst):
+    L = gbpf.load()
+    f = L.gbpf_debug_pieces
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]
+    cnt = C.c_int(0)
+    assert f(g.ctx, which, lst, C.byref(cnt), None, 0) == 0
+    out = np.zeros(max(1, 8 * cnt.value), np.int32)
+    assert f(g.ctx, which, lst, C.byref(cnt), out.ctypes.data, out.shape[0]) == 0
+    return out[:8 * cnt.value].reshape(-1, 8)
+
+
+def _selftest_sweep(g, which, prec, stall, hold, spin, x_dev):
+    L = gbpf.load()
+    f = L.gbpf_selftest_sweep
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_void_p, C.c_void_p]
+    st = C.c_int(-1)
+    rc = f(g.ctx, which, prec, stall, hold, spin, x_dev.data_ptr(), C.byref(st))
+    assert rc == 0
+    return st.value
+
+
+@pytest.mark.parametrize("which,name", [(gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")])
+def test_sweep_gives_up_together_and_context_survives(oracle, which, name):
+    """The substitution sweeps' give-up path, made to happen for certain with
+    the ring's self-test hooks: the producer stops issuing at a chosen piece
+    (its copies never come, so the consumers' bounded waits run out), or the
+    consumers keep one stage (so the producer's bounded wait runs out).  The
+    stop points cover the first piece, block-wide pieces, the first piece of
+    a single-warp run (the scatter tail) and the backward sweep.  Every such
+    solve returns PF_ERR_TIMEOUT instead of hanging; afterwards an ordinary
+    solve matches the oracle and a full power flow converges."""
     case = gridgen.config(1)
-    g = _grid(case, ncase)
-    vm = torch.zeros((ncase, case.n), dtype=torch.float64, device=DEV)
-    va = torch.zeros_like(vm)
-    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-8, max_iter=200, spin_limit=1)
-    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase, check=False)
-    assert st in (gbpf.PF_OK, gbpf.PF_ERR_TIMEOUT)
-    assert all(s in (gbpf.PF_OK, gbpf.PF_ERR_TIMEOUT) for s in res["status"])
+    g = _grid(case)
+    gbpf.pf_factor(g.ctx, which, gbpf.PF_FP64)
+    fwd, bwd = _pieces(g, which, 2), _pieces(g, which, 3)
+    if fwd.shape[0] == 0:
+        fwd, bwd = _pieces(g, which, 0), _pieces(g, which, 1)
+    nf, nb = fwd.shape[0], bwd.shape[0]
+    run_f = [j for j in range(nf) if 2 <= fwd[j, 4] <= 4]
+    run_b = [j for j in range(nb) if 2 <= bwd[j, 4] <= 4]
+    assert run_f and run_b and nf > 8 and nb > 8
+    stalls = sorted({0, nf // 2, run_f[0], run_f[-1], nf - 1, nf, nf + run_b[0], nf + nb - 1})
+    holds = sorted(h for h in {0, run_f[0], nf // 3, nf, nf + run_b[0]} if h + 4 < nf + nb)
+    n = g.info.n[which]
+    rhs = torch.ones(n, dtype=torch.float64, device=DEV)
+    for stall in stalls:
+        x = rhs.clone()
+        assert _selftest_sweep(g, which, gbpf.PF_FP64, stall, -1, 20000, x) == gbpf.PF_ERR_TIMEOUT, stall
+    for hold in holds:
+        x = rhs.clone()
+        assert _selftest_sweep(g, which, gbpf.PF_FP64, -1, hold, 20000, x) == gbpf.PF_ERR_TIMEOUT, hold
+    # the hooks off: the same self-test solve completes and is correct
+    x = rhs.clone()
+    assert _selftest_sweep(g, which, gbpf.PF_FP64, -1, -1, 1 << 22, x) == gbpf.PF_OK
+    an, Lx0, d0, _ = oracle.factor_bmatrix(case, name)
+    xs = oracle.lu_solve(n, an["Lp"], an["Li"], Lx0, Lx0 * d0[np.repeat(np.arange(n), np.diff(an["Lp"]))],
+                         d0, np.ones(n))
+    x_ref = np.empty(n)
+    x_ref[an["perm"]] = xs
+    assert np.max(np.abs(x.cpu().numpy() - x_ref)) <= 1e-11 * np.max(np.abs(x_ref))
     opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-11, max_iter=300)
-    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+    vm = torch.zeros((1, case.n), dtype=torch.float64, device=DEV)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, torch.zeros_like(vm), 1)
     assert st == gbpf.PF_OK
-    rc, vm0, va0, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
-    assert np.max(np.abs(vm.cpu().numpy()[0] - vm0)) <= 1e-8
     g.close()
 
 
