@@ -101,7 +101,8 @@ typedef struct {
                            residual that small cannot change a convergence decision) */
     int32_t flat_start; /* 1: theta = slack angle / 0, V = 1 (PQ) or vset; 0: use vm/va */
     int32_t spin_limit; /* bound on every device-side wait (0 = library default) */
-    int32_t engine;     /* PF_ENGINE_AUTO, PF_ENGINE_BLOCK or PF_ENGINE_LANES (FDPF only) */
+    int32_t engine;     /* PF_ENGINE_AUTO, PF_ENGINE_BLOCK, PF_ENGINE_LANES or
+                           PF_ENGINE_CLUSTER (FDPF only) */
     int32_t fallback;   /* FDPF only: 1 = cases the fast decoupled iteration leaves
                            unconverged (PF_ERR_NOT_CONVERGED, PF_ERR_NONFINITE) are
                            re-run by Newton-Raphson from a flat start in the same
@@ -115,14 +116,22 @@ typedef struct {
  * in groups of 32 cases, one case per lane; the mismatch, convergence test
  * and update run over (bus, case) pairs, each substitution over blocks of
  * 4, 2 or 1 cases whose vectors fit in shared memory, and one half-iteration
- * pair is a CUDA graph replayed until every case has retired.  AUTO picks
- * BLOCK; LANES falls back to BLOCK where not even one case fits. */
-enum { PF_ENGINE_AUTO = 0, PF_ENGINE_BLOCK = 1, PF_ENGINE_LANES = 2 };
+ * pair is a CUDA graph replayed until every case has retired.  CLUSTER
+ * (FDPF, FP64, a batch of one case without outage): the case runs on a
+ * 16-block cluster that shares the substitutions as well as the mismatch --
+ * every row of L belongs to one block, which keeps its factor entries in
+ * shared memory for the whole run; a level of the elimination tree is one
+ * step of all blocks followed by a cluster barrier, and the narrow top of
+ * the tree is solved with the explicit inverse of its block of L (three
+ * steps in all); it needs the factors' programs to fit in shared memory.
+ * AUTO picks BLOCK; LANES and CLUSTER fall back to BLOCK where they do not
+ * apply. */
+enum { PF_ENGINE_AUTO = 0, PF_ENGINE_BLOCK = 1, PF_ENGINE_LANES = 2, PF_ENGINE_CLUSTER = 3 };
 
 /* Kernel mappings of a context, chosen by pf_autotune (or set directly with
  * pf_set_tuning; 0 in a field = the library's default choice):
- *   engine   PF_ENGINE_BLOCK or PF_ENGINE_LANES, used by FDPF runs whose
- *            options ask for PF_ENGINE_AUTO;
+ *   engine   PF_ENGINE_BLOCK, PF_ENGINE_LANES or PF_ENGINE_CLUSTER, used
+ *            by FDPF runs whose options ask for PF_ENGINE_AUTO;
  *   cluster  thread blocks per case of a single-case FDPF run (1, 8, 16;
  *            capped at what fits the GPU);
  *   factor   1: dependency-driven factor over all SMs, 2: one thread block

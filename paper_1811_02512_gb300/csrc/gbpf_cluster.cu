@@ -1,0 +1,488 @@
+// gbpf_cluster.cu -- single-case fast-decoupled power flow with the
+// substitutions spread over a thread-block cluster (sm_103a).
+//
+// One case runs on the C = 16 CTAs of a cluster, one per SM.  The nodal
+// mismatch is split by bus slices as in k_fdpf (Section II.A).  The
+// substitutions of Section III.C are split by rows: every row (column) of
+// the factor has an owner CTA, which keeps that row's entries of L (and of
+// the tail inverse below) resident in its shared memory for the whole
+// launch, and holds the row's entry of the solution vector.  A step of a
+// sweep is one level of the elimination tree (the paper's hierarchical
+// parallelism, Section II.B): every CTA computes its rows of the level,
+// reading the entries of lower (forward) or higher (backward) levels from
+// their owners' shared memory over the cluster's distributed shared memory,
+// and the step ends with a cluster barrier.
+//
+// The narrow top of the elimination tree (the tail, rows [t0, n): a long run
+// of levels with at most 16 rows each, 118 levels of B' at 10,000 buses)
+// would cost one barrier per level.  It is solved instead with the explicit
+// inverse W = L_TT^-1 of the tail's diagonal block of L (a partitioned
+// inverse of the factor): with L = [[L_BB, 0], [L_TB, L_TT]],
+//   forward   c_T = b_T - L_TB z_B,  z_T = W c_T,
+//   backward  x_T = W^T D_T^-1 z_T,  then the bottom levels as usual,
+// so the tail takes three steps whatever its height.  W has a nonzero (i, j)
+// exactly when i is an ancestor of j in the elimination tree; it is formed
+// after every factorisation by k_tail_inverse (one thread per tail column,
+// walking the column's ancestor path with the recurrence
+// w_i = -sum_k L_ik w_k), and gathered with the factor's values into the
+// CTAs' packed value arrays by k_cl_values.
+#include "gbpf_device.cuh"
+
+namespace gbpf {
+
+namespace {
+
+constexpr int kClThreads = 512;
+
+// ------------------------------------------------------------ DSMEM access
+
+__device__ __forceinline__ uint32_t cl_mapa(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ double ld_cl(uint32_t a) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_cl(uint32_t a, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+// Cluster barrier with release / acquire semantics at cluster scope: the
+// shared-memory writes of every CTA before it are visible to every CTA
+// after it.
+__device__ __forceinline__ void cl_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The same for phases that exchange data through global memory as well:
+// the release / acquire of the cluster barrier covers every state space
+// (global stores before it are visible to loads after it in the cluster).
+__device__ __forceinline__ void cl_barrier_global() { cl_barrier(); }
+
+// ------------------------------------------------------------ tail inverse
+
+// W = L_TT^-1 of the top set T of one matrix: W(it, jt) = Wd[it * nt + jt]
+// (T-relative indices), written only where it is structurally nonzero (it
+// an ancestor of, or equal to, jt).  One warp per column jt solves
+// L_TT w = e_jt right-looking along jt's ancestor path: at path node k
+// (ascending; tpar: parent, -1 at a root) w_k is final, and every entry
+// L(i, k) of column k -- all on the path, since its rows are ancestors of k
+// -- gives w_i -= L(i, k) w_k, one lane per entry (distinct rows, so no
+// conflict).  The path's values live in shared memory by distance from jt
+// (depth[jt] - depth[k]); the columns of L_TT (tcp, the depth of each
+// entry's row in tcdep, its factor position in tcpos) are staged into shared
+// memory first.  The order of operations is fixed.
+__global__ void __launch_bounds__(kTailInvWarps * 32) k_tail_inverse(const ClMat m, const double *F, double *Wd) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    const int nt = m.nt, ne = m.ntail_e, D = m.tdepth_max;
+    double *Lv = reinterpret_cast<double *>(tsm);
+    double *wp = Lv + ne;                                   // [kTailInvWarps][D]
+    int *Ld = reinterpret_cast<int *>(wp + kTailInvWarps * D);
+    int *cp = Ld + ne;                                      // [nt + 1]
+    int *dep = cp + nt + 1, *par = dep + nt;
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+        Lv[q] = F[m.tcpos[q]];
+        Ld[q] = m.tcdep[q];
+    }
+    for (int i = threadIdx.x; i <= nt; i += blockDim.x) cp[i] = m.tcp[i];
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        dep[i] = m.tdepth[i];
+        par[i] = m.tpar[i];
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *w = wp + warp * D;
+    for (int i = lane; i < D; i += 32) w[i] = 0.0;
+    __syncthreads();
+    const int jt = blockIdx.x * kTailInvWarps + warp;
+    if (jt >= nt) return;
+    const int dj = dep[jt];
+    if (lane == 0) w[0] = 1.0;
+    for (int k = jt; k >= 0; k = par[k]) {
+        __syncwarp();
+        const double wk = w[dj - dep[k]];
+        if (lane == 0) Wd[(long long)k * nt + jt] = wk;
+        for (int q = cp[k] + lane; q < cp[k + 1]; q += 32) {
+            const int pos = dj - Ld[q];
+            w[pos] = fma(-Lv[q], wk, w[pos]);
+        }
+    }
+}
+
+// Packed values of the CTAs' programs (blockIdx.y = matrix): per slot
+// {kind, a, b}: 0 the factor value F[a]; 1 the negated tail-inverse entry
+// -Wd[a] (forward tail step); 2 -Wd[a] * F[b] (backward tail step, the
+// inverse diagonal folded in).
+__global__ void k_cl_values(const ClMat m0, const ClMat m1, const double *F0, const double *F1,
+                            const double *W0, const double *W1) {
+    const ClMat &m = blockIdx.y ? m1 : m0;
+    const double *F = blockIdx.y ? F1 : F0;
+    const double *Wd = blockIdx.y ? W1 : W0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m.nval; s += gridDim.x * blockDim.x) {
+        const int4 src = m.vsrc[s];
+        double v;
+        if (src.x == 0) v = F[src.y];
+        else if (src.x == 1) v = -Wd[src.y];
+        else v = -Wd[src.y] * F[src.z];
+        m.vals[s] = v;
+    }
+}
+
+// ------------------------------------------------------------ run kernel
+
+struct ClRun {
+    DevNet dn;
+    DevCases dc;
+    ClMat m[2];
+    const int *fs0, *fs1;
+    double tol;
+    int max_iter;
+    int flat;
+    double *vm, *va;
+    double *ef;    // [4 nbus]: e, f, cos(theta), sin(theta)
+    double *iv;    // [nbus]: 1 / V
+    double *bmax;  // [16]: per-CTA mismatch maxima
+    pf_case_result *res;
+};
+
+// Shared-memory program of one matrix in one CTA (byte offsets of the
+// regions are the same in every CTA, so a slot's address in another CTA is
+// that CTA's base plus the same offset).
+struct ClSmem {
+    double *X;        // vector region
+    int4 *tasks;      // {out, in, diag value or -1, first entry}, one sentinel
+    int4 *steps;      // {first task, end task, lanes per task, 0}
+    uint32_t *addr;   // entry sources as shared::cluster addresses
+    double *vals;     // entry values, then the diagonal values
+};
+
+// One step of a sweep in this CTA: for each task t of the step,
+// X[out] = (diag ? vals[diag] X[in] : X[in]) - sum_e vals[e] X(addr[e]),
+// with G lanes per task (up to four entries per lane in flight, the lanes'
+// partial sums shuffle-reduced in lane order: the order of operations is
+// fixed).  Warps without a task skip the step: on GB300 the FP64 pipe
+// (about 1.7 FMA per cycle per SM) is shared by all warps, so idle
+// arithmetic would delay the busy ones.
+__device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
+    const int G = si.z;
+    const int per_warp = 32 / G;  // tasks per warp and round
+    const int warp = int(threadIdx.x) >> 5, lane = int(threadIdx.x) & 31;
+    const int grp = lane / G, gl = lane % G;
+    for (int tb = si.x + warp * per_warp; tb < si.y; tb += (kClThreads / 32) * per_warp) {
+        const int t = tb + grp;
+        const bool act = t < si.y;
+        double acc = 0.0, b = 0.0, dv = 1.0;
+        int4 tk = make_int4(0, 0, -1, 0);
+        if (act) {
+            tk = S.tasks[t];
+            const int e1 = S.tasks[t + 1].w;
+            // every load that does not depend on the entries first: the task's
+            // own word and diagonal value, then four entries' sources and
+            // values, then their words, then the multiply-adds
+            b = S.X[tk.y];
+            if (tk.z >= 0) dv = S.vals[tk.z];
+            double a1 = 0.0;
+            for (int e = tk.w + gl; e < e1; e += 4 * G) {
+                uint32_t p[4];
+                double v[4], x[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const bool in = e + u * G < e1;
+                    p[u] = in ? S.addr[e + u * G] : 0u;
+                    v[u] = in ? S.vals[e + u * G] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) x[u] = e + u * G < e1 ? ld_cl(p[u]) : 0.0;
+                acc = fma(v[0], x[0], acc);
+                a1 = fma(v[1], x[1], a1);
+                acc = fma(v[2], x[2], acc);
+                a1 = fma(v[3], x[3], a1);
+            }
+            acc += a1;
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (act && gl == 0) S.X[tk.x] = (tk.z >= 0 ? dv * b : b) - acc;
+    }
+}
+
+// Mismatch of one half-iteration (as k_fdpf's cluster_mismatch): the CTA's
+// bus slice forms e + jf, then (after a cluster barrier) the currents of its
+// rows; dP/V (which = 0) or dQ/V (which = 1) goes straight into the owner's
+// vector slot of the matrix (rhsref: owner << 16 | word, -1 for a bus
+// outside the matrix).  Returns the cluster maximum of the half-iteration's
+// part (full: of both parts).
+template <int C>
+__device__ double cl_mismatch(const ClRun &a, int rank, int which, const uint32_t *xbase, double *red,
+                              bool full) {
+    const DevNet &dn = a.dn;
+    const int nbus = dn.nbus;
+    const int slice = (nbus + C - 1) / C;
+    const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
+    double *e = a.ef;
+    double *f = e + nbus;
+    const double *cs = e + 2 * nbus;
+    const double *sn = e + 3 * nbus;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        e[i] = a.vm[i] * cs[i];
+        f[i] = a.vm[i] * sn[i];
+    }
+    cl_barrier_global();
+    const int *rhsref = a.m[which].rhsref;
+    const bool wantP = full || which == 0, wantQ = full || which == 1;
+    unsigned long long mx = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        double ir, ii;
+        bus_current(dn, i, -1, e, f, ir, ii);
+        const int t = dn.btype[i];
+        double dP = 0.0, dQ = 0.0;
+        if (wantP && t != PF_BUS_SLACK) dP = a.dc.Psp[i] - (e[i] * ir + f[i] * ii);
+        if (wantQ && t == PF_BUS_PQ) dQ = a.dc.Qsp[i] - (f[i] * ir - e[i] * ii);
+        const unsigned long long kp = abs_key(dP), kq = abs_key(dQ);
+        mx = kp > mx ? kp : mx;
+        mx = kq > mx ? kq : mx;
+        const int r = rhsref[i];
+        if (r >= 0) st_cl(xbase[which * C + (r >> 16)] + 8u * unsigned(r & 0xffff), (which == 0 ? dP : dQ) * a.iv[i]);
+    }
+    mx = block_max_key(mx, red);
+    if (threadIdx.x == 0) a.bmax[rank] = __longlong_as_double(static_cast<long long>(mx));
+    cl_barrier_global();
+    double m = 0.0;
+    for (int r = 0; r < C; r++) m = nan_max(m, a.bmax[r]);
+    return m;
+}
+
+template <int C>
+__global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[33];
+    __shared__ uint32_t xbase[2 * C];  // vector region of matrix m in CTA r: xbase[m * C + r]
+    __shared__ int nsteps[2];
+    const int rank = int(cluster_rank());
+    const DevNet &dn = a.dn;
+    const int nbus = dn.nbus;
+    // the CTA's programs into shared memory (same layout in every CTA)
+    ClSmem S[2];
+    for (int w = 0; w < 2; w++) {
+        const ClMat &m = a.m[w];
+        S[w].X = reinterpret_cast<double *>(smem_raw + m.so_x);
+        S[w].tasks = reinterpret_cast<int4 *>(smem_raw + m.so_tasks);
+        S[w].steps = reinterpret_cast<int4 *>(smem_raw + m.so_steps);
+        S[w].addr = reinterpret_cast<uint32_t *>(smem_raw + m.so_addr);
+        S[w].vals = reinterpret_cast<double *>(smem_raw + m.so_vals);
+        if (threadIdx.x < C)
+            xbase[w * C + threadIdx.x] = cl_mapa(smem_u32(smem_raw + m.so_x), threadIdx.x);
+    }
+    __syncthreads();
+    for (int w = 0; w < 2; w++) {
+        const ClMat &m = a.m[w];
+        const int tb = m.tptr[rank], te = m.tptr[rank + 1];
+        for (int t = threadIdx.x; t < te - tb; t += blockDim.x) S[w].tasks[t] = m.tasks[tb + t];
+        const int sb = m.sptr[rank], se = m.sptr[rank + 1];
+        for (int s = threadIdx.x; s < se - sb; s += blockDim.x) S[w].steps[s] = m.steps[sb + s];
+        if (threadIdx.x == 0) nsteps[w] = se - sb;
+        const int eb = m.eptr[rank], ee = m.eptr[rank + 1];
+        for (int e = threadIdx.x; e < ee - eb; e += blockDim.x) {
+            const int r = m.refs[eb + e];
+            S[w].addr[e] = xbase[w * C + (r >> 16)] + 8u * unsigned(r & 0xffff);
+        }
+        const int vb = m.vptr[rank], ve = m.vptr[rank + 1];
+        for (int v = threadIdx.x; v < ve - vb; v += blockDim.x) S[w].vals[v] = m.vals[vb + v];
+    }
+    // every CTA of the cluster has started (its shared memory exists) before
+    // anyone writes to it
+    cl_barrier();
+    const int slice = (nbus + C - 1) / C;
+    const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
+    double *vm = a.vm, *va = a.va, *iv = a.iv;
+    double *cs = a.ef + 2 * nbus, *sn = cs + nbus;
+    int status = PF_ERR_NOT_CONVERGED;
+    if (a.fs0[0] != PF_OK) status = a.fs0[0];
+    else if (a.fs1[0] != PF_OK) status = a.fs1[0];
+    int iters = 0;
+    double mis = INFINITY;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        if (a.flat) {
+            const int t = dn.btype[i];
+            vm[i] = (t == PF_BUS_PQ) ? 1.0 : dn.vset[i];
+            va[i] = (t == PF_BUS_SLACK) ? dn.va0[i] : 0.0;
+        }
+        sincos(va[i], &sn[i], &cs[i]);
+        iv[i] = 1.0 / vm[i];
+    }
+    bool rotated = false;
+    auto exact_check = [&](int which) {
+        if (rotated)
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) sincos(va[i], &sn[i], &cs[i]);
+        rotated = false;
+        return cl_mismatch<C>(a, rank, which, xbase, red, true);
+    };
+    // a step is followed by a cluster barrier (it read or feeds other CTAs'
+    // words) or by the CTA's own barrier (a level of its own subtrees); every
+    // CTA has the same number of cluster barriers
+    auto solve = [&](int w) {
+        const int ns = nsteps[w];
+        for (int s = 0; s < ns; s++) {
+            const int4 si = S[w].steps[s];
+            cl_step(S[w], si);
+            if (si.w) cl_barrier();
+            else __syncthreads();
+        }
+    };
+    // x of bus i after a solve of matrix w (owner << 16 | word, -1: none)
+    auto xval = [&](int w, int i) {
+        const int r = a.m[w].xref[i];
+        return r >= 0 ? ld_cl(xbase[w * C + (r >> 16)] + 8u * unsigned(r & 0xffff)) : 0.0;
+    };
+    if (status == PF_ERR_NOT_CONVERGED) {
+        for (int it = 0; it < a.max_iter; it++) {
+            mis = cl_mismatch<C>(a, rank, 0, xbase, red, false);
+            if (mis <= a.tol) mis = exact_check(0);
+            if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
+            if (mis <= a.tol) { status = PF_OK; break; }
+            solve(0);
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                if (a.m[0].xref[i] < 0) continue;
+                const double d = xval(0, i);
+                va[i] += d;
+                if (fabs(d) <= kRotMax) {
+                    double sd, cd;
+                    small_sincos(d, &sd, &cd);
+                    const double c0 = cs[i], s0 = sn[i];
+                    cs[i] = c0 * cd - s0 * sd;
+                    sn[i] = s0 * cd + c0 * sd;
+                } else {
+                    sincos(va[i], &sn[i], &cs[i]);
+                }
+            }
+            rotated = true;
+            iters++;
+            mis = cl_mismatch<C>(a, rank, 1, xbase, red, false);
+            if (mis <= a.tol) mis = exact_check(1);
+            if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
+            if (mis <= a.tol) { status = PF_OK; break; }
+            solve(1);
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                if (a.m[1].xref[i] < 0) continue;
+                vm[i] += xval(1, i);
+                iv[i] = 1.0 / vm[i];
+            }
+            iters++;
+        }
+        if (status == PF_ERR_NOT_CONVERGED) {
+            mis = exact_check(0);
+            if (mis <= a.tol) status = PF_OK;
+        }
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        a.res[0].status = status;
+        a.res[0].iters = iters;
+        a.res[0].ir_steps = 0;
+        a.res[0].method = PF_FDPF;
+        a.res[0].max_mismatch = mis;
+    }
+    // no CTA leaves while another may still read its shared memory
+    cl_barrier();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+
+size_t tail_inverse_smem(int nt, int ne, int depth_max) {
+    return sizeof(double) * (size_t(ne) + size_t(kTailInvWarps) * size_t(depth_max)) +
+           sizeof(int) * (size_t(ne) + 3 * size_t(nt) + 1);
+}
+
+cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0, const double *F1,
+                              double *W0, double *W1, cudaStream_t s) {
+    const ClMat *mm[2] = {&m0, &m1};
+    const double *FF[2] = {F0, F1};
+    double *WW[2] = {W0, W1};
+    for (int w = 0; w < 2; w++) {
+        const ClMat &m = *mm[w];
+        if (m.nt == 0) continue;
+        const size_t smem = tail_inverse_smem(m.nt, m.ntail_e, m.tdepth_max);
+        cudaError_t e = cudaFuncSetAttribute(k_tail_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_tail_inverse<<<(m.nt + kTailInvWarps - 1) / kTailInvWarps, kTailInvWarps * 32, smem, s>>>(m, FF[w], WW[w]);
+    }
+    const int nv = m0.nval > m1.nval ? m0.nval : m1.nval;
+    k_cl_values<<<dim3(unsigned((nv + 255) / 256), 2), 256, 0, s>>>(m0, m1, F0, F1, W0, W1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fdpf_cl(const DevNet &dn, const DevCases &dc, const ClMat &m0, const ClMat &m1,
+                           const int *fs0, const int *fs1, const pf_run_opts &o, double *vm, double *va,
+                           double *ef, double *iv, double *bmax, pf_case_result *res, size_t smem,
+                           cudaStream_t s) {
+    ClRun a;
+    a.dn = dn;
+    a.dc = dc;
+    a.m[0] = m0;
+    a.m[1] = m1;
+    a.fs0 = fs0;
+    a.fs1 = fs1;
+    a.tol = o.tol;
+    a.max_iter = o.max_iter;
+    a.flat = o.flat_start;
+    a.vm = vm;
+    a.va = va;
+    a.ef = ef;
+    a.iv = iv;
+    a.bmax = bmax;
+    a.res = res;
+    cudaError_t e = cudaFuncSetAttribute(k_fdpf_cl<kClCtas>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fdpf_cl<kClCtas>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClCtas);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fdpf_cl<kClCtas>, a);
+}
+
+// Whether a cluster of kClCtas CTAs with `smem` bytes each can be resident.
+bool fdpf_cl_fits(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_fdpf_cl<kClCtas>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fdpf_cl<kClCtas>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClCtas);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, k_fdpf_cl<kClCtas>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters >= 1;
+}
+
+}  // namespace gbpf

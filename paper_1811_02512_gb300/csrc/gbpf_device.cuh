@@ -657,16 +657,39 @@ __device__ __forceinline__ void small_sincos(double x, double *s, double *c) {
 // Current at bus i of one case: I_i = sum_k Y_ik V_k on the base admittance
 // matrix, minus the terms of the case's outaged branch (if any) at its end
 // buses; returns (Re I_i, Im I_i).  The injection is S_i = V_i conj(I_i):
-// P_i = e_i Re I_i + f_i Im I_i, Q_i = f_i Re I_i - e_i Im I_i.
+// P_i = e_i Re I_i + f_i Im I_i, Q_i = f_i Re I_i - e_i Im I_i.  Each
+// admittance entry costs four fused multiply-adds (GB300's FP64 rate makes
+// this loop the throughput floor of batches).
 __device__ __forceinline__ void bus_current(const DevNet &dn, int i, int outage,
                                             const double *e, const double *f, double &ir_out,
                                             double &ii_out) {
     double ir = 0.0, ii = 0.0;
-    for (int p = dn.rowptr[i]; p < dn.rowptr[i + 1]; p++) {
-        const int k = dn.col[p];
-        const double g = dn.G[p], b = dn.B[p];
-        ir += g * e[k] - b * f[k];
-        ii += g * f[k] + b * e[k];
+    // four entries at a time: all their loads are issued before the first
+    // multiply-add waits, so a row costs one memory latency per four entries
+    // (the row's order of operations is the same as one at a time)
+    const int pe = dn.rowptr[i + 1];
+    for (int p = dn.rowptr[i]; p < pe; p += 4) {
+        int k[4];
+        double g[4], b[4], ek[4], fk[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            k[u] = p + u < pe ? dn.col[p + u] : i;
+            g[u] = p + u < pe ? dn.G[p + u] : 0.0;
+            b[u] = p + u < pe ? dn.B[p + u] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            ek[u] = e[k[u]];
+            fk[u] = f[k[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (p + u >= pe) break;
+            ir = fma(g[u], ek[u], ir);
+            ir = fma(-b[u], fk[u], ir);
+            ii = fma(g[u], fk[u], ii);
+            ii = fma(b[u], ek[u], ii);
+        }
     }
     if (outage >= 0 && dn.bstatus[outage] && (i == dn.bf[outage] || i == dn.bt[outage])) {
         const double r = dn.br[outage], x = dn.bx[outage], bc = dn.bb[outage], t = dn.btap[outage];

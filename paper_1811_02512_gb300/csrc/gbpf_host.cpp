@@ -702,12 +702,336 @@ pf_status analyze_matrix(pf_ctx *ctx, int which, HostMat &H) {
     return build_layout(ctx, H);
 }
 
+// Program of the cluster engine for matrix `which` (see ClMat).  The
+// elimination forest is cut into a top set T, closed under taking parents
+// (it starts as the narrow tail of the tree), and the subtrees hanging below
+// it.  Each subtree belongs wholly to one CTA, so its levels need only the
+// CTA's own barrier and read only the CTA's own vector words; subtrees go to
+// the least-loaded CTA, largest first, after the root of any subtree heavier
+// than half a CTA's share has been moved into T (its children become
+// subtrees).  Weight of a row: entries of its row and of its column of L,
+// plus one.  T is solved through the inverse of its block of L (three
+// cluster-wide steps); its rows go to the least-loaded CTA, heaviest first.
+// A CTA's steps: its forward subtree levels (leaves have no entries), a
+// cluster barrier, T's c = b - L_TB z_B, z = W c and x = W^T D^-1 z (each
+// ending with a cluster barrier), its backward subtree levels, and a final
+// cluster barrier.  Lanes per task: the smallest power of two that leaves at
+// most four entries to a lane (at most 32).  A top set too large for the
+// inverse leaves the program unusable (ok = 0).  Host only.
+pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P) {
+    const HostMat &H = ctx->hm[which];
+    const int C = kClCtas, n = H.n, nbus = ctx->nbus;
+    P = HostCl();
+    P.rhsref.assign(nbus, -1);
+    P.xref.assign(nbus, -1);
+    P.tptr.assign(C + 1, 0);
+    P.eptr.assign(C + 1, 0);
+    P.vptr.assign(C + 1, 0);
+    P.sptr.assign(C + 1, 0);
+    if (n == 0) {
+        P.ok = 1;
+        P.tasks.assign(C, int4{0, 0, -1, 0});
+        for (int r = 0; r <= C; r++) P.tptr[r] = r;
+        P.max_tasks = 1;
+        P.steps.push_back(int4{0, 0, 1, 0});
+        P.refs.push_back(0);
+        P.vsrc.push_back(int4{0, 0, 0, 0});
+        return PF_OK;
+    }
+    auto rowlen = [&](int i) { return H.Fp[i + 1] - H.Fp[i]; };
+    auto collen = [&](int i) { return H.Cp[i + 1] - H.Cp[i]; };
+    std::vector<int> par(n);
+    std::vector<std::vector<int>> kids(n);
+    for (int j = 0; j < n; j++) {
+        par[j] = collen(j) > 0 ? H.Cr[H.Cp[j]] : -1;
+        if (par[j] >= 0) kids[par[j]].push_back(j);
+    }
+    std::vector<int64_t> sw(n);
+    for (int j = 0; j < n; j++) sw[j] = rowlen(j) + collen(j) + 1;
+    for (int j = 0; j < n; j++)
+        if (par[j] >= 0) sw[par[j]] += sw[j];  // children come first in level order
+    // top set: the narrow tail, then split roots
+    std::vector<char> inT(n, 0);
+    if (H.nt > 0)
+        for (int i = H.t0; i < n; i++) inT[i] = 1;
+    int64_t total = 0;
+    for (int j = 0; j < n; j++)
+        if (!inT[j]) total += rowlen(j) + collen(j) + 1;
+    const int64_t share = (total + C - 1) / C;
+    std::vector<int> roots;
+    for (int j = 0; j < n; j++)
+        if (!inT[j] && (par[j] < 0 || inT[par[j]])) roots.push_back(j);
+    auto heavier = [&](int x, int y) { return sw[x] != sw[y] ? sw[x] < sw[y] : x > y; };
+    std::make_heap(roots.begin(), roots.end(), heavier);
+    while (!roots.empty() && 2 * sw[roots.front()] > share) {
+        std::pop_heap(roots.begin(), roots.end(), heavier);
+        const int r0 = roots.back();
+        roots.pop_back();
+        inT[r0] = 1;
+        for (int c : kids[r0]) {
+            roots.push_back(c);
+            std::push_heap(roots.begin(), roots.end(), heavier);
+        }
+    }
+    std::vector<int> &tnode = P.tnode;
+    std::vector<int> trel(n, -1);
+    for (int i = 0; i < n; i++)
+        if (inT[i]) {
+            trel[i] = int(tnode.size());
+            tnode.push_back(i);
+        }
+    const int nt = int(tnode.size());
+    P.nt = nt;
+    // owners: subtrees by weight to the least-loaded CTA, T rows likewise
+    std::vector<int> owner(n, 0);
+    std::vector<int64_t> load(C, 0);
+    std::sort(roots.begin(), roots.end(), [&](int x, int y) { return sw[x] != sw[y] ? sw[x] > sw[y] : x < y; });
+    for (int r0 : roots) {
+        const int r = int(std::min_element(load.begin(), load.end()) - load.begin());
+        owner[r0] = r;
+        load[r] += sw[r0];
+    }
+    for (int j = n - 1; j >= 0; j--)
+        if (!inT[j] && par[j] >= 0 && !inT[par[j]]) owner[j] = owner[par[j]];
+    P.bottom_load_max = *std::max_element(load.begin(), load.end());
+    P.bottom_load_avg = total / C;
+    // T: parents, the pattern of W = L_TT^-1 (it an ancestor of jt) by row and
+    // by column, depths, and the columns of L_TT
+    std::vector<std::vector<int>> wrow(nt), wcol(nt);
+    if (nt > 0) {
+        P.tpar.assign(nt, -1);
+        for (int jt = 0; jt < nt; jt++) {
+            const int pj = par[tnode[jt]];
+            P.tpar[jt] = pj >= 0 ? trel[pj] : -1;
+            if (pj >= 0 && (P.tpar[jt] < 0 || P.tpar[jt] <= jt)) return fail(ctx, PF_ERR_ARG, "internal: top set");
+        }
+        for (int jt = 0; jt < nt; jt++)
+            for (int it = P.tpar[jt]; it >= 0; it = P.tpar[it]) {
+                wrow[it].push_back(jt);
+                wcol[jt].push_back(it);
+            }
+        for (auto &v : wrow) std::sort(v.begin(), v.end());
+        P.tdepth.assign(nt, 0);
+        for (int jt = nt - 1; jt >= 0; jt--)  // parents come after their children
+            if (P.tpar[jt] >= 0) P.tdepth[jt] = P.tdepth[P.tpar[jt]] + 1;
+        P.tdepth_max = 1 + *std::max_element(P.tdepth.begin(), P.tdepth.end());
+        P.tcp.assign(nt + 1, 0);
+        for (int jt = 0; jt < nt; jt++) {
+            const int j = tnode[jt];
+            for (int p = H.Cp[j]; p < H.Cp[j + 1]; p++) {
+                if (!inT[H.Cr[p]]) return fail(ctx, PF_ERR_ARG, "internal: top set column");
+                P.tcdep.push_back(P.tdepth[trel[H.Cr[p]]]);
+                P.tcpos.push_back(H.offLc + p);
+            }
+            P.tcp[jt + 1] = int(P.tcdep.size());
+        }
+        if (P.tcdep.empty()) {
+            P.tcdep.push_back(0);
+            P.tcpos.push_back(0);
+        }
+        if (nt > kClTailMax || tail_inverse_smem(nt, P.tcp[nt], P.tdepth_max) > kTailInvSmem) return PF_OK;
+        std::vector<int> ord(nt);
+        std::vector<int64_t> wt(nt);
+        for (int it = 0; it < nt; it++) {
+            const int i = tnode[it];
+            int below = 0;
+            for (int q = H.Fp[i]; q < H.Fp[i + 1]; q++) below += !inT[H.Fc[q]];
+            wt[it] = below + int64_t(wrow[it].size()) + int64_t(wcol[it].size()) + collen(i) + 1;
+            ord[it] = it;
+        }
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return wt[x] > wt[y]; });
+        std::vector<int64_t> tl(C, 0);
+        for (int it : ord) {
+            const int r = int(std::min_element(tl.begin(), tl.end()) - tl.begin());
+            owner[tnode[it]] = r;
+            tl[r] += wt[it];
+        }
+    }
+    // vector words: xb for every row, then tc and tx for T rows
+    std::vector<int> cnt(C, 0), xw(n, 0), tcw(std::max(1, nt), 0), txw(std::max(1, nt), 0);
+    for (int i = 0; i < n; i++) xw[i] = cnt[owner[i]]++;
+    for (int it = 0; it < nt; it++) {
+        tcw[it] = cnt[owner[tnode[it]]]++;
+        txw[it] = cnt[owner[tnode[it]]]++;
+    }
+    P.nx = *std::max_element(cnt.begin(), cnt.end());
+    if (P.nx > 65535) return PF_OK;
+    auto ref_xb = [&](int i) { return (owner[i] << 16) | xw[i]; };
+    auto ref_tc = [&](int i) { return (owner[i] << 16) | tcw[trel[i]]; };
+    auto ref_tx = [&](int i) { return (owner[i] << 16) | txw[trel[i]]; };
+    for (int i = 0; i < n; i++) {
+        P.rhsref[H.bus_new[i]] = ref_xb(i);
+        P.xref[H.bus_new[i]] = inT[i] ? ref_tx(i) : ref_xb(i);
+    }
+    // per CTA: its bottom rows by level
+    std::vector<std::vector<std::vector<int>>> mine(C, std::vector<std::vector<int>>(H.nlev));
+    {
+        std::vector<int> lev(n, 0);
+        for (int l = 0; l < H.nlev; l++)
+            for (int i = H.lvl_ptr[l]; i < H.lvl_ptr[l + 1]; i++) lev[i] = l;
+        for (int i = 0; i < n; i++)
+            if (!inT[i]) mine[owner[i]][lev[i]].push_back(i);
+    }
+    for (int r = 0; r < C; r++) {
+        std::vector<int4> tasks, steps;
+        std::vector<int> refs;
+        std::vector<int4> esrc, dsrc;
+        std::vector<int> dtask;  // tasks whose diagonal index needs the final entry count
+        int maxlen = 0;
+        auto add = [&](int out, int in, int dsrcpos) {
+            tasks.push_back(int4{out, in, -1, int(refs.size())});
+            if (dsrcpos >= 0) {
+                tasks.back().z = int(dsrc.size());
+                dtask.push_back(int(tasks.size()) - 1);
+                dsrc.push_back(int4{0, dsrcpos, 0, 0});
+            }
+        };
+        auto close = [&]() { maxlen = std::max(maxlen, int(refs.size()) - tasks.back().w); };
+        // a step over the tasks added since tb; cluster = 1: a cluster barrier follows
+        auto step = [&](int tb, int cluster) {
+            int G = 1;
+            while (G < 32 && maxlen > 4 * G) G *= 2;
+            steps.push_back(int4{tb, int(tasks.size()), G, cluster});
+            maxlen = 0;
+        };
+        for (int l = 1; l < H.nlev; l++) {  // forward subtree levels
+            const int tb = int(tasks.size());
+            for (int i : mine[r][l]) {
+                if (rowlen(i) == 0) continue;
+                add(xw[i], xw[i], -1);
+                for (int q = H.Fp[i]; q < H.Fp[i + 1]; q++) {
+                    refs.push_back(ref_xb(H.Fc[q]));
+                    esrc.push_back(int4{0, H.offLr + q, 0, 0});
+                }
+                close();
+            }
+            if (int(tasks.size()) > tb) step(tb, 0);
+        }
+        step(int(tasks.size()), 1);
+        if (nt > 0) {
+            for (int kind = 1; kind <= 3; kind++) {
+                const int tb = int(tasks.size());
+                for (int it = 0; it < nt; it++) {
+                    const int i = tnode[it];
+                    if (owner[i] != r) continue;
+                    if (kind == 1) {  // c = b - L_TB z_B
+                        add(tcw[it], xw[i], -1);
+                        for (int q = H.Fp[i]; q < H.Fp[i + 1]; q++)
+                            if (!inT[H.Fc[q]]) {
+                                refs.push_back(ref_xb(H.Fc[q]));
+                                esrc.push_back(int4{0, H.offLr + q, 0, 0});
+                            }
+                    } else if (kind == 2) {  // z = W c
+                        add(xw[i], tcw[it], -1);
+                        for (int jt : wrow[it]) {
+                            refs.push_back(ref_tc(tnode[jt]));
+                            esrc.push_back(int4{1, it * nt + jt, 0, 0});
+                        }
+                    } else {  // x = W^T D^-1 z
+                        add(txw[it], xw[i], H.offDi + i);
+                        for (int at : wcol[it]) {
+                            refs.push_back(ref_xb(tnode[at]));
+                            esrc.push_back(int4{2, at * nt + it, H.offDi + tnode[at], 0});
+                        }
+                    }
+                    close();
+                }
+                step(tb, 1);
+            }
+        }
+        for (int l = H.nlev - 1; l >= 0; l--) {  // backward subtree levels
+            const int tb = int(tasks.size());
+            for (int i : mine[r][l]) {
+                add(xw[i], xw[i], H.offDi + i);
+                for (int p = H.Cp[i]; p < H.Cp[i + 1]; p++) {
+                    const int k = H.Cr[p];
+                    refs.push_back(inT[k] ? ref_tx(k) : ref_xb(k));
+                    esrc.push_back(int4{0, H.offLc + p, 0, 0});
+                }
+                close();
+            }
+            if (int(tasks.size()) > tb) step(tb, 0);
+        }
+        step(int(tasks.size()), 1);
+        const int ne = int(refs.size());
+        for (int t : dtask) tasks[t].z += ne;
+        tasks.push_back(int4{0, 0, -1, ne});  // sentinel
+        P.tptr[r + 1] = P.tptr[r] + int(tasks.size());
+        P.eptr[r + 1] = P.eptr[r] + ne;
+        P.vptr[r + 1] = P.vptr[r] + ne + int(dsrc.size());
+        P.sptr[r + 1] = P.sptr[r] + int(steps.size());
+        P.tasks.insert(P.tasks.end(), tasks.begin(), tasks.end());
+        P.steps.insert(P.steps.end(), steps.begin(), steps.end());
+        P.refs.insert(P.refs.end(), refs.begin(), refs.end());
+        P.vsrc.insert(P.vsrc.end(), esrc.begin(), esrc.end());
+        P.vsrc.insert(P.vsrc.end(), dsrc.begin(), dsrc.end());
+        P.max_tasks = std::max(P.max_tasks, tasks.size());
+        P.max_steps = std::max(P.max_steps, steps.size());
+        P.max_e = std::max(P.max_e, size_t(ne));
+        P.max_v = std::max(P.max_v, size_t(ne) + dsrc.size());
+    }
+    if (P.refs.empty()) P.refs.push_back(0);
+    if (P.vsrc.empty()) P.vsrc.push_back(int4{0, 0, 0, 0});
+    P.ok = 1;
+    return PF_OK;
+}
+
+// Dynamic shared memory of the cluster engine's CTA for both matrices'
+// programs, and the byte offsets of their regions (16-byte aligned).
+size_t cluster_smem_layout(pf_ctx *ctx) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 15) / 16 * 16;
+        return int(o);
+    };
+    for (int w = 0; w < 2; w++) {
+        const HostCl &P = ctx->hcl[w];
+        ClMat &M = ctx->cl[w];
+        M.so_x = take(sizeof(double) * std::max(1, P.nx));
+        M.so_tasks = take(sizeof(int4) * std::max<size_t>(1, P.max_tasks));
+        M.so_steps = take(sizeof(int4) * std::max<size_t>(1, P.max_steps));
+        M.so_addr = take(sizeof(uint32_t) * std::max<size_t>(1, P.max_e));
+        M.so_vals = take(sizeof(double) * std::max<size_t>(1, P.max_v));
+    }
+    return off;
+}
+
 // Uploads an int array padded by 16 bytes so that 16-byte-rounded bulk
 // copies of its tail stay inside the allocation.
 pf_status upload_padded(pf_ctx *ctx, int **dst, const std::vector<int> &v) {
     std::vector<int> tmp(v);
     tmp.resize(v.size() + 8, 0);
     return upload(ctx, dst, tmp.data(), tmp.size());
+}
+
+pf_status upload_cluster(pf_ctx *ctx, int w) {
+    const HostCl &P = ctx->hcl[w];
+    ClMat &M = ctx->cl[w];
+    M.nt = P.nt;
+    M.nval = int(P.vsrc.size());
+    if (P.nt > 0) {
+        TRY(upload_padded(ctx, &M.tpar, P.tpar));
+        TRY(upload_padded(ctx, &M.tcp, P.tcp));
+        TRY(upload_padded(ctx, &M.tcdep, P.tcdep));
+        TRY(upload_padded(ctx, &M.tcpos, P.tcpos));
+        TRY(upload_padded(ctx, &M.tdepth, P.tdepth));
+        M.ntail_e = P.tcp[P.nt];
+        M.tdepth_max = P.tdepth_max;
+        TRY(dalloc(ctx, &ctx->clW[w], size_t(P.nt) * size_t(P.nt)));
+    }
+    TRY(upload(ctx, &M.vsrc, P.vsrc.data(), P.vsrc.size()));
+    TRY(dalloc(ctx, &M.vals, P.vsrc.size()));
+    TRY(upload(ctx, &M.tasks, P.tasks.data(), P.tasks.size()));
+    TRY(upload_padded(ctx, &M.tptr, P.tptr));
+    TRY(upload(ctx, &M.steps, P.steps.data(), P.steps.size()));
+    TRY(upload_padded(ctx, &M.sptr, P.sptr));
+    TRY(upload_padded(ctx, &M.refs, P.refs));
+    TRY(upload_padded(ctx, &M.eptr, P.eptr));
+    TRY(upload_padded(ctx, &M.vptr, P.vptr));
+    TRY(upload_padded(ctx, &M.rhsref, P.rhsref));
+    TRY(upload_padded(ctx, &M.xref, P.xref));
+    return PF_OK;
 }
 
 pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
@@ -1199,6 +1523,23 @@ NrLaunch nr_launch(pf_ctx *ctx, int prec) {
     return L;
 }
 
+// Whether a run can use the cluster engine: FDPF in FP64 on one case of the
+// base network (no outage instance), with both programs fitting one CTA's
+// shared memory and a 16-block cluster resident.
+bool cluster_applies(pf_ctx *ctx, const pf_run_opts *o) {
+    if (o->method != PF_FDPF || o->precision != PF_FP64 || ctx->dc.ncase != 1 || ctx->dc.ninst != 1)
+        return false;
+    if (!ctx->hcl[0].ok || !ctx->hcl[1].ok) return false;
+    if (ctx->cl_smem + 4096 > ctx->smem_optin || ctx->num_sms < kClCtas) return false;
+    return fdpf_cl_fits(ctx->cl_smem);
+}
+
+pf_status ensure_cluster(pf_ctx *ctx) {
+    if (ctx->cl[0].tasks) return PF_OK;
+    for (int w = 0; w < 2; w++) TRY(upload_cluster(ctx, w));
+    return PF_OK;
+}
+
 // Epochs for the Jacobian factorisations of one NR or adjoint launch (at
 // most `count`); the flags are cleared when the counter would wrap.
 unsigned nr_epochs(pf_ctx *ctx, unsigned count, cudaStream_t s) {
@@ -1328,6 +1669,8 @@ pf_status pf_analyze(pf_ctx *ctx, pf_symbolic_info *info) {
             TRY(analyze_matrix(ctx, w, ctx->hm[w]));
             if (ctx->on_device) TRY(upload_matrix(ctx, ctx->hm[w], ctx->dm[w]));
         }
+        for (int w = 0; w < 2; w++) TRY(build_cluster(ctx, w, ctx->hcl[w]));
+        ctx->cl_smem = cluster_smem_layout(ctx);
         ctx->analyzed = true;
     }
     auto t1 = std::chrono::steady_clock::now();
@@ -1604,6 +1947,28 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
     const int nmax = std::max(ctx->dm[0].n, ctx->dm[1].n);
     const bool lanes_ok = opts->method == PF_FDPF && lane_width(nmax, prec, ctx->smem_optin) > 0;
     const int want = opts->engine != PF_ENGINE_AUTO ? opts->engine : ctx->tune.engine;
+    if (want == PF_ENGINE_CLUSTER && cluster_applies(ctx, opts)) {
+        TRY(ensure_cluster(ctx));
+        TRY(factor_both(ctx, prec, s, false));
+        Workspace &wc = ctx->ws;
+        cudaError_t e = counted(ctx, PF_K_FACTOR, 1, s, [&] {
+            return launch_cl_prepare(ctx->cl[0], ctx->cl[1], wc.F64[0], wc.F64[1], ctx->clW[0], ctx->clW[1], s);
+        });
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster prepare");
+        e = counted(ctx, PF_K_RUN, 1, s, [&] {
+            return launch_fdpf_cl(ctx->dn, ctx->dc, ctx->cl[0], ctx->cl[1], wc.fstatus[0][prec],
+                                  wc.fstatus[1][prec], *opts, vm_dev, va_dev, wc.ef, wc.iv, wc.bmax, wc.res,
+                                  ctx->cl_smem, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster fdpf launch");
+        e = cudaMemcpyAsync(res_host, wc.res, sizeof(pf_case_result), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster fdpf run");
+        if (res_host[0].status != PF_OK)
+            return fail(ctx, pf_status(res_host[0].status), "case 0: status %d after %d iterations",
+                        res_host[0].status, res_host[0].iters);
+        return PF_OK;
+    }
     const int engine = want == PF_ENGINE_LANES && lanes_ok ? PF_ENGINE_LANES : PF_ENGINE_BLOCK;
     const bool lowrank = engine == PF_ENGINE_BLOCK && ctx->tune.outage == 2 && ctx->dc.ninst > 1;
     TRY(factor_both(ctx, prec, s, lowrank));
@@ -1793,7 +2158,7 @@ pf_status pf_get_tuning(const pf_ctx *ctx, pf_tuning *out) {
 
 pf_status pf_set_tuning(pf_ctx *ctx, const pf_tuning *t) {
     if (!ctx || !t) return fail(ctx, PF_ERR_ARG, "null pointer");
-    if (t->engine < 0 || t->engine > PF_ENGINE_LANES || t->factor < 0 || t->factor > 2 || t->tail < 0 ||
+    if (t->engine < 0 || t->engine > PF_ENGINE_CLUSTER || t->factor < 0 || t->factor > 2 || t->tail < 0 ||
         t->tail > 2 || t->outage < 0 || t->outage > 2 ||
         (t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16))
         return fail(ctx, PF_ERR_ARG, "tuning field out of range");
@@ -1820,6 +2185,7 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     const int nmax = std::max(ctx->dm[0].n, ctx->dm[1].n);
     if (o.method == PF_FDPF && ncase >= 32 && lane_width(nmax, prec, ctx->smem_optin) > 0)
         engines.push_back(PF_ENGINE_LANES);
+    if (cluster_applies(ctx, &o)) engines.push_back(PF_ENGINE_CLUSTER);
     std::vector<int> clusters{0};
     if (o.method == PF_FDPF) {
         const int cmax = fdpf_cluster_size(ncase, ctx->num_sms, prec, ctx->smem_optin, nmax);
@@ -1833,11 +2199,13 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     if (o.method == PF_FDPF && (ctx->dm[0].npf2 > 0 || ctx->dm[1].npf2 > 0)) tails.push_back(1);
     std::vector<int> outages{1};
     if (o.method == PF_FDPF && ctx->dc.ninst > 1) outages.push_back(2);
+    // the lane engine has no cluster, tail or outage choice; the cluster
+    // engine no cluster size (its own) and no outage form (one base case)
     for (int e : engines)
-        for (int c : (e == PF_ENGINE_LANES ? std::vector<int>{0} : clusters))
+        for (int c : (e != PF_ENGINE_BLOCK ? std::vector<int>{0} : clusters))
             for (int f : factors)
                 for (int t : (e == PF_ENGINE_LANES ? std::vector<int>{0} : tails))
-                    for (int u : (e == PF_ENGINE_LANES ? std::vector<int>{1} : outages))
+                    for (int u : (e != PF_ENGINE_BLOCK ? std::vector<int>{1} : outages))
                         cand.push_back(pf_tuning{e, c, f, t, u, 0.0});
     std::vector<pf_case_result> res(static_cast<size_t>(ncase));
     cudaEvent_t a = nullptr, b = nullptr;
@@ -2185,6 +2553,46 @@ int gbpf_debug_gather(const pf_ctx *ctx, int which, long long *sizes, int *Cp, i
             const int4 e = H.gl[size_t(q)];
             gl[4 * q] = e.x, gl[4 * q + 1] = e.y, gl[4 * q + 2] = e.z, gl[4 * q + 3] = e.w;
         }
+    return 0;
+}
+
+// Test hook (host only, no GPU needed): the cluster engine's program of
+// matrix `which`.  sizes[12] receives {C, nt, steps (all CTAs), nx, tasks,
+// entries, values, dynamic shared memory of a CTA, offDi, offLc, offLr, ok};
+// the arrays are copied when cap (ints per array) covers them: tasks, steps
+// and vsrc (4 ints each), tptr, eptr, vptr, sptr (C + 1), refs, rhsref and
+// xref (nbus), tnode (nt: the level-order rows of the top set).  Returns 0, or -1 for a bad argument
+// or a context that has not been analysed.
+int gbpf_debug_cluster(const pf_ctx *ctx, int which, long long *sizes, int *tasks, int *tptr,
+                       int *steps, int *refs, int *eptr, int *vsrc, int *vptr, int *sptr, int *rhsref,
+                       int *xref, int *tnode, long long cap) {
+    if (!ctx || !sizes || which < 0 || which > 1 || !ctx->analyzed) return -1;
+    const gbpf::HostCl &P = ctx->hcl[which];
+    const gbpf::HostMat &H = ctx->hm[which];
+    const long long v[12] = {gbpf::kClCtas, P.nt, (long long)P.steps.size(), P.nx, (long long)P.tasks.size(),
+                             (long long)P.refs.size(), (long long)P.vsrc.size(), (long long)ctx->cl_smem,
+                             H.offDi, H.offLc, H.offLr, P.ok};
+    for (int i = 0; i < 12; i++) sizes[i] = v[i];
+    auto put4 = [&](const std::vector<int4> &a, int *dst) {
+        if (dst && cap >= 4 * (long long)a.size())
+            for (size_t i = 0; i < a.size(); i++) {
+                dst[4 * i] = a[i].x, dst[4 * i + 1] = a[i].y, dst[4 * i + 2] = a[i].z, dst[4 * i + 3] = a[i].w;
+            }
+    };
+    auto put = [&](const std::vector<int> &a, int *dst) {
+        if (dst && cap >= (long long)a.size()) std::copy(a.begin(), a.end(), dst);
+    };
+    put4(P.tasks, tasks);
+    put(P.tptr, tptr);
+    put4(P.steps, steps);
+    put(P.refs, refs);
+    put(P.eptr, eptr);
+    put4(P.vsrc, vsrc);
+    put(P.vptr, vptr);
+    put(P.sptr, sptr);
+    put(P.rhsref, rhsref);
+    put(P.xref, xref);
+    put(P.tnode, tnode);
     return 0;
 }
 

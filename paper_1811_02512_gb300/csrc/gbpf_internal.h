@@ -114,6 +114,64 @@ struct DevMat {
     int jD = 0, jDi = 0, jLc = 0, jUc = 0, jLr = 0, jUr = 0, jstride = 0;  // block layout (elements)
 };
 
+// Cluster-distributed substitution program of one matrix for the
+// single-case engine of gbpf_cluster.cu.  Every row of L (level order) has an
+// owner CTA among kClCtas; a CTA's shared memory holds a "vector region" of
+// words: its rows' entries of the solution (xb), and for its tail rows the
+// forward intermediate c (tc) and the backward result (tx).  A reference to a
+// word is owner << 16 | word.  The program of a CTA is a list of steps (one
+// per level of the elimination tree, three for the tail), each a range of
+// tasks {out word, in word, diagonal value index or -1, first entry}; a task
+// computes X[out] = (diag ? val[diag] X[in] : X[in]) - sum over its entries
+// of val[e] X(ref[e]).  Values are packed per CTA ([entries | diagonal
+// values]) and gathered after every factorisation from vsrc {kind, a, b}:
+// 0 the factor value F[a], 1 -W[a], 2 -W[a] F[b], W being the dense inverse
+// of the tail block of L by column (W[jt * nt + it]).
+constexpr int kClCtas = 16;
+constexpr int kClTailMax = 2048;   // largest tail whose dense inverse is formed
+constexpr int kTailInvWarps = 16;  // T columns (one per warp) per block of k_tail_inverse
+// shared memory of k_tail_inverse for a tail of nt rows with ne entries and
+// paths of at most depth_max nodes (a tail whose need exceeds kTailInvSmem
+// gets no inverse)
+size_t tail_inverse_smem(int nt, int ne, int depth_max);
+constexpr size_t kTailInvSmem = 160 * 1024;
+struct ClMat {
+    int nt = 0;                    // rows of the top set T with an inverse (0: none)
+    int *tpar = nullptr;           // [nt] T-relative parent, -1 at a root
+    int *tcp = nullptr;            // [nt + 1] columns of L_TT (all of a T column's rows are in T)
+    int *tcdep = nullptr;          // [ntail_e] depth of each entry's row
+    int *tcpos = nullptr;          // [ntail_e] factor position of each entry
+    int ntail_e = 0;
+    int *tdepth = nullptr;         // [nt] distance from its root
+    int tdepth_max = 0;            // longest path in T (nodes)
+    int nval = 0;
+    int4 *vsrc = nullptr;          // [nval] value sources
+    double *vals = nullptr;        // [nval] gathered values
+    int4 *tasks = nullptr;         // all CTAs' tasks, each CTA's ending in a sentinel
+    int *tptr = nullptr;           // [C + 1]
+    int4 *steps = nullptr;         // all CTAs' steps {first task, end task, lanes per task,
+                                   // 1: a cluster barrier follows (0: the CTA's own)}, CTA-relative
+    int *sptr = nullptr;           // [C + 1]
+    int *refs = nullptr, *eptr = nullptr;  // entry references, [C + 1]
+    int *vptr = nullptr;           // [C + 1] value blocks
+    int *rhsref = nullptr;         // [nbus] word of the bus's right-hand side, -1: not in the matrix
+    int *xref = nullptr;           // [nbus] word of the bus's solution, -1: not in the matrix
+    // byte offsets of the CTA's regions in dynamic shared memory
+    int so_x = 0, so_tasks = 0, so_steps = 0, so_addr = 0, so_vals = 0;
+};
+
+// Host form of a ClMat.
+struct HostCl {
+    int ok = 0;                    // the program fits (top set small enough for its inverse)
+    int nt = 0, nx = 0, tdepth_max = 0;
+    std::vector<int> tnode;        // level-order rows of the top set, ascending
+    std::vector<int> tpar, tcp, tcdep, tcpos, tdepth;
+    std::vector<int4> vsrc, tasks, steps;
+    std::vector<int> tptr, refs, eptr, vptr, sptr, rhsref, xref;
+    size_t max_tasks = 0, max_steps = 0, max_e = 0, max_v = 0;  // per CTA (tasks with the sentinel)
+    int64_t bottom_load_max = 0, bottom_load_avg = 0;          // subtree weight per CTA
+};
+
 // Host copy of the symbolic data of one matrix.  Step numbering (the
 // minimum-degree elimination order) for the published symbolic result;
 // level order for the device layout.
@@ -281,6 +339,12 @@ struct pf_ctx {
     std::string err;
     std::vector<void *> allocations;  // everything owned by the context
     pf_tuning tune = {0, 0, 0, 0, 0, 0.0};  // kernel mappings (pf_autotune / pf_set_tuning)
+    // programs of the cluster engine (host, device), their tail-inverse
+    // scratch and the dynamic shared memory of one CTA
+    gbpf::HostCl hcl[2];
+    gbpf::ClMat cl[2];
+    double *clW[2] = {nullptr, nullptr};
+    size_t cl_smem = 0;
 };
 
 namespace gbpf {
@@ -421,6 +485,18 @@ struct LaneRun {
 };
 cudaError_t lane_run(const LaneRun &r, cudaStream_t s);
 int lane_width(int nmax, int prec, size_t smem_optin);
+
+// Single-case engine with the substitutions spread over a cluster
+// (gbpf_cluster.cu): the tail inverses and packed values of both matrices
+// after a factorisation (W0/W1: nt^2 doubles of scratch each), and the
+// iteration kernel (smem: dynamic shared memory of one CTA).
+cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0, const double *F1,
+                              double *W0, double *W1, cudaStream_t s);
+cudaError_t launch_fdpf_cl(const DevNet &dn, const DevCases &dc, const ClMat &m0, const ClMat &m1,
+                           const int *fs0, const int *fs1, const pf_run_opts &o, double *vm, double *va,
+                           double *ef, double *iv, double *bmax, pf_case_result *res, size_t smem,
+                           cudaStream_t s);
+bool fdpf_cl_fits(size_t smem);
 
 cudaError_t launch_objective(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
                              double *ef, double *J, double *gva, double *gvm, cudaStream_t s);

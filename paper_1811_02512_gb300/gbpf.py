@@ -222,7 +222,7 @@ def pf_mismatch(ctx, vm_dev, va_dev, dp_dev, dq_dev, maxmis_dev, ncase, stream=N
                                    _ptr(maxmis_dev), int(ncase), _stream(stream)), "pf_mismatch")
 
 
-PF_ENGINE_AUTO, PF_ENGINE_BLOCK, PF_ENGINE_LANES = 0, 1, 2
+PF_ENGINE_AUTO, PF_ENGINE_BLOCK, PF_ENGINE_LANES, PF_ENGINE_CLUSTER = 0, 1, 2, 3
 
 
 def run_opts(method=PF_FDPF, precision=PF_FP64, tol=1e-8, max_iter=None, ir_max=5, ir_tol=1e-10,

@@ -549,3 +549,130 @@ def test_pack_create_validates(lib):
     assert lib.pf_pack_create(arr, 1, C.byref(h)) == gbpf.PF_OK
     lib.pf_pack_destroy(h)
     gbpf.pf_destroy(ctx)
+
+
+def _cluster_program(lib, g, which):
+    f = lib.gbpf_debug_cluster
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 12 + [C.c_longlong]
+    sz = np.zeros(12, np.int64)
+    assert f(g.ctx, which, sz.ctypes.data, *([None] * 11), 0) == 0
+    Cc, nt, nstep, nx, ntask, nref, nval = (int(v) for v in sz[:7])
+    cap = max(4 * ntask, 4 * nval, 4 * nstep, nref, g.nbus, nt, Cc + 1, 1)
+    arrs = [np.zeros(cap, np.int32) for _ in range(11)]
+    assert f(g.ctx, which, sz.ctypes.data, *(a.ctypes.data for a in arrs), cap) == 0
+    tasks, tptr, steps, refs, eptr, vsrc, vptr, sptr, rhsref, xref, tnode = arrs
+    return dict(C=Cc, nt=nt, nx=nx, smem=int(sz[7]), offDi=int(sz[8]), offLc=int(sz[9]),
+                offLr=int(sz[10]), ok=int(sz[11]),
+                tasks=tasks[:4 * ntask].reshape(-1, 4), tptr=tptr[:Cc + 1],
+                steps=steps[:4 * nstep].reshape(-1, 4), sptr=sptr[:Cc + 1], refs=refs[:nref],
+                eptr=eptr[:Cc + 1], vsrc=vsrc[:4 * nval].reshape(-1, 4), vptr=vptr[:Cc + 1],
+                rhsref=rhsref[:g.nbus], xref=xref[:g.nbus], tnode=tnode[:nt])
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_cluster_program_solves_like_oracle(lib, oracle, cfg):
+    """The cluster engine's substitution program, run on the CPU with the
+    device's synchronisation: the oracle's factor is placed in the library's
+    level-order layout and the top set's inverse is formed densely from it.
+    Between two cluster barriers a CTA runs its steps in order; a step reads
+    its own CTA's words as they stood before the step and every other CTA's
+    words as they stood at the last cluster barrier, so a dependence that the
+    barriers do not cover would read a stale value.  The result equals the
+    oracle's LDL^T solve; the top set is closed under parents, every CTA
+    passes the same number of cluster barriers, every index stays inside its
+    buffer, and the programs of the 10,000-bus grid fit one CTA's shared
+    memory."""
+    import scipy.sparse as sp
+    case = gridgen.config(cfg)
+    g = gbpf.Grid(case)
+    rng = np.random.default_rng(7 + cfg)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        P = _cluster_program(lib, g, which)
+        assert P["ok"] == 1
+        an, Lx, d, _ = oracle.factor_bmatrix(case, name)
+        n = an["buses"].shape[0]
+        lev = an["level"]
+        order = np.lexsort((np.arange(n), lev))  # level order: (level, step)
+        new = np.empty(n, np.int64)
+        new[order] = np.arange(n)
+        cols = np.repeat(np.arange(n), np.diff(an["Lp"]))
+        L = sp.csc_matrix((Lx, (new[an["Li"]], new[cols])), shape=(n, n))
+        L.sort_indices()
+        dl = np.empty(n)
+        dl[new] = d
+        nnz = L.nnz
+        F = np.zeros(P["offLr"] + nnz + 64)
+        F[:n] = dl
+        F[P["offDi"]:P["offDi"] + n] = 1.0 / dl
+        F[P["offLc"]:P["offLc"] + nnz] = L.data
+        Lr = L.tocsr()
+        Lr.sort_indices()
+        F[P["offLr"]:P["offLr"] + nnz] = Lr.data
+        nt, T = P["nt"], P["tnode"]
+        Wd = np.zeros(max(1, nt * nt))
+        if nt:
+            inT = np.zeros(n, bool)
+            inT[T] = True
+            parent = np.array([L[:, j].indices[0] if L.indptr[j + 1] > L.indptr[j] else -1 for j in range(n)])
+            assert np.all((parent[T] < 0) | inT[np.maximum(parent[T], 0)])  # closed under parents
+            W = np.linalg.inv(L[T][:, T].toarray() + np.eye(nt))
+            Wd = W.flatten()  # W(it, jt) at it * nt + jt
+        vs = P["vsrc"]
+        vals = np.empty(vs.shape[0])
+        k0, k1, k2 = vs[:, 0] == 0, vs[:, 0] == 1, vs[:, 0] == 2
+        assert np.all(k0 | k1 | k2)
+        assert np.all(vs[k0, 1] < P["offLr"] + nnz) and np.all(vs[k1 | k2, 1] < max(1, nt * nt))
+        vals[k0] = F[vs[k0, 1]]
+        vals[k1] = -Wd[vs[k1, 1]]
+        vals[k2] = -Wd[vs[k2, 1]] * F[vs[k2, 2]]
+        Cc, nx = P["C"], P["nx"]
+        # every index the device program uses stays inside its buffers
+        assert np.all((P["refs"] >> 16) < Cc) and np.all((P["refs"] & 0xffff) < max(1, nx))
+        prog = []
+        for r in range(Cc):
+            T_ = P["tasks"][P["tptr"][r]:P["tptr"][r + 1]]
+            S_ = P["steps"][P["sptr"][r]:P["sptr"][r + 1]]
+            ne = P["eptr"][r + 1] - P["eptr"][r]
+            nv = P["vptr"][r + 1] - P["vptr"][r]
+            assert T_[-1][3] == ne and np.all(np.diff(T_[:, 3]) >= 0)
+            assert np.all(T_[:-1, 0] < nx) and np.all(T_[:-1, 1] < nx) and np.all(T_[:-1, 2] < nv)
+            assert np.all(S_[:, 0] <= S_[:, 1]) and np.all(S_[:, 1] <= T_.shape[0] - 1)
+            assert np.all(S_[1:, 0] == S_[:-1, 1]) and np.all(np.isin(S_[:, 2], [1, 2, 4, 8, 16, 32]))
+            prog.append((T_, S_, P["refs"][P["eptr"][r]:P["eptr"][r + 1]], vals[P["vptr"][r]:P["vptr"][r + 1]]))
+        nbar = {int(np.sum(p[1][:, 3])) for p in prog}
+        assert len(nbar) == 1
+        b_loc = rng.standard_normal(n)
+        X = np.zeros((Cc, max(1, nx)))
+        rr = P["rhsref"][an["buses"]]
+        assert np.all(rr >= 0) and np.all(P["rhsref"][np.setdiff1d(np.arange(g.nbus), an["buses"])] == -1)
+        X[rr >> 16, rr & 0xffff] = b_loc
+        pos = [0] * Cc
+        for _ in range(nbar.pop()):
+            snapC = X.copy()
+            for r in range(Cc):
+                T_, S_, R, V = prog[r]
+                while True:
+                    tb, te, G, cl = S_[pos[r]]
+                    pos[r] += 1
+                    snapR = X[r].copy()
+                    for t in range(tb, te):
+                        out, inn, dg, e0 = T_[t]
+                        e1 = T_[t + 1][3]
+                        rf = R[e0:e1]
+                        o, w = rf >> 16, rf & 0xffff
+                        xs = np.where(o == r, snapR[w], snapC[o, w])
+                        X[r, out] = snapR[inn] * (V[dg] if dg >= 0 else 1.0) - np.dot(V[e0:e1], xs)
+                    if cl:
+                        break
+        assert all(pos[r] == prog[r][1].shape[0] for r in range(Cc))
+        xr = P["xref"][an["buses"]]
+        assert np.all(xr >= 0)
+        x = X[xr >> 16, xr & 0xffff]
+        xs = oracle.lu_solve(n, an["Lp"], an["Li"], Lx, Lx * d[cols], d, b_loc[an["perm"]])
+        ref = np.empty(n)
+        ref[an["perm"]] = xs
+        assert np.max(np.abs(x - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref))), (name, np.max(np.abs(x - ref)))
+        if cfg == 1:
+            assert P["smem"] + 4096 <= 232448, P["smem"]
+    g.close()
