@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--mapping", default=None,
                     help="engine,cluster,factor,tail,outage: set this kernel mapping instead of tuning")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
+    ap.add_argument("--ir-tol", type=float, default=None,
+                    help="FP32 runs: relative residual at which a linear solve needs no further "
+                         "refinement (default 1e-6: an inexact-Newton forcing term far below the "
+                         "fast decoupled iteration's own contraction)")
     return ap.parse_args()
 
 
@@ -160,26 +164,68 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline model
 
-def algorithmic_bytes_per_half_iteration(info, nbus, nnz_y, prec_bytes):
-    """Streaming bytes of one fast-decoupled half-iteration of one case:
-    mismatch (V, theta read, Y values + pattern read, rhs written) plus one
-    LDL^T solve pair (forward + backward: L values read twice, row/column
-    indices read once each, D read once, vector read and written)."""
+def matrix_offdiag(case, which):
+    """Off-diagonal entries of B' (which 0: non-slack buses) or B'' (1: PQ
+    buses) on the bus graph: twice the in-service branches joining two of
+    its buses (parallel branches counted once)."""
+    inm = case.btype != 3 if which == 0 else case.btype == 1
+    on = case.status != 0
+    pairs = {(min(f, t), max(f, t)) for f, t in zip(case.f[on], case.t[on]) if inm[f] and inm[t]}
+    return 2 * len(pairs)
+
+
+def hbm_bytes_per_launch(info, case, prec_bytes, half_iters, resid, n_outage_solves, ncase):
+    """Algorithmic DRAM bytes of one launch of the iteration kernel (the
+    streaming model): data every case shares -- the admittance matrix (values
+    and pattern) and both factors (L values read by the forward and by the
+    backward sweep, their indices, the inverse diagonal) -- counted once per
+    launch; per case and half-iteration only vectors: the mismatch reads V
+    and theta and writes the right-hand side (24 bytes per bus), a solve
+    reads and writes its vector (16 bytes per unknown), every FP64 residual
+    of a refined solve reads x and writes r (16 bytes per unknown), and every
+    solve of an outage case with the low-rank form reads its two columns
+    Z (2 n s bytes).  half_iters, resid and n_outage_solves are totals over
+    the launch's cases."""
+    nbus, nnz_y = case.n, info.nnz_ybus
+    shared = 20 * nnz_y + 4 * (nbus + 1)
+    for w in (0, 1):
+        n, nnzl = info.n[w], info.nnz_l[w]
+        shared += 2 * nnzl * prec_bytes + 2 * 4 * nnzl + 4 * (n + 1) * 2 + n * prec_bytes
     n_mean = 0.5 * (info.n[0] + info.n[1])
-    nnzl_mean = 0.5 * (info.nnz_l[0] + info.nnz_l[1])
-    mismatch = 16 * nbus + nnz_y * (8 + 8 + 4) + 4 * (nbus + 1) + 16 * nbus
-    solve = 2 * nnzl_mean * prec_bytes + nnzl_mean * (4 + 4 + 4) + n_mean * prec_bytes \
-        + 16 * n_mean
-    return mismatch + solve
+    per_half = 24 * nbus + 16 * n_mean
+    return shared + half_iters * per_half + resid * 16 * n_mean + n_outage_solves * 2 * n_mean * prec_bytes
 
 
-def measured_traffic(workload, prec_name, ncase):
+def fp64_flops_per_launch(info, case, half_iters, resid):
+    """Algorithmic FP64 operations of one launch of the iteration kernel (a
+    fused multiply-add counts two): per case and half-iteration the nodal
+    mismatch, four multiply-adds per admittance entry (8 nnz(Y)) and about
+    six operations per bus (rectangular voltages, the half-iteration's
+    injection, the scaling by 1/V), and the state update (about 15 per
+    unknown: the angle step rotates the cached cos/sin by a short series,
+    the magnitude step refreshes 1/V); per FP64 residual of a refined solve
+    two per entry of the matrix (n + its off-diagonal entries).  The FP32
+    substitutions run on the FP32 pipe and are not counted."""
+    n_mean = 0.5 * (info.n[0] + info.n[1])
+    off_mean = 0.5 * (matrix_offdiag(case, 0) + matrix_offdiag(case, 1))
+    per_half = 8 * info.nnz_ybus + 6 * case.n + 15 * n_mean
+    return half_iters * per_half + resid * 2 * (n_mean + off_mean)
+
+
+def fp64_peak_tflops(sm_mhz):
+    """Dense FP64 peak of a GB300 from its unit counts and clock: 152 SMs,
+    two FP64 fused multiply-adds per SM and cycle (the 1.25 TFLOP/s nominal
+    at 2,070 MHz)."""
+    return 152 * 2 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def measured_traffic(workload, prec_name, ncase, kernel):
     """DRAM bytes per launch of the iteration kernel from the committed ncu
     summary of the same kernel and workload (scaled by cases when the capture
     ran fewer cases), or None when there is no such capture."""
-    files = {("plain10k", "fp64"): "k_fdpf_plain10k_fp64.md",
-             ("batch10k", "fp32"): "k_fdpf_batch128_fp32.md"}
-    name = files.get((workload, prec_name))
+    files = {("plain10k", "fp64", "k_fdpf_cl"): "k_fdpf_cl_plain10k_fp64.md",
+             ("batch10k", "fp32", "k_fdpf"): "k_fdpf_batch128_fp32.md"}
+    name = files.get((workload, prec_name, kernel))
     if not name:
         return None
     vals = {}
@@ -216,6 +262,49 @@ def _oracle_job(args):
         if time.perf_counter() > deadline:
             break
     return done, time.perf_counter() - t0
+
+
+def _oracle_accuracy_job(args):
+    """Tight oracle solutions of some cases of a workload and their largest
+    differences from the GPU's results (V, theta of those cases)."""
+    from oracle import oracle as O
+    from paper_1811_02512_gb300 import gridgen
+    workload, ids, ncase, vm, va = args
+    base = gridgen.config(0 if workload == "plain120" else 1)
+    sc = gridgen.scenarios(base, n_load=ncase // 2, n_outage=ncase - ncase // 2) if ncase > 1 else None
+    out = []
+    for k, cid in enumerate(ids):
+        c = base if sc is None else gridgen.apply_scenario(base, sc, cid)
+        rc, vm0, va0, _, _ = O.power_flow(c, O.NR, tol=1e-12, max_iter=30)
+        out.append((cid, rc, float(np.max(np.abs(vm[k] - vm0))), float(np.max(np.abs(va[k] - va0)))))
+    return out
+
+
+def oracle_accuracy(workload, vm, va, ncase):
+    """Per-result error of a timed run against the oracle run to a tight
+    mismatch (Newton-Raphson to 1e-12 p.u.): max |dV| and max |dtheta| of
+    every case, the oracle spread over the host cores (spawn)."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    ids = list(range(ncase))
+    chunks = [ids[r::cores] for r in range(cores) if ids[r::cores]]
+    jobs = [(workload, ch, ncase, vm[ch], va[ch]) for ch in chunks]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = [r for part in pool.map(_oracle_accuracy_job, jobs) for r in part]
+    res.sort()
+    dv = np.array([r[2] for r in res])
+    da = np.array([r[3] for r in res])
+    return {"cases": ncase, "reference": "oracle Newton-Raphson to 1e-12 p.u., FP64",
+            "max_dV_pu": float(dv.max()), "max_dtheta_rad": float(da.max()),
+            "median_dV_pu": float(np.median(dv)), "median_dtheta_rad": float(np.median(da)),
+            "worst_case": int(res[int(np.argmax(np.maximum(dv, da)))][0]),
+            "oracle_failed": int(sum(r[1] != O.OK for r in res)),
+            "per_case_dV_pu": [float(f"{v:.3g}") for v in dv],
+            "per_case_dtheta_rad": [float(f"{v:.3g}") for v in da],
+            "seconds": time.perf_counter() - t0, "cores": cores}
 
 
 def cpu_baseline(workload, sample_s, ncase):
@@ -282,35 +371,23 @@ def batched_line(args):
     one launch, FP32 factor + FP64 refinement -- measured by this script's
     batch10k workload in a child process; its main figures."""
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "batch10k", "--steps", "5",
-           "--warmup", str(max(3, args.warmup)), "--no-cpu-baseline"]
+           "--warmup", str(max(3, args.warmup)), "--cpu-sample-s", "3"]
     try:
         out = subprocess.run(cmd, capture_output=True, text=True, timeout=900, check=True).stdout
         d = json.loads([ln for ln in out.splitlines() if ln.startswith("{")][-1])
     except (subprocess.SubprocessError, ValueError, IndexError) as exc:
         return {"unavailable": str(exc)[:200]}
     keep = ("value", "unit", "ms_per_step", "dtype", "converged", "gpu_launches", "roofline", "e2e",
-            "clocks")
+            "clocks", "ir_steps_mean", "ir_steps_max", "iters_mean", "accuracy", "cpu_baseline")
     r = {k: d.get(k) for k in keep}
     r["config"] = d.get("config")
     return r
 
 
 def aggregate_ranks(total_ms, solves_local, world, device):
-    """Whole-job throughput of a weak-scaling run: every rank solved
-    solves_local cases; the job time is the slowest rank's (max over ranks,
-    the only collective).  Returns (max ms, total solves, solves/s)."""
-    import torch
-    t = torch.tensor([total_ms, float(solves_local)], dtype=torch.float64, device=device)
-    if world > 1:
-        import torch.distributed as dist
-        tmax = t[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t[1:].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms, solves = float(tmax.item()), float(tsum.item())
-    else:
-        solves = float(solves_local)
-    return total_ms, solves, solves / (total_ms / 1e3)
+    """Whole-job throughput (see shard.job_throughput)."""
+    from paper_1811_02512_gb300 import shard
+    return shard.job_throughput(total_ms, solves_local, world, device)
 
 
 # ------------------------------------------------------------------ uneven multi-grid batch
@@ -321,12 +398,12 @@ def _pack_case(g):
     return gridgen.with_loading_factor(gridgen.delaunay_raw(n, seed, name=f"multigrid{g}"))
 
 
-def pack_cases(ngrid):
-    """The first ngrid grids of the uneven batch, generated in spawned processes."""
+def pack_cases(lo, hi):
+    """Grids lo..hi-1 of the uneven batch, generated in spawned processes."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
-    with ctx.Pool(min(ngrid, os.cpu_count() or 1)) as pool:
-        return pool.map(_pack_case, range(ngrid))
+    with ctx.Pool(max(1, min(hi - lo, os.cpu_count() or 1))) as pool:
+        return pool.map(_pack_case, range(lo, hi))
 
 
 def run_adjoint(args, dev, local, world, rank):
@@ -422,8 +499,10 @@ def run_pack(args, dev, local, world, rank):
     import torch
     from concurrent.futures import ThreadPoolExecutor
     from paper_1811_02512_gb300 import gbpf
+    from paper_1811_02512_gb300 import shard
     t0 = time.perf_counter()
-    cases = pack_cases(args.ngrid)
+    lo, hi = shard.case_range(rank, world, args.ngrid)  # a job of several ranks splits the grids
+    cases = pack_cases(lo, hi)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
@@ -435,7 +514,8 @@ def run_pack(args, dev, local, world, rank):
     tot = int(pk.offset[-1])
     prec_name = args.precision or "fp32"
     prec = gbpf.PF_FP64 if prec_name == "fp64" else gbpf.PF_FP32
-    opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=TOL, max_iter=200)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=TOL, max_iter=200,
+                         ir_tol=args.ir_tol if args.ir_tol is not None else 1e-6)
     vm = torch.zeros(tot, dtype=torch.float64, device=dev)
     va = torch.zeros_like(vm)
     stream = torch.cuda.current_stream(dev)
@@ -521,9 +601,10 @@ def run_pack(args, dev, local, world, rank):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     prec_bytes = 8 if prec == gbpf.PF_FP64 else 4
     alg = 0.0
-    for k, g in enumerate(grids):
-        per_half = algorithmic_bytes_per_half_iteration(g.info, g.nbus, g.info.nnz_ybus, prec_bytes)
-        alg += per_half * (float(res["iters"][k]) + 1.0)
+    for k, g in enumerate(grids):  # every grid has its own matrices: all of its data per launch
+        hi_k = float(res["iters"][k]) + 1.0
+        resid_k = (float(res["iters"][k]) + float(res["ir_steps"][k])) if prec == gbpf.PF_FP32 else 0.0
+        alg += hbm_bytes_per_launch(g.info, g.case, prec_bytes, hi_k, resid_k, 0.0, 1)
     achieved = alg / (run_ms / 1e3) / 1e9
     sizes = [g.nbus for g in grids]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -535,7 +616,7 @@ def run_pack(args, dev, local, world, rank):
                        "tol_pu": TOL, "method": "fdpf",
                        "l2": "flushed between timed steps (2.5x L2 buffer write)",
                        "generate_s": gen_s, "analyze_s": analyze_s,
-                       "parallelism": "grids-in-blocks"},
+                       "parallelism": f"grids partitioned over {world} ranks" if world > 1 else "grids-in-blocks"},
             "converged": converged, "iters_mean": float(np.mean(res["iters"])),
             "gpu_launches": launches,
             "sequential_plain_fp64": {"value": seq_ok / (seq_ms / 1e3), "unit": UNIT,
@@ -581,7 +662,15 @@ def main():
             dist.destroy_process_group()
         return
 
-    base, ncase, load_scale, outage = make_workload(args.workload, args.ncase)
+    from paper_1811_02512_gb300 import shard
+    base, ncase_all, load_scale, outage = make_workload(args.workload, args.ncase)
+    # a batch shards by case: rank r solves its own slice (symbolic analysis
+    # repeated on every rank); a single case runs as independent replicas
+    lo, hi = shard.case_range(rank, world, ncase_all) if ncase_all > 1 else (0, 1)
+    ncase = hi - lo
+    if ncase_all > 1:
+        load_scale = load_scale[lo:hi]
+        outage = outage[lo:hi]
     prec_name = workload_precision(args.workload, args.precision)
     prec = gbpf.PF_FP64 if prec_name == "fp64" else gbpf.PF_FP32
     t0 = time.perf_counter()
@@ -591,8 +680,9 @@ def main():
     method = gbpf.PF_FDPF if args.method == "fdpf" else gbpf.PF_NR
     engine = {"auto": gbpf.PF_ENGINE_AUTO, "block": gbpf.PF_ENGINE_BLOCK,
               "lanes": gbpf.PF_ENGINE_LANES}[args.engine]
+    ir_tol = args.ir_tol if args.ir_tol is not None else 1e-6
     opts = gbpf.run_opts(method, prec, tol=TOL, max_iter=200 if method == gbpf.PF_FDPF else 20,
-                         engine=engine)
+                         engine=engine, ir_tol=ir_tol)
     vm = torch.zeros((ncase, base.n), dtype=torch.float64, device=dev)
     va = torch.zeros_like(vm)
     stream = torch.cuda.current_stream(dev)
@@ -610,41 +700,59 @@ def main():
         t0 = time.perf_counter()
         tuning = gbpf.pf_autotune(g.ctx, opts, vm, va, reps=2 if ncase == 1 else 1, stream=stream)
         tuning["tune_s"] = time.perf_counter() - t0
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, args.warmup)):  # the second identical run captures a CUDA graph
         st, res = step()
     torch.cuda.synchronize()
-    converged = int(np.sum(res["status"] == gbpf.PF_OK))
-    iters = res["iters"].astype(np.int64)
-    gbpf.pf_set_profiling(g.ctx, True)
-    for k in range(gbpf.PF_K_COUNT if hasattr(gbpf, "PF_K_COUNT") else 7):
+    for k in range(len(gbpf.KERNEL_KINDS)):
         gbpf.pf_get_profile(g.ctx, k, reset=True)
+
+    def timed(nsteps):
+        tot = 0.0
+        for _ in range(nsteps):
+            flush.fill_(1.0)  # evict L2 between timed steps (buffer > 2 x L2)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = step()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot, out
 
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # evict L2 between timed steps (buffer > 2 x L2)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        st, res = step()
-        b.record(stream)
-        b.synchronize()
-        total_ms += a.elapsed_time(b)
+    total_ms, (st, res) = timed(args.steps)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    prof = {}
     launches = 0
+    for k in range(len(gbpf.KERNEL_KINDS)):  # launch counts are kept without profiling
+        launches += gbpf.pf_get_profile(g.ctx, k, reset=True)[0]
+    # untimed: the same steps with every kernel bracketed by CUDA events (the
+    # kernel breakdown and the roofline's kernel time), then without the
+    # CUDA graph (its gain)
+    gbpf.pf_set_profiling(g.ctx, True)
+    nprof = min(args.steps, 5)
+    timed(nprof)
+    prof = {}
     for k, nm in enumerate(gbpf.KERNEL_KINDS):
         n, ms = gbpf.pf_get_profile(g.ctx, k, reset=True)
-        prof[nm] = (n, ms)
-        launches += n
+        prof[nm] = (n / nprof, ms / nprof)
     gbpf.pf_set_profiling(g.ctx, False)
+    gbpf.pf_set_graphs(g.ctx, False)
+    direct_ms, _ = timed(nprof)
+    gbpf.pf_set_graphs(g.ctx, True)
+    converged = int(np.sum(res["status"] == gbpf.PF_OK))
+    iters = res["iters"].astype(np.int64)
+    irs = res["ir_steps"].astype(np.int64)
+    # the results of the last timed step, every rank's slice, for the
+    # accuracy check and the converged count of the whole batch
+    status_t = torch.from_numpy(res["status"].astype(np.int32)).to(dev)
+    vm_all, va_all, st_all = shard.gather_cases(vm, va, status_t, ncase_all, rank, world)
 
     total_ms, solves, value = aggregate_ranks(total_ms, converged * args.steps, world, dev)
 
@@ -658,6 +766,8 @@ def main():
     d2h = out_host.numel() * 8 + ncase * 24
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     te0 = time.perf_counter()
     for _ in range(e2e_steps):
         g.set_cases(ncase, ls_host.numpy(), outage)
@@ -665,8 +775,8 @@ def main():
         out_host[0].copy_(vm, non_blocking=True)
         out_host[1].copy_(va, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - te0
-    e2e_val = int(np.sum(res_e["status"] == gbpf.PF_OK)) * e2e_steps / e2e_s
+    e2e_ms = (time.perf_counter() - te0) * 1e3
+    _, _, e2e_val = aggregate_ranks(e2e_ms, int(np.sum(res_e["status"] == gbpf.PF_OK)) * e2e_steps, world, dev)
 
     # roofline of the dominant kernel (the power-flow iteration kernel)
     peaks = {}
@@ -677,17 +787,39 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     run_n, run_ms = prof["run"]
+    kernel_ms = run_ms / max(run_n, 1e-9)
     prec_bytes = 8 if prec == gbpf.PF_FP64 else 4
-    per_half = algorithmic_bytes_per_half_iteration(g.info, base.n, g.info.nnz_ybus, prec_bytes)
     half_iters = float(np.sum(res["iters"])) + float(np.sum(res["status"] == gbpf.PF_OK))
-    alg_bytes = per_half * half_iters  # per launch (one launch per step)
-    achieved = alg_bytes / (run_ms / max(run_n, 1) / 1e3) / 1e9 if run_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": "k_fdpf", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": measured_traffic(args.workload, prec_name, ncase) if method == gbpf.PF_FDPF else None,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel_ms_per_launch": run_ms / max(run_n, 1)}
+    # FP64 residuals: one per solve of a refined (FP32) run plus one per
+    # refinement step; outage solves with the low-rank correction
+    resid = (float(np.sum(res["iters"])) + float(np.sum(irs))) if prec == gbpf.PF_FP32 else 0.0
+    lowrank = tuning is not None and tuning.get("outage") == 2 and outage is not None
+    out_solves = float(np.sum(res["iters"][outage >= 0])) if lowrank else 0.0
+    alg_bytes = hbm_bytes_per_launch(g.info, base, prec_bytes, half_iters, resid, out_solves, ncase)
+    hbm = {"bound": "hbm", "achieved": alg_bytes / (kernel_ms / 1e3) / 1e9 if kernel_ms > 0 else 0.0,
+           "peak": hbm_peak, "unit": "GB/s",
+           "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+           "algorithmic_bytes_per_launch": alg_bytes}
+    hbm["frac"] = hbm["achieved"] / hbm_peak
+    engine_used = (tuning or {}).get("engine", engine)
+    kname = "k_fdpf_cl" if engine_used == gbpf.PF_ENGINE_CLUSTER else "k_fdpf"
+    hbm["traffic"] = measured_traffic(args.workload, prec_name, ncase, kname) if method == gbpf.PF_FDPF else None
+    if ncase_all > 1:
+        # a batch is bound by the FP64 pipe (GB300 runs FP64 at 1/64 of FP32)
+        flops = fp64_flops_per_launch(g.info, base, half_iters, resid)
+        peak = fp64_peak_tflops(clk.get("sm_mhz"))
+        achieved = flops / (kernel_ms / 1e3) / 1e12 if kernel_ms > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": hbm["traffic"],
+                    "peak_source": "FP64 unit count x SM clock (2 DFMA/cycle/SM x 152 SMs)",
+                    "algorithmic_fp64_flops_per_launch": flops, "kernel_ms_per_launch": kernel_ms,
+                    "hbm": hbm}
+    else:
+        roofline = dict(hbm, kernel=kname, kernel_ms_per_launch=kernel_ms)
+        # a single case is latency bound: time per half-iteration and per
+        # dependent step of its substitutions
+        roofline["latency"] = {"us_per_half_iteration": kernel_ms * 1e3 / max(half_iters, 1),
+                               "levels": [int(g.info.nlevels[0]), int(g.info.nlevels[1])]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
@@ -695,21 +827,31 @@ def main():
             "dtype": "f64" if prec == gbpf.PF_FP64 else "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "nbus": base.n, "nbranch": base.m,
-                       "ncase": ncase, "precision": prec_name, "tol_pu": TOL,
+                       "ncase": ncase_all, "ncase_per_rank": ncase, "precision": prec_name, "tol_pu": TOL,
+                       "ir_tol": ir_tol if prec == gbpf.PF_FP32 else None,
                        "method": args.method, "engine": args.engine,
                        "l2": "flushed between timed steps (2.5x L2 buffer write)",
                        "loading_factor": base.lam, "analyze_ms": analyze_ms,
                        "tuning": tuning,
-                       "parallelism": "replicas" if ncase == 1 else "cases-in-blocks"},
-            "converged": converged, "ncase": ncase,
-            "iters_mean": float(np.mean(iters)), "gpu_launches": launches,
-            "kernel_ms": {k: v[1] for k, v in prof.items()},
-            "kernel_launches": {k: v[0] for k, v in prof.items()},
+                       "parallelism": (f"cases partitioned over {world} ranks" if world > 1 else "cases-in-blocks")
+                       if ncase_all > 1 else ("replicas" if world > 1 else "one case")},
+            "converged": int(torch.sum(st_all == gbpf.PF_OK).item()), "ncase": ncase_all,
+            "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
+            "ir_steps_mean": float(np.mean(irs)), "ir_steps_max": int(np.max(irs)),
+            "gpu_launches": launches,
+            "kernel_ms_per_step": {k: v[1] for k, v in prof.items()},
+            "kernel_launches_per_step": {k: v[0] for k, v in prof.items()},
+            "cuda_graph": {"launches_per_step": launches / args.steps,
+                           "ms_per_step_graph": total_ms / args.steps,
+                           "ms_per_step_direct": direct_ms / nprof},
             "roofline": roofline, "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_s, ncase)
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_s, ncase_all)
+        # the same leg checks each result of the last timed step against the
+        # oracle run to a tight mismatch
+        line["accuracy"] = oracle_accuracy(args.workload, vm_all.cpu().numpy(), va_all.cpu().numpy(), ncase_all)
     if rank == 0 and world == 1 and args.workload == "plain10k" and not args.no_batched:
         line["batched_fp32_ir"] = batched_line(args)
     if rank == 0:

@@ -267,6 +267,17 @@ enum {
  * (0).  Launch counts are always kept.  Synchronous. */
 pf_status pf_set_profiling(pf_ctx *ctx, int32_t on);
 
+/* CUDA graphs of repeated runs (on by default): a fast decoupled
+ * pf_run_to_tol on the block or cluster engine whose arguments (state
+ * pointers, options, tuning, batch) repeat those of the previous call is
+ * captured once into a CUDA graph of its device work -- admittance and
+ * matrix assembly, both factorisations, the low-rank or tail-inverse
+ * preparation, the iteration kernel -- and later identical calls launch that
+ * graph instead of the individual kernels.  Off (0): every call launches its
+ * kernels directly.  Runs with profiling on are always direct.  Not part of
+ * the paper's method: it only removes launch overhead.  Synchronous. */
+pf_status pf_set_graphs(pf_ctx *ctx, int32_t on);
+
 /* Launch count and summed device time (ms, 0 unless profiling was on) of one
  * kernel kind since the last reset; reset = 1 clears both afterwards.
  * Synchronises with the recorded events. */

@@ -48,6 +48,12 @@ __device__ __forceinline__ double ld_cl(uint32_t a) {
     return v;
 }
 
+__device__ __forceinline__ unsigned long long ld_cl_u64(uint32_t a) {
+    unsigned long long v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void st_cl(uint32_t a, double v) {
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
@@ -169,6 +175,38 @@ struct ClSmem {
 // arithmetic would delay the busy ones.
 __device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
     const int G = si.z;
+    if (G == 1) {
+        // one thread per task (most subtree levels): exactly one multiply-add
+        // per entry, in two chains
+        for (int t = si.x + int(threadIdx.x); t < si.y; t += kClThreads) {
+            const int4 tk = S.tasks[t];
+            const int e1 = S.tasks[t + 1].w;
+            const double b = S.X[tk.y];
+            const double dv = tk.z >= 0 ? S.vals[tk.z] : 1.0;
+            double acc = 0.0, a1 = 0.0;
+            int e = tk.w;
+            for (; e + 4 <= e1; e += 4) {
+                const uint32_t p0 = S.addr[e], p1 = S.addr[e + 1], p2 = S.addr[e + 2], p3 = S.addr[e + 3];
+                const double v0 = S.vals[e], v1 = S.vals[e + 1], v2 = S.vals[e + 2], v3 = S.vals[e + 3];
+                const double x0 = ld_cl(p0), x1 = ld_cl(p1), x2 = ld_cl(p2), x3 = ld_cl(p3);
+                acc = fma(v0, x0, acc);
+                a1 = fma(v1, x1, a1);
+                acc = fma(v2, x2, acc);
+                a1 = fma(v3, x3, a1);
+            }
+            const int r = e1 - e;  // 0 to 3 entries left
+            if (r > 0) {
+                const uint32_t p0 = S.addr[e], p1 = S.addr[r > 1 ? e + 1 : e], p2 = S.addr[r > 2 ? e + 2 : e];
+                const double v0 = S.vals[e], v1 = S.vals[r > 1 ? e + 1 : e], v2 = S.vals[r > 2 ? e + 2 : e];
+                const double x0 = ld_cl(p0), x1 = ld_cl(p1), x2 = ld_cl(p2);
+                acc = fma(v0, x0, acc);
+                if (r > 1) a1 = fma(v1, x1, a1);
+                if (r > 2) acc = fma(v2, x2, acc);
+            }
+            S.X[tk.x] = fma(dv, b, -(acc + a1));
+        }
+        return;
+    }
     const int per_warp = 32 / G;  // tasks per warp and round
     const int warp = int(threadIdx.x) >> 5, lane = int(threadIdx.x) & 31;
     const int grp = lane / G, gl = lane % G;
@@ -205,7 +243,7 @@ __device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
             acc += a1;
         }
         for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (act && gl == 0) S.X[tk.x] = (tk.z >= 0 ? dv * b : b) - acc;
+        if (act && gl == 0) S.X[tk.x] = fma(dv, b, -acc);
     }
 }
 
@@ -217,7 +255,7 @@ __device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
 // part (full: of both parts).
 template <int C>
 __device__ double cl_mismatch(const ClRun &a, int rank, int which, const uint32_t *xbase, double *red,
-                              bool full) {
+                              unsigned long long *mkey, const uint32_t *kbase, bool full) {
     const DevNet &dn = a.dn;
     const int nbus = dn.nbus;
     const int slice = (nbus + C - 1) / C;
@@ -248,11 +286,20 @@ __device__ double cl_mismatch(const ClRun &a, int rank, int which, const uint32_
         if (r >= 0) st_cl(xbase[which * C + (r >> 16)] + 8u * unsigned(r & 0xffff), (which == 0 ? dP : dQ) * a.iv[i]);
     }
     mx = block_max_key(mx, red);
-    if (threadIdx.x == 0) a.bmax[rank] = __longlong_as_double(static_cast<long long>(mx));
-    cl_barrier_global();
-    double m = 0.0;
-    for (int r = 0; r < C; r++) m = nan_max(m, a.bmax[r]);
-    return m;
+    // the CTAs' maxima are exchanged as integer keys through distributed
+    // shared memory: slot `which` of each CTA's mkey
+    if (threadIdx.x == 0) mkey[which] = mx;
+    cl_barrier();
+    unsigned long long k = 0;
+    if (threadIdx.x < C) k = ld_cl_u64(kbase[threadIdx.x] + 8u * unsigned(which));
+    for (int o = C / 2; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, k, o);
+        k = u > k ? u : k;
+    }
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if ((threadIdx.x >> 5) == 0 && (threadIdx.x & 31) == 0) red[32] = __longlong_as_double(static_cast<long long>(k));
+    __syncthreads();
+    return red[32];
 }
 
 template <int C>
@@ -261,6 +308,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
     __shared__ double red[33];
     __shared__ uint32_t xbase[2 * C];  // vector region of matrix m in CTA r: xbase[m * C + r]
     __shared__ int nsteps[2];
+    __shared__ unsigned long long mkey[2];  // this CTA's mismatch maximum (key) per half-iteration kind
+    __shared__ uint32_t kbase[C];           // mkey of CTA r
     const int rank = int(cluster_rank());
     const DevNet &dn = a.dn;
     const int nbus = dn.nbus;
@@ -276,6 +325,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
         if (threadIdx.x < C)
             xbase[w * C + threadIdx.x] = cl_mapa(smem_u32(smem_raw + m.so_x), threadIdx.x);
     }
+    if (threadIdx.x < C) kbase[threadIdx.x] = cl_mapa(smem_u32(mkey), threadIdx.x);
     __syncthreads();
     for (int w = 0; w < 2; w++) {
         const ClMat &m = a.m[w];
@@ -318,7 +368,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
         if (rotated)
             for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) sincos(va[i], &sn[i], &cs[i]);
         rotated = false;
-        return cl_mismatch<C>(a, rank, which, xbase, red, true);
+        return cl_mismatch<C>(a, rank, which, xbase, red, mkey, kbase, true);
     };
     // a step is followed by a cluster barrier (it read or feeds other CTAs'
     // words) or by the CTA's own barrier (a level of its own subtrees); every
@@ -339,7 +389,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
     };
     if (status == PF_ERR_NOT_CONVERGED) {
         for (int it = 0; it < a.max_iter; it++) {
-            mis = cl_mismatch<C>(a, rank, 0, xbase, red, false);
+            mis = cl_mismatch<C>(a, rank, 0, xbase, red, mkey, kbase, false);
             if (mis <= a.tol) mis = exact_check(0);
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
@@ -360,7 +410,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
             }
             rotated = true;
             iters++;
-            mis = cl_mismatch<C>(a, rank, 1, xbase, red, false);
+            mis = cl_mismatch<C>(a, rank, 1, xbase, red, mkey, kbase, false);
             if (mis <= a.tol) mis = exact_check(1);
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }

@@ -80,6 +80,14 @@ void dfree(pf_ctx *ctx, void *p) {
         if (_st != PF_OK) return _st;       \
     } while (0)
 
+// Forgets the context's CUDA graph of a run (see run_device_work).
+void drop_graph(pf_ctx *ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    ctx->gkey.clear();
+    ctx->gkey_last.clear();
+}
+
 // Enqueues `launch` (which returns the cudaError_t of its launches) on stream
 // s, counting `nlaunch` kernel launches of kind `kind`; with profiling on the
 // launch is bracketed by CUDA events on the same stream.
@@ -97,9 +105,15 @@ cudaError_t counted(pf_ctx *ctx, int kind, int nlaunch, cudaStream_t s, F launch
         cudaEventRecord(b, s);
         k.pending.push_back({a, b});
     }
-    if (e == cudaSuccess) k.launches += nlaunch;
+    if (e == cudaSuccess && !ctx->graph_capturing) k.launches += nlaunch;
+    if (e == cudaSuccess && ctx->graph_capturing) ctx->glaunches[kind] += nlaunch;
     return e;
 }
+
+// Done-flag epoch of the factorisations captured in a CUDA graph: the graph
+// clears the flags itself (a memset node) and always publishes this epoch,
+// which direct factorisations never reach (they restart at 1 below it).
+constexpr unsigned kGraphEpoch = 0xFFFFFFF0u;
 
 void drain_events(pf_ctx *ctx, KernelStat &k) {
     for (auto &pr : k.pending) {
@@ -1285,7 +1299,7 @@ pf_status assemble_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
 pf_status factor_job(pf_ctx *ctx, int which, int prec, FactorJob &J, cudaStream_t s) {
     Workspace &w = ctx->ws;
     const DevMat &m = ctx->dm[which];
-    if (++w.fepoch[which] == 0u) {
+    if (++w.fepoch[which] >= kGraphEpoch) {
         cudaError_t z = cudaMemsetAsync(w.fdone[which], 0,
                                         size_t(ctx->dc.ninst) * size_t(std::max(1, m.n)) * sizeof(unsigned), s);
         if (z != cudaSuccess) return cuda_fail(ctx, z, "factor flags");
@@ -1316,13 +1330,20 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int bl
     fs.done = w.fdone[which];
     fs.sync = w.fsync[which];
     fs.amax = w.famax[which];
-    if (++w.fepoch[which] == 0u) {  // wrapped: clear the flags, restart at 1
+    if (ctx->graph_capturing) {  // every replay clears the flags and publishes kGraphEpoch
         cudaError_t z = cudaMemsetAsync(w.fdone[which], 0,
                                         size_t(ctx->dc.ninst) * size_t(std::max(1, m.n)) * sizeof(unsigned), s);
         if (z != cudaSuccess) return cuda_fail(ctx, z, "factor flags");
-        w.fepoch[which] = 1u;
+        fs.epoch = kGraphEpoch;
+    } else {
+        if (++w.fepoch[which] >= kGraphEpoch) {  // wrapped: clear the flags, restart at 1
+            cudaError_t z = cudaMemsetAsync(w.fdone[which], 0,
+                                            size_t(ctx->dc.ninst) * size_t(std::max(1, m.n)) * sizeof(unsigned), s);
+            if (z != cudaSuccess) return cuda_fail(ctx, z, "factor flags");
+            w.fepoch[which] = 1u;
+        }
+        fs.epoch = w.fepoch[which];
     }
-    fs.epoch = w.fepoch[which];
     fs.spin = 0;
     fs.nsm = ctx->num_sms;
     fs.mode = ctx->tune.factor;
@@ -1706,6 +1727,8 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
                        const int32_t *outage) {
     if (!ctx || ncase < 1) return fail(ctx, PF_ERR_ARG, "ncase must be >= 1");
     if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
+    drop_graph(ctx);  // its launches point into the batch's arrays
+    ctx->set_gen++;
     std::vector<int> out(ncase, -1), inst(ncase, 0), inst_out(1, -1);
     for (int c = 0; c < ncase; c++) {
         if (outage) {
@@ -1908,6 +1931,140 @@ pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, do
 }  // extern "C"
 
 namespace {
+// Device work of one fast decoupled run on the block or the cluster engine,
+// enqueued on s without any host synchronisation: the admittance matrix,
+// B' and B'' assembled and factorised (B'' on the side stream), then the
+// low-rank outage data or the tail inverses, then the iteration kernel.
+pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev, int engine,
+                     cudaStream_t s) {
+    Workspace &w = ctx->ws;
+    const int prec = opts->precision;
+    TRY(assemble_ybus(ctx, s));
+    if (engine == PF_ENGINE_CLUSTER) {
+        TRY(ensure_cluster(ctx));
+        TRY(factor_both(ctx, prec, s, false));
+        cudaError_t e = counted(ctx, PF_K_FACTOR, 1, s, [&] {
+            return launch_cl_prepare(ctx->cl[0], ctx->cl[1], w.F64[0], w.F64[1], ctx->clW[0], ctx->clW[1], s);
+        });
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster prepare");
+        e = counted(ctx, PF_K_RUN, 1, s, [&] {
+            return launch_fdpf_cl(ctx->dn, ctx->dc, ctx->cl[0], ctx->cl[1], w.fstatus[0][prec],
+                                  w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.iv, w.bmax, w.res,
+                                  ctx->cl_smem, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster fdpf launch");
+        return PF_OK;
+    }
+    const bool lowrank = ctx->tune.outage == 2 && ctx->dc.ninst > 1;
+    TRY(factor_both(ctx, prec, s, lowrank));
+    if (lowrank) {
+        TRY(prepare_lowrank(ctx, prec, s));
+        // the outage instances' own factors were not computed: pf_solve and
+        // pf_get_factor need pf_factor first
+        w.factored[0][prec] = w.factored[1][prec] = false;
+    }
+    const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
+    const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
+    int cl = fdpf_cluster_size(ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin,
+                               std::max(ctx->dm[0].n, ctx->dm[1].n));
+    if (ctx->tune.cluster > 0 && ctx->tune.cluster < cl) cl = ctx->tune.cluster < 8 ? 1 : 8;
+    const bool tail = ctx->tune.tail != 2;
+    cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
+        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, tail ? w.TV[0][prec] : nullptr,
+                           tail ? w.TV[1][prec] : nullptr, w.A[0], w.A[1], w.fstatus[0][prec],
+                           w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.iv, w.vec, w.bmax, w.res,
+                           ctx->smem_optin, cl, s, lowrank ? w.LZ[0][prec] : nullptr,
+                           lowrank ? w.LZ[1][prec] : nullptr, lowrank ? w.LK[0] : nullptr,
+                           lowrank ? w.LK[1] : nullptr);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
+    return PF_OK;
+}
+
+
+// The device work of a run, from a CUDA graph when the same arguments come
+// again: the first call with a set of arguments runs directly (allocating
+// whatever it needs), the second captures the work on the context's own
+// stream, instantiates it and launches it on s, later ones only launch it.
+// The key is everything the captured launches bake in: the state pointers,
+// the options, the tuning, the engine and the batch (set_gen changes with
+// every pf_set_cases and pf_set_injections keeps the arrays in place).
+// With profiling on, or after a capture that failed, runs are direct.
+pf_status run_device_work(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev, int engine,
+                          cudaStream_t s) {
+    std::vector<unsigned char> key(2 * sizeof(void *) + sizeof(pf_run_opts) + 5 * sizeof(int32_t) +
+                                   3 * sizeof(int));
+    unsigned char *k = key.data();
+    auto put = [&](const void *p, size_t n) {
+        memcpy(k, p, n);
+        k += n;
+    };
+    put(&vm_dev, sizeof(void *));
+    put(&va_dev, sizeof(void *));
+    pf_run_opts o;
+    memset(&o, 0, sizeof(o));
+    o.method = opts->method;
+    o.precision = opts->precision;
+    o.tol = opts->tol;
+    o.max_iter = opts->max_iter;
+    o.ir_max = opts->ir_max;
+    o.ir_tol = opts->ir_tol;
+    o.ir_abs = opts->ir_abs;
+    o.flat_start = opts->flat_start;
+    o.spin_limit = opts->spin_limit;
+    o.engine = opts->engine;
+    o.fallback = opts->fallback;
+    put(&o, sizeof(o));
+    const int32_t t[5] = {ctx->tune.engine, ctx->tune.cluster, ctx->tune.factor, ctx->tune.tail,
+                          ctx->tune.outage};
+    put(t, sizeof(t));
+    const int extra[3] = {engine, ctx->set_gen, ctx->dc.ncase};
+    put(extra, sizeof(extra));
+    const bool graphs = !ctx->profiling && !ctx->graphs_off;
+    if (graphs && ctx->gexec && key == ctx->gkey) {
+        cudaError_t e = cudaGraphLaunch(ctx->gexec, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+        for (int q = 0; q < PF_K_COUNT; q++) ctx->kstat[q].launches += ctx->glaunches[q];
+        return PF_OK;
+    }
+    if (!graphs || key != ctx->gkey_last) {
+        ctx->gkey_last = key;
+        return issue_fdpf(ctx, opts, vm_dev, va_dev, engine, s);
+    }
+    // the same arguments a second time: capture
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    ctx->gkey.clear();
+    if (!ctx->gstream && cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->graphs_off = true;
+        return issue_fdpf(ctx, opts, vm_dev, va_dev, engine, s);
+    }
+    for (int q = 0; q < PF_K_COUNT; q++) ctx->glaunches[q] = 0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed);
+    pf_status st = PF_ERR_CUDA;
+    if (e == cudaSuccess) {
+        ctx->graph_capturing = true;
+        st = issue_fdpf(ctx, opts, vm_dev, va_dev, engine, ctx->gstream);
+        ctx->graph_capturing = false;
+        e = cudaStreamEndCapture(ctx->gstream, &graph);
+    }
+    if (e == cudaSuccess && st == PF_OK) e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || st != PF_OK) {  // no graphs for this context: run directly
+        cudaGetLastError();
+        ctx->gexec = nullptr;
+        ctx->graphs_off = true;
+        return issue_fdpf(ctx, opts, vm_dev, va_dev, engine, s);
+    }
+    ctx->gkey = key;
+    e = cudaGraphLaunch(ctx->gexec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    for (int q = 0; q < PF_K_COUNT; q++) ctx->kstat[q].launches += ctx->glaunches[q];
+    return PF_OK;
+}
+
 pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
                    pf_case_result *res_host, void *stream) {
     if (!ctx || !opts || !vm_dev || !va_dev || !res_host) return fail(ctx, PF_ERR_ARG, "null pointer");
@@ -1947,40 +2104,13 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
     const int nmax = std::max(ctx->dm[0].n, ctx->dm[1].n);
     const bool lanes_ok = opts->method == PF_FDPF && lane_width(nmax, prec, ctx->smem_optin) > 0;
     const int want = opts->engine != PF_ENGINE_AUTO ? opts->engine : ctx->tune.engine;
-    if (want == PF_ENGINE_CLUSTER && cluster_applies(ctx, opts)) {
-        TRY(ensure_cluster(ctx));
-        TRY(factor_both(ctx, prec, s, false));
-        Workspace &wc = ctx->ws;
-        cudaError_t e = counted(ctx, PF_K_FACTOR, 1, s, [&] {
-            return launch_cl_prepare(ctx->cl[0], ctx->cl[1], wc.F64[0], wc.F64[1], ctx->clW[0], ctx->clW[1], s);
-        });
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster prepare");
-        e = counted(ctx, PF_K_RUN, 1, s, [&] {
-            return launch_fdpf_cl(ctx->dn, ctx->dc, ctx->cl[0], ctx->cl[1], wc.fstatus[0][prec],
-                                  wc.fstatus[1][prec], *opts, vm_dev, va_dev, wc.ef, wc.iv, wc.bmax, wc.res,
-                                  ctx->cl_smem, s);
-        });
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster fdpf launch");
-        e = cudaMemcpyAsync(res_host, wc.res, sizeof(pf_case_result), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster fdpf run");
-        if (res_host[0].status != PF_OK)
-            return fail(ctx, pf_status(res_host[0].status), "case 0: status %d after %d iterations",
-                        res_host[0].status, res_host[0].iters);
-        return PF_OK;
-    }
-    const int engine = want == PF_ENGINE_LANES && lanes_ok ? PF_ENGINE_LANES : PF_ENGINE_BLOCK;
-    const bool lowrank = engine == PF_ENGINE_BLOCK && ctx->tune.outage == 2 && ctx->dc.ninst > 1;
-    TRY(factor_both(ctx, prec, s, lowrank));
-    if (lowrank) {
-        TRY(prepare_lowrank(ctx, prec, s));
-        // the outage instances' own factors were not computed: pf_solve and
-        // pf_get_factor need pf_factor first
-        w.factored[0][prec] = w.factored[1][prec] = false;
-    }
-    const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
-    const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
+    const bool use_cluster = want == PF_ENGINE_CLUSTER && cluster_applies(ctx, opts);
+    const int engine = use_cluster ? PF_ENGINE_CLUSTER
+                                   : (want == PF_ENGINE_LANES && lanes_ok ? PF_ENGINE_LANES : PF_ENGINE_BLOCK);
     if (engine == PF_ENGINE_LANES) {
+        TRY(factor_both(ctx, prec, s, false));
+        const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
+        const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
         TRY(ensure_lanes(ctx, prec));
         LaneRun r;
         r.dn = ctx->dn;
@@ -2012,22 +2142,11 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
                             c, res_host[c].status, res_host[c].iters);
         return PF_OK;
     }
-    int cl = fdpf_cluster_size(ctx->dc.ncase, ctx->num_sms, prec, ctx->smem_optin,
-                               std::max(ctx->dm[0].n, ctx->dm[1].n));
-    if (ctx->tune.cluster > 0 && ctx->tune.cluster < cl) cl = ctx->tune.cluster < 8 ? 1 : 8;
-    const bool tail = ctx->tune.tail != 2;
-    cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
-        return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, tail ? w.TV[0][prec] : nullptr,
-                           tail ? w.TV[1][prec] : nullptr,
-                           w.A[0], w.A[1],
-                           w.fstatus[0][prec], w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef,
-                           w.iv, w.vec, w.bmax, w.res, ctx->smem_optin, cl, s,
-                           lowrank ? w.LZ[0][prec] : nullptr, lowrank ? w.LZ[1][prec] : nullptr,
-                           lowrank ? w.LK[0] : nullptr, lowrank ? w.LK[1] : nullptr);
-    });
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
-    e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,
-                        cudaMemcpyDeviceToHost, s);
+    // block and cluster engines: the device work of the run, enqueued
+    // directly or from a CUDA graph of it
+    TRY(run_device_work(ctx, opts, vm_dev, va_dev, engine, s));
+    cudaError_t e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,
+                                    cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf run");
     for (int c = 0; c < ctx->dc.ncase; c++)
@@ -2092,6 +2211,13 @@ pf_status pf_objective(pf_ctx *ctx, const double *vm_dev, const double *va_dev, 
         return launch_objective(ctx->dn, ctx->dc, vm_dev, va_dev, ctx->ws.ef, J_dev, gva_dev, gvm_dev, s);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "objective launch");
+    return PF_OK;
+}
+
+pf_status pf_set_graphs(pf_ctx *ctx, int32_t on) {
+    if (!ctx) return PF_ERR_ARG;
+    drop_graph(ctx);
+    ctx->graphs_off = !on;
     return PF_OK;
 }
 
@@ -2214,6 +2340,8 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
         return fail(ctx, PF_ERR_CUDA, "event creation");
     }
     const pf_tuning saved = ctx->tune;
+    const bool graphs_saved = ctx->graphs_off;
+    ctx->graphs_off = true;  // every candidate timed on direct launches
     pf_tuning best{0, 0, 0, 0, 0, -1.0};
     pf_status last = PF_OK;
     for (const pf_tuning &t : cand) {
@@ -2241,6 +2369,7 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    ctx->graphs_off = graphs_saved;
     if (best.ms < 0) {
         ctx->tune = saved;
         return fail(ctx, last == PF_OK ? PF_ERR_NOT_CONVERGED : last, "no mapping converged");
@@ -2443,6 +2572,8 @@ void pf_pack_destroy(pf_pack *pk) {
 
 void pf_destroy(pf_ctx *ctx) {
     if (!ctx) return;
+    drop_graph(ctx);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     if (ctx->ws.side) {
         cudaStreamSynchronize(ctx->ws.side);
         cudaStreamDestroy(ctx->ws.side);

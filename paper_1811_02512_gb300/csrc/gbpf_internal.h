@@ -345,6 +345,17 @@ struct pf_ctx {
     gbpf::ClMat cl[2];
     double *clW[2] = {nullptr, nullptr};
     size_t cl_smem = 0;
+    // CUDA graph of the device work of one fast decoupled pf_run_to_tol
+    // (block and cluster engines), captured on an internal stream for a given
+    // set of arguments (key) and replayed on the caller's stream; the launch
+    // counts of one replay per kernel kind
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey, gkey_last;
+    int64_t glaunches[PF_K_COUNT] = {};
+    bool graph_capturing = false;
+    bool graphs_off = false;
+    int set_gen = 0;  // bumped by every pf_set_cases (the batch's arrays are new)
 };
 
 namespace gbpf {

@@ -380,6 +380,9 @@ __global__ void __launch_bounds__(kFactorThreads)
         while (G > 1 && G * nk > bd) G >>= 1;
         const int gl = tid & (G - 1), ngr = bd / G;
         for (int jb = 0; jb < nk; jb += ngr) {  // uniform trip count: shuffles stay convergent
+            // a warp without a target of this level skips it (warp-uniform):
+            // idle FP64 arithmetic would take the busy warps' FP64 issue slots
+            if (jb + (tid >> 5) * (32 / G) >= nk) continue;
             const int j = jb + tid / G;
             const bool act = j < nk;
             const int4 info = act ? ti[j] : make_int4(0, 0, 0, 0);

@@ -88,6 +88,8 @@ def load():
         L.pf_run_to_tol.argtypes = [_P, C.POINTER(pf_run_opts), _P, _P, _P, _P]
         L.pf_get_ybus.argtypes = [_P, _P, _P, _P, _P]
         L.pf_set_profiling.argtypes = [_P, C.c_int32]
+        L.pf_set_graphs.argtypes = [_P, C.c_int32]
+        L.pf_set_graphs.restype = S
         L.pf_get_profile.argtypes = [_P, C.c_int32, _P, _P, C.c_int32]
         L.pf_set_injections.argtypes = [_P, _P, _P, _P]
         L.pf_adjoint.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]
@@ -342,6 +344,11 @@ def pf_get_tuning(ctx):
     t = pf_tuning()
     _check(ctx, load().pf_get_tuning(ctx, C.byref(t)), "pf_get_tuning")
     return {k: getattr(t, k) for k, _ in pf_tuning._fields_}
+
+
+def pf_set_graphs(ctx, on):
+    """CUDA-graph replay of repeated runs on (default) or off."""
+    _check(ctx, load().pf_set_graphs(ctx, int(bool(on))), "pf_set_graphs")
 
 
 def pf_set_tuning(ctx, engine=0, cluster=0, factor=0, tail=0, outage=0):

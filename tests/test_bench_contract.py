@@ -26,3 +26,21 @@ def test_cpu_baseline_leg_on_a_short_sample(oracle):
     assert r["kind"] == "oracle" and r["unit"] == bench.UNIT
     assert r["cores"] == (os.cpu_count() or 1)
     assert r["value"] > 0 and "120-bus" in r["sample"]
+
+
+def test_accuracy_leg_against_the_oracle_itself(oracle):
+    """The accuracy part of the cpu_baseline leg on the 120-bus grid: fed the
+    oracle's own tight solution it reports errors at rounding level, and the
+    per-case lists have one entry per case."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from paper_1811_02512_gb300 import gridgen
+    case = gridgen.config(0)
+    rc, vm, va, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
+    acc = bench.oracle_accuracy("plain120", vm[None], va[None], 1)
+    assert acc["cases"] == 1 and acc["oracle_failed"] == 0
+    assert acc["max_dV_pu"] <= 1e-12 and acc["max_dtheta_rad"] <= 1e-12
+    assert len(acc["per_case_dV_pu"]) == 1 and len(acc["per_case_dtheta_rad"]) == 1
+    acc = bench.oracle_accuracy("plain120", vm[None] + 1e-6, va[None], 1)
+    assert abs(acc["max_dV_pu"] - 1e-6) < 1e-9

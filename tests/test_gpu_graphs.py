@@ -1,0 +1,82 @@
+"""CUDA-graph replay of repeated pf_run_to_tol calls (pf_set_graphs).
+
+The second identical call captures the run's device work into a graph and
+later calls launch it.  Every kernel is deterministic (fixed orders of
+operations), so replayed runs must give bit-identical results to direct
+ones; the factor's dependency flags use a reserved epoch inside the graph,
+so direct factorisations and solves between replays must stay correct."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1811_02512_gb300 import gbpf, gridgen  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_02512_gb300 import build
+    build.build()
+    gbpf.load()
+
+
+def _launches(g):
+    return sum(gbpf.pf_get_profile(g.ctx, k)[0] for k in range(len(gbpf.KERNEL_KINDS)))
+
+
+@pytest.mark.parametrize("engine,ncase,prec", [(gbpf.PF_ENGINE_BLOCK, 6, gbpf.PF_FP32),
+                                               (gbpf.PF_ENGINE_BLOCK, 6, gbpf.PF_FP64),
+                                               (gbpf.PF_ENGINE_CLUSTER, 1, gbpf.PF_FP64)])
+def test_graph_replays_match_direct_runs(oracle, engine, ncase, prec):
+    base = gridgen.config(1)
+    g = gbpf.Grid(base)
+    if ncase > 1:
+        sc = gridgen.scenarios(base, n_load=3, n_outage=3, seed=77)
+        g.set_cases(sc.ncase, sc.load_scale, sc.outage)
+        gbpf.pf_set_tuning(g.ctx, engine=engine, cluster=1, factor=1, tail=1, outage=2)
+    else:
+        g.set_cases(1)
+        gbpf.pf_set_tuning(g.ctx, engine=engine, factor=1, tail=1)
+    vm = torch.zeros((ncase, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=1e-10, max_iter=300)
+    gbpf.pf_set_graphs(g.ctx, False)
+    st, res0 = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+    assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    ref = (vm.clone(), va.clone())
+    gbpf.pf_set_graphs(g.ctx, True)
+    counts = []
+    for k in range(4):  # direct, capture + launch, replay, replay
+        vm.zero_()
+        va.zero_()
+        before = _launches(g)
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+        assert st == gbpf.PF_OK, (k, gbpf.pf_last_error(g.ctx))
+        counts.append(_launches(g) - before)
+        assert torch.equal(vm, ref[0]) and torch.equal(va, ref[1]), k
+        assert np.array_equal(res["iters"], res0["iters"])
+    assert counts[0] > 0 and counts[1] == counts[2] == counts[3] == counts[0]
+    # a direct factorisation and solve between replays (the flags' epochs)
+    name = "bp"
+    an, Lx0, d0, _ = oracle.factor_bmatrix(base, name)
+    n = an["buses"].shape[0]
+    gbpf.pf_factor(g.ctx, gbpf.PF_MAT_BP, gbpf.PF_FP64)
+    rhs = torch.ones((1, n), dtype=torch.float64, device=DEV)
+    gbpf.pf_solve(g.ctx, gbpf.PF_MAT_BP, gbpf.PF_FP64, rhs, 1)
+    torch.cuda.synchronize()
+    xs = oracle.lu_solve(n, an["Lp"], an["Li"], Lx0, Lx0 * d0[np.repeat(np.arange(n), np.diff(an["Lp"]))],
+                         d0, np.ones(n))
+    x_ref = np.empty(n)
+    x_ref[an["perm"]] = xs
+    assert np.max(np.abs(rhs.cpu().numpy()[0] - x_ref)) <= 1e-11 * np.max(np.abs(x_ref))
+    vm.zero_()
+    va.zero_()
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)  # a replay again
+    assert st == gbpf.PF_OK
+    assert torch.equal(vm, ref[0]) and torch.equal(va, ref[1])
+    g.close()
