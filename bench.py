@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--mapping", default=None,
                     help="engine,cluster,factor,tail,outage: set this kernel mapping instead of tuning")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel directly instead of replaying CUDA graphs (profilers)")
     ap.add_argument("--ir-tol", type=float, default=None,
                     help="FP32 runs: relative residual at which a linear solve needs no further "
                          "refinement (default 1e-6: an inexact-Newton forcing term far below the "
@@ -691,6 +693,8 @@ def main():
     def step():
         return gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase, stream=stream)
 
+    if args.no_graphs:
+        gbpf.pf_set_graphs(g.ctx, False)
     tuning = None
     if args.mapping:
         e_, c_, f_, t_, o_ = (int(v) for v in args.mapping.split(","))
@@ -745,7 +749,7 @@ def main():
     gbpf.pf_set_profiling(g.ctx, False)
     gbpf.pf_set_graphs(g.ctx, False)
     direct_ms, _ = timed(nprof)
-    gbpf.pf_set_graphs(g.ctx, True)
+    gbpf.pf_set_graphs(g.ctx, not args.no_graphs)
     converged = int(np.sum(res["status"] == gbpf.PF_OK))
     iters = res["iters"].astype(np.int64)
     irs = res["ir_steps"].astype(np.int64)

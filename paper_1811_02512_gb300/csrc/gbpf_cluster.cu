@@ -326,6 +326,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
             xbase[w * C + threadIdx.x] = cl_mapa(smem_u32(smem_raw + m.so_x), threadIdx.x);
     }
     if (threadIdx.x < C) kbase[threadIdx.x] = cl_mapa(smem_u32(mkey), threadIdx.x);
+    {  // the admittance matrix is read every half-iteration: start it towards the L2
+        const int part = rank * kClThreads + int(threadIdx.x), parts = C * kClThreads;
+        l2_prefetch(dn.col, sizeof(int) * size_t(dn.nnz), part, parts);
+        l2_prefetch(dn.G, sizeof(double) * size_t(dn.nnz), part, parts);
+        l2_prefetch(dn.B, sizeof(double) * size_t(dn.nnz), part, parts);
+    }
     __syncthreads();
     for (int w = 0; w < 2; w++) {
         const ClMat &m = a.m[w];

@@ -162,6 +162,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Asks the L2 to fetch bytes [0, nbytes) of an array (rounded down to 16-byte
+// multiples, within the allocation), in chunks of 32 KB spread over the
+// calling threads: part (of nparts) is this thread's share.  A hint only:
+// later loads of the range hit the L2 instead of waiting for DRAM.
+__device__ __forceinline__ void l2_prefetch(const void *base, size_t nbytes, int part, int nparts) {
+    constexpr size_t kChunk = 32768;
+    const uintptr_t b0 = reinterpret_cast<uintptr_t>(base);
+    const uintptr_t a0 = (b0 + 15) & ~uintptr_t(15);
+    if (nbytes < (a0 - b0) + 16) return;
+    const size_t usable = (nbytes - (a0 - b0)) & ~size_t(15);
+    for (size_t off = size_t(part) * kChunk; off < usable; off += size_t(nparts) * kChunk) {
+        const unsigned len = unsigned(usable - off < kChunk ? usable - off : kChunk);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0 + off), "r"(len) : "memory");
+    }
+}
+
 // ------------------------------------------------------------ cluster barrier
 
 __device__ __forceinline__ unsigned cluster_rank() {

@@ -297,8 +297,12 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
             const int cb = H.lvl_ptr[l], ce = H.lvl_ptr[l + 1];
             const int kb = H.Cp[cb] + cb - H.ft_g0, ke = H.Cp[ce] + ce - H.ft_g0;
             const int tb = H.tptr[kb], te = H.tptr[ke];
+            int maxterms = 0;
+            for (int k = kb; k < ke; k++) maxterms = std::max(maxterms, H.tptr[k + 1] - H.tptr[k]);
+            int G = 1;
+            while (G < 32 && maxterms > 4 * G) G *= 2;
             H.tlev[2 * li] = int4{kb, ke, tb, te};
-            H.tlev[2 * li + 1] = int4{cb - t0, ce - t0, 0, 0};
+            H.tlev[2 * li + 1] = int4{cb - t0, ce - t0, G, 0};
             H.ft_kmax = std::max(H.ft_kmax, ke - kb);
             for (int k = kb; k < ke; k++) {
                 const int c = H.tcol[k];
@@ -1112,6 +1116,7 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
         TRY(upload_padded(ctx, &D.gsplit, H.gsplit));
         if (H.tterm.empty()) return fail(ctx, PF_ERR_ARG, "internal: tail terms");
         TRY(upload(ctx, &D.tterm, H.tterm.data(), H.tterm.size()));
+        D.ft_tterms = int(H.tterm.size());
         TRY(upload(ctx, &D.tlev, H.tlev.data(), H.tlev.size()));
         TRY(upload(ctx, &D.tinfo, H.tinfo.data(), H.tinfo.size()));
         D.ft_kmax = H.ft_kmax;
@@ -1204,6 +1209,11 @@ pf_status ensure_factor_storage(pf_ctx *ctx, int which, int prec) {
     if (prec == PF_FP64 && !w.F64[which]) TRY(dalloc(ctx, &w.F64[which], sz));
     if (prec == PF_FP32 && !w.F32[which]) TRY(dalloc(ctx, &w.F32[which], sz));
     if (!w.fstatus[which][prec]) TRY(dalloc(ctx, &w.fstatus[which][prec], size_t(ctx->dc.ninst)));
+    if (m.ft_ng > 0 && !w.TP[which][prec]) {
+        const size_t np = size_t(ctx->dc.ninst) * size_t(m.ft_ng);
+        if (prec == PF_FP64) TRY(dalloc(ctx, reinterpret_cast<double **>(&w.TP[which][prec]), np));
+        else TRY(dalloc(ctx, reinterpret_cast<float **>(&w.TP[which][prec]), np));
+    }
     if (m.npf2 > 0 && !w.TV[which][prec]) {
         const size_t nt = size_t(ctx->dc.ninst) * size_t(m.tv_stride);
         if (prec == PF_FP64) TRY(dalloc(ctx, reinterpret_cast<double **>(&w.TV[which][prec]), nt));
@@ -1237,6 +1247,8 @@ void free_case_storage(pf_ctx *ctx) {
         for (int b = 0; b < 2; b++) {
             dfree(ctx, w.TV[a][b]);
             w.TV[a][b] = nullptr;
+            dfree(ctx, w.TP[a][b]);
+            w.TP[a][b] = nullptr;
         }
         dfree(ctx, w.fsync[a]); w.fsync[a] = nullptr;
         dfree(ctx, w.famax[a]); w.famax[a] = nullptr;
@@ -1350,6 +1362,7 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int bl
     fs.blocks_per_sm = blocks_per_sm;
     fs.tail = ctx->tune.tail != 2;
     fs.smem_optin = ctx->smem_optin;
+    fs.partg = w.TP[which][prec];
     e = counted(ctx, PF_K_FACTOR, 2, s, [&] {
         return launch_factor(m, prec, w.A[which], F, nf, w.fstatus[which][prec], fs, s);
     });

@@ -98,8 +98,10 @@ struct DevMat {
     // target; ft_tmax = most terms of one tail level
     int2 *tterm = nullptr;
     int ft_tmax = 0;
+    int ft_tterms = 0;         // tail terms in tterm
     // per tail level li: tlev[2 li] = {first target, end target, first term,
-    // end term}, tlev[2 li + 1] = {first column - t0, end column - t0, 0, 0};
+    // end term}, tlev[2 li + 1] = {first column - t0, end column - t0, lanes
+    // per target, 0};
     // per target: tinfo = {first term, end term (both relative to its level's
     // first), L entry - e0 (-1 for the diagonal), column - t0}; ft_kmax = most
     // targets of one tail level
@@ -276,6 +278,7 @@ struct Workspace {
     double *famax[2] = {nullptr, nullptr};    // [ninst]
     unsigned fepoch[2] = {0u, 0u};
     void *TV[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mat][prec] tail values
+    void *TP[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mat][prec] tail targets' parts
     // low-rank outages, per matrix: Z [ninst][2][n] of the factor type (per
     // precision), K [ninst][4], solve scratch
     void *LZ[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -382,6 +385,8 @@ struct FactorSync {
     int blocks_per_sm = 2;     // dependency-driven grid: blocks per SM
     bool tail = true;          // factor the narrow top in one block (k_factor_tail) when it fits
     size_t smem_optin = 0;
+    void *partg = nullptr;     // [ninst][ft_ng] of the factor type: the tail targets' parts
+                               // from columns below the tail (k_factor_tail_pre)
 };
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
                           int *fstatus, const FactorSync &fs, cudaStream_t s);

@@ -276,6 +276,15 @@ __global__ void __launch_bounds__(kDepThreads)
     __shared__ T terms_all[kDepThreads / 32][kDepChunk];
     const int lane = threadIdx.x & 31;
     T *terms = terms_all[threadIdx.x >> 5];
+    {  // the gather lists and patterns are read once each, in column order:
+       // start them (and the assembled values) towards the L2 all at once
+        const int part = int(blockIdx.x * blockDim.x + threadIdx.x), parts = int(gridDim.x * blockDim.x);
+        l2_prefetch(m.gl, sizeof(int4) * size_t(m.nupd), part, parts);
+        l2_prefetch(m.gp, sizeof(int) * size_t(m.n + m.nnz + 1), part, parts);
+        l2_prefetch(m.Fc, sizeof(int) * size_t(m.nnz), part, parts);
+        l2_prefetch(m.Cpos, sizeof(int) * size_t(m.nnz), part, parts);
+        l2_prefetch(A, sizeof(double) * size_t(ninst) * size_t(m.stride), part, parts);
+    }
     const unsigned total = unsigned(ncols) * unsigned(ninst);
     const unsigned spin = fs.spin ? fs.spin : kDefaultSpin;
     for (;;) {
@@ -294,15 +303,38 @@ __global__ void __launch_bounds__(kDepThreads)
     }
 }
 
+// The part of every tail target that comes from columns below the tail
+// (final once k_factor_dep is done): part = a - sum_{k < t0} L(i,k) D(k)
+// L(c,k) over the target's gather terms, one warp per target (lanes stride
+// its terms, then a shuffle reduction in lane order), spread over many
+// blocks; k_factor_tail continues from it.
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_factor_tail_pre(DevMat m, const double *A, const T *F, T *partg) {
+    const int inst = blockIdx.y;
+    const int k = blockIdx.x * 8 + int(threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (k >= m.ft_ng) return;
+    const T *v = F + (long long)inst * m.stride;
+    const T *Lc = v + m.offLc;
+    const int qe = m.gsplit[k];
+    T s = T(0);
+    for (int q = m.gp[m.ft_g0 + k] + lane; q < qe; q += 32) {
+        const int4 e = m.gl[q];
+        s += Lc[e.x] * (Lc[e.y] * v[e.z]);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) partg[(long long)inst * m.ft_ng + k] = T(A[(long long)inst * m.stride + m.tapos[k]]) - s;
+}
+
 // The columns [t0, n) of one instance per block (the narrow top of the
-// elimination tree), after k_factor_dep has finished the columns below t0.
+// elimination tree), after k_factor_dep has finished the columns below t0
+// and k_factor_tail_pre the targets' parts from those columns.
 // Shared memory holds the tail's entries, D and 1/D, one partial value per
 // gather target, the level table and, double-buffered, the packed terms and
-// target descriptors of one level.  First every target subtracts, in
-// parallel, its update terms from columns below the tail (read from the
-// factor in global memory); then level by level each target subtracts its
-// terms from tail columns (the level's terms and descriptors were staged
-// while the previous level was computed).  Within the tail the entries are
+// target descriptors of one level.  Level by level each target subtracts
+// its terms from tail columns (the level's terms and descriptors were staged
+// while the previous level was computed), with the lanes per target the
+// level table gives (enough for about four terms per lane).  Within the tail the entries are
 // kept unnormalised, U(i,c) = L(i,c) D(c), so that an update term
 // L(i,k) D(k) L(c,k) is U(i,k) (U(c,k) / D(k)) and a level needs no
 // division pass before the next one: one block barrier per level.  L = U / D
@@ -310,14 +342,12 @@ __global__ void __launch_bounds__(kDepThreads)
 // fixed.
 template <class T>
 __global__ void __launch_bounds__(kFactorThreads)
-    k_factor_tail(DevMat m, const double *A, T *F, int *fstatus, const double *amaxv) {
+    k_factor_tail(DevMat m, const T *partg, T *F, int *fstatus, const double *amaxv) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int R = 4;  // terms per thread prefetched into registers
     const int inst = blockIdx.x;
     const int bd = int(blockDim.x), tid = int(threadIdx.x);
-    const double *a = A + (long long)inst * m.stride;
     T *v = F + (long long)inst * m.stride;
-    const T *Lc = v + m.offLc;
     const int tmax = m.ft_tmax, kmax = m.ft_kmax, ntl = m.ntl;
     int4 *lev = reinterpret_cast<int4 *>(smem_raw);  // [2 ntl]
     int4 *tib = lev + 2 * ntl;                        // [2][kmax]
@@ -327,25 +357,13 @@ __global__ void __launch_bounds__(kFactorThreads)
     T *Di = Dt + m.nt;
     T *part = Di + m.nt;
     const int g0 = m.ft_g0;
+    // the level loop reads the term and target tables once, one level ahead:
+    // fetch all of them into the L2 now, so that no level waits for DRAM
+    l2_prefetch(m.tterm, sizeof(int2) * size_t(m.ft_tterms), tid, bd);
+    l2_prefetch(m.tinfo, sizeof(int4) * size_t(m.ft_ng), tid, bd);
     for (int i = tid; i < 2 * ntl; i += bd) lev[i] = m.tlev[i];
-    for (int k = tid; k < m.ft_ng; k += bd) {
-        const int g = g0 + k;
-        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-        int q = m.gp[g];
-        const int qe = m.gsplit[k];
-        for (; q + 4 <= qe; q += 4) {
-            const int4 e = m.gl[q], f = m.gl[q + 1], h = m.gl[q + 2], u = m.gl[q + 3];
-            s0 += Lc[e.x] * (Lc[e.y] * v[e.z]);
-            s1 += Lc[f.x] * (Lc[f.y] * v[f.z]);
-            s2 += Lc[h.x] * (Lc[h.y] * v[h.z]);
-            s3 += Lc[u.x] * (Lc[u.y] * v[u.z]);
-        }
-        for (; q < qe; q++) {
-            const int4 e = m.gl[q];
-            s0 += Lc[e.x] * (Lc[e.y] * v[e.z]);
-        }
-        part[k] = T(a[m.tapos[k]]) - ((s0 + s1) + (s2 + s3));
-    }
+    for (int k = tid; k < m.ft_ng; k += bd) part[k] = partg[(long long)inst * m.ft_ng + k];
+    (void)g0;
     {
         const int4 L0 = m.tlev[0];
         for (int i = tid; i < L0.w - L0.z; i += bd) tbuf[i] = m.tterm[L0.z + i];
@@ -376,7 +394,7 @@ __global__ void __launch_bounds__(kFactorThreads)
         // levels, whose diagonals gather the most terms, split their sums
         // over up to a warp and reduce them with shuffles
         const int nk = L.y - L.x;
-        int G = 32;
+        int G = lev[2 * li + 1].z;  // lanes per target: about four terms per lane
         while (G > 1 && G * nk > bd) G >>= 1;
         const int gl = tid & (G - 1), ngr = bd / G;
         for (int jb = 0; jb < nk; jb += ngr) {  // uniform trip count: shuffles stay convergent
@@ -818,394 +836,11 @@ __global__ void k_mismatch_rows(DevNet dn, DevCases dc, const double *ef, double
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(maxmis + c, mx);
 }
 
-// ------------------------------------------------------------ Section III
-
-struct RunArgs {
-    DevNet dn;
-    DevCases dc;
-    DevMat m0, m1;  // B', B''
-    const void *F0, *F1;
-    const void *TV0, *TV1;  // gathered tail values per instance (or null)
-    // low-rank outages: outage cases solve with the base factor (instance 0)
-    // and the correction x += Z K (x[p0], x[p1]) of their instance (or null)
-    const void *Z0, *Z1;     // [ninst][2][n] T
-    const double *K0, *K1;   // [ninst][4]
-    const double *A0, *A1;  // FP64 assembled values of B', B'' (refinement residuals)
-    const int *fs0, *fs1;
-    double tol;
-    int max_iter;
-    int ir_max;
-    double ir_tol, ir_abs;
-    int flat;
-    unsigned spin;
-    double *vm, *va;
-    double *ef;    // [ncase][4 nbus]: e, f, cos(theta), sin(theta)
-    double *iv;    // [ncase][nbus]: 1 / V
-    double *xg;    // [ncase][3 nbus]: right-hand side / solution, refined FP64 x, FP32 work
-    double *bmax;  // [ncase][16]: per-CTA mismatch maxima, [15] = solve status
-    pf_case_result *res;
-    int use_smem;
-};
-
-// One half-iteration's mismatch for case c on the C CTAs of its cluster: each
-// CTA owns a slice of buses, forms e + jf from V and the cached cos/sin of
-// theta, then (after a cluster barrier) the currents of its rows and writes
-// dP/V (which = 0, B' unknowns) or dQ/V (which = 1, B'' unknowns) into the
-// exchange vector in level order.  Returns the case maximum (cluster-uniform)
-// of |dP| over non-slack and |dQ| over PQ buses when `full`, else of the
-// half-iteration's own part only (|dP| or |dQ|): a lower bound of the full
-// maximum, so a partial maximum above the tolerance already decides "not
-// converged" and only one at or below it needs the full check.  Skipping the
-// other part saves FP64 work, which bounds batches on this part.
-template <int C>
-__device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which, double *red,
-                                   bool full) {
-    const DevNet &dn = a.dn;
-    const int nbus = dn.nbus;
-    const int slice = (nbus + C - 1) / C;
-    const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
-    const double *vm = a.vm + (long long)c * nbus;
-    double *e = a.ef + (long long)c * 4 * nbus;
-    double *f = e + nbus;
-    const double *cs = e + 2 * nbus;
-    const double *sn = e + 3 * nbus;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        e[i] = vm[i] * cs[i];
-        f[i] = vm[i] * sn[i];
-    }
-    cluster_sync<C>();
-    const int outage = a.dc.outage[c];
-    const int *nob = which == 0 ? a.m0.new_of_bus : a.m1.new_of_bus;
-    double *xg = a.xg + (long long)c * 3 * nbus;
-    const bool wantP = full || which == 0, wantQ = full || which == 1;
-    unsigned long long mx = 0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        double ir, ii;
-        bus_current(dn, i, outage, e, f, ir, ii);
-        const int t = dn.btype[i];
-        const long long idx = (long long)c * nbus + i;
-        double dP = 0.0, dQ = 0.0;
-        if (wantP && t != PF_BUS_SLACK) dP = a.dc.Psp[idx] - (e[i] * ir + f[i] * ii);
-        if (wantQ && t == PF_BUS_PQ) dQ = a.dc.Qsp[idx] - (f[i] * ir - e[i] * ii);
-        const unsigned long long kp = abs_key(dP), kq = abs_key(dQ);
-        mx = kp > mx ? kp : mx;
-        mx = kq > mx ? kq : mx;
-        const int k = nob[i];
-        if (k >= 0) xg[k] = (which == 0 ? dP : dQ) * a.iv[(long long)c * nbus + i];
-    }
-    mx = block_max_key(mx, red);
-    if (threadIdx.x == 0) a.bmax[(long long)c * 16 + rank] = __longlong_as_double(static_cast<long long>(mx));
-    cluster_sync<C>();
-    double m = 0.0;
-    for (int r = 0; r < C; r++) m = nan_max(m, a.bmax[(long long)c * 16 + r]);
-    return m;
-}
-
-// Low-rank outage correction of one case's solve (Woodbury): the outage
-// takes the branch's share U S U^T out of the base matrix A (U the unit
-// columns of the branch's two buses p0, p1 in level order, absent ones
-// skipped), so (A - U S U^T)^-1 b = y + Z K (U^T y) with y = A^-1 b, Z =
-// A^-1 U and K = (I - S U^T Z)^-1 S, both computed once per factorisation.
-template <class T>
-struct LowRank {
-    const T *Z = nullptr;     // [2][n] columns A^-1 e_p0, A^-1 e_p1 (null: no correction)
-    const double *K = nullptr;
-    int p0 = -1, p1 = -1;
-};
-
-template <class T, class X>
-__device__ void lowrank_correct(const LowRank<T> &lr, X *x, int n, double *red) {
-    if (!lr.Z) return;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double y0 = lr.p0 >= 0 ? double(x[lr.p0]) : 0.0, y1 = lr.p1 >= 0 ? double(x[lr.p1]) : 0.0;
-        red[0] = lr.K[0] * y0 + lr.K[1] * y1;
-        red[1] = lr.K[2] * y0 + lr.K[3] * y1;
-    }
-    __syncthreads();
-    const double s0 = red[0], s1 = red[1];
-    for (int r = threadIdx.x; r < n; r += blockDim.x)
-        x[r] = X(double(x[r]) + double(lr.Z[r]) * s0 + double(lr.Z[n + r]) * s1);
-    __syncthreads();
-}
-
-// Solves one matrix of case c in the cluster's CTA 0 (the others wait at the
-// following cluster barrier): the exchange vector is staged into shared
-// memory, solved with the TMA-staged sweeps and written back.  With an FP32
-// factor the solve is refined in FP64: x += solve32(r), r = b - A x with the
-// FP64 assembled A, until ||r||inf <= ir_tol ||b||inf or ir_max corrections
-// (the refined x lives in the second half of the exchange vector).
-template <class T>
-__device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T *xs,
-                            const DevMat &m, const T *F, const T *tv, const double *A, int c,
-                            double *red, int &ir_steps, const LowRank<T> &lr) {
-    const int nbus = a.dn.nbus;
-    double *xg = a.xg + (long long)c * 3 * nbus;
-    bool ok = true;
-    if constexpr (sizeof(T) == sizeof(double)) {
-        if (xs) {
-            for (int r = threadIdx.x; r < m.n; r += blockDim.x) xs[r] = T(xg[r]);
-            __syncthreads();
-            ok = block_solve<T, T>(R, stages, m, F, xs, a.spin, tv);
-            if (ok) lowrank_correct<T, T>(lr, xs, m.n, red);
-            for (int r = threadIdx.x; r < m.n; r += blockDim.x) xg[r] = double(xs[r]);
-        } else {
-            ok = block_solve<T, double>(R, stages, m, F, xg, a.spin, tv);
-            if (ok) lowrank_correct<T, double>(lr, xg, m.n, red);
-        }
-    } else {
-        double *x64 = xg + nbus;
-        T *xv = xs ? xs : reinterpret_cast<T *>(x64 + m.n);  // FP32 work vector
-        unsigned long long bk = 0;
-        for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
-            xv[r] = T(xg[r]);
-            const unsigned long long k = abs_key(xg[r]);
-            bk = k > bk ? k : bk;
-        }
-        const double bn = __longlong_as_double(static_cast<long long>(block_max_key(bk, red)));
-        for (int k = 0;; k++) {
-            ok = block_solve<T, T>(R, stages, m, F, xv, a.spin, tv);
-            if (!ok) break;
-            lowrank_correct<T, T>(lr, xv, m.n, red);
-            for (int r = threadIdx.x; r < m.n; r += blockDim.x)
-                x64[r] = (k == 0 ? 0.0 : x64[r]) + double(xv[r]);
-            __syncthreads();
-            if (k >= a.ir_max) break;
-            unsigned long long rk = 0;
-            for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
-                double s = xg[r] - A[r] * x64[r];
-                for (int e = m.Ap[r]; e < m.Ap[r + 1]; e++) s -= A[m.Apos[e]] * x64[m.Aj[e]];
-                xv[r] = T(s);
-                const unsigned long long k = abs_key(s);
-                rk = k > rk ? k : rk;
-            }
-            const double rn = __longlong_as_double(static_cast<long long>(block_max_key(rk, red)));
-            if (!(rn > a.ir_tol * bn) || !(rn > a.ir_abs)) break;
-            ir_steps++;
-        }
-        for (int r = threadIdx.x; r < m.n; r += blockDim.x) xg[r] = x64[r];
-    }
-    return ok;
-}
-
-// The whole fast-decoupled power flow of one case per cluster of C CTAs
-// (Section III): P half-iteration B' dtheta = dP / V, Q half-iteration
-// B'' dV = dQ / V, with the mismatch checked before every half-iteration.
-// With C = 1 every case is one independent block (batches); with C > 1 one
-// case spreads its FP64 mismatch over C SMs (single large cases).
-template <class T, int C>
-__device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char *smem_raw,
-                                          double *red, Ring &R, bool init_ring) {
-    const DevNet &dn = a.dn;
-    const int nbus = dn.nbus;
-    const int rank = C == 1 ? 0 : int(cluster_rank());
-    unsigned char *stages = smem_raw;
-    T *xs = a.use_smem ? reinterpret_cast<T *>(smem_raw + kStages * kStageBytes) : nullptr;
-    if (init_ring) ring_init(&R);
-    const int inst = a.dc.inst[c];
-    double *vm = a.vm + (long long)c * nbus;
-    double *va = a.va + (long long)c * nbus;
-    double *cs = a.ef + (long long)c * 4 * nbus + 2 * nbus;
-    double *sn = cs + nbus;
-    const double *xg = a.xg + (long long)c * 3 * nbus;
-    double *flag = a.bmax + (long long)c * 16 + 15;
-    const bool lowrank = a.Z0 != nullptr && inst > 0;
-    const int finst = lowrank ? 0 : inst;  // the instance whose factor the solves use
-    const T *F0 = static_cast<const T *>(a.F0) + (long long)finst * a.m0.stride;
-    const T *F1 = static_cast<const T *>(a.F1) + (long long)finst * a.m1.stride;
-    const T *TV0 = a.TV0 ? static_cast<const T *>(a.TV0) + (long long)finst * a.m0.tv_stride : nullptr;
-    const T *TV1 = a.TV1 ? static_cast<const T *>(a.TV1) + (long long)finst * a.m1.tv_stride : nullptr;
-    LowRank<T> lr0, lr1;
-    if (lowrank) {
-        const int e = a.dc.inst_outage[inst];
-        lr0.Z = static_cast<const T *>(a.Z0) + (long long)inst * 2 * a.m0.n;
-        lr0.K = a.K0 + 4LL * inst;
-        lr0.p0 = a.m0.br_slot[3 * e];
-        lr0.p1 = a.m0.br_slot[3 * e + 1];
-        lr1.Z = static_cast<const T *>(a.Z1) + (long long)inst * 2 * a.m1.n;
-        lr1.K = a.K1 + 4LL * inst;
-        lr1.p0 = a.m1.br_slot[3 * e];
-        lr1.p1 = a.m1.br_slot[3 * e + 1];
-    }
-    const double *A0 = a.A0 + (long long)inst * a.m0.stride;
-    const double *A1 = a.A1 + (long long)inst * a.m1.stride;
-    int ir_steps = 0;
-    const int slice = (nbus + C - 1) / C;
-    const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
-    int status = PF_ERR_NOT_CONVERGED;
-    if (a.fs0[finst] != PF_OK) status = a.fs0[finst];
-    else if (a.fs1[finst] != PF_OK) status = a.fs1[finst];
-    int iters = 0;
-    double mis = INFINITY;
-    double *iv = a.iv + (long long)c * nbus;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        if (a.flat) {
-            const int t = dn.btype[i];
-            vm[i] = (t == PF_BUS_PQ) ? 1.0 : dn.vset[i];
-            va[i] = (t == PF_BUS_SLACK) ? dn.va0[i] : 0.0;
-        }
-        sincos(va[i], &sn[i], &cs[i]);
-        iv[i] = 1.0 / vm[i];
-    }
-    cluster_sync<C>();
-    // cos/sin of the angles are rotated by each step (small_sincos) rather than
-    // re-evaluated, and each half-iteration evaluates only its own part of the
-    // mismatch; before a convergence decision the cos/sin are recomputed
-    // exactly and the full mismatch re-checked, so the decision is taken on
-    // both parts at the exact state
-    bool rotated = false;
-    auto exact_check = [&](int which) {
-        if (rotated)
-            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) sincos(va[i], &sn[i], &cs[i]);
-        rotated = false;
-        return cluster_mismatch<C>(a, c, rank, which, red, true);
-    };
-    if (status == PF_ERR_NOT_CONVERGED) {
-        for (int it = 0; it < a.max_iter; it++) {
-            mis = cluster_mismatch<C>(a, c, rank, 0, red, false);
-            if (mis <= a.tol) mis = exact_check(0);
-            if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
-            if (mis <= a.tol) { status = PF_OK; break; }
-            if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, TV0, A0, c, red, ir_steps, lr0);
-                if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
-            }
-            cluster_sync<C>();
-            if (*flag != 0.0) { status = PF_ERR_TIMEOUT; break; }
-            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-                const int k = a.m0.new_of_bus[i];
-                if (k >= 0) {
-                    const double d = xg[k];
-                    va[i] += d;
-                    if (fabs(d) <= kRotMax) {
-                        double sd, cd;
-                        small_sincos(d, &sd, &cd);
-                        const double c0 = cs[i], s0 = sn[i];
-                        cs[i] = c0 * cd - s0 * sd;
-                        sn[i] = s0 * cd + c0 * sd;
-                    } else {
-                        sincos(va[i], &sn[i], &cs[i]);
-                    }
-                }
-            }
-            rotated = true;
-            iters++;
-            mis = cluster_mismatch<C>(a, c, rank, 1, red, false);
-            if (mis <= a.tol) mis = exact_check(1);
-            if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
-            if (mis <= a.tol) { status = PF_OK; break; }
-            if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, TV1, A1, c, red, ir_steps, lr1);
-                if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
-            }
-            cluster_sync<C>();
-            if (*flag != 0.0) { status = PF_ERR_TIMEOUT; break; }
-            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-                const int k = a.m1.new_of_bus[i];
-                if (k >= 0) {
-                    vm[i] += xg[k];
-                    iv[i] = 1.0 / vm[i];
-                }
-            }
-            iters++;
-        }
-        if (status == PF_ERR_NOT_CONVERGED) {
-            mis = exact_check(0);
-            if (mis <= a.tol) status = PF_OK;
-        }
-    }
-    if (rank == 0 && threadIdx.x == 0) {
-        a.res[c].status = status;
-        a.res[c].iters = iters;
-        a.res[c].ir_steps = ir_steps;
-        a.res[c].method = PF_FDPF;
-        a.res[c].max_mismatch = mis;
-    }
-    cluster_sync<C>();
-}
-
-template <class T, int C>
-__global__ void __launch_bounds__(kRunThreads, C == 1 ? 2 : 1) k_fdpf(RunArgs a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double red[33];
-    __shared__ Ring R;
-    fdpf_case<T, C>(a, int(blockIdx.x) / C, smem_raw, red, R, true);
-}
-
-// Uneven multi-grid batch: one persistent launch over the grids of a pack,
-// each grid with its own network, symbolic layout and factors (args[g]).
-// Blocks take grids from a counter in the order given by order[] (largest
-// first); a grid's solve vector is in shared memory when it fits the
-// launch's reservation (args[g].use_smem), else in its global scratch.
-template <class T>
-__global__ void __launch_bounds__(kRunThreads, 1)
-    k_fdpf_pack(const RunArgs *args, const int *order, int ngrid, unsigned *counter) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double red[33];
-    __shared__ Ring R;
-    __shared__ int next;
-    // the staging ring is initialised once and its phases run on across the
-    // grids; after a wait that gave up (ring error) the block runs no more
-    // grids and reports those it takes as timed out
-    ring_init(&R);
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned q = atomicAdd(counter, 1u);
-            next = q < unsigned(ngrid) ? order[q] : -1;
-        }
-        __syncthreads();
-        const int g = next;
-        const bool broken = R.err != 0;
-        __syncthreads();
-        if (g < 0) break;
-        if (broken) {
-            if (threadIdx.x == 0) {
-                args[g].res[0].status = PF_ERR_TIMEOUT;
-                args[g].res[0].iters = 0;
-                args[g].res[0].ir_steps = 0;
-                args[g].res[0].method = PF_FDPF;
-                args[g].res[0].max_mismatch = INFINITY;
-            }
-            continue;
-        }
-        fdpf_case<T, 1>(args[g], 0, smem_raw, red, R, false);
-        __syncthreads();
-    }
-}
-
 int grid_for(long long total, int threads) {
     long long b = (total + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > 65535LL * 16) b = 65535LL * 16;
     return int(b);
-}
-
-template <class T, int C>
-cudaError_t launch_fdpf_t(const RunArgs &a, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_fdpf<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(a.dc.ncase) * C);
-    cfg.blockDim = dim3(kRunThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    int na = 0;
-    if (C > 1) {
-        if (C > 8) {
-            e = cudaFuncSetAttribute(k_fdpf<T, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            if (e != cudaSuccess) return e;
-        }
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        na = 1;
-    }
-    cfg.attrs = attr;
-    cfg.numAttrs = na;
-    return cudaLaunchKernelEx(&cfg, k_fdpf<T, C>, a);
 }
 
 }  // namespace
@@ -1329,7 +964,8 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
         const size_t tsmem = elt * (size_t(m.ft_ne) + 2 * size_t(m.nt) + size_t(m.ft_ng)) +
                              sizeof(int2) * 2 * size_t(m.ft_tmax > 0 ? m.ft_tmax : 0) +
                              sizeof(int4) * 2 * (size_t(m.ft_kmax) + size_t(m.ntl));
-        const bool tail = fs.tail && m.ft_ng > 0 && m.ft_tmax >= 0 && tsmem + 1024 <= fs.smem_optin;
+        const bool tail = fs.tail && m.ft_ng > 0 && m.ft_tmax >= 0 && fs.partg &&
+                          tsmem + 1024 <= fs.smem_optin;
         const int ncols = tail ? m.t0 : m.n;
         const int per_sm = fs.blocks_per_sm > 0 && fs.blocks_per_sm < 2 ? fs.blocks_per_sm : 2;  // resident blocks per SM (registers)
         long long blocks = ((long long)ncols * ninst + kDepThreads / 32 - 1) / (kDepThreads / 32);
@@ -1341,20 +977,24 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
                 k_factor_dep<double><<<int(blocks), kDepThreads, 0, s>>>(m, A, static_cast<double *>(F),
                                                                           fstatus, ninst, fs, ncols);
             if (tail) {
+                k_factor_tail_pre<double><<<dim3(unsigned((m.ft_ng + 7) / 8), unsigned(ninst)), 256, 0, s>>>(
+                    m, A, static_cast<const double *>(F), static_cast<double *>(fs.partg));
                 e = cudaFuncSetAttribute(k_factor_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
                 if (e == cudaSuccess)
-                    k_factor_tail<double><<<ninst, kFactorThreads, tsmem, s>>>(m, A, static_cast<double *>(F),
-                                                                               fstatus, fs.amax);
+                    k_factor_tail<double><<<ninst, kFactorThreads, tsmem, s>>>(
+                        m, static_cast<const double *>(fs.partg), static_cast<double *>(F), fstatus, fs.amax);
             }
         } else {
             if (ncols > 0)
                 k_factor_dep<float><<<int(blocks), kDepThreads, 0, s>>>(m, A, static_cast<float *>(F),
                                                                          fstatus, ninst, fs, ncols);
             if (tail) {
+                k_factor_tail_pre<float><<<dim3(unsigned((m.ft_ng + 7) / 8), unsigned(ninst)), 256, 0, s>>>(
+                    m, A, static_cast<const float *>(F), static_cast<float *>(fs.partg));
                 e = cudaFuncSetAttribute(k_factor_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
                 if (e == cudaSuccess)
-                    k_factor_tail<float><<<ninst, kFactorThreads, tsmem, s>>>(m, A, static_cast<float *>(F),
-                                                                              fstatus, fs.amax);
+                    k_factor_tail<float><<<ninst, kFactorThreads, tsmem, s>>>(
+                        m, static_cast<const float *>(fs.partg), static_cast<float *>(F), fstatus, fs.amax);
             }
         }
         return e != cudaSuccess ? e : cudaGetLastError();
@@ -1437,186 +1077,6 @@ cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *
     dim3 grid((dn.nbus + 255) / 256, ncase);
     k_mismatch_rows<<<grid, 256, 0, s>>>(dn, dc, ef, dp, dq, maxmis);
     return cudaGetLastError();
-}
-
-// Cluster size of the power-flow kernel: a case spreads its nodal work over
-// 16 (or 8) SMs when the batch is too small to fill the GPU with one block per
-// case and such clusters can be resident; otherwise one block per case.
-cudaError_t launch_fdpf_pack(const RunArgs *args_dev, const int *order_dev, int ngrid,
-                             unsigned *counter_dev, int prec, size_t smem, int nsm, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(counter_dev, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    const int blocks = ngrid < nsm ? ngrid : nsm;
-    if (prec == PF_FP64) {
-        e = cudaFuncSetAttribute(k_fdpf_pack<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        k_fdpf_pack<double><<<blocks, kRunThreads, smem, s>>>(args_dev, order_dev, ngrid, counter_dev);
-    } else {
-        e = cudaFuncSetAttribute(k_fdpf_pack<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        k_fdpf_pack<float><<<blocks, kRunThreads, smem, s>>>(args_dev, order_dev, ngrid, counter_dev);
-    }
-    return cudaGetLastError();
-}
-
-// Fills the run arguments of one grid of a pack (the single-case form of
-// launch_fdpf's arguments); use_smem is decided by the caller.
-void fill_run_args(RunArgs &a, const DevNet &dn, const DevCases &dc, const DevMat *m, const void *F0,
-                   const void *F1, const void *TV0, const void *TV1, const double *A0,
-                   const double *A1, const int *fstat0, const int *fstat1, const pf_run_opts &o,
-                   double *vm, double *va, double *ef, double *iv, double *xg, double *bmax,
-                   pf_case_result *res) {
-    a.TV0 = m[0].npf2 > 0 ? TV0 : nullptr;
-    a.TV1 = m[1].npf2 > 0 ? TV1 : nullptr;
-    a.Z0 = a.Z1 = nullptr;
-    a.K0 = a.K1 = nullptr;
-    a.iv = iv;
-    a.A0 = A0;
-    a.A1 = A1;
-    a.ir_max = o.ir_max;
-    a.ir_tol = o.ir_tol;
-    a.ir_abs = o.ir_abs > 0 ? o.ir_abs : 0.01 * o.tol;
-    a.dn = dn;
-    a.dc = dc;
-    a.m0 = m[0];
-    a.m1 = m[1];
-    a.F0 = F0;
-    a.F1 = F1;
-    a.fs0 = fstat0;
-    a.fs1 = fstat1;
-    a.tol = o.tol;
-    a.max_iter = o.max_iter;
-    a.flat = o.flat_start;
-    a.spin = o.spin_limit > 0 ? unsigned(o.spin_limit) : kDefaultSpin;
-    a.vm = vm;
-    a.va = va;
-    a.ef = ef;
-    a.xg = xg;
-    a.bmax = bmax;
-    a.res = res;
-    a.use_smem = 0;
-}
-
-size_t run_args_bytes() { return sizeof(RunArgs); }
-
-cudaError_t launch_pack(const PackGrid *grids, int ngrid, int prec, const pf_run_opts &o,
-                        const int *order_host, void *args_dev, int *order_dev, unsigned *counter_dev,
-                        size_t smem_optin, int nsm, cudaStream_t s) {
-    // the launch reserves shared memory for the largest grid whose solve
-    // vector fits; larger grids keep theirs in global scratch
-    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
-    const size_t ring = size_t(kStages) * kStageBytes;
-    int ns = 0;
-    for (int g = 0; g < ngrid; g++) {
-        const int nm = grids[g].m[0].n > grids[g].m[1].n ? grids[g].m[0].n : grids[g].m[1].n;
-        if (ring + elt * size_t(nm) + 2048 <= smem_optin && nm > ns) ns = nm;
-    }
-    std::vector<RunArgs> A(static_cast<size_t>(ngrid));
-    for (int g = 0; g < ngrid; g++) {
-        const PackGrid &p = grids[g];
-        fill_run_args(A[g], p.dn, p.dc, p.m, p.F0, p.F1, p.TV0, p.TV1, p.A0, p.A1, p.fs0, p.fs1, o,
-                      p.vm, p.va, p.ef, p.iv, p.xg, p.bmax, p.res);
-        const int nm = p.m[0].n > p.m[1].n ? p.m[0].n : p.m[1].n;
-        A[g].use_smem = nm <= ns;
-    }
-    cudaError_t e = cudaMemcpyAsync(args_dev, A.data(), sizeof(RunArgs) * size_t(ngrid),
-                                    cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(order_dev, order_host, sizeof(int) * size_t(ngrid), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // A is released on return
-    if (e != cudaSuccess) return e;
-    return launch_fdpf_pack(static_cast<const RunArgs *>(args_dev), order_dev, ngrid, counter_dev, prec,
-                            ring + elt * size_t(ns), nsm, s);
-}
-
-int fdpf_cluster_size(int ncase, int num_sms, int prec, size_t smem_optin, int nmax) {
-    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
-    size_t smem = size_t(kStages) * kStageBytes + elt * size_t(nmax);
-    if (smem + 2048 > smem_optin) smem = size_t(kStages) * kStageBytes;
-    for (int C : {16, 8}) {
-        if (ncase * C > num_sms) continue;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(unsigned(C));
-        cfg.blockDim = dim3(kRunThreads);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        cudaError_t e;
-        if (prec == PF_FP64) {
-            auto *k = (C == 16) ? k_fdpf<double, 16> : k_fdpf<double, 8>;
-            if (C == 16) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-            e = cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg);
-        } else {
-            auto *k = (C == 16) ? k_fdpf<float, 16> : k_fdpf<float, 8>;
-            if (C == 16) cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-            e = cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg);
-        }
-        if (e == cudaSuccess && nclusters >= ncase) return C;
-        cudaGetLastError();
-    }
-    return 1;
-}
-
-cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
-                        const void *F0, const void *F1, const void *TV0, const void *TV1,
-                        const double *A0, const double *A1, const int *fstat0, const int *fstat1,
-                        const pf_run_opts &o, double *vm, double *va, double *ef, double *iv,
-                        double *xg, double *bmax, pf_case_result *res, size_t smem_optin,
-                        int cluster, cudaStream_t s, const void *Z0, const void *Z1, const double *K0,
-                        const double *K1) {
-    RunArgs a;
-    a.Z0 = Z0;
-    a.Z1 = Z1;
-    a.K0 = K0;
-    a.K1 = K1;
-    a.TV0 = m[0].npf2 > 0 ? TV0 : nullptr;
-    a.TV1 = m[1].npf2 > 0 ? TV1 : nullptr;
-    a.iv = iv;
-    a.A0 = A0;
-    a.A1 = A1;
-    a.ir_max = o.ir_max;
-    a.ir_tol = o.ir_tol;
-    a.ir_abs = o.ir_abs > 0 ? o.ir_abs : 0.01 * o.tol;
-    a.dn = dn;
-    a.dc = dc;
-    a.m0 = m[0];
-    a.m1 = m[1];
-    a.F0 = F0;
-    a.F1 = F1;
-    a.fs0 = fstat0;
-    a.fs1 = fstat1;
-    a.tol = o.tol;
-    a.max_iter = o.max_iter;
-    a.flat = o.flat_start;
-    a.spin = o.spin_limit > 0 ? unsigned(o.spin_limit) : kDefaultSpin;
-    a.vm = vm;
-    a.va = va;
-    a.ef = ef;
-    a.xg = xg;
-    a.bmax = bmax;
-    a.res = res;
-    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
-    const int nmax = m[0].n > m[1].n ? m[0].n : m[1].n;
-    const size_t ring = size_t(kStages) * kStageBytes;
-    size_t smem = ring + elt * size_t(nmax);
-    a.use_smem = smem + 2048 <= smem_optin;
-    if (!a.use_smem) smem = ring;
-    if (prec == PF_FP64) {
-        if (cluster >= 16) return launch_fdpf_t<double, 16>(a, smem, s);
-        if (cluster >= 8) return launch_fdpf_t<double, 8>(a, smem, s);
-        return launch_fdpf_t<double, 1>(a, smem, s);
-    }
-    if (cluster >= 16) return launch_fdpf_t<float, 16>(a, smem, s);
-    if (cluster >= 8) return launch_fdpf_t<float, 8>(a, smem, s);
-    return launch_fdpf_t<float, 1>(a, smem, s);
 }
 
 }  // namespace gbpf

@@ -173,7 +173,10 @@ def test_tail_factor_tables_vs_oracle(lib, oracle, cfg):
         seen_entry = np.zeros(sz["ne"], np.int32)
         for li, (ncol, ntgt, nterm) in enumerate(ref):
             kb, ke, tb, te = tlev[2 * li]
-            cb, ce = tlev[2 * li + 1][:2]
+            cb, ce, G = tlev[2 * li + 1][:3]
+            # lanes per target: about four terms per lane, a power of two up to 32
+            most = max(int(tinfo[k][1] - tinfo[k][0]) for k in range(kb, ke)) if ke > kb else 0
+            assert G in (1, 2, 4, 8, 16, 32) and (G == 32 or most <= 4 * G) and (G == 1 or most > 2 * G)
             assert (ke - kb, te - tb, ce - cb) == (ntgt, nterm, ncol), li
             if li + 1 < len(ref):
                 assert tlev[2 * li + 2][0] == ke and tlev[2 * li + 2][2] == te
