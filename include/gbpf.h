@@ -103,11 +103,19 @@ typedef struct {
     int32_t spin_limit; /* bound on every device-side wait (0 = library default) */
     int32_t engine;     /* PF_ENGINE_AUTO, PF_ENGINE_BLOCK, PF_ENGINE_LANES or
                            PF_ENGINE_CLUSTER (FDPF only) */
-    int32_t fallback;   /* FDPF only: 1 = cases the fast decoupled iteration leaves
-                           unconverged (PF_ERR_NOT_CONVERGED, PF_ERR_NONFINITE) are
-                           re-run by Newton-Raphson from a flat start in the same
-                           call (at most 30 Newton steps, same precision and
-                           tolerance); their results then report method PF_NR */
+    int32_t fallback;   /* FDPF only (Section III, FDPF first, then NR): 1 = a case
+                           the fast decoupled iteration leaves unconverged
+                           (PF_ERR_NOT_CONVERGED, PF_ERR_NONFINITE) switches to
+                           Newton-Raphson from a flat start on the device, inside
+                           the same iteration launch (at most 30 Newton steps,
+                           same precision and tolerance; no host synchronisation,
+                           converged cases are not re-run); its result then
+                           reports method PF_NR.  The BLOCK and CLUSTER engines
+                           carry it (a run that asks for it does not use LANES);
+                           ignored where the Newton-Raphson factor scratch does
+                           not fit shared memory (the grid's Newton-Raphson runs
+                           would not launch either).  Allocates the Newton-Raphson
+                           storage on first use. */
 } pf_run_opts;
 
 /* Engines of pf_run_to_tol.  BLOCK: one thread block (or, for a few large

@@ -26,7 +26,7 @@
 // walking the column's ancestor path with the recurrence
 // w_i = -sum_k L_ik w_k), and gathered with the factor's values into the
 // CTAs' packed value arrays by k_cl_values.
-#include "gbpf_device.cuh"
+#include "gbpf_nr.cuh"
 
 namespace gbpf {
 
@@ -153,6 +153,12 @@ struct ClRun {
     double *iv;    // [nbus]: 1 / V
     double *bmax;  // [16]: per-CTA mismatch maxima
     pf_case_result *res;
+    // FDPF -> NR fallback (Section III): an unconverged or non-finite end
+    // restarts the case from a flat start under Newton-Raphson (nr) on the
+    // same cluster, its shared memory reused for the staging ring and the
+    // factor scratch; the result then reports method PF_NR
+    int fallback;
+    NrArgs nr;
 };
 
 // Shared-memory program of one matrix in one CTA (byte offsets of the
@@ -303,9 +309,10 @@ __device__ double cl_mismatch(const ClRun &a, int rank, int which, const uint32_
 }
 
 template <int C>
-__global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
+__global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(const __grid_constant__ ClRun a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[33];
+    __shared__ Ring R;  // the fallback's staging ring
     __shared__ uint32_t xbase[2 * C];  // vector region of matrix m in CTA r: xbase[m * C + r]
     __shared__ int nsteps[2];
     __shared__ unsigned long long mkey[2];  // this CTA's mismatch maximum (key) per half-iteration kind
@@ -348,6 +355,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
         const int vb = m.vptr[rank], ve = m.vptr[rank + 1];
         for (int v = threadIdx.x; v < ve - vb; v += blockDim.x) S[w].vals[v] = m.vals[vb + v];
     }
+    if (a.fallback) ring_init(&R);
     // every CTA of the cluster has started (its shared memory exists) before
     // anyone writes to it
     cl_barrier();
@@ -433,6 +441,11 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(ClRun a) {
             if (mis <= a.tol) status = PF_OK;
         }
     }
+    if (a.fallback && (status == PF_ERR_NOT_CONVERGED || status == PF_ERR_NONFINITE)) {
+        cl_barrier();  // no CTA still reads or writes another's programs
+        nr_fallback<double, C>(a.nr, 0, rank, smem_raw, red, &R);  // writes the case's result
+        return;
+    }
     if (rank == 0 && threadIdx.x == 0) {
         a.res[0].status = status;
         a.res[0].iters = iters;
@@ -474,7 +487,7 @@ cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0
 cudaError_t launch_fdpf_cl(const DevNet &dn, const DevCases &dc, const ClMat &m0, const ClMat &m1,
                            const int *fs0, const int *fs1, const pf_run_opts &o, double *vm, double *va,
                            double *ef, double *iv, double *bmax, pf_case_result *res, size_t smem,
-                           cudaStream_t s) {
+                           cudaStream_t s, const NrLaunch *fb, size_t smem_optin) {
     ClRun a;
     a.dn = dn;
     a.dc = dc;
@@ -491,6 +504,14 @@ cudaError_t launch_fdpf_cl(const DevNet &dn, const DevCases &dc, const ClMat &m0
     a.iv = iv;
     a.bmax = bmax;
     a.res = res;
+    a.fallback = 0;
+    if (fb) {  // the Newton-Raphson fallback's layout, when it fits
+        const size_t need = nr_args_within(*fb, smem, a.nr);
+        if (need + 4096 <= smem_optin && (need == smem || fdpf_cl_fits(need))) {
+            smem = need;
+            a.fallback = 1;
+        }
+    }
     cudaError_t e = cudaFuncSetAttribute(k_fdpf_cl<kClCtas>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return e;

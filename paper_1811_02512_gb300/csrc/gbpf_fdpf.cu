@@ -52,6 +52,7 @@ void fill_run_args(RunArgs &a, const DevNet &dn, const DevCases &dc, const DevMa
     a.bmax = bmax;
     a.res = res;
     a.use_smem = 0;
+    a.fallback = 0;
 }
 
 size_t run_args_bytes() { return sizeof(RunArgs); }
@@ -107,7 +108,7 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         const pf_run_opts &o, double *vm, double *va, double *ef, double *iv,
                         double *xg, double *bmax, pf_case_result *res, size_t smem_optin,
                         int cluster, cudaStream_t s, const void *Z0, const void *Z1, const double *K0,
-                        const double *K1) {
+                        const double *K1, const NrLaunch *fb) {
     RunArgs a;
     a.Z0 = Z0;
     a.Z1 = Z1;
@@ -145,6 +146,14 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
     size_t smem = ring + elt * size_t(nmax);
     a.use_smem = smem + 2048 <= smem_optin;
     if (!a.use_smem) smem = ring;
+    a.fallback = 0;
+    if (fb) {  // the Newton-Raphson fallback's factor scratch, when it fits
+        const size_t need = nr_args_within(*fb, smem, a.nr);
+        if (need + 2048 <= smem_optin) {
+            smem = need;
+            a.fallback = 1;
+        }
+    }
     return prec == PF_FP64 ? fdpf_run_f64(a, smem, cluster, s) : fdpf_run_f32(a, smem, cluster, s);
 }
 

@@ -13,7 +13,7 @@
 #include <cstdint>
 #include <vector>
 
-#include "gbpf_device.cuh"
+#include "gbpf_nr.cuh"
 
 namespace gbpf {
 
@@ -42,6 +42,11 @@ struct RunArgs {
     double *bmax;  // [ncase][16]: per-CTA mismatch maxima, [15] = solve status
     pf_case_result *res;
     int use_smem;
+    // FDPF -> NR fallback (Section III): a case that ends unconverged or
+    // non-finite restarts from a flat start under Newton-Raphson (nr) in the
+    // same launch; its result then reports method PF_NR
+    int fallback;
+    NrArgs nr;
 };
 
 
@@ -317,6 +322,10 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
             if (mis <= a.tol) status = PF_OK;
         }
     }
+    if (a.fallback && (status == PF_ERR_NOT_CONVERGED || status == PF_ERR_NONFINITE)) {
+        nr_fallback<T, C>(a.nr, c, rank, smem_raw, red, &R);  // writes the case's result
+        return;
+    }
     if (rank == 0 && threadIdx.x == 0) {
         a.res[c].status = status;
         a.res[c].iters = iters;
@@ -328,7 +337,7 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
 }
 
 template <class T, int C>
-__global__ void __launch_bounds__(kRunThreads, C == 1 ? 2 : 1) k_fdpf(RunArgs a) {
+__global__ void __launch_bounds__(kRunThreads, C == 1 ? 2 : 1) k_fdpf(const __grid_constant__ RunArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[33];
     __shared__ Ring R;

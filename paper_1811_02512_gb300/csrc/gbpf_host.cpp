@@ -114,6 +114,11 @@ cudaError_t counted(pf_ctx *ctx, int kind, int nlaunch, cudaStream_t s, F launch
 // clears the flags itself (a memset node) and always publishes this epoch,
 // which direct factorisations never reach (they restart at 1 below it).
 constexpr unsigned kGraphEpoch = 0xFFFFFFF0u;
+// The same for the Jacobian flags of the Newton-Raphson fallback inside a
+// graph: its factorisations publish kNrGraphEpoch + 1, + 2, ... (direct
+// launches stay below 0xF0000000 + their count, nr_epochs).
+constexpr unsigned kNrGraphEpoch = 0xFFFF0000u;
+constexpr int kFallbackIters = 30;  // Newton-Raphson steps of the FDPF -> NR fallback
 
 void drain_events(pf_ctx *ctx, KernelStat &k) {
     for (auto &pr : k.pending) {
@@ -1887,58 +1892,13 @@ pf_status pf_mismatch(pf_ctx *ctx, const double *vm_dev, const double *va_dev, d
 namespace {
 pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
                    pf_case_result *res_host, void *stream);
-
-// FDPF -> NR fallback: the cases left unconverged by the fast decoupled
-// iteration restart from a flat start under Newton-Raphson; the others keep
-// their results (their NR run stops at step 0, already within tolerance).
-pf_status nr_fallback(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
-                      pf_case_result *res_host, void *stream) {
-    const int ncase = ctx->dc.ncase;
-    std::vector<int> mask(static_cast<size_t>(ncase), 0);
-    bool any = false;
-    for (int c = 0; c < ncase; c++)
-        if (res_host[c].status == PF_ERR_NOT_CONVERGED || res_host[c].status == PF_ERR_NONFINITE) {
-            mask[c] = 1;
-            any = true;
-        }
-    if (!any) return PF_OK;
-    Workspace &w = ctx->ws;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (!w.fbmask) TRY(dalloc(ctx, &w.fbmask, size_t(ncase)));
-    cudaError_t e = cudaMemcpyAsync(w.fbmask, mask.data(), sizeof(int) * size_t(ncase), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_reset_flat(ctx->dn, ncase, w.fbmask, vm_dev, va_dev, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // mask is released on return
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "fallback reset");
-    pf_run_opts o = *opts;
-    o.method = PF_NR;
-    o.max_iter = 30;
-    o.flat_start = 0;
-    o.fallback = 0;
-    std::vector<pf_case_result> nr(static_cast<size_t>(ncase));
-    const pf_status st = run_once(ctx, &o, vm_dev, va_dev, nr.data(), stream);
-    if (st != PF_OK && st != PF_ERR_NOT_CONVERGED && st != PF_ERR_NONFINITE && st != PF_ERR_SINGULAR &&
-        st != PF_ERR_TIMEOUT)
-        return st;
-    for (int c = 0; c < ncase; c++)
-        if (mask[c]) res_host[c] = nr[size_t(c)];
-    return PF_OK;
-}
 }  // namespace
 
 extern "C" {
 
 pf_status pf_run_to_tol(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev,
                         pf_case_result *res_host, void *stream) {
-    pf_status st = run_once(ctx, opts, vm_dev, va_dev, res_host, stream);
-    if (!opts || opts->method != PF_FDPF || !opts->fallback) return st;
-    if (st != PF_ERR_NOT_CONVERGED && st != PF_ERR_NONFINITE && st != PF_ERR_SINGULAR && st != PF_ERR_TIMEOUT)
-        return st;  // converged, or no per-case results to fall back from
-    TRY(nr_fallback(ctx, opts, vm_dev, va_dev, res_host, stream));
-    for (int c = 0; c < ctx->dc.ncase; c++)
-        if (res_host[c].status != PF_OK)
-            return fail(ctx, pf_status(res_host[c].status), "case %d: status %d after %d iterations (%s)", c,
-                        res_host[c].status, res_host[c].iters, res_host[c].method == PF_NR ? "NR" : "FDPF");
-    return PF_OK;
+    return run_once(ctx, opts, vm_dev, va_dev, res_host, stream);
 }
 
 }  // extern "C"
@@ -1953,6 +1913,29 @@ pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doubl
     Workspace &w = ctx->ws;
     const int prec = opts->precision;
     TRY(assemble_ybus(ctx, s));
+    // FDPF -> NR fallback (Section III): unconverged cases switch to
+    // Newton-Raphson from a flat start inside the iteration launch
+    NrLaunch fbl;
+    const NrLaunch *fb = nullptr;
+    if (opts->fallback) {
+        TRY(ensure_nr_storage(ctx, prec));
+        fbl = nr_launch(ctx, prec);
+        fbl.o = *opts;
+        fbl.o.method = PF_NR;
+        fbl.o.max_iter = kFallbackIters;
+        fbl.o.flat_start = 1;
+        fbl.vm = vm_dev;
+        fbl.va = va_dev;
+        if (ctx->graph_capturing) {  // every replay clears the flags and counts from kNrGraphEpoch
+            cudaError_t e = cudaMemsetAsync(
+                w.jdone, 0, size_t(ctx->dc.ncase) * size_t(std::max(1, ctx->dm[0].n)) * sizeof(unsigned), s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "fallback flags");
+            fbl.epoch0 = kNrGraphEpoch;
+        } else {
+            fbl.epoch0 = nr_epochs(ctx, unsigned(kFallbackIters) + 2u, s);
+        }
+        fb = &fbl;
+    }
     if (engine == PF_ENGINE_CLUSTER) {
         TRY(ensure_cluster(ctx));
         TRY(factor_both(ctx, prec, s, false));
@@ -1963,7 +1946,7 @@ pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doubl
         e = counted(ctx, PF_K_RUN, 1, s, [&] {
             return launch_fdpf_cl(ctx->dn, ctx->dc, ctx->cl[0], ctx->cl[1], w.fstatus[0][prec],
                                   w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.iv, w.bmax, w.res,
-                                  ctx->cl_smem, s);
+                                  ctx->cl_smem, s, fb, ctx->smem_optin);
         });
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster fdpf launch");
         return PF_OK;
@@ -1988,7 +1971,7 @@ pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doubl
                            w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.iv, w.vec, w.bmax, w.res,
                            ctx->smem_optin, cl, s, lowrank ? w.LZ[0][prec] : nullptr,
                            lowrank ? w.LZ[1][prec] : nullptr, lowrank ? w.LK[0] : nullptr,
-                           lowrank ? w.LK[1] : nullptr);
+                           lowrank ? w.LK[1] : nullptr, fb);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
     return PF_OK;
@@ -2115,7 +2098,8 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
     }
     Workspace &w = ctx->ws;
     const int nmax = std::max(ctx->dm[0].n, ctx->dm[1].n);
-    const bool lanes_ok = opts->method == PF_FDPF && lane_width(nmax, prec, ctx->smem_optin) > 0;
+    // the lane engine has no Newton-Raphson fallback: runs that ask for it use the others
+    const bool lanes_ok = opts->method == PF_FDPF && !opts->fallback && lane_width(nmax, prec, ctx->smem_optin) > 0;
     const int want = opts->engine != PF_ENGINE_AUTO ? opts->engine : ctx->tune.engine;
     const bool use_cluster = want == PF_ENGINE_CLUSTER && cluster_applies(ctx, opts);
     const int engine = use_cluster ? PF_ENGINE_CLUSTER
@@ -2164,8 +2148,8 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf run");
     for (int c = 0; c < ctx->dc.ncase; c++)
         if (res_host[c].status != PF_OK)
-            return fail(ctx, pf_status(res_host[c].status), "case %d: status %d after %d iterations",
-                        c, res_host[c].status, res_host[c].iters);
+            return fail(ctx, pf_status(res_host[c].status), "case %d: status %d after %d iterations (%s)",
+                        c, res_host[c].status, res_host[c].iters, res_host[c].method == PF_NR ? "NR" : "FDPF");
     return PF_OK;
 }
 

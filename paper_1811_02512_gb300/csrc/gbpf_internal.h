@@ -305,7 +305,6 @@ struct Workspace {
     unsigned *jdone = nullptr;   // [ncase][n] Jacobian column done flags (epochs)
     unsigned *jsync = nullptr;   // [ncase][2]
     unsigned jepoch = 0;         // last epoch handed to a launch
-    int *fbmask = nullptr;       // [ncase] cases re-run by the NR fallback
     LaneSet lanes;
 };
 
@@ -372,8 +371,6 @@ cudaError_t launch_assemble_slots(const DevNet &dn, const DevCases &dc, const De
                                   double *A, cudaStream_t s);
 cudaError_t launch_branch_flows(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
                                 int ncase, double *flows, double *loss, cudaStream_t s);
-cudaError_t launch_reset_flat(const DevNet &dn, int ncase, const int *mask, double *vm, double *va,
-                              cudaStream_t s);
 struct FactorSync {
     unsigned *done = nullptr;  // [ninst][n]
     unsigned *sync = nullptr;  // [0] column counter, [1] abort flag
@@ -422,6 +419,9 @@ cudaError_t launch_selftest_sweep(const DevMat &m, int prec, const void *F, cons
 cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
                             double *dp, double *dq, double *maxmis, double *ef, int ncase,
                             cudaStream_t s);
+struct NrLaunch;
+// fb (optional): the Newton-Raphson launch that unconverged cases fall back
+// to inside the same launch (ignored when its factor scratch does not fit).
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
                         const void *F0, const void *F1, const void *TV0, const void *TV1,
                         const double *A0, const double *A1,
@@ -429,7 +429,7 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         double *va, double *ef, double *iv, double *xg, double *bmax,
                         pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s,
                         const void *Z0 = nullptr, const void *Z1 = nullptr, const double *K0 = nullptr,
-                        const double *K1 = nullptr);
+                        const double *K1 = nullptr, const NrLaunch *fb = nullptr);
 // Z = A^-1 U and K = (I - S U^T Z)^-1 S of every outage instance of matrix
 // `which` from the base factor F (instance 0): the low-rank form of the
 // outage cases.  gvec: [2 (ninst - 1)][n] scratch of the factor type.
@@ -511,7 +511,7 @@ cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0
 cudaError_t launch_fdpf_cl(const DevNet &dn, const DevCases &dc, const ClMat &m0, const ClMat &m1,
                            const int *fs0, const int *fs1, const pf_run_opts &o, double *vm, double *va,
                            double *ef, double *iv, double *bmax, pf_case_result *res, size_t smem,
-                           cudaStream_t s);
+                           cudaStream_t s, const NrLaunch *fb = nullptr, size_t smem_optin = 0);
 bool fdpf_cl_fits(size_t smem);
 
 cudaError_t launch_objective(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,

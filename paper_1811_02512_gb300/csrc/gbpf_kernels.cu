@@ -651,20 +651,6 @@ __global__ void k_branch_flows(DevNet dn, DevCases dc, const double *vm, const d
     }
 }
 
-// Flat start (V = 1 at PQ buses, set-point elsewhere; angle 0 but the
-// slack's) for the cases with mask[c] != 0, the others untouched.
-__global__ void k_reset_flat(DevNet dn, int ncase, const int *mask, double *vm, double *va) {
-    const long long total = (long long)ncase * dn.nbus;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int c = int(idx / dn.nbus), i = int(idx - (long long)c * dn.nbus);
-        if (!mask[c]) continue;
-        const int t = dn.btype[i];
-        vm[idx] = t == PF_BUS_PQ ? 1.0 : dn.vset[i];
-        va[idx] = t == PF_BUS_SLACK ? dn.va0[i] : 0.0;
-    }
-}
-
 // Total active loss of case c (block per case, fixed summation order).
 __global__ void k_case_loss(DevNet dn, const double *vm, const double *flows, double *loss) {
     __shared__ double red[32];
@@ -887,12 +873,6 @@ cudaError_t launch_lowrank(const DevMat &m, const DevNet &dn, const DevCases &dc
                                                                static_cast<float *>(gvec), use_smem, status);
         k_lowrank_k<float><<<(dc.ninst + 127) / 128, 128, 0, s>>>(m, dn, dc, which, static_cast<const float *>(Z), Kd);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reset_flat(const DevNet &dn, int ncase, const int *mask, double *vm, double *va,
-                              cudaStream_t s) {
-    k_reset_flat<<<grid_for((long long)ncase * dn.nbus, 256), 256, 0, s>>>(dn, ncase, mask, vm, va);
     return cudaGetLastError();
 }
 

@@ -483,6 +483,102 @@ def test_fdpf_nr_fallback(oracle):
     g.close()
 
 
+# Load levels of the 120-bus grid: at 1.0 and 2.0 times the nominal loads the
+# fast decoupled iteration reaches 1e-10 in 18 and 40 half-iterations, at 2.4
+# it is still at 2e-5 after 60 while Newton-Raphson converges in 7 steps
+# (checked on the oracle).
+MIXED_LOADS = (1.0, 2.4, 2.0, 2.4)
+
+
+def _mixed_batch(base):
+    return np.stack([np.full(base.n, s) for s in MIXED_LOADS])
+
+
+def _run_launches(g):
+    return gbpf.pf_get_profile(g.ctx, gbpf.PF_K_RUN)[0]
+
+
+@pytest.mark.parametrize("prec", [gbpf.PF_FP64, gbpf.PF_FP32])
+@pytest.mark.parametrize("cluster", [1, 16])
+def test_fdpf_nr_fallback_in_launch(oracle, prec, cluster):
+    """FDPF -> NR inside the iteration launch (Section III): in a batch whose
+    heavy-load cases the fast decoupled iteration leaves unconverged, those
+    cases (and only those) switch to Newton-Raphson from a flat start within
+    the same launch -- one iteration launch per run, no second one -- and
+    report method PF_NR; the others keep their FDPF results.  Every case
+    matches the oracle's Newton-Raphson solution of its own loading.  Direct
+    runs, a capture and graph replays give bit-identical results."""
+    base = gridgen.config(0)
+    ls = _mixed_batch(base)
+    ncase = ls.shape[0]
+    refs = []
+    for c in range(ncase):
+        cc = base.copy()
+        cc.pd = cc.pd * ls[c]
+        cc.qd = cc.qd * ls[c]
+        rc, v0, a0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+        assert rc == oracle.OK
+        refs.append((v0, a0))
+    g = _grid(base, ncase, ls)
+    gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, cluster=cluster, factor=1, tail=1, outage=1)
+    vm = torch.zeros((ncase, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=1e-10, max_iter=30)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+    assert st == gbpf.PF_ERR_NOT_CONVERGED
+    assert list(res["status"]) == [0 if s < 2.2 else gbpf.PF_ERR_NOT_CONVERGED for s in MIXED_LOADS]
+    opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=1e-10, max_iter=30, fallback=1)
+    first = None
+    for k in range(4):  # direct (graphs off), capture + launch, replay, replay
+        gbpf.pf_set_graphs(g.ctx, k > 0)
+        vm.zero_()
+        va.zero_()
+        before = _run_launches(g)
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+        assert st == gbpf.PF_OK, (k, gbpf.pf_last_error(g.ctx))
+        assert _run_launches(g) - before == 1, k
+        assert list(res["method"]) == [gbpf.PF_FDPF if s < 2.2 else gbpf.PF_NR for s in MIXED_LOADS]
+        assert all(res["status"] == gbpf.PF_OK) and all(res["max_mismatch"] <= 1e-10)
+        for c in range(ncase):
+            assert np.max(np.abs(vm.cpu().numpy()[c] - refs[c][0])) <= 1e-8, (k, c)
+            assert np.max(np.abs(va.cpu().numpy()[c] - refs[c][1])) <= 1e-8, (k, c)
+        if first is None:
+            first = (vm.clone(), va.clone(), res.copy())
+        else:
+            assert torch.equal(vm, first[0]) and torch.equal(va, first[1]), k
+            assert np.array_equal(res["iters"], first[2]["iters"]), k
+    g.close()
+
+
+def test_fdpf_nr_fallback_cluster_engine(oracle):
+    """The same switch on the single-case cluster engine: the case's cluster
+    of 16 CTAs drops its resident substitution programs and runs
+    Newton-Raphson in the same launch."""
+    base = gridgen.config(0)
+    cc = base.copy()
+    cc.pd = cc.pd * 2.4
+    cc.qd = cc.qd * 2.4
+    rc, v0, a0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+    assert rc == oracle.OK
+    g = _grid(base, 1, np.full((1, base.n), 2.4))
+    gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_CLUSTER, cluster=0, factor=1, tail=1)
+    vm = torch.zeros((1, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    for fb in (0, 1):
+        opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-10, max_iter=30, fallback=fb)
+        before = _run_launches(g)
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, 1)
+        assert _run_launches(g) - before == 1
+        if not fb:
+            assert st == gbpf.PF_ERR_NOT_CONVERGED and res[0]["method"] == gbpf.PF_FDPF
+            continue
+        assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+        assert res[0]["method"] == gbpf.PF_NR and res[0]["max_mismatch"] <= 1e-10
+        assert np.max(np.abs(vm.cpu().numpy()[0] - v0)) <= 1e-8
+        assert np.max(np.abs(va.cpu().numpy()[0] - a0)) <= 1e-8
+    g.close()
+
+
 @pytest.mark.parametrize("precision", [gbpf.PF_FP64, gbpf.PF_FP32])
 def test_largest_grid_single_case(oracle, precision):
     """The largest grid of the uneven multi-grid set (79,035 buses: its FP64
