@@ -67,14 +67,14 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip pf_autotune (untimed) before the warm-up")
     ap.add_argument("--mapping", default=None,
-                    help="engine,cluster,factor,tail,outage: set this kernel mapping instead of tuning")
+                    help="engine,cluster,factor,tail,outage[,threads]: set this kernel mapping instead of tuning")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly instead of replaying CUDA graphs (profilers)")
     ap.add_argument("--ir-tol", type=float, default=None,
                     help="FP32 runs: relative residual at which a linear solve needs no further "
-                         "refinement (default 1e-6: an inexact-Newton forcing term far below the "
-                         "fast decoupled iteration's own contraction)")
+                         "refinement (default 1e-3: an inexact-Newton forcing term far below the "
+                         "fast decoupled iteration's own contraction, about 0.45 per half-iteration)")
     return ap.parse_args()
 
 
@@ -219,6 +219,16 @@ def fp64_peak_tflops(sm_mhz):
     two FP64 fused multiply-adds per SM and cycle (the 1.25 TFLOP/s nominal
     at 2,070 MHz)."""
     return 152 * 2 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+# Relative residual at which an FP32 solve of a timed fast decoupled run needs
+# no refinement: the forcing term of an inexact Newton step.  The fast
+# decoupled iteration contracts the mismatch by about 0.45 per half-iteration
+# (8 decades in 23 half-iterations on the 10k grid), so a linear-solve error
+# of 1e-3 relative changes its course by rounding only; every convergence
+# decision is still taken on the FP64 mismatch (same iteration counts and the
+# same error against the tight oracle as FP64 runs, measured).
+IR_TOL = 1e-3
 
 
 def measured_traffic(workload, prec_name, ncase, kernel):
@@ -517,7 +527,7 @@ def run_pack(args, dev, local, world, rank):
     prec_name = args.precision or "fp32"
     prec = gbpf.PF_FP64 if prec_name == "fp64" else gbpf.PF_FP32
     opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=TOL, max_iter=200,
-                         ir_tol=args.ir_tol if args.ir_tol is not None else 1e-6)
+                         ir_tol=args.ir_tol if args.ir_tol is not None else IR_TOL)
     vm = torch.zeros(tot, dtype=torch.float64, device=dev)
     va = torch.zeros_like(vm)
     stream = torch.cuda.current_stream(dev)
@@ -682,7 +692,7 @@ def main():
     method = gbpf.PF_FDPF if args.method == "fdpf" else gbpf.PF_NR
     engine = {"auto": gbpf.PF_ENGINE_AUTO, "block": gbpf.PF_ENGINE_BLOCK,
               "lanes": gbpf.PF_ENGINE_LANES}[args.engine]
-    ir_tol = args.ir_tol if args.ir_tol is not None else 1e-6
+    ir_tol = args.ir_tol if args.ir_tol is not None else IR_TOL
     opts = gbpf.run_opts(method, prec, tol=TOL, max_iter=200 if method == gbpf.PF_FDPF else 20,
                          engine=engine, ir_tol=ir_tol)
     vm = torch.zeros((ncase, base.n), dtype=torch.float64, device=dev)
@@ -697,8 +707,10 @@ def main():
         gbpf.pf_set_graphs(g.ctx, False)
     tuning = None
     if args.mapping:
-        e_, c_, f_, t_, o_ = (int(v) for v in args.mapping.split(","))
-        gbpf.pf_set_tuning(g.ctx, engine=e_, cluster=c_, factor=f_, tail=t_, outage=o_)
+        m_ = [int(v) for v in args.mapping.split(",")]
+        e_, c_, f_, t_, o_ = m_[:5]
+        gbpf.pf_set_tuning(g.ctx, engine=e_, cluster=c_, factor=f_, tail=t_, outage=o_,
+                           threads=m_[5] if len(m_) > 5 else 0)
         tuning = gbpf.pf_get_tuning(g.ctx)
     elif not args.no_autotune and args.engine == "auto":
         t0 = time.perf_counter()

@@ -150,7 +150,14 @@ enum { PF_ENGINE_AUTO = 0, PF_ENGINE_BLOCK = 1, PF_ENGINE_LANES = 2, PF_ENGINE_C
  *            2: outage cases reuse the base factors with a low-rank
  *            (Woodbury) correction of each solve by the outaged branch's
  *            share (block engine; FP32 runs still refine against each
- *            case's exact matrix in FP64).
+ *            case's exact matrix in FP64);
+ *   threads  threads of each block of the block engine when it runs one
+ *            block per case (512, 256 or 128): smaller blocks let more
+ *            cases share an SM (2, 4 or 6 to 8), so that their latency-bound
+ *            substitutions overlap one another's FP64 mismatch work; a
+ *            block of 256 or 128 threads keeps its solve vector in global
+ *            memory (L1/L2) when shared memory would otherwise limit the
+ *            cases per SM.
  * ms is the time of one run of the chosen mapping as measured by
  * pf_autotune (0 when set directly). */
 typedef struct {
@@ -159,6 +166,7 @@ typedef struct {
     int32_t factor;
     int32_t tail;
     int32_t outage;
+    int32_t threads;
     double ms;
 } pf_tuning;
 
@@ -330,7 +338,8 @@ pf_status pf_branch_flows(pf_ctx *ctx, const double *vm_dev, const double *va_de
 
 /* Project autotuner: runs pf_run_to_tol with opts (engine AUTO) under every
  * applicable mapping of pf_tuning -- engines for FDPF batches, cluster sizes
- * for single cases, the two factor forms, the two tail forms -- `reps` times
+ * for single cases, block sizes for one block per case, the two factor
+ * forms, the two tail forms, the two outage forms -- `reps` times
  * each after one untimed run, times them with CUDA events on `stream`, and
  * keeps the fastest mapping whose cases all converged; it becomes the
  * context's tuning (used by later runs) and is written to *out.  vm_dev,

@@ -107,8 +107,8 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         const double *A0, const double *A1, const int *fstat0, const int *fstat1,
                         const pf_run_opts &o, double *vm, double *va, double *ef, double *iv,
                         double *xg, double *bmax, pf_case_result *res, size_t smem_optin,
-                        int cluster, cudaStream_t s, const void *Z0, const void *Z1, const double *K0,
-                        const double *K1, const NrLaunch *fb) {
+                        size_t smem_per_sm, int cluster, int threads, cudaStream_t s, const void *Z0,
+                        const void *Z1, const double *K0, const double *K1, const NrLaunch *fb) {
     RunArgs a;
     a.Z0 = Z0;
     a.Z1 = Z1;
@@ -145,6 +145,16 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
     const size_t ring = size_t(kStages) * kStageBytes;
     size_t smem = ring + elt * size_t(nmax);
     a.use_smem = smem + 2048 <= smem_optin;
+    // one block per case with fewer threads: as many blocks per SM as the
+    // registers allow (64 per thread), the solve vector in shared memory
+    // only when it does not lower that count
+    if (cluster > 1 || (threads != 256 && threads != 128)) threads = kRunThreads;
+    if (threads < kRunThreads) {
+        const size_t blocks = size_t(65536 / (threads * 64)) < size_t(2048 / threads)
+                                  ? size_t(65536 / (threads * 64)) : size_t(2048 / threads);
+        const size_t budget = smem_per_sm / blocks;
+        a.use_smem = smem + 2048 <= budget && smem + 2048 <= smem_optin;
+    }
     if (!a.use_smem) smem = ring;
     a.fallback = 0;
     if (fb) {  // the Newton-Raphson fallback's factor scratch, when it fits
@@ -154,7 +164,8 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
             a.fallback = 1;
         }
     }
-    return prec == PF_FP64 ? fdpf_run_f64(a, smem, cluster, s) : fdpf_run_f32(a, smem, cluster, s);
+    return prec == PF_FP64 ? fdpf_run_f64(a, smem, cluster, threads, s)
+                           : fdpf_run_f32(a, smem, cluster, threads, s);
 }
 
 }  // namespace gbpf

@@ -386,13 +386,13 @@ __global__ void __launch_bounds__(kRunThreads, 1)
 }
 
 template <class T, int C>
-cudaError_t launch_fdpf_t(const RunArgs &a, size_t smem, cudaStream_t s) {
+cudaError_t launch_fdpf_t(const RunArgs &a, size_t smem, int threads, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_fdpf<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(a.dc.ncase) * C);
-    cfg.blockDim = dim3(kRunThreads);
+    cfg.blockDim = dim3(unsigned(threads));
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -448,11 +448,13 @@ bool fdpf_clusters_fit_t(int C, int ncase, size_t smem) {
     return nclusters >= ncase;
 }
 
+// threads: of each block (kRunThreads for clusters; 512, 256 or 128 for
+// one block per case).
 template <class T>
-cudaError_t fdpf_run_t(const RunArgs &a, size_t smem, int cluster, cudaStream_t s) {
-    if (cluster >= 16) return launch_fdpf_t<T, 16>(a, smem, s);
-    if (cluster >= 8) return launch_fdpf_t<T, 8>(a, smem, s);
-    return launch_fdpf_t<T, 1>(a, smem, s);
+cudaError_t fdpf_run_t(const RunArgs &a, size_t smem, int cluster, int threads, cudaStream_t s) {
+    if (cluster >= 16) return launch_fdpf_t<T, 16>(a, smem, kRunThreads, s);
+    if (cluster >= 8) return launch_fdpf_t<T, 8>(a, smem, kRunThreads, s);
+    return launch_fdpf_t<T, 1>(a, smem, threads, s);
 }
 
 }  // namespace
@@ -463,7 +465,7 @@ cudaError_t fdpf_pack_f32(const RunArgs *args_dev, const int *order_dev, int ngr
                           size_t smem, int blocks, cudaStream_t s);
 bool fdpf_clusters_fit_f64(int C, int ncase, size_t smem);
 bool fdpf_clusters_fit_f32(int C, int ncase, size_t smem);
-cudaError_t fdpf_run_f64(const RunArgs &a, size_t smem, int cluster, cudaStream_t s);
-cudaError_t fdpf_run_f32(const RunArgs &a, size_t smem, int cluster, cudaStream_t s);
+cudaError_t fdpf_run_f64(const RunArgs &a, size_t smem, int cluster, int threads, cudaStream_t s);
+cudaError_t fdpf_run_f32(const RunArgs &a, size_t smem, int cluster, int threads, cudaStream_t s);
 
 }  // namespace gbpf

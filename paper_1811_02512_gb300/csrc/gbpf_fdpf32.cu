@@ -11,8 +11,8 @@ cudaError_t fdpf_pack_f32(const RunArgs *args_dev, const int *order_dev, int ngr
 
 bool fdpf_clusters_fit_f32(int C, int ncase, size_t smem) { return fdpf_clusters_fit_t<float>(C, ncase, smem); }
 
-cudaError_t fdpf_run_f32(const RunArgs &a, size_t smem, int cluster, cudaStream_t s) {
-    return fdpf_run_t<float>(a, smem, cluster, s);
+cudaError_t fdpf_run_f32(const RunArgs &a, size_t smem, int cluster, int threads, cudaStream_t s) {
+    return fdpf_run_t<float>(a, smem, cluster, threads, s);
 }
 
 }  // namespace gbpf

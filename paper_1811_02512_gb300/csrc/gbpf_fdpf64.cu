@@ -11,8 +11,8 @@ cudaError_t fdpf_pack_f64(const RunArgs *args_dev, const int *order_dev, int ngr
 
 bool fdpf_clusters_fit_f64(int C, int ncase, size_t smem) { return fdpf_clusters_fit_t<double>(C, ncase, smem); }
 
-cudaError_t fdpf_run_f64(const RunArgs &a, size_t smem, int cluster, cudaStream_t s) {
-    return fdpf_run_t<double>(a, smem, cluster, s);
+cudaError_t fdpf_run_f64(const RunArgs &a, size_t smem, int cluster, int threads, cudaStream_t s) {
+    return fdpf_run_t<double>(a, smem, cluster, threads, s);
 }
 
 }  // namespace gbpf

@@ -1145,6 +1145,9 @@ pf_status ensure_device(pf_ctx *ctx) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     ctx->smem_optin = size_t(optin);
+    int per_sm = 0;
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+    ctx->smem_per_sm = size_t(per_sm);
 
     // device network tables
     DevNet &dn = ctx->dn;
@@ -1969,7 +1972,8 @@ pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doubl
         return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, tail ? w.TV[0][prec] : nullptr,
                            tail ? w.TV[1][prec] : nullptr, w.A[0], w.A[1], w.fstatus[0][prec],
                            w.fstatus[1][prec], *opts, vm_dev, va_dev, w.ef, w.iv, w.vec, w.bmax, w.res,
-                           ctx->smem_optin, cl, s, lowrank ? w.LZ[0][prec] : nullptr,
+                           ctx->smem_optin, ctx->smem_per_sm, cl, ctx->tune.threads, s,
+                           lowrank ? w.LZ[0][prec] : nullptr,
                            lowrank ? w.LZ[1][prec] : nullptr, lowrank ? w.LK[0] : nullptr,
                            lowrank ? w.LK[1] : nullptr, fb);
     });
@@ -1988,7 +1992,7 @@ pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doubl
 // With profiling on, or after a capture that failed, runs are direct.
 pf_status run_device_work(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double *va_dev, int engine,
                           cudaStream_t s) {
-    std::vector<unsigned char> key(2 * sizeof(void *) + sizeof(pf_run_opts) + 5 * sizeof(int32_t) +
+    std::vector<unsigned char> key(2 * sizeof(void *) + sizeof(pf_run_opts) + 6 * sizeof(int32_t) +
                                    3 * sizeof(int));
     unsigned char *k = key.data();
     auto put = [&](const void *p, size_t n) {
@@ -2011,8 +2015,8 @@ pf_status run_device_work(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, 
     o.engine = opts->engine;
     o.fallback = opts->fallback;
     put(&o, sizeof(o));
-    const int32_t t[5] = {ctx->tune.engine, ctx->tune.cluster, ctx->tune.factor, ctx->tune.tail,
-                          ctx->tune.outage};
+    const int32_t t[6] = {ctx->tune.engine, ctx->tune.cluster, ctx->tune.factor, ctx->tune.tail,
+                          ctx->tune.outage, ctx->tune.threads};
     put(t, sizeof(t));
     const int extra[3] = {engine, ctx->set_gen, ctx->dc.ncase};
     put(extra, sizeof(extra));
@@ -2283,7 +2287,8 @@ pf_status pf_set_tuning(pf_ctx *ctx, const pf_tuning *t) {
     if (!ctx || !t) return fail(ctx, PF_ERR_ARG, "null pointer");
     if (t->engine < 0 || t->engine > PF_ENGINE_CLUSTER || t->factor < 0 || t->factor > 2 || t->tail < 0 ||
         t->tail > 2 || t->outage < 0 || t->outage > 2 ||
-        (t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16))
+        (t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16) ||
+        (t->threads != 0 && t->threads != 128 && t->threads != 256 && t->threads != 512))
         return fail(ctx, PF_ERR_ARG, "tuning field out of range");
     ctx->tune = *t;
     ctx->tune.ms = t->ms;
@@ -2324,12 +2329,15 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     if (o.method == PF_FDPF && ctx->dc.ninst > 1) outages.push_back(2);
     // the lane engine has no cluster, tail or outage choice; the cluster
     // engine no cluster size (its own) and no outage form (one base case)
+    // block sizes matter only for one block per case of a batch
     for (int e : engines)
         for (int c : (e != PF_ENGINE_BLOCK ? std::vector<int>{0} : clusters))
             for (int f : factors)
                 for (int t : (e == PF_ENGINE_LANES ? std::vector<int>{0} : tails))
                     for (int u : (e != PF_ENGINE_BLOCK ? std::vector<int>{1} : outages))
-                        cand.push_back(pf_tuning{e, c, f, t, u, 0.0});
+                        for (int th : (e == PF_ENGINE_BLOCK && c == 1 && ncase > 1 ? std::vector<int>{512, 256, 128}
+                                                                                    : std::vector<int>{0}))
+                            cand.push_back(pf_tuning{e, c, f, t, u, th, 0.0});
     std::vector<pf_case_result> res(static_cast<size_t>(ncase));
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
@@ -2339,7 +2347,7 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     const pf_tuning saved = ctx->tune;
     const bool graphs_saved = ctx->graphs_off;
     ctx->graphs_off = true;  // every candidate timed on direct launches
-    pf_tuning best{0, 0, 0, 0, 0, -1.0};
+    pf_tuning best{0, 0, 0, 0, 0, 0, -1.0};
     pf_status last = PF_OK;
     for (const pf_tuning &t : cand) {
         ctx->tune = t;

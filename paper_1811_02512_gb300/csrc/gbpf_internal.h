@@ -338,9 +338,10 @@ struct pf_ctx {
     int device = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
+    size_t smem_per_sm = 0;
     std::string err;
     std::vector<void *> allocations;  // everything owned by the context
-    pf_tuning tune = {0, 0, 0, 0, 0, 0.0};  // kernel mappings (pf_autotune / pf_set_tuning)
+    pf_tuning tune = {0, 0, 0, 0, 0, 0, 0.0};  // kernel mappings (pf_autotune / pf_set_tuning)
     // programs of the cluster engine (host, device), their tail-inverse
     // scratch and the dynamic shared memory of one CTA
     gbpf::HostCl hcl[2];
@@ -427,7 +428,8 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         const double *A0, const double *A1,
                         const int *fstat0, const int *fstat1, const pf_run_opts &o, double *vm,
                         double *va, double *ef, double *iv, double *xg, double *bmax,
-                        pf_case_result *res, size_t smem_optin, int cluster, cudaStream_t s,
+                        pf_case_result *res, size_t smem_optin, size_t smem_per_sm, int cluster,
+                        int threads, cudaStream_t s,
                         const void *Z0 = nullptr, const void *Z1 = nullptr, const double *K0 = nullptr,
                         const double *K1 = nullptr, const NrLaunch *fb = nullptr);
 // Z = A^-1 U and K = (I - S U^T Z)^-1 S of every outage instance of matrix

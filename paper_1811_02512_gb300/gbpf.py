@@ -328,7 +328,7 @@ def pf_branch_flows(ctx, vm_dev, va_dev, ncase, flows_dev, loss_dev, stream=None
 
 class pf_tuning(C.Structure):
     _fields_ = [("engine", C.c_int32), ("cluster", C.c_int32), ("factor", C.c_int32),
-                ("tail", C.c_int32), ("outage", C.c_int32), ("ms", C.c_double)]
+                ("tail", C.c_int32), ("outage", C.c_int32), ("threads", C.c_int32), ("ms", C.c_double)]
 
 
 def pf_autotune(ctx, opts, vm_dev, va_dev, reps=3, stream=None):
@@ -351,8 +351,8 @@ def pf_set_graphs(ctx, on):
     _check(ctx, load().pf_set_graphs(ctx, int(bool(on))), "pf_set_graphs")
 
 
-def pf_set_tuning(ctx, engine=0, cluster=0, factor=0, tail=0, outage=0):
-    t = pf_tuning(engine, cluster, factor, tail, outage, 0.0)
+def pf_set_tuning(ctx, engine=0, cluster=0, factor=0, tail=0, outage=0, threads=0):
+    t = pf_tuning(engine, cluster, factor, tail, outage, threads, 0.0)
     _check(ctx, load().pf_set_tuning(ctx, C.byref(t)), "pf_set_tuning")
 
 

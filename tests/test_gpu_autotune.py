@@ -56,6 +56,7 @@ def test_autotune_single_and_batch(oracle):
     t = gbpf.pf_autotune(g.ctx, opts, vm, va, reps=2)
     assert t["ms"] > 0 and t["factor"] in (1, 2) and t["tail"] in (1, 2)
     assert t["cluster"] in (1, 8, 16) or (t["engine"] == gbpf.PF_ENGINE_CLUSTER and t["cluster"] == 0)
+    assert t["threads"] == 0  # block sizes are a batch choice
     assert gbpf.pf_get_tuning(g.ctx) == t
     g.close()
     sc = gridgen.scenarios(base, n_load=32, n_outage=32, seed=5)
@@ -66,6 +67,7 @@ def test_autotune_single_and_batch(oracle):
     opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP32, tol=1e-11, max_iter=300)
     t = gbpf.pf_autotune(g.ctx, opts, vm, va, reps=1)
     assert t["ms"] > 0 and t["engine"] in (gbpf.PF_ENGINE_BLOCK, gbpf.PF_ENGINE_LANES)
+    assert t["threads"] in (128, 256, 512) if t["engine"] == gbpf.PF_ENGINE_BLOCK else t["threads"] == 0
     st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
     assert st == gbpf.PF_OK
     v, a = vm.cpu().numpy(), va.cpu().numpy()
@@ -129,4 +131,43 @@ def test_cluster_engine_matches_oracle(oracle, cfg):
             assert st == gbpf.PF_OK, (fac, tail, gbpf.pf_last_error(g.ctx))
             assert np.max(np.abs(vm.cpu().numpy()[0] - vm0)) <= 1e-8, (fac, tail)
             assert np.max(np.abs(va.cpu().numpy()[0] - va0)) <= 1e-8, (fac, tail)
+    g.close()
+
+
+@pytest.mark.parametrize("precision", [gbpf.PF_FP64, gbpf.PF_FP32])
+@pytest.mark.parametrize("threads", [256, 128])
+def test_smaller_case_blocks_match_oracle(oracle, precision, threads):
+    """One block per case with 256 or 128 threads (more cases per SM, the
+    solve vector in global memory): a batch of load and outage cases of the
+    10k grid, both outage forms, against the oracle's solution of each
+    sampled case; the run reports the same iteration counts as 512-thread
+    blocks give."""
+    base = gridgen.config(1)
+    sc = gridgen.scenarios(base, n_load=6, n_outage=6, seed=21)
+    g = gbpf.Grid(base)
+    g.set_cases(sc.ncase, sc.load_scale, sc.outage)
+    vm = torch.zeros((sc.ncase, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, precision, tol=1e-11, max_iter=300)
+    refs = {}
+    for c in (0, 5, 6, 11):
+        rc, vm0, va0, _, _ = oracle.power_flow(gridgen.apply_scenario(base, sc, c), oracle.NR, tol=1e-12,
+                                               max_iter=30)
+        assert rc == oracle.OK
+        refs[c] = (vm0, va0)
+    for outage in (1, 2):
+        its = {}
+        for th in (512, threads):
+            gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, cluster=1, factor=1, tail=1, outage=outage,
+                               threads=th)
+            vm.zero_()
+            va.zero_()
+            st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+            assert st == gbpf.PF_OK, (th, outage, gbpf.pf_last_error(g.ctx))
+            its[th] = res["iters"].copy()
+            v, a = vm.cpu().numpy(), va.cpu().numpy()
+            for c, (vm0, va0) in refs.items():
+                assert np.max(np.abs(v[c] - vm0)) <= 1e-8, (th, outage, c)
+                assert np.max(np.abs(a[c] - va0)) <= 1e-8, (th, outage, c)
+        assert np.max(np.abs(its[512] - its[threads])) <= 1
     g.close()

@@ -529,11 +529,13 @@ def test_tuning_fields_validated(lib):
     ctx = gbpf.pf_create(*_tables(case))
     gbpf.pf_analyze(ctx)
     assert gbpf.pf_get_tuning(ctx) == {"engine": 0, "cluster": 0, "factor": 0, "tail": 0, "outage": 0,
-                                       "ms": 0.0}
-    gbpf.pf_set_tuning(ctx, engine=gbpf.PF_ENGINE_LANES, cluster=8, factor=1, tail=2, outage=2)
+                                       "threads": 0, "ms": 0.0}
+    gbpf.pf_set_tuning(ctx, engine=gbpf.PF_ENGINE_LANES, cluster=8, factor=1, tail=2, outage=2, threads=256)
     t = gbpf.pf_get_tuning(ctx)
-    assert (t["engine"], t["cluster"], t["factor"], t["tail"], t["outage"]) == (gbpf.PF_ENGINE_LANES, 8, 1, 2, 2)
-    for bad in ({"cluster": 3}, {"factor": 3}, {"tail": -1}, {"engine": 7}, {"outage": 3}):
+    assert (t["engine"], t["cluster"], t["factor"], t["tail"], t["outage"], t["threads"]) == \
+        (gbpf.PF_ENGINE_LANES, 8, 1, 2, 2, 256)
+    for bad in ({"cluster": 3}, {"factor": 3}, {"tail": -1}, {"engine": 7}, {"outage": 3}, {"threads": 64},
+                {"threads": 1024}):
         with pytest.raises(gbpf.PFError) as e:
             gbpf.pf_set_tuning(ctx, **bad)
         assert e.value.status == gbpf.PF_ERR_ARG
