@@ -198,7 +198,7 @@ def hbm_bytes_per_launch(info, case, prec_bytes, half_iters, resid, n_outage_sol
     return shared + half_iters * per_half + resid * 16 * n_mean + n_outage_solves * 2 * n_mean * prec_bytes
 
 
-def fp64_flops_per_launch(info, case, half_iters, resid):
+def fp64_flops_per_launch(info, case, half_iters, resid, solves64=0.0):
     """Algorithmic FP64 operations of one launch of the iteration kernel (a
     fused multiply-add counts two): per case and half-iteration the nodal
     mismatch, four multiply-adds per admittance entry (8 nnz(Y)) and about
@@ -206,12 +206,16 @@ def fp64_flops_per_launch(info, case, half_iters, resid):
     injection, the scaling by 1/V), and the state update (about 15 per
     unknown: the angle step rotates the cached cos/sin by a short series,
     the magnitude step refreshes 1/V); per FP64 residual of a refined solve
-    two per entry of the matrix (n + its off-diagonal entries).  The FP32
-    substitutions run on the FP32 pipe and are not counted."""
+    two per entry of the matrix (n + its off-diagonal entries); per FP64
+    substitution pair two per entry of L in each direction plus the n
+    multiplications by D^-1.  The FP32 substitutions of refined runs run on
+    the FP32 pipe and are not counted."""
     n_mean = 0.5 * (info.n[0] + info.n[1])
+    nnzl_mean = 0.5 * (info.nnz_l[0] + info.nnz_l[1])
     off_mean = 0.5 * (matrix_offdiag(case, 0) + matrix_offdiag(case, 1))
     per_half = 8 * info.nnz_ybus + 6 * case.n + 15 * n_mean
-    return half_iters * per_half + resid * 2 * (n_mean + off_mean)
+    return (half_iters * per_half + resid * 2 * (n_mean + off_mean)
+            + solves64 * (4 * nnzl_mean + n_mean))
 
 
 def fp64_peak_tflops(sm_mhz):
@@ -822,7 +826,8 @@ def main():
     hbm["traffic"] = measured_traffic(args.workload, prec_name, ncase, kname) if method == gbpf.PF_FDPF else None
     if ncase_all > 1:
         # a batch is bound by the FP64 pipe (GB300 runs FP64 at 1/64 of FP32)
-        flops = fp64_flops_per_launch(g.info, base, half_iters, resid)
+        solves64 = float(np.sum(res["iters"])) if prec == gbpf.PF_FP64 else 0.0
+        flops = fp64_flops_per_launch(g.info, base, half_iters, resid, solves64)
         peak = fp64_peak_tflops(clk.get("sm_mhz"))
         achieved = flops / (kernel_ms / 1e3) / 1e12 if kernel_ms > 0 else 0.0
         roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

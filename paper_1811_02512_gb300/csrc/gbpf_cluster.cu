@@ -6,26 +6,30 @@
 // substitutions of Section III.C are split by rows: every row (column) of
 // the factor has an owner CTA, which keeps that row's entries of L (and of
 // the tail inverse below) resident in its shared memory for the whole
-// launch, and holds the row's entry of the solution vector.  A step of a
-// sweep is one level of the elimination tree (the paper's hierarchical
-// parallelism, Section II.B): every CTA computes its rows of the level,
-// reading the entries of lower (forward) or higher (backward) levels from
-// their owners' shared memory over the cluster's distributed shared memory,
-// and the step ends with a cluster barrier.
+// launch, and holds the row's entry of the solution vector.
 //
-// The narrow top of the elimination tree (the tail, rows [t0, n): a long run
-// of levels with at most 16 rows each, 118 levels of B' at 10,000 buses)
-// would cost one barrier per level.  It is solved instead with the explicit
-// inverse W = L_TT^-1 of the tail's diagonal block of L (a partitioned
-// inverse of the factor): with L = [[L_BB, 0], [L_TB, L_TT]],
+// The elimination forest is cut into a top set T (closed under taking
+// parents; it holds the narrow top of the tree, a long run of levels with
+// at most 16 rows each, 118 levels of B' at 10,000 buses) and the subtrees
+// below it.  Every subtree belongs wholly to one CTA, so a level of it (the
+// paper's hierarchical parallelism, Section II.B) reads only the CTA's own
+// words and ends with the CTA's own barrier.  T is solved with the explicit
+// inverse W = L_TT^-1 of its diagonal block of L (a partitioned inverse of
+// the factor): with L = [[L_BB, 0], [L_TB, L_TT]],
 //   forward   c_T = b_T - L_TB z_B,  z_T = W c_T,
-//   backward  x_T = W^T D_T^-1 z_T,  then the bottom levels as usual,
-// so the tail takes three steps whatever its height.  W has a nonzero (i, j)
-// exactly when i is an ancestor of j in the elimination tree; it is formed
-// after every factorisation by k_tail_inverse (one thread per tail column,
-// walking the column's ancestor path with the recurrence
-// w_i = -sum_k L_ik w_k), and gathered with the factor's values into the
-// CTAs' packed value arrays by k_cl_values.
+//   backward  x_T = W^T D_T^-1 z_T,  then the subtrees' levels as usual,
+// three cluster-wide steps whatever T's height, each reading other CTAs'
+// words over the cluster's distributed shared memory and ending with a
+// cluster barrier.  W has a nonzero (i, j) exactly when i is an ancestor of
+// j in the elimination tree; it is formed after every factorisation by
+// k_tail_inverse (a warp per column of T, right-looking along the column's
+// ancestor path: w_i -= L_ik w_k), and gathered with the factor's values
+// into the CTAs' packed value arrays by k_cl_values.
+//
+// A case the fast decoupled iteration leaves unconverged can fall back to
+// Newton-Raphson (Section III) in the same launch: the cluster then reuses
+// its shared memory for the Newton-Raphson staging ring and factor scratch
+// (gbpf_nr.cuh).
 #include "gbpf_nr.cuh"
 
 namespace gbpf {
