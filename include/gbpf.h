@@ -145,7 +145,12 @@ enum { PF_ENGINE_AUTO = 0, PF_ENGINE_BLOCK = 1, PF_ENGINE_LANES = 2, PF_ENGINE_C
  *   factor   1: dependency-driven factor over all SMs, 2: one thread block
  *            per instance (level by level);
  *   tail     1: narrow top of the elimination tree substituted as a one-warp
- *            scatter, 2: level by level (warp per narrow level);
+ *            scatter, 2: level by level (warp per narrow level), 3: through
+ *            the top's partitioned inverse W = L_TT^-1 (z_T = W c_T, x_T =
+ *            W^T D_T^-1 z_T: two parallel gathers instead of a level chain;
+ *            W formed after every factorisation; block engine runs whose
+ *            solves all use the base factor: one instance, or low-rank
+ *            outages -- other runs use form 1);
  *   outage   1: every single-branch outage case has its own B'/B'' factors,
  *            2: outage cases reuse the base factors with a low-rank
  *            (Woodbury) correction of each solve by the outaged branch's

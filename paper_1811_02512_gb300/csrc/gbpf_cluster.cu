@@ -87,7 +87,8 @@ __device__ __forceinline__ void cl_barrier_global() { cl_barrier(); }
 // (depth[jt] - depth[k]); the columns of L_TT (tcp, the depth of each
 // entry's row in tcdep, its factor position in tcpos) are staged into shared
 // memory first.  The order of operations is fixed.
-__global__ void __launch_bounds__(kTailInvWarps * 32) k_tail_inverse(const ClMat m, const double *F, double *Wd) {
+template <class T>
+__global__ void __launch_bounds__(kTailInvWarps * 32) k_tail_inverse(const ClMat m, const T *F, double *Wd) {
     extern __shared__ __align__(16) unsigned char tsm[];
     const int nt = m.nt, ne = m.ntail_e, D = m.tdepth_max;
     double *Lv = reinterpret_cast<double *>(tsm);
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(kTailInvWarps * 32) k_tail_inverse(const ClMat
     int *cp = Ld + ne;                                      // [nt + 1]
     int *dep = cp + nt + 1, *par = dep + nt;
     for (int q = threadIdx.x; q < ne; q += blockDim.x) {
-        Lv[q] = F[m.tcpos[q]];
+        Lv[q] = double(F[m.tcpos[q]]);
         Ld[q] = m.tcdep[q];
     }
     for (int i = threadIdx.x; i <= nt; i += blockDim.x) cp[i] = m.tcp[i];
@@ -119,6 +120,21 @@ __global__ void __launch_bounds__(kTailInvWarps * 32) k_tail_inverse(const ClMat
         for (int q = cp[k] + lane; q < cp[k + 1]; q += 32) {
             const int pos = dj - Ld[q];
             w[pos] = fma(-Lv[q], wk, w[pos]);
+        }
+    }
+}
+
+// Tail-inverse values of instance 0 (tail form 3 of the block engine):
+// forward entries W(i, j), backward entries W(j, i) / D(j), from the dense W.
+template <class T>
+__global__ void k_tw_values(const DevMat m, const double *Wd, const T *F, T *TW) {
+    const int tot = m.tw_nfe + m.tw_nbe;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+        if (e < m.tw_nfe) {
+            TW[e] = T(Wd[m.twfs[e]]);
+        } else {
+            const int b = e - m.tw_nfe;
+            TW[m.tw_boff + b] = T(Wd[m.twbs[b]] * double(F[m.offDi + m.twbd[b]]));
         }
     }
 }
@@ -470,6 +486,36 @@ size_t tail_inverse_smem(int nt, int ne, int depth_max) {
            sizeof(int) * (size_t(ne) + 3 * size_t(nt) + 1);
 }
 
+cudaError_t launch_tail_w(const DevMat &m, int prec, const void *F, double *Wd, void *TW, cudaStream_t s) {
+    if (m.npf3 <= 0 || m.tw_ne <= 0) return cudaSuccess;
+    ClMat t;  // the top's structure in the form k_tail_inverse reads
+    t.nt = m.nt;
+    t.ntail_e = m.tw_ne;
+    t.tdepth_max = m.tw_depmax;
+    t.tpar = m.twpar;
+    t.tcp = m.twcp;
+    t.tcdep = m.twcdep;
+    t.tcpos = m.twcpos;
+    t.tdepth = m.twdep;
+    const size_t smem = tail_inverse_smem(t.nt, t.ntail_e, t.tdepth_max);
+    const dim3 grid((t.nt + kTailInvWarps - 1) / kTailInvWarps);
+    const int tot = m.tw_nfe + m.tw_nbe;
+    const int vb = (tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024;
+    cudaError_t e;
+    if (prec == PF_FP64) {
+        e = cudaFuncSetAttribute(k_tail_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_tail_inverse<double><<<grid, kTailInvWarps * 32, smem, s>>>(t, static_cast<const double *>(F), Wd);
+        k_tw_values<double><<<vb, 256, 0, s>>>(m, Wd, static_cast<const double *>(F), static_cast<double *>(TW));
+    } else {
+        e = cudaFuncSetAttribute(k_tail_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        k_tail_inverse<float><<<grid, kTailInvWarps * 32, smem, s>>>(t, static_cast<const float *>(F), Wd);
+        k_tw_values<float><<<vb, 256, 0, s>>>(m, Wd, static_cast<const float *>(F), static_cast<float *>(TW));
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0, const double *F1,
                               double *W0, double *W1, cudaStream_t s) {
     const ClMat *mm[2] = {&m0, &m1};
@@ -479,9 +525,11 @@ cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0
         const ClMat &m = *mm[w];
         if (m.nt == 0) continue;
         const size_t smem = tail_inverse_smem(m.nt, m.ntail_e, m.tdepth_max);
-        cudaError_t e = cudaFuncSetAttribute(k_tail_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaError_t e = cudaFuncSetAttribute(k_tail_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
         if (e != cudaSuccess) return e;
-        k_tail_inverse<<<(m.nt + kTailInvWarps - 1) / kTailInvWarps, kTailInvWarps * 32, smem, s>>>(m, FF[w], WW[w]);
+        k_tail_inverse<double><<<(m.nt + kTailInvWarps - 1) / kTailInvWarps, kTailInvWarps * 32, smem, s>>>(
+            m, FF[w], WW[w]);
     }
     const int nv = m0.nval > m1.nval ? m0.nval : m1.nval;
     k_cl_values<<<dim3(unsigned((nv + 255) / 256), 2), 256, 0, s>>>(m0, m1, F0, F1, W0, W1);

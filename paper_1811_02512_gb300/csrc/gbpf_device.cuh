@@ -16,7 +16,7 @@ namespace {
 constexpr int kFactorThreads = 512;
 constexpr int kSolveThreads = 512;
 constexpr int kRunThreads = 512;
-constexpr int kStages = 4;                  // ring depth of the staged sweeps
+constexpr int kStages = kRingStages;        // ring depth of the staged sweeps
 constexpr int kStageBytes = kPieceBytes;    // one piece per stage
 constexpr unsigned kDefaultSpin = 1u << 22; // bound of every mbarrier wait
 
@@ -617,6 +617,48 @@ __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces
     return staged_sweep<T, X, NB, TRANS>(R, stages, pieces, np, S, x, spin);
 }
 
+// The narrow top [t0, n) of a substitution through its partitioned inverse
+// (tail form 3, see DevMat): on entry x[t0..n) holds c_T = b_T - L_TB z_B;
+// z_T = W c_T, then x_T = W^T D_T^-1 z_T.  Each gather runs a thread per
+// chunk of a row's entries into partial sums, then a thread per row adding
+// its own term and its chunks' sums in chunk order (a fixed order of
+// operations).  `scratch` (the staging ring, idle between the two sweeps)
+// holds z_T and the partial sums; the producer's proxy fence before its next
+// copy orders these writes before the ring is refilled.
+template <class T, class X>
+__device__ void tail_inverse_solve(const DevMat &m, const T *tw, const T *Dinv, X *x, unsigned char *scratch) {
+    const int t0 = m.t0, nt = m.nt;
+    T *z = reinterpret_cast<T *>(scratch);
+    T *part = z + nt;
+    for (int k = threadIdx.x; k < m.tw_nfc; k += blockDim.x) {
+        const int2 c = m.twfc[k];
+        T acc = T(0);
+        for (int e = c.x; e < c.y; e++) acc = fma(tw[e], T(x[t0 + m.twfj[e]]), acc);
+        part[k] = acc;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nt; r += blockDim.x) {
+        T acc = T(x[t0 + r]);
+        for (int k = m.twfr[r]; k < m.twfr[r + 1]; k++) acc += part[k];
+        z[r] = acc;
+    }
+    __syncthreads();
+    const T *twb = tw + m.tw_boff;
+    for (int k = threadIdx.x; k < m.tw_nbc; k += blockDim.x) {
+        const int2 c = m.twbc[k];
+        T acc = T(0);
+        for (int e = c.x; e < c.y; e++) acc = fma(twb[e], z[m.twbj[e]], acc);
+        part[k] = acc;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nt; r += blockDim.x) {
+        T acc = z[r] * Dinv[t0 + r];
+        for (int k = m.twbr[r]; k < m.twbr[r + 1]; k++) acc += part[k];
+        x[t0 + r] = X(acc);
+    }
+    __syncthreads();
+}
+
 // L D L^T x = x in place (level order): forward substitution over the rows
 // of L (levels ascending), then back substitution over the columns of L
 // (levels descending) with the normalisation y = z / d of Eq. 4 fused in as
@@ -626,10 +668,22 @@ __device__ bool staged_sweep(Ring *R, unsigned char *stages, const Piece *pieces
 // scatter tail), the sweeps run the tail levels as a one-warp scatter: the
 // forward sweep ends with the tail rows' entries below the tail and the
 // forward scatter; the backward sweep starts with the tail rows' inverse
-// diagonal and the backward scatter.
+// diagonal and the backward scatter.  With the tail-inverse values tw as
+// well (tail form 3), the top is instead two gathers through its partitioned
+// inverse between the two sweeps (tail_inverse_solve).
 template <class T, class X>
 __device__ bool block_solve(Ring *R, unsigned char *stages, const DevMat &m, const T *F, X *x,
-                            unsigned spin, const T *tv = nullptr) {
+                            unsigned spin, const T *tv = nullptr, const T *tw = nullptr) {
+    if (tv && tw && m.npf3 > 0) {
+        // the narrow top through its partitioned inverse (tail form 3)
+        const SweepSrc<T> Sf{m.Fp, m.Fc, F + m.offLr, nullptr, m.lvl_ptr, m.SKf, m.SIf, tv + m.tv_f,
+                             m.PPp, m.PPc, tv + m.tv_p, m.ZP};
+        if (!staged_sweep<T, X, 1, false>(R, stages, m.pf3, m.npf3, Sf, x, spin)) return false;
+        tail_inverse_solve<T, X>(m, tw, F + m.offDi, x, stages);
+        const SweepSrc<T> Sb{m.Cp, m.Cr, F + m.offLc, F + m.offDi, m.lvl_ptr, m.SKb, m.SIb,
+                             tv + m.tv_b, nullptr, nullptr, nullptr, m.ZP};
+        return staged_sweep<T, X, 1, false>(R, stages, m.pb3, m.npb3, Sb, x, spin);
+    }
     if (tv && m.npf2 > 0) {
         const SweepSrc<T> Sf{m.Fp, m.Fc, F + m.offLr, nullptr, m.lvl_ptr, m.SKf, m.SIf, tv + m.tv_f,
                              m.PPp, m.PPc, tv + m.tv_p, m.ZP};

@@ -25,6 +25,7 @@ void fill_run_args(RunArgs &a, const DevNet &dn, const DevCases &dc, const DevMa
                    pf_case_result *res) {
     a.TV0 = m[0].npf2 > 0 ? TV0 : nullptr;
     a.TV1 = m[1].npf2 > 0 ? TV1 : nullptr;
+    a.TW0 = a.TW1 = nullptr;
     a.Z0 = a.Z1 = nullptr;
     a.K0 = a.K1 = nullptr;
     a.iv = iv;
@@ -108,7 +109,8 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         const pf_run_opts &o, double *vm, double *va, double *ef, double *iv,
                         double *xg, double *bmax, pf_case_result *res, size_t smem_optin,
                         size_t smem_per_sm, int cluster, int threads, cudaStream_t s, const void *Z0,
-                        const void *Z1, const double *K0, const double *K1, const NrLaunch *fb) {
+                        const void *Z1, const double *K0, const double *K1, const NrLaunch *fb,
+                        const void *TW0, const void *TW1) {
     RunArgs a;
     a.Z0 = Z0;
     a.Z1 = Z1;
@@ -116,6 +118,8 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
     a.K1 = K1;
     a.TV0 = m[0].npf2 > 0 ? TV0 : nullptr;
     a.TV1 = m[1].npf2 > 0 ? TV1 : nullptr;
+    a.TW0 = m[0].npf3 > 0 && a.TV0 ? TW0 : nullptr;
+    a.TW1 = m[1].npf3 > 0 && a.TV1 ? TW1 : nullptr;
     a.iv = iv;
     a.A0 = A0;
     a.A1 = A1;

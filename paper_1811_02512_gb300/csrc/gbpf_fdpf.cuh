@@ -23,6 +23,7 @@ struct RunArgs {
     DevMat m0, m1;  // B', B''
     const void *F0, *F1;
     const void *TV0, *TV1;  // gathered tail values per instance (or null)
+    const void *TW0, *TW1;  // tail-inverse values of instance 0 (tail form 3; or null)
     // low-rank outages: outage cases solve with the base factor (instance 0)
     // and the correction x += Z K (x[p0], x[p1]) of their instance (or null)
     const void *Z0, *Z1;     // [ninst][2][n] T
@@ -145,7 +146,7 @@ __device__ void lowrank_correct(const LowRank<T> &lr, X *x, int n, double *red) 
 // (the refined x lives in the second half of the exchange vector).
 template <class T>
 __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T *xs,
-                            const DevMat &m, const T *F, const T *tv, const double *A, int c,
+                            const DevMat &m, const T *F, const T *tv, const T *tw, const double *A, int c,
                             double *red, int &ir_steps, const LowRank<T> &lr) {
     const int nbus = a.dn.nbus;
     double *xg = a.xg + (long long)c * 3 * nbus;
@@ -154,11 +155,11 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
         if (xs) {
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) xs[r] = T(xg[r]);
             __syncthreads();
-            ok = block_solve<T, T>(R, stages, m, F, xs, a.spin, tv);
+            ok = block_solve<T, T>(R, stages, m, F, xs, a.spin, tv, tw);
             if (ok) lowrank_correct<T, T>(lr, xs, m.n, red);
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) xg[r] = double(xs[r]);
         } else {
-            ok = block_solve<T, double>(R, stages, m, F, xg, a.spin, tv);
+            ok = block_solve<T, double>(R, stages, m, F, xg, a.spin, tv, tw);
             if (ok) lowrank_correct<T, double>(lr, xg, m.n, red);
         }
     } else {
@@ -172,7 +173,7 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
         }
         const double bn = __longlong_as_double(static_cast<long long>(block_max_key(bk, red)));
         for (int k = 0;; k++) {
-            ok = block_solve<T, T>(R, stages, m, F, xv, a.spin, tv);
+            ok = block_solve<T, T>(R, stages, m, F, xv, a.spin, tv, tw);
             if (!ok) break;
             lowrank_correct<T, T>(lr, xv, m.n, red);
             for (int r = threadIdx.x; r < m.n; r += blockDim.x)
@@ -182,7 +183,30 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
             unsigned long long rk = 0;
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
                 double s = xg[r] - A[r] * x64[r];
-                for (int e = m.Ap[r]; e < m.Ap[r + 1]; e++) s -= A[m.Apos[e]] * x64[m.Aj[e]];
+                // the row's entries four at a time: their indices and values
+                // are loaded before the (ordered) subtractions
+                const int e1 = m.Ap[r + 1];
+                int e = m.Ap[r];
+                for (; e + 3 < e1; e += 4) {
+                    const int p0 = m.Apos[e], p1 = m.Apos[e + 1], p2 = m.Apos[e + 2], p3 = m.Apos[e + 3];
+                    const int j0 = m.Aj[e], j1 = m.Aj[e + 1], j2 = m.Aj[e + 2], j3 = m.Aj[e + 3];
+                    const double a0 = A[p0], a1 = A[p1], a2 = A[p2], a3 = A[p3];
+                    const double y0 = x64[j0], y1 = x64[j1], y2 = x64[j2], y3 = x64[j3];
+                    s -= a0 * y0;
+                    s -= a1 * y1;
+                    s -= a2 * y2;
+                    s -= a3 * y3;
+                }
+                if (e < e1) {
+                    const int rem = e1 - e;  // 1 to 3 entries
+                    const int p0 = m.Apos[e], p1 = m.Apos[rem > 1 ? e + 1 : e], p2 = m.Apos[rem > 2 ? e + 2 : e];
+                    const int j0 = m.Aj[e], j1 = m.Aj[rem > 1 ? e + 1 : e], j2 = m.Aj[rem > 2 ? e + 2 : e];
+                    const double a0 = A[p0], a1 = A[p1], a2 = A[p2];
+                    const double y0 = x64[j0], y1 = x64[j1], y2 = x64[j2];
+                    s -= a0 * y0;
+                    if (rem > 1) s -= a1 * y1;
+                    if (rem > 2) s -= a2 * y2;
+                }
                 xv[r] = T(s);
                 const unsigned long long k = abs_key(s);
                 rk = k > rk ? k : rk;
@@ -223,6 +247,8 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
     const T *F1 = static_cast<const T *>(a.F1) + (long long)finst * a.m1.stride;
     const T *TV0 = a.TV0 ? static_cast<const T *>(a.TV0) + (long long)finst * a.m0.tv_stride : nullptr;
     const T *TV1 = a.TV1 ? static_cast<const T *>(a.TV1) + (long long)finst * a.m1.tv_stride : nullptr;
+    const T *TW0 = a.TW0 && finst == 0 ? static_cast<const T *>(a.TW0) : nullptr;
+    const T *TW1 = a.TW1 && finst == 0 ? static_cast<const T *>(a.TW1) : nullptr;
     LowRank<T> lr0, lr1;
     if (lowrank) {
         const int e = a.dc.inst_outage[inst];
@@ -275,7 +301,7 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, TV0, A0, c, red, ir_steps, lr0);
+                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m0, F0, TV0, TW0, A0, c, red, ir_steps, lr0);
                 if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
             }
             cluster_sync<C>();
@@ -303,7 +329,7 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
             if (rank == 0) {
-                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, TV1, A1, c, red, ir_steps, lr1);
+                const bool ok = rank0_solve<T>(a, &R, stages, xs, a.m1, F1, TV1, TW1, A1, c, red, ir_steps, lr1);
                 if (threadIdx.x == 0) *flag = ok ? 0.0 : 1.0;
             }
             cluster_sync<C>();

@@ -174,6 +174,102 @@ std::vector<int> min_degree_order(int n, std::vector<std::vector<int>> adj) {
 // ---------------------------------------------------------------- analysis
 
 
+// Partitioned inverse of the narrow top [t0, n) of one matrix (tail form 3,
+// see DevMat): the columns of L_TT with their rows' depths for
+// k_tail_inverse, and the chunked gather lists of z_T = W c_T (row i: its
+// descendants j) and x_T = W^T D^-1 z_T (row i: its ancestors).  Chunks hold
+// at most cw entries, cw the smallest power of two from 8 whose partial sums
+// and the top's vector fit the idle staging ring.  Leaves pf3 / pb3 empty
+// (no form 3) when the top is too large for a dense inverse.
+void build_tail_inverse(HostMat &H) {
+    const int n = H.n, t0 = H.t0, nt = H.nt;
+    auto clear = [&] {
+        H.pf3.clear();
+        H.pb3.clear();
+        H.tw_nfe = H.tw_nbe = H.tw_ne = 0;
+    };
+    if (nt <= 0 || nt > kClTailMax) return clear();
+    std::vector<int> par(nt), dep(nt);
+    for (int it = 0; it < nt; it++) {
+        const int j = t0 + it;
+        par[it] = H.Cp[j] < H.Cp[j + 1] ? H.Cr[H.Cp[j]] - t0 : -1;  // the first row of column j
+        if (par[it] >= nt || (par[it] >= 0 && par[it] <= it)) return clear();
+    }
+    int depmax = 0;
+    for (int it = nt - 1; it >= 0; it--) {
+        dep[it] = par[it] < 0 ? 0 : dep[par[it]] + 1;
+        depmax = std::max(depmax, dep[it] + 1);
+    }
+    H.twcp.assign(nt + 1, 0);
+    H.twcdep.clear();
+    H.twcpos.clear();
+    for (int it = 0; it < nt; it++) {
+        const int j = t0 + it;
+        for (int p = H.Cp[j]; p < H.Cp[j + 1]; p++) {
+            const int i = H.Cr[p] - t0;
+            if (i < 0 || i >= nt) return clear();
+            H.twcdep.push_back(dep[i]);
+            H.twcpos.push_back(H.offLc + p);
+        }
+        H.twcp[it + 1] = int(H.twcdep.size());
+    }
+    H.tw_ne = int(H.twcdep.size());
+    if (tail_inverse_smem(nt, H.tw_ne, depmax) > kTailInvSmem) return clear();
+    H.twpar = par;
+    H.twdep = dep;
+    H.tw_depmax = depmax;
+    std::vector<std::vector<int>> fr(nt), br(nt);
+    for (int jt = 0; jt < nt; jt++)
+        for (int a = par[jt]; a >= 0; a = par[a]) {
+            fr[a].push_back(jt);  // W(a, jt): a row-a entry of the forward gather
+            br[jt].push_back(a);  // W(a, jt) / D(a): a row-jt entry of the backward gather
+        }
+    auto nchunks = [&](const std::vector<std::vector<int>> &rows, int cw) {
+        int c = 0;
+        for (const auto &r : rows) c += int((r.size() + size_t(cw) - 1) / size_t(cw));
+        return c;
+    };
+    int cw = 8;
+    while ((size_t(nt) + size_t(std::max(nchunks(fr, cw), nchunks(br, cw)))) * sizeof(double) >
+           size_t(kRingStages) * kPieceBytes)
+        cw *= 2;
+    auto lists = [&](const std::vector<std::vector<int>> &rows, bool fwd, std::vector<int> &rp,
+                     std::vector<int2> &ch, std::vector<int> &cj, std::vector<int> &src,
+                     std::vector<int> *dsrc) {
+        rp.assign(nt + 1, 0);
+        ch.clear();
+        cj.clear();
+        src.clear();
+        if (dsrc) dsrc->clear();
+        for (int it = 0; it < nt; it++) {
+            const auto &r = rows[it];
+            for (size_t e0 = 0; e0 < r.size(); e0 += size_t(cw)) {
+                const size_t e1 = std::min(r.size(), e0 + size_t(cw));
+                ch.push_back(int2{int(cj.size()), int(cj.size() + (e1 - e0))});
+                for (size_t e = e0; e < e1; e++) {
+                    const int j = r[e];
+                    cj.push_back(j);
+                    src.push_back(fwd ? it * nt + j : j * nt + it);
+                    if (dsrc) dsrc->push_back(t0 + j);
+                }
+            }
+            rp[it + 1] = int(ch.size());
+        }
+    };
+    lists(fr, true, H.twfr, H.twfc, H.twfj, H.twfs, nullptr);
+    lists(br, false, H.twbr, H.twbc, H.twbj, H.twbs, &H.twbd);
+    auto pad32 = [](int64_t v) { return int((v + 31) / 32 * 32); };
+    H.tw_nfe = int(H.twfj.size());
+    H.tw_nbe = int(H.twbj.size());
+    H.tw_boff = pad32(std::max(1, H.tw_nfe));
+    H.tw_stride = H.tw_boff + pad32(std::max(1, H.tw_nbe));
+    for (auto *v : {&H.twfj, &H.twbj, &H.twfs, &H.twbs, &H.twbd})
+        if (v->empty()) v->push_back(0);
+    if (H.twfc.empty()) H.twfc.push_back(int2{0, 0});
+    if (H.twbc.empty()) H.twbc.push_back(int2{0, 0});
+    (void)n;
+}
+
 // Scatter tail of one matrix (see DevMat): the schedules, the gathered value
 // layout and the sweeps' piece lists that use them (pf2, pb2).  Without a
 // tail (no narrow level at the top, or more than 32767 tail rows) the lists
@@ -368,6 +464,7 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
     TRY(make_pieces(H.Fp, true, 12, 12, wide, lt));
     H.pf2 = wide;
     TRY(row_pieces(H.PPp, 5, 12, 12, H.pf2));
+    H.pf3 = H.pf2;
     TRY(scatter_pieces(H.SKf, H.pf2));
     // backward: inverse diagonal of the tail rows, scatter, wide levels
     std::vector<int> zp(n + 1, 0);
@@ -375,8 +472,12 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
     TRY(scatter_pieces(H.SKb, H.pb2));
     TRY(make_pieces(H.Cp, false, 12, 12, wide, lt));
     H.pb2.insert(H.pb2.end(), wide.begin(), wide.end());
+    H.pb3 = wide;
     set_run_ends(H.pf2);
     set_run_ends(H.pb2);
+    set_run_ends(H.pf3);
+    set_run_ends(H.pb3);
+    build_tail_inverse(H);
     return PF_OK;
 }
 
@@ -1102,6 +1203,35 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
     D.ntl = H.ntl;
     D.npf2 = int(H.pf2.size());
     D.npb2 = int(H.pb2.size());
+    D.npf3 = D.npb3 = 0;
+    if (H.nt > 0 && H.tw_ne > 0 && !H.pf3.empty() && !H.pb3.empty()) {
+        TRY(upload(ctx, &D.pf3, H.pf3.data(), H.pf3.size()));
+        TRY(upload(ctx, &D.pb3, H.pb3.data(), H.pb3.size()));
+        TRY(upload(ctx, &D.twfc, H.twfc.data(), H.twfc.size()));
+        TRY(upload(ctx, &D.twbc, H.twbc.data(), H.twbc.size()));
+        TRY(upload_padded(ctx, &D.twfr, H.twfr));
+        TRY(upload_padded(ctx, &D.twbr, H.twbr));
+        TRY(upload_padded(ctx, &D.twfj, H.twfj));
+        TRY(upload_padded(ctx, &D.twbj, H.twbj));
+        TRY(upload_padded(ctx, &D.twfs, H.twfs));
+        TRY(upload_padded(ctx, &D.twbs, H.twbs));
+        TRY(upload_padded(ctx, &D.twbd, H.twbd));
+        TRY(upload_padded(ctx, &D.twpar, H.twpar));
+        TRY(upload_padded(ctx, &D.twcp, H.twcp));
+        TRY(upload_padded(ctx, &D.twcdep, H.twcdep));
+        TRY(upload_padded(ctx, &D.twcpos, H.twcpos));
+        TRY(upload_padded(ctx, &D.twdep, H.twdep));
+        D.npf3 = int(H.pf3.size());
+        D.npb3 = int(H.pb3.size());
+        D.tw_nfc = int(H.twfr.back());
+        D.tw_nbc = int(H.twbr.back());
+        D.tw_nfe = H.tw_nfe;
+        D.tw_nbe = H.tw_nbe;
+        D.tw_boff = H.tw_boff;
+        D.tw_stride = H.tw_stride;
+        D.tw_ne = H.tw_ne;
+        D.tw_depmax = H.tw_depmax;
+    }
     if (H.nt > 0) {
         TRY(upload(ctx, &D.pf2, H.pf2.data(), H.pf2.size()));
         TRY(upload(ctx, &D.pb2, H.pb2.data(), H.pb2.size()));
@@ -1222,6 +1352,11 @@ pf_status ensure_factor_storage(pf_ctx *ctx, int which, int prec) {
         if (prec == PF_FP64) TRY(dalloc(ctx, reinterpret_cast<double **>(&w.TP[which][prec]), np));
         else TRY(dalloc(ctx, reinterpret_cast<float **>(&w.TP[which][prec]), np));
     }
+    if (m.npf3 > 0 && !w.TW[which][prec]) {
+        if (prec == PF_FP64) TRY(dalloc(ctx, reinterpret_cast<double **>(&w.TW[which][prec]), size_t(m.tw_stride)));
+        else TRY(dalloc(ctx, reinterpret_cast<float **>(&w.TW[which][prec]), size_t(m.tw_stride)));
+    }
+    if (m.npf3 > 0 && !w.TWd[which]) TRY(dalloc(ctx, &w.TWd[which], size_t(m.nt) * size_t(m.nt)));
     if (m.npf2 > 0 && !w.TV[which][prec]) {
         const size_t nt = size_t(ctx->dc.ninst) * size_t(m.tv_stride);
         if (prec == PF_FP64) TRY(dalloc(ctx, reinterpret_cast<double **>(&w.TV[which][prec]), nt));
@@ -1257,7 +1392,11 @@ void free_case_storage(pf_ctx *ctx) {
             w.TV[a][b] = nullptr;
             dfree(ctx, w.TP[a][b]);
             w.TP[a][b] = nullptr;
+            dfree(ctx, w.TW[a][b]);
+            w.TW[a][b] = nullptr;
         }
+        dfree(ctx, w.TWd[a]);
+        w.TWd[a] = nullptr;
         dfree(ctx, w.fsync[a]); w.fsync[a] = nullptr;
         dfree(ctx, w.famax[a]); w.famax[a] = nullptr;
         for (int b = 0; b < 2; b++) {
@@ -1292,6 +1431,8 @@ void free_case_storage(pf_ctx *ctx) {
     dfree(ctx, ctx->dc.inst_outage); ctx->dc.inst_outage = nullptr;
     dfree(ctx, ctx->dc.Psp); ctx->dc.Psp = nullptr;
     dfree(ctx, ctx->dc.Qsp); ctx->dc.Qsp = nullptr;
+    dfree(ctx, w.lsbuf); w.lsbuf = nullptr;
+    w.case_out.clear();
     ctx->dc.ncase = 0;
     ctx->dc.ninst = 1;
 }
@@ -1377,6 +1518,12 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int bl
     if (e != cudaSuccess) return cuda_fail(ctx, e, "factor launch");
     e = launch_tail_values(m, prec, F, w.TV[which][prec], nf, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tail values launch");
+    if (ctx->tune.tail == 3 && m.npf3 > 0 && nf == 1) {
+        e = counted(ctx, PF_K_FACTOR, 2, s, [&] {
+            return launch_tail_w(m, prec, F, w.TWd[which], w.TW[which][prec], s);
+        });
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tail inverse launch");
+    }
     w.factored[which][prec] = true;
     return PF_OK;
 }
@@ -1748,8 +1895,6 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
                        const int32_t *outage) {
     if (!ctx || ncase < 1) return fail(ctx, PF_ERR_ARG, "ncase must be >= 1");
     if (!ctx->analyzed) return fail(ctx, PF_ERR_STATE, "pf_analyze first");
-    drop_graph(ctx);  // its launches point into the batch's arrays
-    ctx->set_gen++;
     std::vector<int> out(ncase, -1), inst(ncase, 0), inst_out(1, -1);
     for (int c = 0; c < ncase; c++) {
         if (outage) {
@@ -1766,6 +1911,25 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
         for (size_t q = 0; q < size_t(ncase) * ctx->nbus; q++)
             if (!std::isfinite(load_scale[q])) return fail(ctx, PF_ERR_ARG, "non-finite load scale");
     TRY(ensure_device(ctx));
+    Workspace &w0 = ctx->ws;
+    if (ctx->dc.ncase == ncase && w0.ncase_alloc == ncase && w0.lsbuf && w0.case_out == out) {
+        // the same cases with new loads: the batch's arrays, factors and CUDA
+        // graph stay; only the specified injections are formed again
+        cudaError_t e = cudaSuccess;
+        if (load_scale) {
+            e = cudaMemcpy(w0.lsbuf, load_scale, sizeof(double) * size_t(ncase) * ctx->nbus,
+                           cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess)
+            e = counted(ctx, PF_K_SPEC, 1, 0, [&] {
+                return launch_case_spec(ctx->dn, ctx->dc, load_scale ? w0.lsbuf : nullptr, 0);
+            });
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "case spec");
+        return PF_OK;
+    }
+    drop_graph(ctx);  // its launches point into the batch's arrays
+    ctx->set_gen++;
     free_case_storage(ctx);
     DevCases &dc = ctx->dc;
     dc.ncase = ncase;
@@ -1775,13 +1939,16 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
     TRY(upload(ctx, &dc.inst_outage, inst_out.data(), inst_out.size()));
     TRY(dalloc(ctx, &dc.Psp, size_t(ncase) * ctx->nbus));
     TRY(dalloc(ctx, &dc.Qsp, size_t(ncase) * ctx->nbus));
-    double *ls = nullptr;
-    if (load_scale) TRY(upload(ctx, &ls, load_scale, size_t(ncase) * ctx->nbus));
-    cudaError_t e = counted(ctx, PF_K_SPEC, 1, 0, [&] { return launch_case_spec(ctx->dn, dc, ls, 0); });
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (ls) dfree(ctx, ls);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "case spec");
     Workspace &w = ctx->ws;
+    TRY(dalloc(ctx, &w.lsbuf, size_t(ncase) * ctx->nbus));
+    cudaError_t e = cudaSuccess;
+    if (load_scale)
+        e = cudaMemcpy(w.lsbuf, load_scale, sizeof(double) * size_t(ncase) * ctx->nbus, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = counted(ctx, PF_K_SPEC, 1, 0, [&] { return launch_case_spec(ctx->dn, dc, load_scale ? w.lsbuf : nullptr, 0); });
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "case spec");
+    w.case_out = out;
     TRY(dalloc(ctx, &w.ef, size_t(ncase) * 4 * ctx->nbus));
     TRY(dalloc(ctx, &w.vec, size_t(ncase) * 3 * ctx->nbus));
     TRY(dalloc(ctx, &w.bmax, size_t(ncase) * 16));
@@ -1968,6 +2135,8 @@ pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doubl
                                std::max(ctx->dm[0].n, ctx->dm[1].n));
     if (ctx->tune.cluster > 0 && ctx->tune.cluster < cl) cl = ctx->tune.cluster < 8 ? 1 : 8;
     const bool tail = ctx->tune.tail != 2;
+    // tail form 3: every case's solves use the factor of instance 0
+    const bool tw = ctx->tune.tail == 3 && (ctx->dc.ninst == 1 || lowrank);
     cudaError_t e = counted(ctx, PF_K_RUN, 1, s, [&] {
         return launch_fdpf(ctx->dn, ctx->dc, ctx->dm, prec, F0, F1, tail ? w.TV[0][prec] : nullptr,
                            tail ? w.TV[1][prec] : nullptr, w.A[0], w.A[1], w.fstatus[0][prec],
@@ -1975,7 +2144,8 @@ pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doubl
                            ctx->smem_optin, ctx->smem_per_sm, cl, ctx->tune.threads, s,
                            lowrank ? w.LZ[0][prec] : nullptr,
                            lowrank ? w.LZ[1][prec] : nullptr, lowrank ? w.LK[0] : nullptr,
-                           lowrank ? w.LK[1] : nullptr, fb);
+                           lowrank ? w.LK[1] : nullptr, fb, tw ? w.TW[0][prec] : nullptr,
+                           tw ? w.TW[1][prec] : nullptr);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fdpf launch");
     return PF_OK;
@@ -2286,7 +2456,7 @@ pf_status pf_get_tuning(const pf_ctx *ctx, pf_tuning *out) {
 pf_status pf_set_tuning(pf_ctx *ctx, const pf_tuning *t) {
     if (!ctx || !t) return fail(ctx, PF_ERR_ARG, "null pointer");
     if (t->engine < 0 || t->engine > PF_ENGINE_CLUSTER || t->factor < 0 || t->factor > 2 || t->tail < 0 ||
-        t->tail > 2 || t->outage < 0 || t->outage > 2 ||
+        t->tail > 3 || t->outage < 0 || t->outage > 2 ||
         (t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16) ||
         (t->threads != 0 && t->threads != 128 && t->threads != 256 && t->threads != 512))
         return fail(ctx, PF_ERR_ARG, "tuning field out of range");
@@ -2325,6 +2495,7 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     if (std::max(ctx->hm[0].max_col, ctx->hm[1].max_col) <= kDepMaxCol) factors.push_back(1);
     std::vector<int> tails{2};
     if (o.method == PF_FDPF && (ctx->dm[0].npf2 > 0 || ctx->dm[1].npf2 > 0)) tails.push_back(1);
+    if (o.method == PF_FDPF && (ctx->dm[0].npf3 > 0 || ctx->dm[1].npf3 > 0)) tails.push_back(3);
     std::vector<int> outages{1};
     if (o.method == PF_FDPF && ctx->dc.ninst > 1) outages.push_back(2);
     // the lane engine has no cluster, tail or outage choice; the cluster
@@ -2336,8 +2507,11 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
                 for (int t : (e == PF_ENGINE_LANES ? std::vector<int>{0} : tails))
                     for (int u : (e != PF_ENGINE_BLOCK ? std::vector<int>{1} : outages))
                         for (int th : (e == PF_ENGINE_BLOCK && c == 1 && ncase > 1 ? std::vector<int>{512, 256, 128}
-                                                                                    : std::vector<int>{0}))
+                                                                                    : std::vector<int>{0})) {
+                            // tail form 3 serves runs whose solves all use instance 0, on the block engine
+                            if (t == 3 && (e != PF_ENGINE_BLOCK || (ctx->dc.ninst > 1 && u != 2))) continue;
                             cand.push_back(pf_tuning{e, c, f, t, u, th, 0.0});
+                        }
     std::vector<pf_case_result> res(static_cast<size_t>(ncase));
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
@@ -2754,6 +2928,54 @@ int gbpf_selftest_sweep(pf_ctx *ctx, int which, int prec, int stall_at, int hold
     if (e == cudaErrorInvalidValue) return -1;
     if (e == cudaSuccess) e = cudaMemcpy(status_host, st, sizeof(int), cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? 0 : -2;
+}
+
+// Test hook (host only, no GPU needed): the partitioned inverse of the
+// narrow top of matrix `which` (tail form 3).  sizes[10] receives {n, t0, nt,
+// forward chunks, backward chunks, forward entries, backward entries, pieces
+// of pf3, pieces of pb3, entries of L_TT}; when cap (ints per array) covers
+// them, par (nt), fr and br (nt + 1), fc and bc (2 per chunk), fj, fs, bj,
+// bs and bd (one per entry) are copied.  Returns 0, or -1 for a bad argument
+// or a matrix that has not been analysed.
+int gbpf_debug_tail_inverse(const pf_ctx *ctx, int which, int *sizes, int *par, int *fr, int *fc, int *fj,
+                            int *fs, int *br, int *bc, int *bj, int *bs, int *bd, int cap) {
+    if (!ctx || !sizes || which < 0 || which > 1) return -1;
+    const gbpf::HostMat &H = ctx->hm[which];
+    if (H.lvl_ptr.empty()) return -1;
+    const bool on = !H.pf3.empty() && H.tw_ne > 0;
+    const int nfc = on ? int(H.twfr.back()) : 0, nbc = on ? int(H.twbr.back()) : 0;
+    sizes[0] = H.n;
+    sizes[1] = H.t0;
+    sizes[2] = on ? H.nt : 0;
+    sizes[3] = nfc;
+    sizes[4] = nbc;
+    sizes[5] = on ? H.tw_nfe : 0;
+    sizes[6] = on ? H.tw_nbe : 0;
+    sizes[7] = int(H.pf3.size());
+    sizes[8] = int(H.pb3.size());
+    sizes[9] = on ? H.tw_ne : 0;
+    if (!on) return 0;
+    auto put = [&](const std::vector<int> &v, int count, int *dst) {
+        if (dst && cap >= count) std::copy(v.begin(), v.begin() + count, dst);
+    };
+    auto put2 = [&](const std::vector<int2> &v, int count, int *dst) {
+        if (dst && cap >= 2 * count)
+            for (int k = 0; k < count; k++) {
+                dst[2 * k] = v[size_t(k)].x;
+                dst[2 * k + 1] = v[size_t(k)].y;
+            }
+    };
+    put(H.twpar, H.nt, par);
+    put(H.twfr, H.nt + 1, fr);
+    put(H.twbr, H.nt + 1, br);
+    put2(H.twfc, nfc, fc);
+    put2(H.twbc, nbc, bc);
+    put(H.twfj, H.tw_nfe, fj);
+    put(H.twfs, H.tw_nfe, fs);
+    put(H.twbj, H.tw_nbe, bj);
+    put(H.twbs, H.tw_nbe, bs);
+    put(H.twbd, H.tw_nbe, bd);
+    return 0;
 }
 
 // Test hook (host only, no GPU needed): the CSR copy of L's pattern and its

@@ -18,6 +18,7 @@ namespace gbpf {
 // level, copied into shared memory by one TMA bulk transfer group.
 constexpr int kPieceBytes = 8192;
 constexpr int kPieceSlack = 128;
+constexpr int kRingStages = 4;  // stages of the staging ring (one piece each)
 
 // One staged piece: rows (columns) [r0, r1) whose entries are [e0, e1) of
 // the CSR (CSC) arrays, all in level order.  mode: 0 one thread per row,
@@ -107,6 +108,28 @@ struct DevMat {
     // targets of one tail level
     int4 *tlev = nullptr, *tinfo = nullptr;
     int ft_kmax = 0;
+    // Partitioned inverse of the same narrow top (tail form 3): with W =
+    // L_TT^-1 of rows T = [t0, n) (unit lower; W(i, j) != 0 only for i an
+    // ancestor of j), the sweeps run below the top (pf3: the wide levels and
+    // the top rows' entries below t0, which leave c_T = b_T - L_TB z_B in
+    // x[t0..n); pb3: the wide levels backward) and the top is two gathers,
+    //   z_T = W c_T,   x_T = W^T D_T^-1 z_T,
+    // each split into chunks of a few entries (twfc/twbc {first, end entry},
+    // rows' chunk ranges twfr/twbr, entries' columns twfj/twbj - t0) whose
+    // partial sums are added per row in chunk order.  Values per instance
+    // (TW): [forward W(i, j) | backward W(j, i) / D(j)] at tw_boff, gathered
+    // after each factorisation from the dense W (twfs/twbs: row * nt + col;
+    // twbd: the D index of a backward entry).  The inverse itself is formed
+    // by k_tail_inverse from the columns of L_TT (twcp, twcdep, twcpos, the
+    // depth twdep and parent twpar of every top row).
+    int npf3 = 0, npb3 = 0;
+    Piece *pf3 = nullptr, *pb3 = nullptr;
+    int tw_nfc = 0, tw_nbc = 0, tw_nfe = 0, tw_nbe = 0, tw_boff = 0, tw_stride = 0;
+    int2 *twfc = nullptr, *twbc = nullptr;
+    int *twfr = nullptr, *twbr = nullptr, *twfj = nullptr, *twbj = nullptr;
+    int *twfs = nullptr, *twbs = nullptr, *twbd = nullptr;
+    int *twpar = nullptr, *twcp = nullptr, *twcdep = nullptr, *twcpos = nullptr, *twdep = nullptr;
+    int tw_ne = 0, tw_depmax = 0;
     int *Ap = nullptr, *Aj = nullptr, *Apos = nullptr;  // off-diagonal A (no fill), by row:
                                                        // column and value slot of each entry
     // Newton-Raphson Jacobian (2 x 2 blocks on the same pattern, B' only)
@@ -128,7 +151,7 @@ struct DevMat {
 // of val[e] X(ref[e]).  Values are packed per CTA ([entries | diagonal
 // values]) and gathered after every factorisation from vsrc {kind, a, b}:
 // 0 the factor value F[a], 1 -W[a], 2 -W[a] F[b], W being the dense inverse
-// of the tail block of L by column (W[jt * nt + it]).
+// of the tail block of L, row-major (W(it, jt) at W[it * nt + jt]).
 constexpr int kClCtas = 16;
 constexpr int kClTailMax = 2048;   // largest tail whose dense inverse is formed
 constexpr int kTailInvWarps = 16;  // T columns (one per warp) per block of k_tail_inverse
@@ -212,6 +235,13 @@ struct HostMat {
     int ft_tmax = 0;
     std::vector<int4> tlev, tinfo;
     int ft_kmax = 0;
+    // partitioned inverse of the narrow top (see DevMat)
+    std::vector<Piece> pf3, pb3;
+    std::vector<int> twpar, twcp, twcdep, twcpos, twdep;
+    int tw_ne = 0, tw_depmax = 0;
+    std::vector<int> twfr, twbr, twfj, twbj, twfs, twbs, twbd;
+    std::vector<int2> twfc, twbc;
+    int tw_nfe = 0, tw_nbe = 0, tw_boff = 0, tw_stride = 0;
 };
 
 // Device arrays of the network and of the case batch.
@@ -279,6 +309,8 @@ struct Workspace {
     unsigned fepoch[2] = {0u, 0u};
     void *TV[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mat][prec] tail values
     void *TP[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mat][prec] tail targets' parts
+    void *TW[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mat][prec] tail inverse values (instance 0)
+    double *TWd[2] = {nullptr, nullptr};  // [mat] dense inverse of the narrow top (FP64, nt x nt)
     // low-rank outages, per matrix: Z [ninst][2][n] of the factor type (per
     // precision), K [ninst][4], solve scratch
     void *LZ[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -295,6 +327,8 @@ struct Workspace {
     int *cstatus = nullptr;   // [ncase] run status
     pf_case_result *res = nullptr; // [ncase]
     int ncase_alloc = 0;
+    double *lsbuf = nullptr;  // [ncase][nbus] load scales of the batch (kept for a cheap re-set)
+    std::vector<int> case_out;  // host copy of the batch's outages (-1: none)
     // Newton-Raphson workspace (allocated on first use): block factors per
     // precision, the FP64 Jacobian and per-case factor status, [ncase][jstride]
     void *JF[2] = {nullptr, nullptr};
@@ -407,6 +441,9 @@ struct FactorJob {
 // column counter and abort flag.
 cudaError_t launch_factor_jobs(const FactorJob *jobs_dev, int njob, const int2 *items_dev,
                                unsigned nitems, unsigned *sync_dev, int prec, int nsm, cudaStream_t s);
+// Partitioned inverse of the narrow top of instance 0 (tail form 3): the
+// dense W = L_TT^-1 into Wd (FP64) and the gathered values into TW (prec).
+cudaError_t launch_tail_w(const DevMat &m, int prec, const void *F, double *Wd, void *TW, cudaStream_t s);
 cudaError_t launch_tail_values(const DevMat &m, int prec, const void *F, void *TV, int ninst,
                                cudaStream_t s);
 cudaError_t launch_solve(const DevMat &m, int prec, const void *F, const void *TV,
@@ -422,7 +459,8 @@ cudaError_t launch_mismatch(const DevNet &dn, const DevCases &dc, const double *
                             cudaStream_t s);
 struct NrLaunch;
 // fb (optional): the Newton-Raphson launch that unconverged cases fall back
-// to inside the same launch (ignored when its factor scratch does not fit).
+// to inside the same launch (ignored when its factor scratch does not fit);
+// TW0/TW1 (optional): tail-inverse values of instance 0 (tail form 3).
 cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, int prec,
                         const void *F0, const void *F1, const void *TV0, const void *TV1,
                         const double *A0, const double *A1,
@@ -431,7 +469,8 @@ cudaError_t launch_fdpf(const DevNet &dn, const DevCases &dc, const DevMat *m, i
                         pf_case_result *res, size_t smem_optin, size_t smem_per_sm, int cluster,
                         int threads, cudaStream_t s,
                         const void *Z0 = nullptr, const void *Z1 = nullptr, const double *K0 = nullptr,
-                        const double *K1 = nullptr, const NrLaunch *fb = nullptr);
+                        const double *K1 = nullptr, const NrLaunch *fb = nullptr,
+                        const void *TW0 = nullptr, const void *TW1 = nullptr);
 // Z = A^-1 U and K = (I - S U^T Z)^-1 S of every outage instance of matrix
 // `which` from the base factor F (instance 0): the low-rank form of the
 // outage cases.  gvec: [2 (ninst - 1)][n] scratch of the factor type.

@@ -1,8 +1,9 @@
 """Project autotuner (pf_autotune) and explicit kernel mappings (pf_set_tuning).
 
 Every mapping the tuner may choose -- cluster size of a single case, the
-dependency-driven or block-per-instance factor, the scatter or level-by-level
-narrow tail, the block or lane engine of a batch -- must reach the oracle's
+dependency-driven or block-per-instance factor, the scatter, level-by-level
+or partitioned-inverse narrow top, the block or lane engine of a batch, the
+block size -- must reach the oracle's
 solution (1e-8 p.u./rad, both sides run tight); the tuner must return one of
 them with a positive time, and leave it set on the context.
 """
@@ -36,7 +37,7 @@ def test_every_single_case_mapping_matches_oracle(oracle):
     g.set_cases(1)
     vm = torch.zeros((1, case.n), dtype=torch.float64, device=DEV)
     va = torch.zeros_like(vm)
-    for prec, cl, fac, tail in itertools.product([gbpf.PF_FP64, gbpf.PF_FP32], [1, 8, 16], [1, 2], [1, 2]):
+    for prec, cl, fac, tail in itertools.product([gbpf.PF_FP64, gbpf.PF_FP32], [1, 8, 16], [1, 2], [1, 2, 3]):
         gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, cluster=cl, factor=fac, tail=tail)
         opts = gbpf.run_opts(gbpf.PF_FDPF, prec, tol=1e-11, max_iter=300)
         st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, 1)
@@ -92,18 +93,21 @@ def test_low_rank_outages_match_oracle(oracle, precision):
     va = torch.zeros_like(vm)
     opts = gbpf.run_opts(gbpf.PF_FDPF, precision, tol=1e-11, max_iter=300)
     out = {}
-    for outage in (1, 2):
-        gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, outage=outage)
+    # (outage form, tail form): per-case factors; low-rank with the scatter
+    # top; low-rank with the top's partitioned inverse (tail form 3); and
+    # form 3 asked for with per-case factors, which runs the scatter top
+    for outage, tail in ((1, 1), (2, 1), (2, 3), (1, 3)):
+        gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, outage=outage, tail=tail)
         st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
-        assert st == gbpf.PF_OK, (outage, gbpf.pf_last_error(g.ctx))
-        out[outage] = (vm.cpu().numpy().copy(), va.cpu().numpy().copy())
+        assert st == gbpf.PF_OK, (outage, tail, gbpf.pf_last_error(g.ctx))
+        out[outage, tail] = (vm.cpu().numpy().copy(), va.cpu().numpy().copy())
     for c in (0, 2, 7, 15):
         cc = gridgen.apply_scenario(base, sc, c)
         rc, vm0, va0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
         assert rc == oracle.OK
-        for outage in (1, 2):
-            assert np.max(np.abs(out[outage][0][c] - vm0)) <= 1e-8, (outage, c)
-            assert np.max(np.abs(out[outage][1][c] - va0)) <= 1e-8, (outage, c)
+        for key in out:
+            assert np.max(np.abs(out[key][0][c] - vm0)) <= 1e-8, (key, c)
+            assert np.max(np.abs(out[key][1][c] - va0)) <= 1e-8, (key, c)
     g.close()
 
 

@@ -43,12 +43,15 @@ def batch(oracle):
     return base, sc, refs
 
 
-@pytest.mark.parametrize("precision,threads", [(gbpf.PF_FP32, 512), (gbpf.PF_FP32, 256), (gbpf.PF_FP64, 512)])
-def test_batch10k_full_size_sampled(batch, precision, threads):
+@pytest.mark.parametrize("precision,threads,tail", [(gbpf.PF_FP32, 512, 1), (gbpf.PF_FP32, 256, 1),
+                                                   (gbpf.PF_FP64, 512, 1), (gbpf.PF_FP32, 512, 3),
+                                                   (gbpf.PF_FP32, 256, 3), (gbpf.PF_FP64, 512, 3)])
+def test_batch10k_full_size_sampled(batch, precision, threads, tail):
     base, sc, refs = batch
     g = gbpf.Grid(base)
     g.set_cases(sc.ncase, sc.load_scale, sc.outage)
-    gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, cluster=1, factor=1, tail=1, outage=2, threads=threads)
+    gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_BLOCK, cluster=1, factor=1, tail=tail, outage=2,
+                       threads=threads)
     vm = torch.zeros((sc.ncase, base.n), dtype=torch.float64, device=DEV)
     va = torch.zeros_like(vm)
     for tol, bound in ((1e-8, 1e-7), (1e-11, 1e-8)):

@@ -80,3 +80,43 @@ def test_graph_replays_match_direct_runs(oracle, engine, ncase, prec):
     assert st == gbpf.PF_OK
     assert torch.equal(vm, ref[0]) and torch.equal(va, ref[1])
     g.close()
+
+
+def test_new_loads_on_the_same_cases_reuse_the_batch(oracle):
+    """pf_set_cases with the same cases (same count, same outages) and new
+    load scales keeps the batch's arrays, factors and CUDA graph and only
+    forms the specified injections again: the replayed run solves the new
+    loads (against the oracle), and going back to the first loads gives the
+    first results bit for bit."""
+    base = gridgen.config(0)
+    sc = gridgen.scenarios(base, n_load=2, n_outage=2, seed=5)
+    loads_b = sc.load_scale * 1.3
+    g = gbpf.Grid(base)
+    g.set_cases(sc.ncase, sc.load_scale, sc.outage)
+    gbpf.pf_set_graphs(g.ctx, True)
+    vm = torch.zeros((sc.ncase, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-11, max_iter=300)
+    for _ in range(3):  # direct, capture + launch, replay
+        st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+        assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    first = (vm.clone(), va.clone())
+    g.set_cases(sc.ncase, loads_b, sc.outage)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+    assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    v, a = vm.cpu().numpy(), va.cpu().numpy()
+    for c in range(sc.ncase):
+        cc = base.copy()
+        cc.pd = cc.pd * loads_b[c]
+        cc.qd = cc.qd * loads_b[c]
+        if sc.outage[c] >= 0:
+            cc.status = cc.status.copy()
+            cc.status[sc.outage[c]] = 0
+        rc, vm0, va0, _, _ = oracle.power_flow(cc, oracle.NR, tol=1e-12, max_iter=30)
+        assert rc == oracle.OK
+        assert np.max(np.abs(v[c] - vm0)) <= 1e-8 and np.max(np.abs(a[c] - va0)) <= 1e-8, c
+    g.set_cases(sc.ncase, sc.load_scale, sc.outage)
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+    assert st == gbpf.PF_OK
+    assert torch.equal(vm, first[0]) and torch.equal(va, first[1])
+    g.close()

@@ -681,3 +681,86 @@ def test_cluster_program_solves_like_oracle(lib, oracle, cfg):
         if cfg == 1:
             assert P["smem"] + 4096 <= 232448, P["smem"]
     g.close()
+
+
+def _tail_inverse(lib, g, which):
+    f = lib.gbpf_debug_tail_inverse
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_void_p] + [C.c_void_p] * 10 + [C.c_int]
+    sizes = np.zeros(10, np.int32)
+    assert f(g.ctx, which, sizes.ctypes.data, *([None] * 10), 0) == 0
+    n, t0, nt, nfc, nbc, nfe, nbe, npf3, npb3, ne = (int(x) for x in sizes)
+    shapes = (nt, nt + 1, 2 * nfc, nfe, nfe, nt + 1, 2 * nbc, nbe, nbe, nbe)
+    arrs = [np.zeros(max(1, k), np.int32) for k in shapes]
+    assert f(g.ctx, which, sizes.ctypes.data, *[a.ctypes.data for a in arrs], max(shapes + (1,))) == 0
+    par, fr, fc, fj, fs, br, bc, bj, bs, bd = (a[:k] for a, k in zip(arrs, shapes))
+    return dict(n=n, t0=t0, nt=nt, nfc=nfc, nbc=nbc, nfe=nfe, nbe=nbe, npf3=npf3, npb3=npb3, ne=ne), \
+        par, fr, fc.reshape(-1, 2), fj, fs, br, bc.reshape(-1, 2), bj, bs, bd
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_tail_inverse_gathers(lib, oracle, cfg):
+    """Tail form 3 (the narrow top solved through W = L_TT^-1): the parents
+    within the top are the elimination tree's (first row of each column of
+    L, from the CSR pattern); the forward gather of row i lists exactly its
+    descendants and the backward gather exactly its ancestors, each pair once,
+    chunked in order; the dense-W sources and diagonal indices point at
+    (ancestor, descendant); the counts agree with the oracle's own symbolic
+    analysis (numbering-independent: the number of ancestor/descendant pairs
+    in the top run of narrow levels); and the chunk partial sums with the
+    top's vector fit the staging ring."""
+    case = gridgen.config_raw(cfg)
+    g = gbpf.Grid(case)
+    for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
+        sz, par, fr, fc, fj, fs, br, bc, bj, bs, bd = _tail_inverse(lib, g, which)
+        nt, t0 = sz["nt"], sz["t0"]
+        assert nt > 0 and sz["npf3"] > 0 and sz["npb3"] > 0
+        offLc, Fp, Fc, *_ = _csr(lib, g, which)
+        n = sz["n"]
+        first_row = np.full(n, -1)
+        for i in range(n - 1, -1, -1):  # the smallest row of each column
+            first_row[Fc[Fp[i]:Fp[i + 1]]] = i
+        for it in range(nt):
+            p = first_row[t0 + it]
+            assert par[it] == (p - t0 if p >= 0 else -1)
+        anc = [[] for _ in range(nt)]
+        for it in range(nt):
+            a = par[it]
+            while a >= 0:
+                anc[it].append(a)
+                a = par[a]
+        desc = [[] for _ in range(nt)]
+        for j in range(nt):
+            for a in anc[j]:
+                desc[a].append(j)
+        assert np.all(np.diff(fr) >= 0) and fr[0] == 0 and fr[-1] == sz["nfc"]
+        assert np.all(np.diff(br) >= 0) and br[0] == 0 and br[-1] == sz["nbc"]
+        for rows, rp, ch, cj, src, fwd in ((desc, fr, fc, fj, fs, True), (anc, br, bc, bj, bs, False)):
+            assert ch[0, 0] == 0 if len(ch) else True
+            for it in range(nt):
+                got = []
+                for k in range(rp[it], rp[it + 1]):
+                    a, b = ch[k]
+                    assert 0 < b - a <= 4096 and (k == 0 or a == ch[k - 1, 1])
+                    got.extend(cj[a:b].tolist())
+                    for e in range(a, b):
+                        assert src[e] == (it * nt + cj[e] if fwd else cj[e] * nt + it)
+                assert got == sorted(rows[it])
+        assert np.array_equal(bd, t0 + bj)
+        # the oracle's count: ancestor/descendant pairs inside its top run
+        an = oracle.analyze(case, name)
+        Lp, Li, lev, nl = an["Lp"], an["Li"], an["level"], an["nlevels"]
+        cnt = np.bincount(lev, minlength=nl + 1)
+        lt = nl
+        while lt >= 1 and cnt[lt] <= 16:
+            lt -= 1
+        parent = np.array([Li[Lp[j]] if Lp[j + 1] > Lp[j] else -1 for j in range(lev.shape[0])])
+        pairs = 0
+        for j in np.nonzero(lev > lt)[0]:
+            a = parent[j]
+            while a >= 0:
+                pairs += 1
+                a = parent[a]
+        assert sz["nfe"] == sz["nbe"] == pairs
+        assert (nt + max(sz["nfc"], sz["nbc"])) * 8 <= 4 * 8192
+    g.close()
