@@ -387,10 +387,18 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
             H.ft_tmax = std::max(H.ft_tmax, H.tptr[ke] - H.tptr[kb]);
         }
     }
-    // level table and per-target descriptors of the tail factor, so that its
-    // level loop needs no dependent global loads
+    // level table, per-target descriptors and warp tasks of the tail factor,
+    // so that its level loop needs no dependent global loads.  Within a level
+    // every target gets the smallest power of two of lanes G that leaves at
+    // most four terms to a lane (at most 32); the level's targets are
+    // reordered by (G, terms) descending and cut into tasks of 32 / G
+    // consecutive targets of one G (a warp's work), listed by decreasing
+    // cost (terms per lane) so that warps taking tasks round-robin balance.
+    // tipos maps a target to its position in the reordered level.
     H.tlev.assign(size_t(2) * size_t(std::max(1, H.ntl)), int4{0, 0, 0, 0});
     H.tinfo.assign(size_t(std::max(1, H.ft_ng)), int4{0, 0, 0, 0});
+    H.tipos.assign(size_t(std::max(1, H.ft_ng)), 0);
+    H.ttask.clear();
     H.ft_kmax = 0;
     if (H.ft_ne < 65536) {
         for (int li = 0; li < H.ntl; li++) {
@@ -398,21 +406,50 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
             const int cb = H.lvl_ptr[l], ce = H.lvl_ptr[l + 1];
             const int kb = H.Cp[cb] + cb - H.ft_g0, ke = H.Cp[ce] + ce - H.ft_g0;
             const int tb = H.tptr[kb], te = H.tptr[ke];
-            int maxterms = 0;
-            for (int k = kb; k < ke; k++) maxterms = std::max(maxterms, H.tptr[k + 1] - H.tptr[k]);
-            int G = 1;
-            while (G < 32 && maxterms > 4 * G) G *= 2;
-            H.tlev[2 * li] = int4{kb, ke, tb, te};
-            H.tlev[2 * li + 1] = int4{cb - t0, ce - t0, G, 0};
-            H.ft_kmax = std::max(H.ft_kmax, ke - kb);
+            struct Tg {
+                int G, cnt, k;
+            };
+            std::vector<Tg> ord;
             for (int k = kb; k < ke; k++) {
+                const int cnt = H.tptr[k + 1] - H.tptr[k];
+                int G = 1;
+                while (G < 32 && cnt > 4 * G) G *= 2;
+                ord.push_back(Tg{G, cnt, k});
+            }
+            std::sort(ord.begin(), ord.end(), [](const Tg &a, const Tg &b) {
+                if (a.G != b.G) return a.G > b.G;
+                if (a.cnt != b.cnt) return a.cnt > b.cnt;
+                return a.k < b.k;
+            });
+            const int nk = ke - kb;
+            std::vector<int4> tasks;  // {first position, targets, G, cost}
+            for (int p = 0; p < nk;) {
+                const int G = ord[size_t(p)].G;
+                int q = p, cost = 0;
+                while (q < nk && q - p < 32 / G && ord[size_t(q)].G == G) {
+                    cost = std::max(cost, (ord[size_t(q)].cnt + G - 1) / G);
+                    q++;
+                }
+                tasks.push_back(int4{p, q - p, G, cost});
+                p = q;
+            }
+            std::stable_sort(tasks.begin(), tasks.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
+            const int t_first = int(H.ttask.size());
+            for (const int4 &t : tasks) H.ttask.push_back(int4{t.x, t.y, t.z, 0});
+            H.tlev[2 * li] = int4{kb, ke, tb, te};
+            H.tlev[2 * li + 1] = int4{cb - t0, ce - t0, t_first, int(H.ttask.size())};
+            H.ft_kmax = std::max(H.ft_kmax, nk);
+            for (int p = 0; p < nk; p++) {
+                const int k = ord[size_t(p)].k;
                 const int c = H.tcol[k];
                 const int t = k - (H.Cp[c] + c - H.ft_g0);
-                H.tinfo[k] = int4{H.tptr[k] - tb, H.tptr[k + 1] - tb,
-                                  t > 0 ? H.Cp[c] + t - 1 - H.ft_e0 : -1, c - t0};
+                H.tinfo[size_t(kb + p)] = int4{H.tptr[k] - tb, H.tptr[k + 1] - tb,
+                                               t > 0 ? H.Cp[c] + t - 1 - H.ft_e0 : -1, c - t0};
+                H.tipos[size_t(k)] = kb + p;
             }
         }
     }
+    if (H.ttask.empty()) H.ttask.push_back(int4{0, 0, 1, 0});
     auto pad32 = [](int64_t v) { return int((v + 31) / 32 * 32); };
     H.tv_f = 0;
     H.tv_b = pad32(int64_t(posf.size()));
@@ -1254,6 +1291,9 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
         D.ft_tterms = int(H.tterm.size());
         TRY(upload(ctx, &D.tlev, H.tlev.data(), H.tlev.size()));
         TRY(upload(ctx, &D.tinfo, H.tinfo.data(), H.tinfo.size()));
+        TRY(upload(ctx, &D.ttask, H.ttask.data(), H.ttask.size()));
+        D.ft_ntask = int(H.ttask.size());
+        TRY(upload_padded(ctx, &D.tipos, H.tipos));
         D.ft_kmax = H.ft_kmax;
         D.ft_tmax = H.ft_ne < 65536 ? H.ft_tmax : -1;
         D.ft_ng = H.ft_ng;
@@ -2928,6 +2968,27 @@ int gbpf_selftest_sweep(pf_ctx *ctx, int which, int prec, int stall_at, int hold
     if (e == cudaErrorInvalidValue) return -1;
     if (e == cudaSuccess) e = cudaMemcpy(status_host, st, sizeof(int), cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? 0 : -2;
+}
+
+// Test hook (host only, no GPU needed): the warp tasks of the tail factor
+// of matrix `which` and the position of every target in its level.
+// *ntask receives the number of tasks; tasks (4 ints each) and tipos (ng
+// ints) are copied when cap covers them.  Returns 0, or -1 for a bad argument
+// or a matrix that has not been analysed.
+int gbpf_debug_tail_tasks(const pf_ctx *ctx, int which, int *ntask, int *tasks, int *tipos, int cap) {
+    if (!ctx || !ntask || which < 0 || which > 1) return -1;
+    const gbpf::HostMat &H = ctx->hm[which];
+    if (H.lvl_ptr.empty()) return -1;
+    *ntask = int(H.ttask.size());
+    if (tasks && cap >= 4 * int(H.ttask.size()))
+        for (size_t i = 0; i < H.ttask.size(); i++) {
+            tasks[4 * i] = H.ttask[i].x;
+            tasks[4 * i + 1] = H.ttask[i].y;
+            tasks[4 * i + 2] = H.ttask[i].z;
+            tasks[4 * i + 3] = H.ttask[i].w;
+        }
+    if (tipos && cap >= H.ft_ng) std::copy(H.tipos.begin(), H.tipos.begin() + H.ft_ng, tipos);
+    return 0;
 }
 
 // Test hook (host only, no GPU needed): the partitioned inverse of the

@@ -101,13 +101,18 @@ struct DevMat {
     int ft_tmax = 0;
     int ft_tterms = 0;         // tail terms in tterm
     // per tail level li: tlev[2 li] = {first target, end target, first term,
-    // end term}, tlev[2 li + 1] = {first column - t0, end column - t0, lanes
-    // per target, 0};
-    // per target: tinfo = {first term, end term (both relative to its level's
-    // first), L entry - e0 (-1 for the diagonal), column - t0}; ft_kmax = most
-    // targets of one tail level
-    int4 *tlev = nullptr, *tinfo = nullptr;
+    // end term}, tlev[2 li + 1] = {first column - t0, end column - t0, first
+    // task, end task}; the level's targets are reordered (position p of level
+    // li holds target k with tipos[k] = first target + p);
+    // per position: tinfo = {first term, end term (both relative to its
+    // level's first), L entry - e0 (-1 for the diagonal), column - t0};
+    // per task (a warp's work): ttask = {first position relative to the
+    // level, targets, lanes per target G, 0}, 32 / G targets at most;
+    // ft_kmax = most targets of one tail level
+    int4 *tlev = nullptr, *tinfo = nullptr, *ttask = nullptr;
+    int *tipos = nullptr;
     int ft_kmax = 0;
+    int ft_ntask = 0;          // entries of ttask
     // Partitioned inverse of the same narrow top (tail form 3): with W =
     // L_TT^-1 of rows T = [t0, n) (unit lower; W(i, j) != 0 only for i an
     // ancestor of j), the sweeps run below the top (pf3: the wide levels and
@@ -233,7 +238,8 @@ struct HostMat {
     std::vector<int> tapos, tcol, gsplit, tptr;
     std::vector<int2> tterm;
     int ft_tmax = 0;
-    std::vector<int4> tlev, tinfo;
+    std::vector<int4> tlev, tinfo, ttask;
+    std::vector<int> tipos;
     int ft_kmax = 0;
     // partitioned inverse of the narrow top (see DevMat)
     std::vector<Piece> pf3, pb3;

@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(kDepThreads)
 // (final once k_factor_dep is done): part = a - sum_{k < t0} L(i,k) D(k)
 // L(c,k) over the target's gather terms, one warp per target (lanes stride
 // its terms, then a shuffle reduction in lane order), spread over many
-// blocks; k_factor_tail continues from it.
+// blocks, stored at the target's position in its level (tipos);
+// k_factor_tail continues from it.
 template <class T>
 __global__ void __launch_bounds__(256)
     k_factor_tail_pre(DevMat m, const double *A, const T *F, T *partg) {
@@ -323,20 +324,22 @@ __global__ void __launch_bounds__(256)
         s += Lc[e.x] * (Lc[e.y] * v[e.z]);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) partg[(long long)inst * m.ft_ng + k] = T(A[(long long)inst * m.stride + m.tapos[k]]) - s;
+    if (lane == 0) partg[(long long)inst * m.ft_ng + m.tipos[k]] = T(A[(long long)inst * m.stride + m.tapos[k]]) - s;
 }
 
 // The columns [t0, n) of one instance per block (the narrow top of the
 // elimination tree), after k_factor_dep has finished the columns below t0
 // and k_factor_tail_pre the targets' parts from those columns.
 // Shared memory holds the tail's entries, D and 1/D, one partial value per
-// gather target, the level table and, double-buffered, the packed terms and
-// target descriptors of one level.  Level by level each target subtracts
-// its terms from tail columns (the level's terms and descriptors were staged
-// while the previous level was computed), with the lanes per target the
-// level table gives (enough for about four terms per lane).  Within the tail the entries are
-// kept unnormalised, U(i,c) = L(i,c) D(c), so that an update term
-// L(i,k) D(k) L(c,k) is U(i,k) (U(c,k) / D(k)) and a level needs no
+// gather target, the level table and, double-buffered, the packed terms,
+// target descriptors and warp tasks of one level.  Level by level the warps
+// take the level's tasks round-robin; a task is 32 / G targets of G lanes
+// each (G chosen per target on the host for about four terms per lane), so
+// a target with many terms gets many lanes whatever the level's width; each
+// target subtracts its terms from tail columns (the level's tables were
+// staged while the previous level was computed).  Within the tail the
+// entries are kept unnormalised, U(i,c) = L(i,c) D(c), so that an update
+// term L(i,k) D(k) L(c,k) is U(i,k) (U(c,k) / D(k)) and a level needs no
 // division pass before the next one: one block barrier per level.  L = U / D
 // is formed once at the end.  The order of operations of every entry is
 // fixed.
@@ -347,27 +350,29 @@ __global__ void __launch_bounds__(kFactorThreads)
     constexpr int R = 4;  // terms per thread prefetched into registers
     const int inst = blockIdx.x;
     const int bd = int(blockDim.x), tid = int(threadIdx.x);
+    const int warp = tid >> 5, lane = tid & 31, nwarps = bd >> 5;
     T *v = F + (long long)inst * m.stride;
     const int tmax = m.ft_tmax, kmax = m.ft_kmax, ntl = m.ntl;
     int4 *lev = reinterpret_cast<int4 *>(smem_raw);  // [2 ntl]
-    int4 *tib = lev + 2 * ntl;                        // [2][kmax]
-    int2 *tbuf = reinterpret_cast<int2 *>(tib + 2 * kmax);  // [2][tmax]
+    int4 *tib = lev + 2 * ntl;                        // [2][kmax] target descriptors
+    int4 *tkb = tib + 2 * kmax;                       // [2][kmax] warp tasks
+    int2 *tbuf = reinterpret_cast<int2 *>(tkb + 2 * kmax);  // [2][tmax]
     T *Ut = reinterpret_cast<T *>(tbuf + 2 * tmax);
     T *Dt = Ut + m.ft_ne;
     T *Di = Dt + m.nt;
     T *part = Di + m.nt;
-    const int g0 = m.ft_g0;
-    // the level loop reads the term and target tables once, one level ahead:
-    // fetch all of them into the L2 now, so that no level waits for DRAM
+    // the level loop reads the term, target and task tables once, one level
+    // ahead: fetch all of them into the L2 now, so that no level waits for DRAM
     l2_prefetch(m.tterm, sizeof(int2) * size_t(m.ft_tterms), tid, bd);
     l2_prefetch(m.tinfo, sizeof(int4) * size_t(m.ft_ng), tid, bd);
+    l2_prefetch(m.ttask, sizeof(int4) * size_t(m.ft_ntask), tid, bd);
     for (int i = tid; i < 2 * ntl; i += bd) lev[i] = m.tlev[i];
     for (int k = tid; k < m.ft_ng; k += bd) part[k] = partg[(long long)inst * m.ft_ng + k];
-    (void)g0;
     {
-        const int4 L0 = m.tlev[0];
+        const int4 L0 = m.tlev[0], T0 = m.tlev[1];
         for (int i = tid; i < L0.w - L0.z; i += bd) tbuf[i] = m.tterm[L0.z + i];
         for (int i = tid; i < L0.y - L0.x; i += bd) tib[i] = m.tinfo[L0.x + i];
+        for (int i = tid; i < T0.w - T0.z; i += bd) tkb[i] = m.ttask[T0.z + i];
     }
     __syncthreads();
     int bad = PF_OK;
@@ -378,8 +383,11 @@ __global__ void __launch_bounds__(kFactorThreads)
         int2 *nbuf = tbuf + (cur ^ 1) * tmax;
         const int4 *ti = tib + cur * kmax;
         int4 *nti = tib + (cur ^ 1) * kmax;
-        const int4 L = lev[2 * li];
+        const int4 *tk = tkb + cur * kmax;
+        int4 *ntk = tkb + (cur ^ 1) * kmax;
+        const int4 L = lev[2 * li], LT = lev[2 * li + 1];
         const int4 N = li + 1 < ntl ? lev[2 * li + 2] : make_int4(0, 0, 0, 0);
+        const int4 NT = li + 1 < ntl ? lev[2 * li + 3] : make_int4(0, 0, 0, 0);
         int2 pre[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
@@ -389,20 +397,19 @@ __global__ void __launch_bounds__(kFactorThreads)
         const bool hp = tid < N.y - N.x;
         int4 pti = make_int4(0, 0, 0, 0);
         if (hp) pti = m.tinfo[N.x + tid];
-        // G lanes per target (G the largest power of two <= 32 with G times
-        // the level's targets <= the block): the few targets of the top
-        // levels, whose diagonals gather the most terms, split their sums
-        // over up to a warp and reduce them with shuffles
-        const int nk = L.y - L.x;
-        int G = lev[2 * li + 1].z;  // lanes per target: about four terms per lane
-        while (G > 1 && G * nk > bd) G >>= 1;
-        const int gl = tid & (G - 1), ngr = bd / G;
-        for (int jb = 0; jb < nk; jb += ngr) {  // uniform trip count: shuffles stay convergent
-            // a warp without a target of this level skips it (warp-uniform):
-            // idle FP64 arithmetic would take the busy warps' FP64 issue slots
-            if (jb + (tid >> 5) * (32 / G) >= nk) continue;
-            const int j = jb + tid / G;
-            const bool act = j < nk;
+        const bool hq = tid < NT.w - NT.z;
+        int4 ptk = make_int4(0, 0, 0, 0);
+        if (hq) ptk = m.ttask[NT.z + tid];
+        // the level's tasks, round-robin over the warps (warp-uniform: the
+        // shuffles of a task stay convergent); a warp without a task idles,
+        // leaving the FP64 issue slots to the busy ones
+        const int ntask = LT.w - LT.z;
+        for (int q0 = warp; q0 < ntask; q0 += nwarps) {
+            const int4 task = tk[q0];
+            const int G = task.z;
+            const int gl = lane & (G - 1), gi = lane / G;
+            const bool act = gi < task.y;
+            const int j = task.x + gi;
             const int4 info = act ? ti[j] : make_int4(0, 0, 0, 0);
             T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
             int q = info.x + gl;
@@ -440,6 +447,8 @@ __global__ void __launch_bounds__(kFactorThreads)
         for (int i = tid + R * bd; i < N.w - N.z; i += bd) nbuf[i] = m.tterm[N.z + i];
         if (hp) nti[tid] = pti;
         for (int i = tid + bd; i < N.y - N.x; i += bd) nti[i] = m.tinfo[N.x + i];
+        if (hq) ntk[tid] = ptk;
+        for (int i = tid + bd; i < NT.w - NT.z; i += bd) ntk[i] = m.ttask[NT.z + i];
         __syncthreads();
     }
     if (bad != PF_OK) atomicCAS(fstatus + inst, PF_OK, bad);
@@ -943,7 +952,7 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
         const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
         const size_t tsmem = elt * (size_t(m.ft_ne) + 2 * size_t(m.nt) + size_t(m.ft_ng)) +
                              sizeof(int2) * 2 * size_t(m.ft_tmax > 0 ? m.ft_tmax : 0) +
-                             sizeof(int4) * 2 * (size_t(m.ft_kmax) + size_t(m.ntl));
+                             sizeof(int4) * 2 * (2 * size_t(m.ft_kmax) + size_t(m.ntl));
         const bool tail = fs.tail && m.ft_ng > 0 && m.ft_tmax >= 0 && fs.partg &&
                           tsmem + 1024 <= fs.smem_optin;
         const int ncols = tail ? m.t0 : m.n;

@@ -169,21 +169,36 @@ def test_tail_factor_tables_vs_oracle(lib, oracle, cfg):
         assert sz["ng"] == sum(r[1] for r in ref) and sz["ne"] == sz["ng"] - nt
         assert sz["nterm"] == sum(r[2] for r in ref)
         assert sz["kmax"] == max(r[1] for r in ref) and sz["tmax"] == max(r[2] for r in ref)
+        ntask, tasks, tipos = _tail_tasks(lib, g, which, sz["ng"])
         seen_diag = np.zeros(nt, np.int32)
         seen_entry = np.zeros(sz["ne"], np.int32)
         for li, (ncol, ntgt, nterm) in enumerate(ref):
             kb, ke, tb, te = tlev[2 * li]
-            cb, ce, G = tlev[2 * li + 1][:3]
-            # lanes per target: about four terms per lane, a power of two up to 32
-            most = max(int(tinfo[k][1] - tinfo[k][0]) for k in range(kb, ke)) if ke > kb else 0
-            assert G in (1, 2, 4, 8, 16, 32) and (G == 32 or most <= 4 * G) and (G == 1 or most > 2 * G)
+            cb, ce, q0, q1 = tlev[2 * li + 1]
             assert (ke - kb, te - tb, ce - cb) == (ntgt, nterm, ncol), li
             if li + 1 < len(ref):
                 assert tlev[2 * li + 2][0] == ke and tlev[2 * li + 2][2] == te
-                assert tlev[2 * li + 3][0] == ce
+                assert tlev[2 * li + 3][0] == ce and tlev[2 * li + 3][2] == q1
             info = tinfo[kb:ke]
-            assert info[0, 0] == 0 and info[-1, 1] == te - tb
-            assert np.array_equal(info[1:, 0], info[:-1, 1]) and np.all(info[:, 1] >= info[:, 0])
+            # the level's targets (reordered) hold term ranges that tile the level's terms
+            rng = info[np.lexsort((info[:, 1], info[:, 0]))]  # by start, empty ranges first
+            assert rng[0, 0] == 0 and rng[-1, 1] == te - tb
+            assert np.array_equal(rng[1:, 0], rng[:-1, 1]) and np.all(info[:, 1] >= info[:, 0])
+            # tipos maps the level's targets one to one onto its positions
+            assert np.array_equal(np.sort(tipos[kb:ke]), np.arange(kb, ke))
+            # warp tasks: 32 / G positions of one G each, every position once;
+            # G the smallest power of two leaving at most four terms to a lane
+            # (at most 32); tasks listed by decreasing terms per lane
+            cover = np.zeros(ke - kb, np.int32)
+            costs = []
+            for x, y, G, _ in tasks[q0:q1]:
+                assert G in (1, 2, 4, 8, 16, 32) and 1 <= y <= 32 // G
+                cover[x:x + y] += 1
+                cnt = info[x:x + y, 1] - info[x:x + y, 0]
+                assert np.all((G == 32) | (cnt <= 4 * G)) and np.all((G == 1) | (cnt > 2 * G))
+                costs.append(int(np.max((cnt + G - 1) // G)))
+            assert np.all(cover == 1), li
+            assert costs == sorted(costs, reverse=True)
             assert np.all((info[:, 3] >= cb) & (info[:, 3] < ce))
             d = info[info[:, 2] < 0]
             assert np.all(d[:, 2] == -1) and d.shape[0] == ncol
@@ -193,6 +208,19 @@ def test_tail_factor_tables_vs_oracle(lib, oracle, cfg):
         assert tlev[-2][1] == sz["ng"] and tlev[-2][3] == sz["nterm"] and tlev[-1][1] == nt
         assert np.all(seen_diag == 1) and np.all(seen_entry == 1)
     g.close()
+
+
+def _tail_tasks(lib, g, which, ng):
+    f = lib.gbpf_debug_tail_tasks
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    n = np.zeros(1, np.int32)
+    assert f(g.ctx, which, n.ctypes.data, None, None, 0) == 0
+    ntask = int(n[0])
+    tasks = np.zeros((max(1, ntask), 4), np.int32)
+    tipos = np.zeros(max(1, ng), np.int32)
+    assert f(g.ctx, which, n.ctypes.data, tasks.ctypes.data, tipos.ctypes.data, max(4 * ntask, ng, 1)) == 0
+    return ntask, tasks[:ntask], tipos[:ng]
 
 
 def _scatter_schedules(lib, g, which):
