@@ -38,42 +38,6 @@ namespace {
 
 constexpr int kClThreads = 512;
 
-// ------------------------------------------------------------ DSMEM access
-
-__device__ __forceinline__ uint32_t cl_mapa(uint32_t saddr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ double ld_cl(uint32_t a) {
-    double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_cl_u64(uint32_t a) {
-    unsigned long long v;
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_cl(uint32_t a, double v) {
-    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
-}
-
-// Cluster barrier with release / acquire semantics at cluster scope: the
-// shared-memory writes of every CTA before it are visible to every CTA
-// after it.
-__device__ __forceinline__ void cl_barrier() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// The same for phases that exchange data through global memory as well:
-// the release / acquire of the cluster barrier covers every state space
-// (global stores before it are visible to loads after it in the cluster).
-__device__ __forceinline__ void cl_barrier_global() { cl_barrier(); }
-
 // ------------------------------------------------------------ tail inverse
 
 // W = L_TT^-1 of the top set T of one matrix: W(it, jt) = Wd[it * nt + jt]

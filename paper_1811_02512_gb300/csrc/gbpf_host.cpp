@@ -1552,6 +1552,13 @@ pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int bl
     fs.tail = ctx->tune.tail != 2;
     fs.smem_optin = ctx->smem_optin;
     fs.partg = w.TP[which][prec];
+    // the tail factor of a few instances on a cluster of SMs each
+    fs.tail_cluster = false;
+    if (m.ft_ng > 0 && nf <= 8 && nf * kTailCtas <= ctx->num_sms) {
+        int &cmax = ctx->tail_cl_max[which][prec];
+        if (cmax < 0) cmax = factor_tail_clusters(m, prec);
+        fs.tail_cluster = nf <= cmax;
+    }
     e = counted(ctx, PF_K_FACTOR, 2, s, [&] {
         return launch_factor(m, prec, w.A[which], F, nf, w.fstatus[which][prec], fs, s);
     });

@@ -388,6 +388,7 @@ struct pf_ctx {
     gbpf::ClMat cl[2];
     double *clW[2] = {nullptr, nullptr};
     size_t cl_smem = 0;
+    int tail_cl_max[2][2] = {{-1, -1}, {-1, -1}};  // [mat][prec] resident tail-factor clusters (-1: not asked)
     // CUDA graph of the device work of one fast decoupled pf_run_to_tol
     // (block and cluster engines), captured on an internal stream for a given
     // set of arguments (key) and replayed on the caller's stream; the launch
@@ -425,7 +426,12 @@ struct FactorSync {
     size_t smem_optin = 0;
     void *partg = nullptr;     // [ninst][ft_ng] of the factor type: the tail targets' parts
                                // from columns below the tail (k_factor_tail_pre)
+    bool tail_cluster = false; // the tail factor of every instance on a cluster of kTailCtas CTAs
 };
+constexpr int kTailCtas = 16;  // CTAs of the tail factor's cluster (one per SM)
+size_t factor_tail_smem(const DevMat &m, int prec);
+// Clusters of the tail factor that can be resident at once (0: none).
+int factor_tail_clusters(const DevMat &m, int prec);
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
                           int *fstatus, const FactorSync &fs, cudaStream_t s);
 // Longest column (strict-lower entries) the dependency-driven factor takes.

@@ -327,6 +327,15 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) partg[(long long)inst * m.ft_ng + m.tipos[k]] = T(A[(long long)inst * m.stride + m.tapos[k]]) - s;
 }
 
+// Barrier of the tail factor's level loop: the block's, or the cluster's with
+// release / acquire semantics (the values written into other CTAs' shared
+// memory before it are visible after it).
+template <int C>
+__device__ __forceinline__ void tail_barrier() {
+    if constexpr (C == 1) __syncthreads();
+    else cl_barrier();
+}
+
 // The columns [t0, n) of one instance per block (the narrow top of the
 // elimination tree), after k_factor_dep has finished the columns below t0
 // and k_factor_tail_pre the targets' parts from those columns.
@@ -343,12 +352,19 @@ __global__ void __launch_bounds__(256)
 // division pass before the next one: one block barrier per level.  L = U / D
 // is formed once at the end.  The order of operations of every entry is
 // fixed.
-template <class T>
+//
+// With C > 1 one instance runs on a cluster of C CTAs (one per SM, C times
+// the FP64 rate of one SM, which bounds a level's terms): every CTA keeps a
+// full copy of the tail's values, takes every C-th task of a level, writes
+// each value it computes into all C copies over distributed shared memory,
+// and a level ends with a cluster barrier instead of the block's.
+template <class T, int C>
 __global__ void __launch_bounds__(kFactorThreads)
     k_factor_tail(DevMat m, const T *partg, T *F, int *fstatus, const double *amaxv) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int R = 4;  // terms per thread prefetched into registers
-    const int inst = blockIdx.x;
+    const int inst = int(blockIdx.x) / C;
+    const int rank = C == 1 ? 0 : int(cluster_rank());
     const int bd = int(blockDim.x), tid = int(threadIdx.x);
     const int warp = tid >> 5, lane = tid & 31, nwarps = bd >> 5;
     T *v = F + (long long)inst * m.stride;
@@ -374,7 +390,8 @@ __global__ void __launch_bounds__(kFactorThreads)
         for (int i = tid; i < L0.y - L0.x; i += bd) tib[i] = m.tinfo[L0.x + i];
         for (int i = tid; i < T0.w - T0.z; i += bd) tkb[i] = m.ttask[T0.z + i];
     }
-    __syncthreads();
+    // (a cluster: every CTA has started, so its shared memory may be written)
+    tail_barrier<C>();
     int bad = PF_OK;
     const double tol = 1e-14 * amaxv[inst];
     for (int li = 0; li < ntl; li++) {
@@ -404,7 +421,7 @@ __global__ void __launch_bounds__(kFactorThreads)
         // shuffles of a task stay convergent); a warp without a task idles,
         // leaving the FP64 issue slots to the busy ones
         const int ntask = LT.w - LT.z;
-        for (int q0 = warp; q0 < ntask; q0 += nwarps) {
+        for (int q0 = rank + C * warp; q0 < ntask; q0 += C * nwarps) {
             const int4 task = tk[q0];
             const int G = task.z;
             const int gl = lane & (G - 1), gi = lane / G;
@@ -431,9 +448,19 @@ __global__ void __launch_bounds__(kFactorThreads)
             const T val = part[L.x + j] - sum;
             if (info.z >= 0) {
                 Ut[info.z] = val;
+                if constexpr (C > 1)
+                    for (int r = 1; r < C; r++)
+                        st_cl(cl_mapa(smem_u32(Ut + info.z), unsigned((rank + r) % C)), val);
             } else {
+                const T dinv = T(1) / val;
                 Dt[info.w] = val;
-                Di[info.w] = T(1) / val;
+                Di[info.w] = dinv;
+                if constexpr (C > 1)
+                    for (int r = 1; r < C; r++) {
+                        const unsigned q = unsigned((rank + r) % C);
+                        st_cl(cl_mapa(smem_u32(Dt + info.w), q), val);
+                        st_cl(cl_mapa(smem_u32(Di + info.w), q), dinv);
+                    }
                 const double dd = double(val);
                 if (!isfinite(dd)) bad = PF_ERR_NONFINITE;
                 else if (fabs(dd) <= tol && bad == PF_OK) bad = PF_ERR_SINGULAR;
@@ -449,15 +476,15 @@ __global__ void __launch_bounds__(kFactorThreads)
         for (int i = tid + bd; i < N.y - N.x; i += bd) nti[i] = m.tinfo[N.x + i];
         if (hq) ntk[tid] = ptk;
         for (int i = tid + bd; i < NT.w - NT.z; i += bd) ntk[i] = m.ttask[NT.z + i];
-        __syncthreads();
+        tail_barrier<C>();
     }
     if (bad != PF_OK) atomicCAS(fstatus + inst, PF_OK, bad);
     const int t0 = m.t0, e0 = m.ft_e0;
-    for (int c = t0 + tid; c < m.n; c += bd) {
+    for (int c = t0 + rank * bd + tid; c < m.n; c += C * bd) {
         v[c] = Dt[c - t0];
         v[m.offDi + c] = Di[c - t0];
     }
-    for (int k = tid; k < m.ft_ng; k += bd) {
+    for (int k = rank * bd + tid; k < m.ft_ng; k += C * bd) {
         const int4 info = m.tinfo[k];
         if (info.z >= 0) {
             const T l = Ut[info.z] / Dt[info.w];
@@ -943,16 +970,86 @@ cudaError_t launch_factor_jobs(const FactorJob *jobs_dev, int njob, const int2 *
     return cudaGetLastError();
 }
 
+namespace {
+// The tail factor of ninst instances: one block each, or (cluster) one
+// cluster of kTailCtas CTAs each.
+template <class T>
+cudaError_t launch_factor_tail(const DevMat &m, const T *partg, T *F, int *fstatus, const double *amax, int ninst,
+                               size_t tsmem, bool cluster, cudaStream_t s) {
+    if (!cluster) {
+        cudaError_t e = cudaFuncSetAttribute(k_factor_tail<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(tsmem));
+        if (e != cudaSuccess) return e;
+        k_factor_tail<T, 1><<<ninst, kFactorThreads, tsmem, s>>>(m, partg, F, fstatus, amax);
+        return cudaGetLastError();
+    }
+    auto *k = k_factor_tail<T, kTailCtas>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(ninst) * kTailCtas);
+    cfg.blockDim = dim3(kFactorThreads);
+    cfg.dynamicSmemBytes = tsmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kTailCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, m, partg, F, fstatus, amax);
+}
+}  // namespace
+
+size_t factor_tail_smem(const DevMat &m, int prec) {
+    const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
+    return elt * (size_t(m.ft_ne) + 2 * size_t(m.nt) + size_t(m.ft_ng)) +
+           sizeof(int2) * 2 * size_t(m.ft_tmax > 0 ? m.ft_tmax : 0) +
+           sizeof(int4) * 2 * (2 * size_t(m.ft_kmax) + size_t(m.ntl));
+}
+
+int factor_tail_clusters(const DevMat &m, int prec) {
+    const size_t tsmem = factor_tail_smem(m, prec);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kTailCtas);
+    cfg.blockDim = dim3(kFactorThreads);
+    cfg.dynamicSmemBytes = tsmem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kTailCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e;
+    if (prec == PF_FP64) {
+        auto *k = k_factor_tail<double, kTailCtas>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+    } else {
+        auto *k = k_factor_tail<float, kTailCtas>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, int ninst,
                           int *fstatus, const FactorSync &fs, cudaStream_t s) {
     const long long total = (long long)m.n * ninst;
     const bool dep = fs.mode == 1 || (fs.mode == 0 && ninst < fs.nsm / 2);
     if (dep && m.max_col <= kDepMaxCol && total < (1ll << 31) && fs.done) {
         k_factor_prep<<<ninst, 256, 0, s>>>(m, A, fstatus, fs);
-        const size_t elt = prec == PF_FP64 ? sizeof(double) : sizeof(float);
-        const size_t tsmem = elt * (size_t(m.ft_ne) + 2 * size_t(m.nt) + size_t(m.ft_ng)) +
-                             sizeof(int2) * 2 * size_t(m.ft_tmax > 0 ? m.ft_tmax : 0) +
-                             sizeof(int4) * 2 * (2 * size_t(m.ft_kmax) + size_t(m.ntl));
+        const size_t tsmem = factor_tail_smem(m, prec);
         const bool tail = fs.tail && m.ft_ng > 0 && m.ft_tmax >= 0 && fs.partg &&
                           tsmem + 1024 <= fs.smem_optin;
         const int ncols = tail ? m.t0 : m.n;
@@ -968,10 +1065,8 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
             if (tail) {
                 k_factor_tail_pre<double><<<dim3(unsigned((m.ft_ng + 7) / 8), unsigned(ninst)), 256, 0, s>>>(
                     m, A, static_cast<const double *>(F), static_cast<double *>(fs.partg));
-                e = cudaFuncSetAttribute(k_factor_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
-                if (e == cudaSuccess)
-                    k_factor_tail<double><<<ninst, kFactorThreads, tsmem, s>>>(
-                        m, static_cast<const double *>(fs.partg), static_cast<double *>(F), fstatus, fs.amax);
+                e = launch_factor_tail<double>(m, static_cast<const double *>(fs.partg), static_cast<double *>(F),
+                                               fstatus, fs.amax, ninst, tsmem, fs.tail_cluster, s);
             }
         } else {
             if (ncols > 0)
@@ -980,10 +1075,8 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
             if (tail) {
                 k_factor_tail_pre<float><<<dim3(unsigned((m.ft_ng + 7) / 8), unsigned(ninst)), 256, 0, s>>>(
                     m, A, static_cast<const float *>(F), static_cast<float *>(fs.partg));
-                e = cudaFuncSetAttribute(k_factor_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
-                if (e == cudaSuccess)
-                    k_factor_tail<float><<<ninst, kFactorThreads, tsmem, s>>>(
-                        m, static_cast<const float *>(fs.partg), static_cast<float *>(F), fstatus, fs.amax);
+                e = launch_factor_tail<float>(m, static_cast<const float *>(fs.partg), static_cast<float *>(F),
+                                              fstatus, fs.amax, ninst, tsmem, fs.tail_cluster, s);
             }
         }
         return e != cudaSuccess ? e : cudaGetLastError();
