@@ -118,9 +118,19 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
 template <class T>
 struct LowRank {
     const T *Z = nullptr;     // [2][n] columns A^-1 e_p0, A^-1 e_p1 (null: no correction)
-    const double *K = nullptr;
+    const double *K = nullptr;  // K00, K01, K10, K11, then S00, S11, S01
     int p0 = -1, p1 = -1;
 };
+
+// Row r (p0 or p1) of U S U^T x: the part of the base matrix's row that the
+// outaged branch contributes, which the residual b - A x of an outage case
+// adds back when it is formed with the base matrix A.
+template <class T>
+__device__ __forceinline__ double lowrank_residual(const LowRank<T> &lr, int r, const double *x) {
+    const double s00 = lr.K[4], s11 = lr.K[5], s01 = lr.K[6];
+    const double x0 = lr.p0 >= 0 ? x[lr.p0] : 0.0, x1 = lr.p1 >= 0 ? x[lr.p1] : 0.0;
+    return r == lr.p0 ? s00 * x0 + s01 * x1 : s01 * x0 + s11 * x1;
+}
 
 template <class T, class X>
 __device__ void lowrank_correct(const LowRank<T> &lr, X *x, int n, double *red) {
@@ -207,6 +217,7 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
                     if (rem > 1) s -= a1 * y1;
                     if (rem > 2) s -= a2 * y2;
                 }
+                if (lr.Z && (r == lr.p0 || r == lr.p1)) s += lowrank_residual(lr, r, x64);
                 xv[r] = T(s);
                 const unsigned long long k = abs_key(s);
                 rk = k > rk ? k : rk;
@@ -253,16 +264,19 @@ __device__ __forceinline__ void fdpf_case(const RunArgs &a, int c, unsigned char
     if (lowrank) {
         const int e = a.dc.inst_outage[inst];
         lr0.Z = static_cast<const T *>(a.Z0) + (long long)inst * 2 * a.m0.n;
-        lr0.K = a.K0 + 4LL * inst;
+        lr0.K = a.K0 + 8LL * inst;
         lr0.p0 = a.m0.br_slot[3 * e];
         lr0.p1 = a.m0.br_slot[3 * e + 1];
         lr1.Z = static_cast<const T *>(a.Z1) + (long long)inst * 2 * a.m1.n;
-        lr1.K = a.K1 + 4LL * inst;
+        lr1.K = a.K1 + 8LL * inst;
         lr1.p0 = a.m1.br_slot[3 * e];
         lr1.p1 = a.m1.br_slot[3 * e + 1];
     }
-    const double *A0 = a.A0 + (long long)inst * a.m0.stride;
-    const double *A1 = a.A1 + (long long)inst * a.m1.stride;
+    // the FP64 matrices of the refinement residuals: the case's own, or with
+    // low-rank outages the base one (the residual adds the branch's share
+    // U S U^T back itself: lowrank_residual)
+    const double *A0 = a.A0 + (long long)finst * a.m0.stride;
+    const double *A1 = a.A1 + (long long)finst * a.m1.stride;
     int ir_steps = 0;
     const int slice = (nbus + C - 1) / C;
     const int i0 = rank * slice, i1 = min(nbus, i0 + slice);

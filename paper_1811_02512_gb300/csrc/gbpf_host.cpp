@@ -1483,13 +1483,14 @@ pf_status assemble_ybus(pf_ctx *ctx, cudaStream_t s) {
     return PF_OK;
 }
 
-// Assembles B' or B'' of every instance from the current admittance matrix.
-pf_status assemble_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s) {
+// Assembles B' or B'' of the first ninst instances (-1: every instance)
+// from the current admittance matrix.
+pf_status assemble_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int ninst = -1) {
     TRY(ensure_factor_storage(ctx, which, prec));
     Workspace &w = ctx->ws;
     const DevMat &m = ctx->dm[which];
     cudaError_t e = counted(ctx, PF_K_ASSEMBLE, 1, s, [&] {
-        return launch_assemble_slots(ctx->dn, ctx->dc, m, which, w.A[which], s);
+        return launch_assemble_slots(ctx->dn, ctx->dc, m, which, w.A[which], s, ninst);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble launch");
     return PF_OK;
@@ -1522,7 +1523,10 @@ pf_status factor_job(pf_ctx *ctx, int which, int prec, FactorJob &J, cudaStream_
 pf_status factor_matrix(pf_ctx *ctx, int which, int prec, cudaStream_t s, int blocks_per_sm = 2,
                         int ninst_f = -1) {
     const int nf = ninst_f > 0 ? ninst_f : ctx->dc.ninst;  // instances factorised (the first nf)
-    TRY(assemble_matrix(ctx, which, prec, s));
+    // only those are assembled: with low-rank outages the outage instances'
+    // matrices are the base one minus the branch's share (U S U^T), which
+    // the iteration applies itself
+    TRY(assemble_matrix(ctx, which, prec, s, nf));
     Workspace &w = ctx->ws;
     const DevMat &m = ctx->dm[which];
     cudaError_t e;
@@ -1601,7 +1605,7 @@ pf_status prepare_lowrank(pf_ctx *ctx, int prec, cudaStream_t s) {
             }
             (void)elt;
         }
-        if (!w.LK[m]) TRY(dalloc(ctx, &w.LK[m], size_t(4) * size_t(ninst)));
+        if (!w.LK[m]) TRY(dalloc(ctx, &w.LK[m], size_t(8) * size_t(ninst)));
         const void *F = prec == PF_FP64 ? (const void *)w.F64[m] : (const void *)w.F32[m];
         const void *TV = ctx->tune.tail != 2 ? w.TV[m][prec] : nullptr;
         cudaError_t e = counted(ctx, PF_K_SOLVE, 2, s, [&] {

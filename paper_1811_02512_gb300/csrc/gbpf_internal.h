@@ -410,7 +410,7 @@ cudaError_t launch_ybus(const DevNet &dn, cudaStream_t s);
 cudaError_t launch_case_spec(const DevNet &dn, const DevCases &dc, const double *load_scale_dev,
                              cudaStream_t s);
 cudaError_t launch_assemble_slots(const DevNet &dn, const DevCases &dc, const DevMat &m, int which,
-                                  double *A, cudaStream_t s);
+                                  double *A, cudaStream_t s, int ninst = -1);
 cudaError_t launch_branch_flows(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,
                                 int ncase, double *flows, double *loss, cudaStream_t s);
 struct FactorSync {

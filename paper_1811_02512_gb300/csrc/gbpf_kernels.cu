@@ -98,9 +98,9 @@ __device__ double branch_slot_value(const DevNet &dn, const DevMat &m, int which
 
 // Values of B' or B'' of every factor instance in the [D | Lc] layout (fill
 // slots zero).
-__global__ void k_assemble_slots(DevNet dn, DevCases dc, DevMat m, int which, double *A) {
+__global__ void k_assemble_slots(DevNet dn, DevCases dc, DevMat m, int which, double *A, int ninst) {
     const int per = m.n + m.nnz;
-    const long long total = (long long)dc.ninst * per;
+    const long long total = (long long)ninst * per;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int inst = int(idx / per), s = int(idx % per);
@@ -786,15 +786,16 @@ __global__ void __launch_bounds__(kSolveThreads)
 }
 
 // K = (I - S U^T Z)^-1 S of every outage instance (S the branch's share of
-// the matrix on its two buses), in FP64; K = 0 when the branch is already
+// the matrix on its two buses), in FP64, and S itself: Kout[8 inst ..] =
+// {K00, K01, K10, K11, S00, S11, S01, 0}; all zero when the branch is already
 // out of service.
 template <class T>
 __global__ void k_lowrank_k(DevMat m, DevNet dn, DevCases dc, int which, const T *Z, double *Kout) {
     for (int inst = 1 + blockIdx.x * blockDim.x + threadIdx.x; inst < dc.ninst; inst += gridDim.x * blockDim.x) {
-        double *Kq = Kout + 4LL * inst;
+        double *Kq = Kout + 8LL * inst;
         const int e = dc.inst_outage[inst];
         if (e < 0 || !dn.bstatus[e]) {
-            Kq[0] = Kq[1] = Kq[2] = Kq[3] = 0.0;
+            Kq[0] = Kq[1] = Kq[2] = Kq[3] = Kq[4] = Kq[5] = Kq[6] = Kq[7] = 0.0;
             continue;
         }
         const int p0 = m.br_slot[3 * e], p1 = m.br_slot[3 * e + 1], sl = m.br_slot[3 * e + 2];
@@ -814,6 +815,10 @@ __global__ void k_lowrank_k(DevMat m, DevNet dn, DevCases dc, int which, const T
         Kq[1] = i00 * s01 + i01 * s11;
         Kq[2] = i10 * s00 + i11 * s01;
         Kq[3] = i10 * s01 + i11 * s11;
+        Kq[4] = s00;  // S itself: the case's matrix is the base one minus U S U^T
+        Kq[5] = s11;
+        Kq[6] = s01;
+        Kq[7] = 0.0;
     }
 }
 
@@ -921,9 +926,10 @@ cudaError_t launch_branch_flows(const DevNet &dn, const DevCases &dc, const doub
 }
 
 cudaError_t launch_assemble_slots(const DevNet &dn, const DevCases &dc, const DevMat &m, int which,
-                                  double *A, cudaStream_t s) {
-    const long long total = (long long)dc.ninst * (m.n + m.nnz);
-    k_assemble_slots<<<grid_for(total, 256), 256, 0, s>>>(dn, dc, m, which, A);
+                                  double *A, cudaStream_t s, int ninst) {
+    if (ninst < 1 || ninst > dc.ninst) ninst = dc.ninst;
+    const long long total = (long long)ninst * (m.n + m.nnz);
+    k_assemble_slots<<<grid_for(total, 256), 256, 0, s>>>(dn, dc, m, which, A, ninst);
     return cudaGetLastError();
 }
 
