@@ -141,7 +141,12 @@ enum { PF_ENGINE_AUTO = 0, PF_ENGINE_BLOCK = 1, PF_ENGINE_LANES = 2, PF_ENGINE_C
  *   engine   PF_ENGINE_BLOCK, PF_ENGINE_LANES or PF_ENGINE_CLUSTER, used
  *            by FDPF runs whose options ask for PF_ENGINE_AUTO;
  *   cluster  thread blocks per case of a single-case FDPF run (1, 8, 16;
- *            capped at what fits the GPU);
+ *            capped at what fits the GPU); with engine PF_ENGINE_CLUSTER
+ *            instead the subtree levels per step of its substitutions (1 to
+ *            8, 0 = 3): g levels of a CTA's subtrees are solved in one step
+ *            through the inverse of their block of L (formed after every
+ *            factorisation), so the per-level barriers drop g-fold at the
+ *            cost of the inverse's extra entries;
  *   factor   1: dependency-driven factor over all SMs, 2: one thread block
  *            per instance (level by level);
  *   tail     1: narrow top of the elimination tree substituted as a one-warp

@@ -106,7 +106,9 @@ __global__ void k_tw_values(const DevMat m, const double *Wd, const T *F, T *TW)
 // Packed values of the CTAs' programs (blockIdx.y = matrix): per slot
 // {kind, a, b}: 0 the factor value F[a]; 1 the negated tail-inverse entry
 // -Wd[a] (forward tail step); 2 -Wd[a] * F[b] (backward tail step, the
-// inverse diagonal folded in).
+// inverse diagonal folded in); 3 -GV[a], 4 -GV[a] * F[b] and 5 GV[a] (the
+// grouped subtree steps: an entry of a group's inverse, the same with the
+// inverse diagonal folded in, a combined entry).
 __global__ void k_cl_values(const ClMat m0, const ClMat m1, const double *F0, const double *F1,
                             const double *W0, const double *W1) {
     const ClMat &m = blockIdx.y ? m1 : m0;
@@ -115,10 +117,52 @@ __global__ void k_cl_values(const ClMat m0, const ClMat m1, const double *F0, co
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m.nval; s += gridDim.x * blockDim.x) {
         const int4 src = m.vsrc[s];
         double v;
-        if (src.x == 0) v = F[src.y];
-        else if (src.x == 1) v = -Wd[src.y];
-        else v = -Wd[src.y] * F[src.z];
+        switch (src.x) {
+            case 0: v = F[src.y]; break;
+            case 1: v = -Wd[src.y]; break;
+            case 2: v = -Wd[src.y] * F[src.z]; break;
+            case 3: v = -m.gv[src.y]; break;
+            case 4: v = -m.gv[src.y] * F[src.z]; break;
+            default: v = m.gv[src.y]; break;
+        }
         m.vals[s] = v;
+    }
+}
+
+// Inverses of the subtree groups' blocks of L (blockIdx.y = matrix): one
+// thread per inverse column j solves L_GG w = e_j along j's path to the top
+// of its group, right-looking (w_q -= L(path[q], path[p]) w_p in the order
+// of the update list), and writes W(path[q], j), q >= 1.
+__global__ void k_cl_group_w(const ClMat m0, const ClMat m1, const double *F0, const double *F1) {
+    const ClMat &m = blockIdx.y ? m1 : m0;
+    const double *F = blockIdx.y ? F1 : F0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.n_gwcol; c += gridDim.x * blockDim.x) {
+        const int4 col = m.gw_col[c];
+        double w[kClGroupMax];
+        w[0] = 1.0;
+#pragma unroll
+        for (int q = 1; q < kClGroupMax; q++) w[q] = 0.0;
+        for (int u = col.x; u < col.y; u++) {
+            const int4 up = m.gw_upd[u];
+            w[up.y] = fma(-F[up.z], w[up.x], w[up.y]);
+        }
+        for (int q = 1; q < col.w; q++) m.gv[col.z + q - 1] = w[q];
+    }
+}
+
+// Combined entries of the grouped steps (blockIdx.y = matrix): the sum, in
+// list order, of W(.) L(.) over the entry's terms (W = 1 for the identity).
+__global__ void k_cl_group_m(const ClMat m0, const ClMat m1, const double *F0, const double *F1) {
+    const ClMat &m = blockIdx.y ? m1 : m0;
+    const double *F = blockIdx.y ? F1 : F0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.n_gm; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int t = m.gm_ptr[e]; t < m.gm_ptr[e + 1]; t++) {
+            const int2 tm = m.gm_term[t];
+            const double w = tm.x < 0 ? 1.0 : m.gv[tm.x];
+            s = fma(w, F[tm.y], s);
+        }
+        m.gv[m.n_gw + e] = s;
     }
 }
 
@@ -495,6 +539,10 @@ cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0
         k_tail_inverse<double><<<(m.nt + kTailInvWarps - 1) / kTailInvWarps, kTailInvWarps * 32, smem, s>>>(
             m, FF[w], WW[w]);
     }
+    const int nc = m0.n_gwcol > m1.n_gwcol ? m0.n_gwcol : m1.n_gwcol;
+    if (nc > 0) k_cl_group_w<<<dim3(unsigned((nc + 255) / 256), 2), 256, 0, s>>>(m0, m1, F0, F1);
+    const int nm = m0.n_gm > m1.n_gm ? m0.n_gm : m1.n_gm;
+    if (nm > 0) k_cl_group_m<<<dim3(unsigned((nm + 255) / 256), 2), 256, 0, s>>>(m0, m1, F0, F1);
     const int nv = m0.nval > m1.nval ? m0.nval : m1.nval;
     k_cl_values<<<dim3(unsigned((nv + 255) / 256), 2), 256, 0, s>>>(m0, m1, F0, F1, W0, W1);
     return cudaGetLastError();

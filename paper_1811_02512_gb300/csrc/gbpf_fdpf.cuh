@@ -125,11 +125,45 @@ struct LowRank {
 // Row r (p0 or p1) of U S U^T x: the part of the base matrix's row that the
 // outaged branch contributes, which the residual b - A x of an outage case
 // adds back when it is formed with the base matrix A.
-template <class T>
-__device__ __forceinline__ double lowrank_residual(const LowRank<T> &lr, int r, const double *x) {
+template <class T, class XR>
+__device__ __forceinline__ double lowrank_residual(const LowRank<T> &lr, int r, const XR *x) {
     const double s00 = lr.K[4], s11 = lr.K[5], s01 = lr.K[6];
-    const double x0 = lr.p0 >= 0 ? x[lr.p0] : 0.0, x1 = lr.p1 >= 0 ? x[lr.p1] : 0.0;
+    const double x0 = lr.p0 >= 0 ? double(x[lr.p0]) : 0.0, x1 = lr.p1 >= 0 ? double(x[lr.p1]) : 0.0;
     return r == lr.p0 ? s00 * x0 + s01 * x1 : s01 * x0 + s11 * x1;
+}
+
+// Row r of the FP64 residual b - A x (x read as XR and promoted to FP64):
+// the diagonal, then the row's off-diagonal entries four at a time (their
+// indices and values loaded before the ordered subtractions), then for a
+// low-rank outage case the branch's share at its two rows.
+template <class T, class XR>
+__device__ __forceinline__ double residual_row(const DevMat &m, const double *A, const double *b, const XR *x,
+                                               int r, const LowRank<T> &lr) {
+    double s = b[r] - A[r] * double(x[r]);
+    const int e1 = m.Ap[r + 1];
+    int e = m.Ap[r];
+    for (; e + 3 < e1; e += 4) {
+        const int p0 = m.Apos[e], p1 = m.Apos[e + 1], p2 = m.Apos[e + 2], p3 = m.Apos[e + 3];
+        const int j0 = m.Aj[e], j1 = m.Aj[e + 1], j2 = m.Aj[e + 2], j3 = m.Aj[e + 3];
+        const double a0 = A[p0], a1 = A[p1], a2 = A[p2], a3 = A[p3];
+        const double y0 = double(x[j0]), y1 = double(x[j1]), y2 = double(x[j2]), y3 = double(x[j3]);
+        s -= a0 * y0;
+        s -= a1 * y1;
+        s -= a2 * y2;
+        s -= a3 * y3;
+    }
+    if (e < e1) {
+        const int rem = e1 - e;  // 1 to 3 entries
+        const int p0 = m.Apos[e], p1 = m.Apos[rem > 1 ? e + 1 : e], p2 = m.Apos[rem > 2 ? e + 2 : e];
+        const int j0 = m.Aj[e], j1 = m.Aj[rem > 1 ? e + 1 : e], j2 = m.Aj[rem > 2 ? e + 2 : e];
+        const double a0 = A[p0], a1 = A[p1], a2 = A[p2];
+        const double y0 = double(x[j0]), y1 = double(x[j1]), y2 = double(x[j2]);
+        s -= a0 * y0;
+        if (rem > 1) s -= a1 * y1;
+        if (rem > 2) s -= a2 * y2;
+    }
+    if (lr.Z && (r == lr.p0 || r == lr.p1)) s += lowrank_residual(lr, r, x);
+    return s;
 }
 
 template <class T, class X>
@@ -192,35 +226,10 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
             if (k >= a.ir_max) break;
             unsigned long long rk = 0;
             for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
-                double s = xg[r] - A[r] * x64[r];
-                // the row's entries four at a time: their indices and values
-                // are loaded before the (ordered) subtractions
-                const int e1 = m.Ap[r + 1];
-                int e = m.Ap[r];
-                for (; e + 3 < e1; e += 4) {
-                    const int p0 = m.Apos[e], p1 = m.Apos[e + 1], p2 = m.Apos[e + 2], p3 = m.Apos[e + 3];
-                    const int j0 = m.Aj[e], j1 = m.Aj[e + 1], j2 = m.Aj[e + 2], j3 = m.Aj[e + 3];
-                    const double a0 = A[p0], a1 = A[p1], a2 = A[p2], a3 = A[p3];
-                    const double y0 = x64[j0], y1 = x64[j1], y2 = x64[j2], y3 = x64[j3];
-                    s -= a0 * y0;
-                    s -= a1 * y1;
-                    s -= a2 * y2;
-                    s -= a3 * y3;
-                }
-                if (e < e1) {
-                    const int rem = e1 - e;  // 1 to 3 entries
-                    const int p0 = m.Apos[e], p1 = m.Apos[rem > 1 ? e + 1 : e], p2 = m.Apos[rem > 2 ? e + 2 : e];
-                    const int j0 = m.Aj[e], j1 = m.Aj[rem > 1 ? e + 1 : e], j2 = m.Aj[rem > 2 ? e + 2 : e];
-                    const double a0 = A[p0], a1 = A[p1], a2 = A[p2];
-                    const double y0 = x64[j0], y1 = x64[j1], y2 = x64[j2];
-                    s -= a0 * y0;
-                    if (rem > 1) s -= a1 * y1;
-                    if (rem > 2) s -= a2 * y2;
-                }
-                if (lr.Z && (r == lr.p0 || r == lr.p1)) s += lowrank_residual(lr, r, x64);
+                const double s = residual_row<T, double>(m, A, xg, x64, r, lr);
                 xv[r] = T(s);
-                const unsigned long long k = abs_key(s);
-                rk = k > rk ? k : rk;
+                const unsigned long long q = abs_key(s);
+                rk = q > rk ? q : rk;
             }
             const double rn = __longlong_as_double(static_cast<long long>(block_max_key(rk, red)));
             if (!(rn > a.ir_tol * bn) || !(rn > a.ir_abs)) break;

@@ -19,6 +19,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <set>
 #include <utility>
@@ -879,7 +880,7 @@ pf_status analyze_matrix(pf_ctx *ctx, int which, HostMat &H) {
 // cluster barrier.  Lanes per task: the smallest power of two that leaves at
 // most four entries to a lane (at most 32).  A top set too large for the
 // inverse leaves the program unusable (ok = 0).  Host only.
-pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P) {
+pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P, int group) {
     const HostMat &H = ctx->hm[which];
     const int C = kClCtas, n = H.n, nbus = ctx->nbus;
     P = HostCl();
@@ -1008,9 +1009,78 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P) {
             tl[r] += wt[it];
         }
     }
-    // vector words: xb for every row, then tc and tx for T rows
-    std::vector<int> cnt(C, 0), xw(n, 0), tcw(std::max(1, nt), 0), txw(std::max(1, nt), 0);
-    for (int i = 0; i < n; i++) xw[i] = cnt[owner[i]]++;
+    // groups of subtree levels: a bottom row's group is its level / g; its
+    // parent inside the group (-1: none), the paths up to the group's top
+    const int g = std::max(1, std::min(group, kClGroupMax));
+    P.group = g;
+    std::vector<int> lev(n, 0);
+    for (int l = 0; l < H.nlev; l++)
+        for (int i = H.lvl_ptr[l]; i < H.lvl_ptr[l + 1]; i++) lev[i] = l;
+    auto grp = [&](int i) { return lev[i] / g; };
+    std::vector<int> gpar(n, -1);
+    for (int j = 0; j < n; j++)
+        if (!inT[j] && par[j] >= 0 && !inT[par[j]] && grp(par[j]) == grp(j)) gpar[j] = par[j];
+    std::vector<std::vector<int>> gdesc(n), ganc(n);  // strict, inside the group
+    for (int j = 0; j < n; j++)
+        for (int a = gpar[j]; a >= 0; a = gpar[a]) {
+            gdesc[a].push_back(j);
+            ganc[j].push_back(a);  // nearest first
+        }
+    for (auto &v : gdesc) std::sort(v.begin(), v.end());
+    std::vector<char> hasfwd(n, 0);
+    for (int i = 0; i < n; i++)
+        if (!inT[i]) hasfwd[i] = rowlen(i) > 0 || !gdesc[i].empty();
+    // values of the groups' inverses: W(ganc[j][q-1], j) at GV index wbase[j] + q - 1
+    std::vector<int> wbase(n, -1);
+    P.gw_col.clear();
+    P.gw_upd.clear();
+    P.gv_info.clear();
+    int ngv = 0;
+    for (int j = 0; j < n; j++) {
+        if (ganc[j].empty()) continue;
+        const int Pn = 1 + int(ganc[j].size());
+        wbase[j] = ngv;
+        const int ub = int(P.gw_upd.size());
+        std::vector<int> path(1, j);
+        path.insert(path.end(), ganc[j].begin(), ganc[j].end());
+        for (int pp = 0; pp + 1 < Pn; pp++) {
+            const int m = path[size_t(pp)];
+            for (int pos = H.Cp[m]; pos < H.Cp[m + 1]; pos++) {
+                const int i = H.Cr[pos];
+                for (int q = pp + 1; q < Pn; q++)
+                    if (path[size_t(q)] == i) P.gw_upd.push_back(int4{pp, q, H.offLc + pos, 0});
+            }
+        }
+        P.gw_col.push_back(int4{ub, int(P.gw_upd.size()), ngv, Pn});
+        for (int q = 1; q < Pn; q++) P.gv_info.push_back(int4{0, path[size_t(q)], j, 0});
+        ngv += Pn - 1;
+    }
+    P.n_gw = ngv;
+    auto widx = [&](int a, int j) {  // GV index of W(a, j), a a strict ancestor of j in its group
+        for (size_t q = 0; q < ganc[j].size(); q++)
+            if (ganc[j][q] == a) return wbase[j] + int(q);
+        return -1;
+    };
+    P.gm_ptr.assign(1, 0);
+    P.gm_term.clear();
+    int nm = 0;
+    // a combined entry: a single identity term is the factor value itself
+    // (kind 0), anything else a GV entry (kind 5) with its terms
+    auto combined = [&](const std::vector<int2> &terms, int type, int i, int k) {
+        if (terms.size() == 1 && terms[0].x < 0) return int4{0, terms[0].y, 0, 0};
+        for (const int2 &t : terms) P.gm_term.push_back(t);
+        P.gm_ptr.push_back(int(P.gm_term.size()));
+        P.gv_info.push_back(int4{type, i, k, 0});
+        return int4{5, P.n_gw + nm++, 0, 0};
+    };
+    // vector words: per bottom row b (its right-hand side, later its
+    // solution) and z (its forward result, when it has a forward task); per
+    // T row xb (right-hand side, then z), tc and tx
+    std::vector<int> cnt(C, 0), xw(n, 0), zw(n, -1), tcw(std::max(1, nt), 0), txw(std::max(1, nt), 0);
+    for (int i = 0; i < n; i++) {
+        xw[i] = cnt[owner[i]]++;
+        if (!inT[i] && hasfwd[i]) zw[i] = cnt[owner[i]]++;
+    }
     for (int it = 0; it < nt; it++) {
         tcw[it] = cnt[owner[tnode[it]]]++;
         txw[it] = cnt[owner[tnode[it]]]++;
@@ -1018,21 +1088,20 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P) {
     P.nx = *std::max_element(cnt.begin(), cnt.end());
     if (P.nx > 65535) return PF_OK;
     auto ref_xb = [&](int i) { return (owner[i] << 16) | xw[i]; };
+    auto ref_z = [&](int i) { return (owner[i] << 16) | (!inT[i] && zw[i] >= 0 ? zw[i] : xw[i]); };
     auto ref_tc = [&](int i) { return (owner[i] << 16) | tcw[trel[i]]; };
     auto ref_tx = [&](int i) { return (owner[i] << 16) | txw[trel[i]]; };
     for (int i = 0; i < n; i++) {
         P.rhsref[H.bus_new[i]] = ref_xb(i);
         P.xref[H.bus_new[i]] = inT[i] ? ref_tx(i) : ref_xb(i);
     }
-    // per CTA: its bottom rows by level
-    std::vector<std::vector<std::vector<int>>> mine(C, std::vector<std::vector<int>>(H.nlev));
-    {
-        std::vector<int> lev(n, 0);
-        for (int l = 0; l < H.nlev; l++)
-            for (int i = H.lvl_ptr[l]; i < H.lvl_ptr[l + 1]; i++) lev[i] = l;
-        for (int i = 0; i < n; i++)
-            if (!inT[i]) mine[owner[i]][lev[i]].push_back(i);
-    }
+    // per CTA: its bottom rows by group
+    int ngrp = 0;
+    for (int i = 0; i < n; i++)
+        if (!inT[i]) ngrp = std::max(ngrp, grp(i) + 1);
+    std::vector<std::vector<std::vector<int>>> mine(C, std::vector<std::vector<int>>(std::max(1, ngrp)));
+    for (int i = 0; i < n; i++)
+        if (!inT[i]) mine[owner[i]][grp(i)].push_back(i);
     for (int r = 0; r < C; r++) {
         std::vector<int4> tasks, steps;
         std::vector<int> refs;
@@ -1055,14 +1124,26 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P) {
             steps.push_back(int4{tb, int(tasks.size()), G, cluster});
             maxlen = 0;
         };
-        for (int l = 1; l < H.nlev; l++) {  // forward subtree levels
+        for (int G0 = 0; G0 < ngrp; G0++) {  // forward subtree groups
             const int tb = int(tasks.size());
-            for (int i : mine[r][l]) {
-                if (rowlen(i) == 0) continue;
-                add(xw[i], xw[i], -1);
-                for (int q = H.Fp[i]; q < H.Fp[i + 1]; q++) {
-                    refs.push_back(ref_xb(H.Fc[q]));
-                    esrc.push_back(int4{0, H.offLr + q, 0, 0});
+            for (int i : mine[r][G0]) {
+                if (!hasfwd[i]) continue;
+                add(zw[i], xw[i], -1);
+                for (int j : gdesc[i]) {  // - W(i, j) b_j
+                    refs.push_back(ref_xb(j));
+                    esrc.push_back(int4{3, widx(i, j), 0, 0});
+                }
+                std::map<int, std::vector<int2>> comb;  // k below the group -> terms W(i, j) L(j, k)
+                std::vector<int> js(1, i);
+                js.insert(js.end(), gdesc[i].begin(), gdesc[i].end());
+                for (int j : js)
+                    for (int q = H.Fp[j]; q < H.Fp[j + 1]; q++) {
+                        const int k = H.Fc[q];
+                        if (grp(k) < G0) comb[k].push_back(int2{j == i ? -1 : widx(i, j), H.offLr + q});
+                    }
+                for (auto &kv : comb) {
+                    refs.push_back(ref_z(kv.first));
+                    esrc.push_back(combined(kv.second, 1, i, kv.first));
                 }
                 close();
             }
@@ -1079,7 +1160,7 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P) {
                         add(tcw[it], xw[i], -1);
                         for (int q = H.Fp[i]; q < H.Fp[i + 1]; q++)
                             if (!inT[H.Fc[q]]) {
-                                refs.push_back(ref_xb(H.Fc[q]));
+                                refs.push_back(ref_z(H.Fc[q]));
                                 esrc.push_back(int4{0, H.offLr + q, 0, 0});
                             }
                     } else if (kind == 2) {  // z = W c
@@ -1100,14 +1181,25 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P) {
                 step(tb, 1);
             }
         }
-        for (int l = H.nlev - 1; l >= 0; l--) {  // backward subtree levels
+        for (int G0 = ngrp - 1; G0 >= 0; G0--) {  // backward subtree groups
             const int tb = int(tasks.size());
-            for (int i : mine[r][l]) {
-                add(xw[i], xw[i], H.offDi + i);
-                for (int p = H.Cp[i]; p < H.Cp[i + 1]; p++) {
-                    const int k = H.Cr[p];
-                    refs.push_back(inT[k] ? ref_tx(k) : ref_xb(k));
-                    esrc.push_back(int4{0, H.offLc + p, 0, 0});
+            for (int i : mine[r][G0]) {
+                add(xw[i], !inT[i] && zw[i] >= 0 ? zw[i] : xw[i], H.offDi + i);
+                for (int a : ganc[i]) {  // - W(a, i) z_a / d_a
+                    refs.push_back(ref_z(a));
+                    esrc.push_back(int4{4, widx(a, i), H.offDi + a, 0});
+                }
+                std::map<int, std::vector<int2>> comb;  // k above the group -> terms W(j, i) L(k, j)
+                std::vector<int> js(1, i);
+                js.insert(js.end(), ganc[i].begin(), ganc[i].end());
+                for (int j : js)
+                    for (int pos = H.Cp[j]; pos < H.Cp[j + 1]; pos++) {
+                        const int k = H.Cr[pos];
+                        if (inT[k] || grp(k) > G0) comb[k].push_back(int2{j == i ? -1 : widx(j, i), H.offLc + pos});
+                    }
+                for (auto &kv : comb) {
+                    refs.push_back(inT[kv.first] ? ref_tx(kv.first) : ref_xb(kv.first));
+                    esrc.push_back(combined(kv.second, 2, i, kv.first));
                 }
                 close();
             }
@@ -1133,6 +1225,11 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P) {
     }
     if (P.refs.empty()) P.refs.push_back(0);
     if (P.vsrc.empty()) P.vsrc.push_back(int4{0, 0, 0, 0});
+    P.n_gm = nm;
+    P.n_gwcol = int(P.gw_col.size());
+    if (P.gw_col.empty()) P.gw_col.push_back(int4{0, 0, 0, 1});
+    if (P.gw_upd.empty()) P.gw_upd.push_back(int4{0, 0, 0, 0});
+    if (P.gm_term.empty()) P.gm_term.push_back(int2{-1, 0});
     P.ok = 1;
     return PF_OK;
 }
@@ -1192,6 +1289,14 @@ pf_status upload_cluster(pf_ctx *ctx, int w) {
     TRY(upload_padded(ctx, &M.vptr, P.vptr));
     TRY(upload_padded(ctx, &M.rhsref, P.rhsref));
     TRY(upload_padded(ctx, &M.xref, P.xref));
+    M.n_gwcol = P.n_gwcol;
+    M.n_gw = P.n_gw;
+    M.n_gm = P.n_gm;
+    TRY(upload(ctx, &M.gw_col, P.gw_col.data(), P.gw_col.size()));
+    TRY(upload(ctx, &M.gw_upd, P.gw_upd.data(), P.gw_upd.size()));
+    TRY(upload_padded(ctx, &M.gm_ptr, P.gm_ptr));
+    TRY(upload(ctx, &M.gm_term, P.gm_term.data(), P.gm_term.size()));
+    TRY(dalloc(ctx, &M.gv, size_t(std::max(1, P.n_gw + P.n_gm))));
     return PF_OK;
 }
 
@@ -1780,6 +1885,28 @@ pf_status ensure_cluster(pf_ctx *ctx) {
     return PF_OK;
 }
 
+// Rebuilds the cluster engine's programs with g subtree levels per step:
+// the device copies are freed (uploaded again on the next use) and a CUDA
+// graph that launched the old ones is dropped.
+pf_status set_cluster_group(pf_ctx *ctx, int g) {
+    if (g == ctx->cl_group) return PF_OK;
+    drop_graph(ctx);
+    for (int w = 0; w < 2; w++) {
+        ClMat &M = ctx->cl[w];
+        void *ptrs[] = {M.tpar, M.tcp, M.tcdep, M.tcpos, M.tdepth, M.vsrc, M.vals, M.tasks, M.tptr, M.steps,
+                        M.sptr, M.refs, M.eptr, M.vptr, M.rhsref, M.xref, M.gw_col, M.gw_upd, M.gm_ptr,
+                        M.gm_term, M.gv};
+        for (void *p : ptrs) dfree(ctx, p);
+        dfree(ctx, ctx->clW[w]);
+        ctx->clW[w] = nullptr;
+        M = ClMat();
+    }
+    ctx->cl_group = g;
+    for (int w = 0; w < 2; w++) TRY(build_cluster(ctx, w, ctx->hcl[w], g));
+    ctx->cl_smem = cluster_smem_layout(ctx);
+    return PF_OK;
+}
+
 // Epochs for the Jacobian factorisations of one NR or adjoint launch (at
 // most `count`); the flags are cleared when the counter would wrap.
 unsigned nr_epochs(pf_ctx *ctx, unsigned count, cudaStream_t s) {
@@ -1909,7 +2036,7 @@ pf_status pf_analyze(pf_ctx *ctx, pf_symbolic_info *info) {
             TRY(analyze_matrix(ctx, w, ctx->hm[w]));
             if (ctx->on_device) TRY(upload_matrix(ctx, ctx->hm[w], ctx->dm[w]));
         }
-        for (int w = 0; w < 2; w++) TRY(build_cluster(ctx, w, ctx->hcl[w]));
+        for (int w = 0; w < 2; w++) TRY(build_cluster(ctx, w, ctx->hcl[w], ctx->cl_group));
         ctx->cl_smem = cluster_smem_layout(ctx);
         ctx->analyzed = true;
     }
@@ -2506,13 +2633,16 @@ pf_status pf_get_tuning(const pf_ctx *ctx, pf_tuning *out) {
 
 pf_status pf_set_tuning(pf_ctx *ctx, const pf_tuning *t) {
     if (!ctx || !t) return fail(ctx, PF_ERR_ARG, "null pointer");
+    const bool cl_engine = t->engine == PF_ENGINE_CLUSTER;
     if (t->engine < 0 || t->engine > PF_ENGINE_CLUSTER || t->factor < 0 || t->factor > 2 || t->tail < 0 ||
         t->tail > 3 || t->outage < 0 || t->outage > 2 ||
-        (t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16) ||
+        (!cl_engine && t->cluster != 0 && t->cluster != 1 && t->cluster != 8 && t->cluster != 16) ||
+        (cl_engine && (t->cluster < 0 || t->cluster > kClGroupMax)) ||
         (t->threads != 0 && t->threads != 128 && t->threads != 256 && t->threads != 512))
         return fail(ctx, PF_ERR_ARG, "tuning field out of range");
     ctx->tune = *t;
     ctx->tune.ms = t->ms;
+    if (cl_engine && ctx->analyzed) TRY(set_cluster_group(ctx, t->cluster > 0 ? t->cluster : kClGroupDefault));
     return PF_OK;
 }
 
@@ -2552,8 +2682,10 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     // the lane engine has no cluster, tail or outage choice; the cluster
     // engine no cluster size (its own) and no outage form (one base case)
     // block sizes matter only for one block per case of a batch
+    // the cluster engine's field `cluster` is its subtree levels per step
     for (int e : engines)
-        for (int c : (e != PF_ENGINE_BLOCK ? std::vector<int>{0} : clusters))
+        for (int c : (e == PF_ENGINE_CLUSTER ? std::vector<int>{1, 2, 3, 4}
+                                             : (e != PF_ENGINE_BLOCK ? std::vector<int>{0} : clusters)))
             for (int f : factors)
                 for (int t : (e == PF_ENGINE_LANES ? std::vector<int>{0} : tails))
                     for (int u : (e != PF_ENGINE_BLOCK ? std::vector<int>{1} : outages))
@@ -2576,6 +2708,7 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
     pf_status last = PF_OK;
     for (const pf_tuning &t : cand) {
         ctx->tune = t;
+        if (t.engine == PF_ENGINE_CLUSTER) TRY(set_cluster_group(ctx, t.cluster > 0 ? t.cluster : kClGroupDefault));
         pf_status st = pf_run_to_tol(ctx, &o, vm_dev, va_dev, res.data(), stream);  // untimed
         if (st != PF_OK) {
             last = st;
@@ -2605,6 +2738,8 @@ pf_status pf_autotune(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doub
         return fail(ctx, last == PF_OK ? PF_ERR_NOT_CONVERGED : last, "no mapping converged");
     }
     ctx->tune = best;
+    if (best.engine == PF_ENGINE_CLUSTER)
+        TRY(set_cluster_group(ctx, best.cluster > 0 ? best.cluster : kClGroupDefault));
     *out = best;
     return PF_OK;
 }
@@ -2954,6 +3089,41 @@ int gbpf_debug_cluster(const pf_ctx *ctx, int which, long long *sizes, int *task
     put(P.rhsref, rhsref);
     put(P.xref, xref);
     put(P.tnode, tnode);
+    return 0;
+}
+
+// Test hook (host only, no GPU needed): the grouped subtree steps' value
+// programs of matrix `which` in the cluster engine.  sizes[6] receives
+// {group, inverse columns, inverse entries, combined entries, updates,
+// terms}; gw_col and gw_upd (4 ints each), gm_ptr (combined entries + 1),
+// gm_term (2 ints each) and gv_info (4 ints per value) are copied when cap
+// (ints per array) covers them.  Returns 0, or -1 for a bad argument or a
+// context that has not been analysed.
+int gbpf_debug_cluster_groups(const pf_ctx *ctx, int which, int *sizes, int *gw_col, int *gw_upd, int *gm_ptr,
+                              int *gm_term, int *gv_info, long long cap) {
+    if (!ctx || !sizes || which < 0 || which > 1 || !ctx->analyzed) return -1;
+    const gbpf::HostCl &P = ctx->hcl[which];
+    sizes[0] = P.group;
+    sizes[1] = P.n_gwcol;
+    sizes[2] = P.n_gw;
+    sizes[3] = P.n_gm;
+    sizes[4] = P.n_gwcol > 0 ? int(P.gw_upd.size()) : 0;
+    sizes[5] = P.n_gm > 0 ? P.gm_ptr.back() : 0;
+    auto put4 = [&](const std::vector<int4> &a, size_t count, int *dst) {
+        if (dst && cap >= 4 * (long long)count)
+            for (size_t i = 0; i < count; i++) {
+                dst[4 * i] = a[i].x, dst[4 * i + 1] = a[i].y, dst[4 * i + 2] = a[i].z, dst[4 * i + 3] = a[i].w;
+            }
+    };
+    put4(P.gw_col, size_t(P.n_gwcol), gw_col);
+    put4(P.gw_upd, size_t(sizes[4]), gw_upd);
+    put4(P.gv_info, P.gv_info.size(), gv_info);
+    if (gm_ptr && cap >= (long long)P.gm_ptr.size()) std::copy(P.gm_ptr.begin(), P.gm_ptr.end(), gm_ptr);
+    if (gm_term && cap >= 2LL * sizes[5])
+        for (int t = 0; t < sizes[5]; t++) {
+            gm_term[2 * t] = P.gm_term[size_t(t)].x;
+            gm_term[2 * t + 1] = P.gm_term[size_t(t)].y;
+        }
     return 0;
 }
 

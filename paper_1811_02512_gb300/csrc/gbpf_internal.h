@@ -156,8 +156,11 @@ struct DevMat {
 // of val[e] X(ref[e]).  Values are packed per CTA ([entries | diagonal
 // values]) and gathered after every factorisation from vsrc {kind, a, b}:
 // 0 the factor value F[a], 1 -W[a], 2 -W[a] F[b], W being the dense inverse
-// of the tail block of L, row-major (W(it, jt) at W[it * nt + jt]).
+// of the tail block of L, row-major (W(it, jt) at W[it * nt + jt]); 3
+// -GV[a], 4 -GV[a] F[b], 5 GV[a], GV the values of the grouped subtree steps.
 constexpr int kClCtas = 16;
+constexpr int kClGroupMax = 8;     // subtree levels per grouped step (at most)
+constexpr int kClGroupDefault = 3; // subtree levels per step unless the tuning names another
 constexpr int kClTailMax = 2048;   // largest tail whose dense inverse is formed
 constexpr int kTailInvWarps = 16;  // T columns (one per warp) per block of k_tail_inverse
 // shared memory of k_tail_inverse for a tail of nt rows with ne entries and
@@ -188,12 +191,39 @@ struct ClMat {
     int *xref = nullptr;           // [nbus] word of the bus's solution, -1: not in the matrix
     // byte offsets of the CTA's regions in dynamic shared memory
     int so_x = 0, so_tasks = 0, so_steps = 0, so_addr = 0, so_vals = 0;
+    // Grouped subtree steps: with `group` g > 1 the subtree levels run g at a
+    // time, each group through the inverse W_G of its block of L (unit lower,
+    // W(i, j) != 0 only for j a descendant of i within the group):
+    //   forward  z_i = b_i + sum_{j desc} W(i,j) b_j - sum_k M(i,k) z_k,
+    //            M(i,k) = sum_{j in {i} + desc} W(i,j) L(j,k), k below the group;
+    //   backward x_i = z_i / d_i + sum_{j anc} W(j,i) z_j / d_j - sum_k M'(i,k) x_k,
+    //            M'(i,k) = sum_{j in {i} + anc} W(j,i) L(k,j), k above the group.
+    // The group values GV = [W entries | combined entries] are formed after
+    // every factorisation: gw_col per inverse column j {first update, end
+    // update, GV index of W(path[1], j), path length P}, gw_upd {p, q, factor
+    // position of L(path[q], path[p]), 0} (w_q -= L w_p along the path);
+    // gm_ptr / gm_term per combined entry its terms {W index or -1 for the
+    // identity, factor position of the L entry}, summed in order.
+    int n_gwcol = 0, n_gw = 0, n_gm = 0;
+    int4 *gw_col = nullptr, *gw_upd = nullptr;
+    int *gm_ptr = nullptr;
+    int2 *gm_term = nullptr;
+    double *gv = nullptr;          // [n_gw + n_gm]
 };
 
 // Host form of a ClMat.
 struct HostCl {
     int ok = 0;                    // the program fits (top set small enough for its inverse)
     int nt = 0, nx = 0, tdepth_max = 0;
+    int group = 1;                 // subtree levels per step (see ClMat)
+    // values of the grouped steps (see ClMat): inverse columns, their updates,
+    // the combined entries' terms, and what every value is (for tests:
+    // {0, row, column} an entry of a group's inverse, {1, row, k} a forward
+    // combined entry, {2, row, k} a backward one)
+    std::vector<int4> gw_col, gw_upd, gv_info;
+    std::vector<int> gm_ptr;
+    std::vector<int2> gm_term;
+    int n_gwcol = 0, n_gw = 0, n_gm = 0;
     std::vector<int> tnode;        // level-order rows of the top set, ascending
     std::vector<int> tpar, tcp, tcdep, tcpos, tdepth;
     std::vector<int4> vsrc, tasks, steps;
@@ -388,6 +418,7 @@ struct pf_ctx {
     gbpf::ClMat cl[2];
     double *clW[2] = {nullptr, nullptr};
     size_t cl_smem = 0;
+    int cl_group = gbpf::kClGroupDefault;  // subtree levels per step of the cluster engine's programs
     int tail_cl_max[2][2] = {{-1, -1}, {-1, -1}};  // [mat][prec] resident tail-factor clusters (-1: not asked)
     // CUDA graph of the device work of one fast decoupled pf_run_to_tol
     // (block and cluster engines), captured on an internal stream for a given

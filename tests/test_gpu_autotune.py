@@ -55,8 +55,9 @@ def test_autotune_single_and_batch(oracle):
     va = torch.zeros_like(vm)
     opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-8, max_iter=200)
     t = gbpf.pf_autotune(g.ctx, opts, vm, va, reps=2)
-    assert t["ms"] > 0 and t["factor"] in (1, 2) and t["tail"] in (1, 2)
-    assert t["cluster"] in (1, 8, 16) or (t["engine"] == gbpf.PF_ENGINE_CLUSTER and t["cluster"] == 0)
+    assert t["ms"] > 0 and t["factor"] in (1, 2) and t["tail"] in (1, 2, 3)
+    # the cluster engine's field is its subtree levels per step
+    assert t["cluster"] in ((1, 2, 3, 4) if t["engine"] == gbpf.PF_ENGINE_CLUSTER else (1, 8, 16))
     assert t["threads"] == 0  # block sizes are a batch choice
     assert gbpf.pf_get_tuning(g.ctx) == t
     g.close()
@@ -111,13 +112,15 @@ def test_low_rank_outages_match_oracle(oracle, precision):
     g.close()
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
-def test_cluster_engine_matches_oracle(oracle, cfg):
+@pytest.mark.parametrize("cfg,group", [(0, 0), (1, 0), (1, 1), (1, 2), (1, 4)])
+def test_cluster_engine_matches_oracle(oracle, cfg, group):
     """The single-case cluster engine (substitutions shared by a 16-block
     cluster, the narrow top of the elimination tree through its explicit
-    inverse): voltages against the oracle's run to a tight mismatch, every
-    factor form, twice in a row on the same context (the programs stay
-    resident, the tail inverses are formed again from each factorisation)."""
+    inverse, the subtree levels `group` at a time through their blocks'
+    inverses; 0 = the default): voltages against the oracle's run to a tight
+    mismatch, every factor form, twice in a row on the same context (the
+    programs stay resident, the inverses are formed again from each
+    factorisation)."""
     case = gridgen.config(cfg)
     rc, vm0, va0, _, _ = oracle.power_flow(case, oracle.NR, tol=1e-12, max_iter=30)
     assert rc == oracle.OK
@@ -126,7 +129,7 @@ def test_cluster_engine_matches_oracle(oracle, cfg):
     vm = torch.zeros((1, case.n), dtype=torch.float64, device=DEV)
     va = torch.zeros_like(vm)
     for fac, tail in itertools.product([1, 2], [1, 2]):
-        gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_CLUSTER, cluster=0, factor=fac, tail=tail)
+        gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_CLUSTER, cluster=group, factor=fac, tail=tail)
         for _ in range(2):
             vm.zero_()
             va.zero_()

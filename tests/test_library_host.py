@@ -603,8 +603,24 @@ def _cluster_program(lib, g, which):
                 rhsref=rhsref[:g.nbus], xref=xref[:g.nbus], tnode=tnode[:nt])
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
-def test_cluster_program_solves_like_oracle(lib, oracle, cfg):
+def _cluster_groups(lib, g, which):
+    f = lib.gbpf_debug_cluster_groups
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 6 + [C.c_longlong]
+    sz = np.zeros(6, np.int32)
+    assert f(g.ctx, which, sz.ctypes.data, *([None] * 5), 0) == 0
+    group, ncol, ngw, ngm, nupd, nterm = (int(v) for v in sz)
+    cap = max(4 * max(ncol, nupd, ngw + ngm), 2 * nterm, ngm + 1, 1)
+    arrs = [np.zeros(cap, np.int32) for _ in range(5)]
+    assert f(g.ctx, which, sz.ctypes.data, *(a.ctypes.data for a in arrs), cap) == 0
+    gw_col, gw_upd, gm_ptr, gm_term, gv_info = arrs
+    return dict(group=group, n_gw=ngw, n_gm=ngm, gw_col=gw_col[:4 * ncol].reshape(-1, 4),
+                gw_upd=gw_upd[:4 * nupd].reshape(-1, 4), gm_ptr=gm_ptr[:ngm + 1],
+                gm_term=gm_term[:2 * nterm].reshape(-1, 2), gv_info=gv_info[:4 * (ngw + ngm)].reshape(-1, 4))
+
+
+@pytest.mark.parametrize("cfg,group", [(0, 0), (0, 2), (1, 0), (1, 1), (1, 4), (1, 6)])
+def test_cluster_program_solves_like_oracle(lib, oracle, cfg, group):
     """The cluster engine's substitution program, run on the CPU with the
     device's synchronisation: the oracle's factor is placed in the library's
     level-order layout and the top set's inverse is formed densely from it.
@@ -615,10 +631,13 @@ def test_cluster_program_solves_like_oracle(lib, oracle, cfg):
     oracle's LDL^T solve; the top set is closed under parents, every CTA
     passes the same number of cluster barriers, every index stays inside its
     buffer, and the programs of the 10,000-bus grid fit one CTA's shared
-    memory."""
+    memory.  The subtree levels run `group` at a time (0: the default)
+    through the groups' inverses, whose values are formed here from the
+    host's value programs as the device forms them."""
     import scipy.sparse as sp
     case = gridgen.config(cfg)
     g = gbpf.Grid(case)
+    gbpf.pf_set_tuning(g.ctx, engine=gbpf.PF_ENGINE_CLUSTER, cluster=group)
     rng = np.random.default_rng(7 + cfg)
     for which, name in ((gbpf.PF_MAT_BP, "bp"), (gbpf.PF_MAT_BPP, "bpp")):
         P = _cluster_program(lib, g, which)
@@ -651,14 +670,52 @@ def test_cluster_program_solves_like_oracle(lib, oracle, cfg):
             assert np.all((parent[T] < 0) | inT[np.maximum(parent[T], 0)])  # closed under parents
             W = np.linalg.inv(L[T][:, T].toarray() + np.eye(nt))
             Wd = W.flatten()  # W(it, jt) at it * nt + jt
+        # the grouped subtree steps' values, as the device forms them from the
+        # host's lists (the solve below checks them against the oracle)
+        GR = _cluster_groups(lib, g, which)
+        ngw, ngm = GR["n_gw"], GR["n_gm"]
+        GV = np.zeros(max(1, ngw + ngm))
+        for ub, ue, base, Pn in GR["gw_col"]:
+            w = np.zeros(8)
+            w[0] = 1.0
+            for p_, q_, fpos, _ in GR["gw_upd"][ub:ue]:
+                assert 0 <= p_ < q_ < Pn <= 8
+                w[q_] -= F[fpos] * w[p_]
+            GV[base:base + Pn - 1] = w[1:Pn]
+        for e in range(ngm):
+            acc = 0.0
+            for wi, fpos in GR["gm_term"][GR["gm_ptr"][e]:GR["gm_ptr"][e + 1]]:
+                assert wi < ngw and fpos < P["offLr"] + nnz
+                acc += (1.0 if wi < 0 else GV[wi]) * F[fpos]
+            GV[ngw + e] = acc
+        # what every value is: an inverse entry W(a, j) has a in j's group
+        # above j; a combined entry's k lies below (forward) or above
+        # (backward) its row's group
+        lev0 = np.empty(n, np.int64)
+        lev0[new] = lev - 1  # level of every level-order row, leaves 0
+        inT0 = np.zeros(n, bool)
+        inT0[P["tnode"]] = True
+        gsz = GR["group"]
+        for typ, i, jk, _ in GR["gv_info"]:
+            assert not inT0[i]
+            if typ == 0:
+                assert lev0[i] // gsz == lev0[jk] // gsz and lev0[i] > lev0[jk]
+            elif typ == 1:
+                assert lev0[jk] // gsz < lev0[i] // gsz
+            else:
+                assert inT0[jk] or lev0[jk] // gsz > lev0[i] // gsz
         vs = P["vsrc"]
         vals = np.empty(vs.shape[0])
-        k0, k1, k2 = vs[:, 0] == 0, vs[:, 0] == 1, vs[:, 0] == 2
-        assert np.all(k0 | k1 | k2)
-        assert np.all(vs[k0, 1] < P["offLr"] + nnz) and np.all(vs[k1 | k2, 1] < max(1, nt * nt))
-        vals[k0] = F[vs[k0, 1]]
-        vals[k1] = -Wd[vs[k1, 1]]
-        vals[k2] = -Wd[vs[k2, 1]] * F[vs[k2, 2]]
+        kinds = [vs[:, 0] == q for q in range(6)]
+        assert np.all(np.logical_or.reduce(kinds))
+        assert np.all(vs[kinds[0], 1] < P["offLr"] + nnz) and np.all(vs[kinds[1] | kinds[2], 1] < max(1, nt * nt))
+        assert np.all(vs[kinds[3] | kinds[4], 1] < max(1, ngw)) and np.all(vs[kinds[5], 1] < ngw + max(1, ngm))
+        vals[kinds[0]] = F[vs[kinds[0], 1]]
+        vals[kinds[1]] = -Wd[vs[kinds[1], 1]]
+        vals[kinds[2]] = -Wd[vs[kinds[2], 1]] * F[vs[kinds[2], 2]]
+        vals[kinds[3]] = -GV[vs[kinds[3], 1]]
+        vals[kinds[4]] = -GV[vs[kinds[4], 1]] * F[vs[kinds[4], 2]]
+        vals[kinds[5]] = GV[vs[kinds[5], 1]]
         Cc, nx = P["C"], P["nx"]
         # every index the device program uses stays inside its buffers
         assert np.all((P["refs"] >> 16) < Cc) and np.all((P["refs"] & 0xffff) < max(1, nx))
@@ -706,7 +763,7 @@ def test_cluster_program_solves_like_oracle(lib, oracle, cfg):
         ref = np.empty(n)
         ref[an["perm"]] = xs
         assert np.max(np.abs(x - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref))), (name, np.max(np.abs(x - ref)))
-        if cfg == 1:
+        if cfg == 1 and group <= 4:  # larger groups may outgrow a CTA (the engine then does not apply)
             assert P["smem"] + 4096 <= 232448, P["smem"]
     g.close()
 
