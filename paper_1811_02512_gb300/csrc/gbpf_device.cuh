@@ -739,6 +739,23 @@ __device__ bool block_solve(Ring *R, unsigned char *stages, const DevMat &m, con
                                         F + m.offDi, m.lvl_ptr, x, spin);
 }
 
+// 1 / v for the pivots of the factorisations, whose reciprocals sit on the
+// level chain: Newton's iteration for the reciprocal, r <- r + r (1 - v r)
+// (each step squares the relative error), started from the correctly rounded
+// FP32 reciprocal (relative error below 2^-24): two steps reach the FP64
+// rounding level (within an ulp or two of the quotient; a self-test checks
+// this against CUDA's division).  Outside the FP32 range, or for a zero or
+// non-finite v, the plain division.
+__device__ __forceinline__ double pivot_recip(double v) {
+    const double a = fabs(v);
+    if (!(a >= 1e-30 && a <= 1e30)) return 1.0 / v;
+    double r = double(__frcp_rn(float(v)));
+    r = fma(r, fma(-v, r, 1.0), r);
+    r = fma(r, fma(-v, r, 1.0), r);
+    return r;
+}
+__device__ __forceinline__ float pivot_recip(float v) { return 1.0f / v; }
+
 // sin and cos of a small angle (|x| <= kRotMax) from their Maclaurin series,
 // truncated after the x^11 (sin) and x^12 (cos) terms in Horner form; for
 // |x| <= 0.2 the first omitted terms are below 2e-19, far under one unit in

@@ -248,9 +248,10 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
         val[j] = t <= cnt ? T(t == 0 ? a[c] : a[m.offLc + c0 + t - 1]) - part[j] : T(0);
     }
     const T d = __shfl_sync(0xffffffffu, val[0], 0);
+    const T dinv = pivot_recip(d);
     if (lane == 0) {
         v[c] = d;
-        v[m.offDi + c] = T(1) / d;
+        v[m.offDi + c] = dinv;
         const double dd = double(d);
         if (!isfinite(dd)) atomicCAS(fstat, PF_OK, PF_ERR_NONFINITE);
         else if (fabs(dd) <= 1e-14 * amax) atomicCAS(fstat, PF_OK, PF_ERR_SINGULAR);
@@ -259,7 +260,7 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
     for (int j = 0; j < kDepTargets; j++) {
         const int t = lane + 32 * j;
         if (t >= 1 && t <= cnt) {
-            const T l = val[j] / d;
+            const T l = val[j] * dinv;
             Lc[c0 + t - 1] = l;
             v[m.offLr + m.Cpos[c0 + t - 1]] = l;
         }
@@ -327,6 +328,18 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) partg[(long long)inst * m.ft_ng + m.tipos[k]] = T(A[(long long)inst * m.stride + m.tapos[k]]) - s;
 }
 
+// Asynchronous global-to-shared copies of 8 and 16 bytes (both addresses
+// aligned to the size), committed as a group and waited for by the issuing
+// thread.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Barrier of the tail factor's level loop: the block's, or the cluster's with
 // release / acquire semantics (the values written into other CTAs' shared
 // memory before it are visible after it).
@@ -362,7 +375,6 @@ template <class T, int C>
 __global__ void __launch_bounds__(kFactorThreads)
     k_factor_tail(DevMat m, const T *partg, T *F, int *fstatus, const double *amaxv) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int R = 4;  // terms per thread prefetched into registers
     const int inst = int(blockIdx.x) / C;
     const int rank = C == 1 ? 0 : int(cluster_rank());
     const int bd = int(blockDim.x), tid = int(threadIdx.x);
@@ -405,18 +417,13 @@ __global__ void __launch_bounds__(kFactorThreads)
         const int4 L = lev[2 * li], LT = lev[2 * li + 1];
         const int4 N = li + 1 < ntl ? lev[2 * li + 2] : make_int4(0, 0, 0, 0);
         const int4 NT = li + 1 < ntl ? lev[2 * li + 3] : make_int4(0, 0, 0, 0);
-        int2 pre[R];
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            const int i = tid + r * bd;
-            if (i < N.w - N.z) pre[r] = m.tterm[N.z + i];
-        }
-        const bool hp = tid < N.y - N.x;
-        int4 pti = make_int4(0, 0, 0, 0);
-        if (hp) pti = m.tinfo[N.x + tid];
-        const bool hq = tid < NT.w - NT.z;
-        int4 ptk = make_int4(0, 0, 0, 0);
-        if (hq) ptk = m.ttask[NT.z + tid];
+        // the next level's terms, targets and tasks go into the other buffers
+        // by asynchronous copies while this level is computed (the barrier
+        // that ended the previous level ended every read of those buffers)
+        for (int i = tid; i < N.w - N.z; i += bd) cp_async8(nbuf + i, m.tterm + N.z + i);
+        for (int i = tid; i < N.y - N.x; i += bd) cp_async16(nti + i, m.tinfo + N.x + i);
+        for (int i = tid; i < NT.w - NT.z; i += bd) cp_async16(ntk + i, m.ttask + NT.z + i);
+        cp_async_commit();
         // the level's tasks, round-robin over the warps (warp-uniform: the
         // shuffles of a task stay convergent); a warp without a task idles,
         // leaving the FP64 issue slots to the busy ones
@@ -452,7 +459,7 @@ __global__ void __launch_bounds__(kFactorThreads)
                     for (int r = 1; r < C; r++)
                         st_cl(cl_mapa(smem_u32(Ut + info.z), unsigned((rank + r) % C)), val);
             } else {
-                const T dinv = T(1) / val;
+                const T dinv = pivot_recip(val);
                 Dt[info.w] = val;
                 Di[info.w] = dinv;
                 if constexpr (C > 1)
@@ -466,16 +473,7 @@ __global__ void __launch_bounds__(kFactorThreads)
                 else if (fabs(dd) <= tol && bad == PF_OK) bad = PF_ERR_SINGULAR;
             }
         }
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            const int i = tid + r * bd;
-            if (i < N.w - N.z) nbuf[i] = pre[r];
-        }
-        for (int i = tid + R * bd; i < N.w - N.z; i += bd) nbuf[i] = m.tterm[N.z + i];
-        if (hp) nti[tid] = pti;
-        for (int i = tid + bd; i < N.y - N.x; i += bd) nti[i] = m.tinfo[N.x + i];
-        if (hq) ntk[tid] = ptk;
-        for (int i = tid + bd; i < NT.w - NT.z; i += bd) ntk[i] = m.ttask[NT.z + i];
+        cp_async_wait_all();
         tail_barrier<C>();
     }
     if (bad != PF_OK) atomicCAS(fstatus + inst, PF_OK, bad);
@@ -1221,6 +1219,27 @@ extern "C" int gbpf_selftest_waits(unsigned limit, long long *out_host) {
     cudaFree(out);
     cudaFree(flags);
     return e == cudaSuccess ? 0 : 1;
+}
+
+namespace gbpf {
+namespace {
+__global__ void k_pivot_recip(const double *v, double *r, double *ref, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        r[i] = pivot_recip(v[i]);
+        ref[i] = 1.0 / v[i];
+    }
+}
+}  // namespace
+}  // namespace gbpf
+
+// Test hook (needs a GPU): the pivots' reciprocal (Newton from the FP32
+// reciprocal) and CUDA's FP64 division 1 / v of n device values.  Returns 0,
+// 1 for a bad argument or a failed launch.
+extern "C" int gbpf_selftest_pivot_recip(const double *v_dev, double *r_dev, double *ref_dev, int n) {
+    if (n < 1) return 1;
+    gbpf::k_pivot_recip<<<(n + 255) / 256, 256>>>(v_dev, r_dev, ref_dev, n);
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
 }
 
 extern "C" int gbpf_selftest_small_sincos(const double *x_dev, double *s_dev, double *c_dev,

@@ -364,6 +364,26 @@ def test_small_angle_rotation_series_vs_cuda_sincos():
     assert ulp_c.max().item() <= 2.0
 
 
+def test_pivot_reciprocal_vs_cuda_division():
+    """The factorisations' pivot reciprocal (Newton's iteration from the FP32
+    reciprocal) agrees with CUDA's FP64 division 1 / v to within 2 ulp over
+    pivots spanning the magnitudes of the admittance matrices and beyond,
+    both signs, and falls back to the division outside the FP32 range."""
+    import ctypes as C
+    L = gbpf.load()
+    rng = np.random.default_rng(3)
+    mags = 10.0 ** rng.uniform(-40, 40, 400000)
+    v_np = np.concatenate([mags, -mags, [1.0, -1.0, 3.0, 1e-30, 1e30, 2e-30, 5e29]])
+    v = torch.from_numpy(v_np).to(DEV)
+    r, ref = torch.empty_like(v), torch.empty_like(v)
+    p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    assert L.gbpf_selftest_pivot_recip(p(v), p(r), p(ref), C.c_int(v.numel())) == 0
+    rel = torch.abs(r - ref) / torch.abs(ref)
+    assert rel.max().item() <= 2.0 * 2.0 ** -52
+    out = (torch.abs(v) < 1e-30) | (torch.abs(v) > 1e30)
+    assert torch.equal(r[out], ref[out])
+
+
 @pytest.mark.parametrize("precision", [gbpf.PF_FP64, gbpf.PF_FP32])
 def test_lane_engine_batched_vs_oracle(oracle, precision):
     """Lockstep lane engine (groups of 32 cases, graph-replayed half-iterations):
