@@ -286,10 +286,11 @@ __device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
 // rows; dP/V (which = 0) or dQ/V (which = 1) goes straight into the owner's
 // vector slot of the matrix (rhsref: owner << 16 | word, -1 for a bus
 // outside the matrix).  Returns the cluster maximum of the half-iteration's
-// part (full: of both parts).
+// part (full: of both parts).  ef_ready: the slice's e + jf were already
+// written with the state (by the update that produced it).
 template <int C>
 __device__ double cl_mismatch(const ClRun &a, int rank, int which, const uint32_t *xbase, double *red,
-                              unsigned long long *mkey, const uint32_t *kbase, bool full) {
+                              unsigned long long *mkey, const uint32_t *kbase, bool full, bool ef_ready) {
     const DevNet &dn = a.dn;
     const int nbus = dn.nbus;
     const int slice = (nbus + C - 1) / C;
@@ -298,10 +299,11 @@ __device__ double cl_mismatch(const ClRun &a, int rank, int which, const uint32_
     double *f = e + nbus;
     const double *cs = e + 2 * nbus;
     const double *sn = e + 3 * nbus;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        e[i] = a.vm[i] * cs[i];
-        f[i] = a.vm[i] * sn[i];
-    }
+    if (!ef_ready)
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            e[i] = a.vm[i] * cs[i];
+            f[i] = a.vm[i] * sn[i];
+        }
     cl_barrier_global();
     const int *rhsref = a.m[which].rhsref;
     const bool wantP = full || which == 0, wantQ = full || which == 1;
@@ -390,6 +392,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(const __grid_constant
     const int slice = (nbus + C - 1) / C;
     const int i0 = rank * slice, i1 = min(nbus, i0 + slice);
     double *vm = a.vm, *va = a.va, *iv = a.iv;
+    double *ef = a.ef;  // e, f, then cos and sin of the angles
     double *cs = a.ef + 2 * nbus, *sn = cs + nbus;
     int status = PF_ERR_NOT_CONVERGED;
     if (a.fs0[0] != PF_OK) status = a.fs0[0];
@@ -404,13 +407,21 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(const __grid_constant
         }
         sincos(va[i], &sn[i], &cs[i]);
         iv[i] = 1.0 / vm[i];
+        ef[i] = vm[i] * cs[i];
+        ef[nbus + i] = vm[i] * sn[i];
     }
+    // e + jf of every bus is written where the state changes (here, and in
+    // the updates below), so the mismatch needs no pass of its own
     bool rotated = false;
     auto exact_check = [&](int which) {
         if (rotated)
-            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) sincos(va[i], &sn[i], &cs[i]);
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                sincos(va[i], &sn[i], &cs[i]);
+                ef[i] = vm[i] * cs[i];
+                ef[nbus + i] = vm[i] * sn[i];
+            }
         rotated = false;
-        return cl_mismatch<C>(a, rank, which, xbase, red, mkey, kbase, true);
+        return cl_mismatch<C>(a, rank, which, xbase, red, mkey, kbase, true, true);
     };
     // a step is followed by a cluster barrier (it read or feeds other CTAs'
     // words) or by the CTA's own barrier (a level of its own subtrees); every
@@ -431,7 +442,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(const __grid_constant
     };
     if (status == PF_ERR_NOT_CONVERGED) {
         for (int it = 0; it < a.max_iter; it++) {
-            mis = cl_mismatch<C>(a, rank, 0, xbase, red, mkey, kbase, false);
+            mis = cl_mismatch<C>(a, rank, 0, xbase, red, mkey, kbase, false, true);
             if (mis <= a.tol) mis = exact_check(0);
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
@@ -449,10 +460,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(const __grid_constant
                 } else {
                     sincos(va[i], &sn[i], &cs[i]);
                 }
+                ef[i] = vm[i] * cs[i];
+                ef[nbus + i] = vm[i] * sn[i];
             }
             rotated = true;
             iters++;
-            mis = cl_mismatch<C>(a, rank, 1, xbase, red, mkey, kbase, false);
+            mis = cl_mismatch<C>(a, rank, 1, xbase, red, mkey, kbase, false, true);
             if (mis <= a.tol) mis = exact_check(1);
             if (!isfinite(mis)) { status = PF_ERR_NONFINITE; break; }
             if (mis <= a.tol) { status = PF_OK; break; }
@@ -461,6 +474,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_fdpf_cl(const __grid_constant
                 if (a.m[1].xref[i] < 0) continue;
                 vm[i] += xval(1, i);
                 iv[i] = 1.0 / vm[i];
+                ef[i] = vm[i] * cs[i];
+                ef[nbus + i] = vm[i] * sn[i];
             }
             iters++;
         }
