@@ -1468,6 +1468,9 @@ pf_status ensure_device(pf_ctx *ctx) {
         if ((st = upload(ctx, &dn.inc_side, inc_side.data(), inc_side.size()))) break;
         if ((st = upload(ctx, &dn.inc_pos, inc_pos.data(), inc_pos.size()))) break;
         if ((st = upload(ctx, &dn.br_pos, br_pos.data(), br_pos.size()))) break;
+        dn.noff = int(ctx->yoff.size());
+        if ((st = upload(ctx, &dn.yoff, ctx->yoff.data(), ctx->yoff.size()))) break;
+        if ((st = upload(ctx, &dn.yoff_br, ctx->yoff_br.data(), ctx->yoff_br.size()))) break;
         if ((st = dalloc(ctx, &dn.G, dn.nnz))) break;
         if ((st = dalloc(ctx, &dn.B, dn.nnz))) break;
         if ((st = dalloc(ctx, &dn.Bp, dn.nnz))) break;
@@ -2017,6 +2020,21 @@ pf_status pf_create(const pf_bus *bus, int32_t nbus, const pf_branch *branch, in
             ctx->inc_br[q] = e; ctx->inc_side[q] = 1; ctx->inc_pos[q] = ypos(ctx, b, a);
         }
     }
+    {   // per off-diagonal entry, in row order, the branches reaching it in
+        // the order of its row's incidence list (ascending branch index)
+        std::vector<std::vector<int>> at(ctx->col.size());
+        for (int i = 0; i < nbus; i++)
+            for (int q = ctx->inc_ptr[i]; q < ctx->inc_ptr[i + 1]; q++) at[ctx->inc_pos[q]].push_back(ctx->inc_br[q]);
+        ctx->yoff.clear();
+        ctx->yoff_br.clear();
+        for (int i = 0; i < nbus; i++)
+            for (int p = ctx->rowptr[i]; p < ctx->rowptr[i + 1]; p++) {
+                if (p == ctx->ydiag[i]) continue;
+                const int lo = int(ctx->yoff_br.size());
+                ctx->yoff_br.insert(ctx->yoff_br.end(), at[p].begin(), at[p].end());
+                ctx->yoff.push_back(int4{p, lo, int(ctx->yoff_br.size()), 0});
+            }
+    }
     for (int e = 0; e < nbranch; e++) {
         const int a = branch[e].from, b = branch[e].to;
         ctx->br_pos[4 * e + 0] = ctx->ydiag[a];
@@ -2427,8 +2445,8 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
     TRY(ensure_cases(ctx));
     cudaStream_t s = (cudaStream_t)stream;
     const int prec = opts->precision;
-    TRY(assemble_ybus(ctx, s));
     if (opts->method == PF_NR) {
+        TRY(assemble_ybus(ctx, s));
         TRY(ensure_nr_storage(ctx, prec));
         NrLaunch L = nr_launch(ctx, prec);
         L.o = *opts;
@@ -2457,6 +2475,7 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
     const int engine = use_cluster ? PF_ENGINE_CLUSTER
                                    : (want == PF_ENGINE_LANES && lanes_ok ? PF_ENGINE_LANES : PF_ENGINE_BLOCK);
     if (engine == PF_ENGINE_LANES) {
+        TRY(assemble_ybus(ctx, s));
         TRY(factor_both(ctx, prec, s, false));
         const void *F0 = prec == PF_FP64 ? (const void *)w.F64[0] : (const void *)w.F32[0];
         const void *F1 = prec == PF_FP64 ? (const void *)w.F64[1] : (const void *)w.F32[1];
@@ -2491,8 +2510,8 @@ pf_status run_once(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, double 
                             c, res_host[c].status, res_host[c].iters);
         return PF_OK;
     }
-    // block and cluster engines: the device work of the run, enqueued
-    // directly or from a CUDA graph of it
+    // block and cluster engines: the device work of the run (the admittance
+    // matrix first), enqueued directly or from a CUDA graph of it
     TRY(run_device_work(ctx, opts, vm_dev, va_dev, engine, s));
     cudaError_t e = cudaMemcpyAsync(res_host, w.res, sizeof(pf_case_result) * ctx->dc.ncase,
                                     cudaMemcpyDeviceToHost, s);

@@ -295,6 +295,11 @@ struct DevNet {
     // bus incidence: for bus i, entries inc_ptr[i]..: branch, side (0 from, 1 to), off-diag position
     int *inc_ptr = nullptr, *inc_br = nullptr, *inc_side = nullptr, *inc_pos = nullptr;
     int *br_pos = nullptr;   // [nbr*4] Ybus positions (ff, tt, ft, tf)
+    // off-diagonal Ybus entries: {position, first, end, 0} into yoff_br, the
+    // branches whose pi model reaches the entry (ascending branch index)
+    int noff = 0;
+    int4 *yoff = nullptr;
+    int *yoff_br = nullptr;
 };
 
 struct DevCases {
@@ -404,7 +409,8 @@ struct pf_ctx {
     gbpf::DevCases dc;
     gbpf::Workspace ws;
     bool on_device = false;   // network and symbolic data uploaded
-    std::vector<int> ydiag, inc_ptr, inc_br, inc_side, inc_pos, br_pos;
+    std::vector<int> ydiag, inc_ptr, inc_br, inc_side, inc_pos, br_pos, yoff_br;
+    std::vector<int4> yoff;
     int device = 0;
     int num_sms = 0;
     size_t smem_optin = 0;

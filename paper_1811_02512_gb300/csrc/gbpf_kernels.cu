@@ -28,42 +28,84 @@ namespace {
 
 // ------------------------------------------------------------ Section III.A
 
-// FormMatrixA: row i of Y = G + jB is owned by one thread, which sums the
-// pi models of the in-service branches incident to bus i (ascending branch
-// index) and the bus shunt.  Also writes the XB B' (1/x weights) on the same
-// pattern.
-__global__ void k_ybus(DevNet dn) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= dn.nbus) return;
-    for (int p = dn.rowptr[i]; p < dn.rowptr[i + 1]; p++) {
-        dn.G[p] = 0.0;
-        dn.B[p] = 0.0;
-        dn.Bp[p] = 0.0;
+// FormMatrixA (Section III.A), one thread per entry of Y = G + jB: threads
+// [0, nbus) the diagonal of bus i -- the pi-model self terms of its
+// in-service incident branches (incidence order: ascending branch index)
+// plus the bus shunt -- and threads [nbus, nbus + noff) one off-diagonal
+// entry each, the negated series admittances of the in-service branches
+// between its two buses (ascending branch index).  Every entry is formed in
+// registers and written once; a diagonal thread reads the indices of four
+// incident branches at a time before their parameters, so a bus of degree
+// up to four costs three dependent round trips to memory.  Also writes the
+// XB B' (1/x weights) on the same pattern.
+__device__ __forceinline__ void ybus_entry(const DevNet &dn, int t) {
+    if (t < dn.nbus) {
+        const int i = t, q1 = dn.inc_ptr[i + 1];
+        double gd = 0.0, bd = 0.0, bpd = 0.0;
+        for (int q = dn.inc_ptr[i]; q < q1; q += 4) {
+            int e[4], sd[4], on[4];
+            double r[4], x[4], b[4], tp[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                e[u] = q + u < q1 ? dn.inc_br[q + u] : -1;
+                sd[u] = q + u < q1 ? dn.inc_side[q + u] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                on[u] = 0;
+                if (e[u] >= 0) {
+                    on[u] = dn.bstatus[e[u]];
+                    r[u] = dn.br[e[u]];
+                    x[u] = dn.bx[e[u]];
+                    b[u] = dn.bb[e[u]];
+                    tp[u] = dn.btap[e[u]];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (!on[u]) continue;
+                const double den = r[u] * r[u] + x[u] * x[u];
+                const double ys_re = r[u] / den, ys_im = -x[u] / den;
+                if (sd[u] == 0) {
+                    gd += ys_re / (tp[u] * tp[u]);
+                    bd += (ys_im + 0.5 * b[u]) / (tp[u] * tp[u]);
+                } else {
+                    gd += ys_re;
+                    bd += ys_im + 0.5 * b[u];
+                }
+                bpd += 1.0 / x[u];
+            }
+        }
+        const int d = dn.ydiag[i];
+        dn.G[d] = gd + dn.gs[i];
+        dn.B[d] = bd + dn.bs[i];
+        dn.Bp[d] = bpd;
+        return;
     }
-    double gd = 0.0, bd = 0.0, bpd = 0.0;
-    for (int q = dn.inc_ptr[i]; q < dn.inc_ptr[i + 1]; q++) {
-        const int e = dn.inc_br[q];
+    const int k = t - dn.nbus;
+    if (k >= dn.noff) return;
+    const int4 o = dn.yoff[k];
+    double g = 0.0, bo = 0.0, bp = 0.0;
+    for (int q = o.y; q < o.z; q++) {
+        const int e = dn.yoff_br[q];
         if (!dn.bstatus[e]) continue;
-        const double r = dn.br[e], x = dn.bx[e], b = dn.bb[e], t = dn.btap[e];
+        const double r = dn.br[e], x = dn.bx[e], tp = dn.btap[e];
         const double den = r * r + x * x;
         const double ys_re = r / den, ys_im = -x / den;
-        const int po = dn.inc_pos[q];
-        dn.G[po] -= ys_re / t;
-        dn.B[po] -= ys_im / t;
-        dn.Bp[po] -= 1.0 / x;
-        if (dn.inc_side[q] == 0) {
-            gd += ys_re / (t * t);
-            bd += (ys_im + 0.5 * b) / (t * t);
-        } else {
-            gd += ys_re;
-            bd += ys_im + 0.5 * b;
-        }
-        bpd += 1.0 / x;
+        g -= ys_re / tp;
+        bo -= ys_im / tp;
+        bp -= 1.0 / x;
     }
-    const int d = dn.ydiag[i];
-    dn.G[d] = gd + dn.gs[i];
-    dn.B[d] = bd + dn.bs[i];
-    dn.Bp[d] = bpd;
+    dn.G[o.x] = g;
+    dn.B[o.x] = bo;
+    dn.Bp[o.x] = bp;
+}
+
+__global__ void k_ybus(DevNet dn) {
+    const long long total = (long long)dn.nbus + dn.noff;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x)
+        ybus_entry(dn, int(t));
 }
 
 // Specified injections of every case: P = pg - pd s, Q = -qd s with the load
@@ -145,9 +187,18 @@ __global__ void k_factor_prep(DevMat m, const double *A, int *fstatus, FactorSyn
     __shared__ double red[33];
     const int inst = blockIdx.x;
     const double *a = A + (long long)inst * m.stride;
-    double mx = 0.0;
-    for (int j = threadIdx.x; j < m.n; j += blockDim.x) mx = fmax(mx, fabs(a[j]));
-    mx = block_max(mx, red);
+    // four independent loads per thread in flight (the launch waits on this)
+    const int st = int(blockDim.x);
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+    int j = threadIdx.x;
+    for (; j + 3 * st < m.n; j += 4 * st) {
+        m0 = fmax(m0, fabs(a[j]));
+        m1 = fmax(m1, fabs(a[j + st]));
+        m2 = fmax(m2, fabs(a[j + 2 * st]));
+        m3 = fmax(m3, fabs(a[j + 3 * st]));
+    }
+    for (; j < m.n; j += st) m0 = fmax(m0, fabs(a[j]));
+    double mx = block_max(fmax(fmax(m0, m1), fmax(m2, m3)), red);
     if (threadIdx.x == 0) {
         fs.amax[inst] = mx;
         fstatus[inst] = PF_OK;
@@ -162,6 +213,7 @@ constexpr int kDepThreads = 256;
 constexpr int kDepTargets = 8;   // targets per lane: columns of up to 255 entries
 static_assert(32 * kDepTargets == kDepMaxCol + 1, "targets per lane cover the longest column");
 constexpr int kDepChunk = 512;   // update terms staged per warp and pass
+constexpr int kDepPre = 2;       // targets per lane whose assembled values are read before the waits
 
 // Numeric factor A = L D L^T (Section III.B, left-looking), driven by the
 // elimination tree's dependencies instead of level barriers, for every
@@ -189,29 +241,41 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
                                               T *terms, unsigned spin, const unsigned *abort) {
     const int lane = threadIdx.x & 31;
     T *Lc = v + m.offLc;
-    bool ok = true;
-    for (int q = m.Fp[c] + lane; q < m.Fp[c + 1] && ok; q += 32)
-        ok = wait_flag(done + m.Fc[q], epoch, spin, abort);
-    if (!__all_sync(0xffffffffu, ok)) return false;
+    // Everything that does not depend on other columns' values is read
+    // before the waits, so that after the last dependency is published only
+    // the factor values themselves are still to be fetched: the targets'
+    // term ranges, the first 128 gather entries and the assembled values of
+    // the first 64 targets (columns rarely have more).
     const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0, tb = c0 + c;
+    const int gb = m.gp[tb], ge = m.gp[tb + cnt + 1];
     int g_lo[kDepTargets], g_hi[kDepTargets];
     T part[kDepTargets];
+    double aval[kDepPre];
 #pragma unroll
     for (int j = 0; j < kDepTargets; j++) {
         const int t = lane + 32 * j;
         g_lo[j] = t <= cnt ? m.gp[tb + t] : 0;
         g_hi[j] = t <= cnt ? m.gp[tb + t + 1] : 0;
+        if (j < kDepPre) aval[j] = t <= cnt ? __ldg(t == 0 ? a + c : a + m.offLc + c0 + t - 1) : 0.0;
         part[j] = T(0);
     }
-    const int gb = m.gp[tb], ge = m.gp[tb + cnt + 1];
+    int4 e0[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+        if (gb + lane + 32 * u < ge) e0[u] = __ldg(m.gl + gb + lane + 32 * u);
+    bool ok = true;
+    for (int q = m.Fp[c] + lane; q < m.Fp[c + 1] && ok; q += 32)
+        ok = wait_flag(done + m.Fc[q], epoch, spin, abort);
+    if (!__all_sync(0xffffffffu, ok)) return false;
     for (int cb = gb; cb < ge; cb += kDepChunk) {
         const int ce = min(ge, cb + kDepChunk);
         // terms of this pass, four per lane in flight
         for (int g0 = cb + lane; g0 < ce; g0 += 128) {
+            const bool first = g0 == gb + lane;  // entries read before the waits
             int4 e[4];
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                if (g0 + 32 * u < ce) e[u] = __ldg(m.gl + g0 + 32 * u);
+                if (g0 + 32 * u < ce) e[u] = first ? e0[u] : __ldg(m.gl + g0 + 32 * u);
             T x[4], y[4], z[4];
 #pragma unroll
             for (int u = 0; u < 4; u++)
@@ -245,7 +309,8 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
 #pragma unroll
     for (int j = 0; j < kDepTargets; j++) {
         const int t = lane + 32 * j;
-        val[j] = t <= cnt ? T(t == 0 ? a[c] : a[m.offLc + c0 + t - 1]) - part[j] : T(0);
+        const double aj = j < kDepPre ? aval[j] : (t <= cnt ? a[m.offLc + c0 + t - 1] : 0.0);
+        val[j] = t <= cnt ? T(aj) - part[j] : T(0);
     }
     const T d = __shfl_sync(0xffffffffu, val[0], 0);
     const T dinv = pivot_recip(d);
@@ -873,7 +938,7 @@ int grid_for(long long total, int threads) {
 // ------------------------------------------------------------ launchers
 
 cudaError_t launch_ybus(const DevNet &dn, cudaStream_t s) {
-    k_ybus<<<grid_for(dn.nbus, 128), 128, 0, s>>>(dn);
+    k_ybus<<<grid_for((long long)dn.nbus + dn.noff, 128), 128, 0, s>>>(dn);
     return cudaGetLastError();
 }
 
@@ -1052,7 +1117,7 @@ cudaError_t launch_factor(const DevMat &m, int prec, const double *A, void *F, i
     const long long total = (long long)m.n * ninst;
     const bool dep = fs.mode == 1 || (fs.mode == 0 && ninst < fs.nsm / 2);
     if (dep && m.max_col <= kDepMaxCol && total < (1ll << 31) && fs.done) {
-        k_factor_prep<<<ninst, 256, 0, s>>>(m, A, fstatus, fs);
+        k_factor_prep<<<ninst, 512, 0, s>>>(m, A, fstatus, fs);
         const size_t tsmem = factor_tail_smem(m, prec);
         const bool tail = fs.tail && m.ft_ng > 0 && m.ft_tmax >= 0 && fs.partg &&
                           tsmem + 1024 <= fs.smem_optin;
