@@ -300,7 +300,9 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
                 s2 += terms[g + 2 - cb];
                 s3 += terms[g + 3 - cb];
             }
-            for (; g < hi; g++) s0 += terms[g - cb];
+            if (g < hi) s0 += terms[g - cb];
+            if (g + 1 < hi) s1 += terms[g + 1 - cb];
+            if (g + 2 < hi) s2 += terms[g + 2 - cb];
             part[j] += (s0 + s1) + (s2 + s3);
         }
         __syncwarp();
@@ -513,7 +515,11 @@ __global__ void __launch_bounds__(kFactorThreads)
                 s2 += term(buf[q + 2 * G]);
                 s3 += term(buf[q + 3 * G]);
             }
-            for (; q < qe; q += G) s0 += term(buf[q]);
+            // the last one to three terms of a lane on separate chains too (a
+            // lane rarely has more than four: the level's critical path)
+            if (q < qe) s0 += term(buf[q]);
+            if (q + G < qe) s1 += term(buf[q + G]);
+            if (q + 2 * G < qe) s2 += term(buf[q + 2 * G]);
             T sum = (s0 + s1) + (s2 + s3);
             for (int o = G >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             if (!act || gl != 0) continue;
