@@ -345,13 +345,18 @@ __global__ void __launch_bounds__(kDepThreads)
     const int lane = threadIdx.x & 31;
     T *terms = terms_all[threadIdx.x >> 5];
     {  // the gather lists and patterns are read once each, in column order:
-       // start them (and the assembled values) towards the L2 all at once
+       // start them (and the assembled values and the column flags) towards
+       // the L2 all at once, so that no step of the elimination tree's chain
+       // waits for DRAM
         const int part = int(blockIdx.x * blockDim.x + threadIdx.x), parts = int(gridDim.x * blockDim.x);
         l2_prefetch(m.gl, sizeof(int4) * size_t(m.nupd), part, parts);
         l2_prefetch(m.gp, sizeof(int) * size_t(m.n + m.nnz + 1), part, parts);
+        l2_prefetch(m.Cp, sizeof(int) * size_t(m.n + 1), part, parts);
+        l2_prefetch(m.Fp, sizeof(int) * size_t(m.n + 1), part, parts);
         l2_prefetch(m.Fc, sizeof(int) * size_t(m.nnz), part, parts);
         l2_prefetch(m.Cpos, sizeof(int) * size_t(m.nnz), part, parts);
         l2_prefetch(A, sizeof(double) * size_t(ninst) * size_t(m.stride), part, parts);
+        l2_prefetch(fs.done, sizeof(unsigned) * size_t(ninst) * size_t(m.n), part, parts);
     }
     const unsigned total = unsigned(ncols) * unsigned(ninst);
     const unsigned spin = fs.spin ? fs.spin : kDefaultSpin;

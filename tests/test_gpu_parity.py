@@ -350,10 +350,17 @@ def test_fp32_batched_cases_refined(oracle):
 
 def test_small_angle_rotation_series_vs_cuda_sincos():
     """The Maclaurin sin/cos used to rotate cached cos/sin by a step agree with
-    the CUDA math library's sincos to within 2 ulp on |x| <= 0.2."""
+    the CUDA math library's sincos to within 2 ulp on |x| <= 0.2, both in
+    full and in the short form that warps of small steps take (|x| <= 1e-3,
+    down to 1e-12, both signs), and across the boundary of the two."""
     import ctypes as C
     L = gbpf.load()
-    x = torch.linspace(-0.2, 0.2, 200001, dtype=torch.float64, device=DEV)
+    rng = np.random.default_rng(11)
+    tiny = 10.0 ** rng.uniform(-12, -3, 65536) * rng.choice([-1.0, 1.0], 65536)
+    x = torch.cat([torch.linspace(-0.2, 0.2, 200001, dtype=torch.float64),
+                   torch.linspace(-1e-3, 1e-3, 65537, dtype=torch.float64),
+                   torch.linspace(0.9e-3, 1.1e-3, 4097, dtype=torch.float64),
+                   torch.from_numpy(tiny)]).to(DEV)
     s, c, sr, cr = (torch.empty_like(x) for _ in range(4))
     p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
     assert L.gbpf_selftest_small_sincos(p(x), p(s), p(c), p(sr), p(cr), C.c_int(x.numel())) == 0
