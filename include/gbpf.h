@@ -229,7 +229,11 @@ pf_status pf_etree_levels_device(int32_t n, const int64_t *Lp_dev, const int32_t
  * [ncase][nbus] (host, NULL = all 1) multiplies pd and qd of every PQ bus of
  * a case; outage[ncase] (host, NULL = none) names a branch taken out of
  * service in that case (-1 = none).  Outages keep the symbolic pattern.
- * Replaces any previous batch.  Synchronous. */
+ * Replaces any previous batch.  A call with the same cases as the current
+ * batch (count and outages) keeps its device arrays, factors and CUDA graph
+ * and only forms the specified injections again.  PF_ERR_ARG for an outage
+ * out of range or a non-finite load scale (then the batch's injections are
+ * unchanged).  Synchronous. */
 pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
                        const int32_t *outage);
 

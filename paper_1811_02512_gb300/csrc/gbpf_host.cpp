@@ -1580,6 +1580,7 @@ void free_case_storage(pf_ctx *ctx) {
     dfree(ctx, ctx->dc.Psp); ctx->dc.Psp = nullptr;
     dfree(ctx, ctx->dc.Qsp); ctx->dc.Qsp = nullptr;
     dfree(ctx, w.lsbuf); w.lsbuf = nullptr;
+    dfree(ctx, w.lsflag); w.lsflag = nullptr;
     w.case_out.clear();
     ctx->dc.ncase = 0;
     ctx->dc.ninst = 1;
@@ -2103,27 +2104,39 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
             inst_out.push_back(out[c]);
         }
     }
-    if (load_scale)
-        for (size_t q = 0; q < size_t(ncase) * ctx->nbus; q++)
-            if (!std::isfinite(load_scale[q])) return fail(ctx, PF_ERR_ARG, "non-finite load scale");
-    TRY(ensure_device(ctx));
+    const size_t nls = size_t(ncase) * size_t(ctx->nbus);
     Workspace &w0 = ctx->ws;
-    if (ctx->dc.ncase == ncase && w0.ncase_alloc == ncase && w0.lsbuf && w0.case_out == out) {
+    if (ctx->on_device && ctx->dc.ncase == ncase && w0.ncase_alloc == ncase && w0.lsbuf && w0.lsflag &&
+        w0.case_out == out) {
         // the same cases with new loads: the batch's arrays, factors and CUDA
-        // graph stay; only the specified injections are formed again
+        // graph stay; only the specified injections are formed again.  Many
+        // scales (a batch's) are checked on the device instead of by a host
+        // loop: non-finite ones leave the injections unchanged.
+        const bool dev_check = load_scale && nls > (size_t(1) << 20);
+        if (load_scale && !dev_check)
+            for (size_t q = 0; q < nls; q++)
+                if (!std::isfinite(load_scale[q])) return fail(ctx, PF_ERR_ARG, "non-finite load scale");
         cudaError_t e = cudaSuccess;
-        if (load_scale) {
-            e = cudaMemcpy(w0.lsbuf, load_scale, sizeof(double) * size_t(ncase) * ctx->nbus,
-                           cudaMemcpyHostToDevice);
-        }
+        int bad = 0;
+        if (dev_check) e = cudaMemsetAsync(w0.lsflag, 0, sizeof(int), 0);
+        if (e == cudaSuccess && load_scale)
+            e = cudaMemcpyAsync(w0.lsbuf, load_scale, sizeof(double) * nls, cudaMemcpyHostToDevice, 0);
+        if (e == cudaSuccess && dev_check) e = launch_finite_check(w0.lsbuf, (long long)nls, w0.lsflag, 0);
         if (e == cudaSuccess)
             e = counted(ctx, PF_K_SPEC, 1, 0, [&] {
-                return launch_case_spec(ctx->dn, ctx->dc, load_scale ? w0.lsbuf : nullptr, 0);
+                return launch_case_spec(ctx->dn, ctx->dc, load_scale ? w0.lsbuf : nullptr, 0,
+                                        dev_check ? w0.lsflag : nullptr);
             });
+        if (e == cudaSuccess && dev_check) e = cudaMemcpyAsync(&bad, w0.lsflag, sizeof(int), cudaMemcpyDeviceToHost, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_fail(ctx, e, "case spec");
+        if (bad) return fail(ctx, PF_ERR_ARG, "non-finite load scale");
         return PF_OK;
     }
+    if (load_scale)
+        for (size_t q = 0; q < nls; q++)
+            if (!std::isfinite(load_scale[q])) return fail(ctx, PF_ERR_ARG, "non-finite load scale");
+    TRY(ensure_device(ctx));
     drop_graph(ctx);  // its launches point into the batch's arrays
     ctx->set_gen++;
     free_case_storage(ctx);
@@ -2137,6 +2150,7 @@ pf_status pf_set_cases(pf_ctx *ctx, int32_t ncase, const double *load_scale,
     TRY(dalloc(ctx, &dc.Qsp, size_t(ncase) * ctx->nbus));
     Workspace &w = ctx->ws;
     TRY(dalloc(ctx, &w.lsbuf, size_t(ncase) * ctx->nbus));
+    TRY(dalloc(ctx, &w.lsflag, 1));
     cudaError_t e = cudaSuccess;
     if (load_scale)
         e = cudaMemcpy(w.lsbuf, load_scale, sizeof(double) * size_t(ncase) * ctx->nbus, cudaMemcpyHostToDevice);

@@ -369,6 +369,7 @@ struct Workspace {
     pf_case_result *res = nullptr; // [ncase]
     int ncase_alloc = 0;
     double *lsbuf = nullptr;  // [ncase][nbus] load scales of the batch (kept for a cheap re-set)
+    int *lsflag = nullptr;    // set when new load scales of the same cases are not all finite
     std::vector<int> case_out;  // host copy of the batch's outages (-1: none)
     // Newton-Raphson workspace (allocated on first use): block factors per
     // precision, the FP64 Jacobian and per-case factor status, [ncase][jstride]
@@ -445,7 +446,8 @@ namespace gbpf {
 // the launch (asynchronous errors surface at the next synchronising call).
 cudaError_t launch_ybus(const DevNet &dn, cudaStream_t s);
 cudaError_t launch_case_spec(const DevNet &dn, const DevCases &dc, const double *load_scale_dev,
-                             cudaStream_t s);
+                             cudaStream_t s, const int *skip = nullptr);
+cudaError_t launch_finite_check(const double *x, long long n, int *bad, cudaStream_t s);
 cudaError_t launch_assemble_slots(const DevNet &dn, const DevCases &dc, const DevMat &m, int which,
                                   double *A, cudaStream_t s, int ninst = -1);
 cudaError_t launch_branch_flows(const DevNet &dn, const DevCases &dc, const double *vm, const double *va,

@@ -109,8 +109,10 @@ __global__ void k_ybus(DevNet dn) {
 }
 
 // Specified injections of every case: P = pg - pd s, Q = -qd s with the load
-// scale s of PQ buses.
-__global__ void k_case_spec(DevNet dn, DevCases dc, const double *ls) {
+// scale s of PQ buses.  Nothing is written when *skip is set (the scales
+// failed their check).
+__global__ void k_case_spec(DevNet dn, DevCases dc, const double *ls, const int *skip) {
+    if (skip && *skip) return;
     const long long total = (long long)dc.ncase * dn.nbus;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -954,8 +956,22 @@ cudaError_t launch_ybus(const DevNet &dn, cudaStream_t s) {
 }
 
 cudaError_t launch_case_spec(const DevNet &dn, const DevCases &dc, const double *ls,
-                             cudaStream_t s) {
-    k_case_spec<<<grid_for((long long)dc.ncase * dn.nbus, 256), 256, 0, s>>>(dn, dc, ls);
+                             cudaStream_t s, const int *skip) {
+    k_case_spec<<<grid_for((long long)dc.ncase * dn.nbus, 256), 256, 0, s>>>(dn, dc, ls, skip);
+    return cudaGetLastError();
+}
+
+// *bad = 1 when any of x[0, n) is not finite (*bad is cleared by the caller).
+__global__ void k_finite_check(const double *x, long long n, int *bad) {
+    bool ok = true;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        ok &= bool(isfinite(x[i]));
+    if (!__all_sync(0xffffffffu, ok) && (threadIdx.x & 31) == 0) *bad = 1;
+}
+
+cudaError_t launch_finite_check(const double *x, long long n, int *bad, cudaStream_t s) {
+    k_finite_check<<<grid_for(n, 256), 256, 0, s>>>(x, n, bad);
     return cudaGetLastError();
 }
 

@@ -119,4 +119,48 @@ def test_new_loads_on_the_same_cases_reuse_the_batch(oracle):
     st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
     assert st == gbpf.PF_OK
     assert torch.equal(vm, first[0]) and torch.equal(va, first[1])
+    # non-finite new scales of the same cases are refused on the device and
+    # leave the injections as they were
+    bad = sc.load_scale.copy()
+    bad[sc.ncase - 1, base.n // 2] = np.inf
+    with pytest.raises(gbpf.PFError) as e:
+        g.set_cases(sc.ncase, bad, sc.outage)
+    assert e.value.status == gbpf.PF_ERR_ARG
+    st, res = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, sc.ncase)
+    assert st == gbpf.PF_OK
+    assert torch.equal(vm, first[0]) and torch.equal(va, first[1])
+    g.close()
+
+
+def test_new_scales_of_a_large_batch_are_checked_on_the_device():
+    """New load scales for the same cases of a batch with more than 2^20 of
+    them (128 cases of the 10k grid) are checked by a device kernel: a NaN is
+    refused with PF_ERR_ARG and leaves the injections (and so the solution)
+    as they were; finite scales are taken."""
+    base = gridgen.config(1)
+    ncase = 128
+    rng = np.random.default_rng(8)
+    loads = 1.0 + 0.05 * rng.standard_normal((ncase, base.n))
+    g = gbpf.Grid(base)
+    g.set_cases(ncase, loads)
+    vm = torch.zeros((ncase, base.n), dtype=torch.float64, device=DEV)
+    va = torch.zeros_like(vm)
+    opts = gbpf.run_opts(gbpf.PF_FDPF, gbpf.PF_FP64, tol=1e-9, max_iter=300)
+    for _ in range(2):
+        st, _ = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+        assert st == gbpf.PF_OK, gbpf.pf_last_error(g.ctx)
+    first = (vm.clone(), va.clone())
+    g.set_cases(ncase, loads * 1.01)
+    st, _ = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+    assert st == gbpf.PF_OK
+    assert not torch.equal(va, first[1])
+    bad = loads.copy()
+    bad[ncase // 2, 7] = np.nan
+    with pytest.raises(gbpf.PFError) as e:
+        g.set_cases(ncase, bad)
+    assert e.value.status == gbpf.PF_ERR_ARG
+    g.set_cases(ncase, loads)
+    st, _ = gbpf.pf_run_to_tol(g.ctx, opts, vm, va, ncase)
+    assert st == gbpf.PF_OK
+    assert torch.equal(vm, first[0]) and torch.equal(va, first[1])
     g.close()
