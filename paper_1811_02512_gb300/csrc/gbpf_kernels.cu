@@ -247,18 +247,24 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
     // before the waits, so that after the last dependency is published only
     // the factor values themselves are still to be fetched: the targets'
     // term ranges, the first 128 gather entries and the assembled values of
-    // the first 64 targets (columns rarely have more).
+    // the first 64 targets (columns rarely have more), with their positions
+    // in the row-ordered copy.
     const int c0 = m.Cp[c], cnt = m.Cp[c + 1] - c0, tb = c0 + c;
+    const int nj = cnt / 32 + 1;  // target slots per lane in use (targets 0..cnt)
     const int gb = m.gp[tb], ge = m.gp[tb + cnt + 1];
     int g_lo[kDepTargets], g_hi[kDepTargets];
     T part[kDepTargets];
     double aval[kDepPre];
+    int cpos[kDepPre];
 #pragma unroll
     for (int j = 0; j < kDepTargets; j++) {
         const int t = lane + 32 * j;
         g_lo[j] = t <= cnt ? m.gp[tb + t] : 0;
         g_hi[j] = t <= cnt ? m.gp[tb + t + 1] : 0;
-        if (j < kDepPre) aval[j] = t <= cnt ? __ldg(t == 0 ? a + c : a + m.offLc + c0 + t - 1) : 0.0;
+        if (j < kDepPre) {
+            aval[j] = t <= cnt ? __ldg(t == 0 ? a + c : a + m.offLc + c0 + t - 1) : 0.0;
+            cpos[j] = t >= 1 && t <= cnt ? __ldg(m.Cpos + c0 + t - 1) : 0;
+        }
         part[j] = T(0);
     }
     int4 e0[4];
@@ -293,6 +299,7 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < kDepTargets; j++) {
+            if (j >= nj) break;  // warp-uniform: no FP64 work for absent targets
             const int lo = max(g_lo[j], cb), hi = min(g_hi[j], ce);
             T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
             int g = lo;
@@ -312,6 +319,7 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
     T val[kDepTargets];
 #pragma unroll
     for (int j = 0; j < kDepTargets; j++) {
+        if (j >= nj) break;
         const int t = lane + 32 * j;
         const double aj = j < kDepPre ? aval[j] : (t <= cnt ? a[m.offLc + c0 + t - 1] : 0.0);
         val[j] = t <= cnt ? T(aj) - part[j] : T(0);
@@ -327,14 +335,16 @@ __device__ __forceinline__ bool factor_column(const DevMat &m, const double *a, 
     }
 #pragma unroll
     for (int j = 0; j < kDepTargets; j++) {
+        if (j >= nj) break;
         const int t = lane + 32 * j;
         if (t >= 1 && t <= cnt) {
             const T l = val[j] * dinv;
             Lc[c0 + t - 1] = l;
-            v[m.offLr + m.Cpos[c0 + t - 1]] = l;
+            v[m.offLr + (j < kDepPre ? cpos[j] : m.Cpos[c0 + t - 1])] = l;
         }
     }
-    __threadfence();
+    // one release by lane 0 after the warp barrier publishes every lane's
+    // entries (the barrier orders them before it; a release is cumulative)
     __syncwarp();
     if (lane == 0) st_release_u32(done + c, epoch);
     return true;
