@@ -60,9 +60,24 @@ __global__ void __launch_bounds__(kTailInvWarps * 32) k_tail_inverse(const ClMat
     int *Ld = reinterpret_cast<int *>(wp + kTailInvWarps * D);
     int *cp = Ld + ne;                                      // [nt + 1]
     int *dep = cp + nt + 1, *par = dep + nt;
-    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
-        Lv[q] = double(F[m.tcpos[q]]);
-        Ld[q] = m.tcdep[q];
+    // the top's entries gathered from the factor, eight per thread in
+    // flight (the positions first, then the values): the gather is most of
+    // this kernel's time
+    const int bd = int(blockDim.x);
+    for (int q0 = threadIdx.x; q0 < ne; q0 += 8 * bd) {
+        int pos[8];
+        T val[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int q = q0 + u * bd;
+            pos[u] = q < ne ? m.tcpos[q] : 0;
+            if (q < ne) Ld[q] = m.tcdep[q];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) val[u] = q0 + u * bd < ne ? F[pos[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (q0 + u * bd < ne) Lv[q0 + u * bd] = double(val[u]);
     }
     for (int i = threadIdx.x; i <= nt; i += blockDim.x) cp[i] = m.tcp[i];
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
@@ -539,21 +554,18 @@ cudaError_t launch_tail_w(const DevMat &m, int prec, const void *F, double *Wd, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_cl_inverse(const ClMat &m, const double *F, double *W, cudaStream_t s) {
+    if (m.nt == 0) return cudaSuccess;
+    const size_t smem = tail_inverse_smem(m.nt, m.ntail_e, m.tdepth_max);
+    cudaError_t e = cudaFuncSetAttribute(k_tail_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e != cudaSuccess) return e;
+    k_tail_inverse<double><<<(m.nt + kTailInvWarps - 1) / kTailInvWarps, kTailInvWarps * 32, smem, s>>>(m, F, W);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0, const double *F1,
                               double *W0, double *W1, cudaStream_t s) {
-    const ClMat *mm[2] = {&m0, &m1};
-    const double *FF[2] = {F0, F1};
-    double *WW[2] = {W0, W1};
-    for (int w = 0; w < 2; w++) {
-        const ClMat &m = *mm[w];
-        if (m.nt == 0) continue;
-        const size_t smem = tail_inverse_smem(m.nt, m.ntail_e, m.tdepth_max);
-        cudaError_t e = cudaFuncSetAttribute(k_tail_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
-        if (e != cudaSuccess) return e;
-        k_tail_inverse<double><<<(m.nt + kTailInvWarps - 1) / kTailInvWarps, kTailInvWarps * 32, smem, s>>>(
-            m, FF[w], WW[w]);
-    }
     const int nc = m0.n_gwcol > m1.n_gwcol ? m0.n_gwcol : m1.n_gwcol;
     if (nc > 0) k_cl_group_w<<<dim3(unsigned((nc + 255) / 256), 2), 256, 0, s>>>(m0, m1, F0, F1);
     const int nm = m0.n_gm > m1.n_gm ? m0.n_gm : m1.n_gm;

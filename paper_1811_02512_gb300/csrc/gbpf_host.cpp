@@ -1730,13 +1730,25 @@ pf_status prepare_lowrank(pf_ctx *ctx, int prec, cudaStream_t s) {
 // instances) the two factorisations are independent chains of dependent
 // columns: B'' runs on a second stream beside B', each launch capped at one
 // block per SM so both are resident at once.
-pf_status factor_both(pf_ctx *ctx, int prec, cudaStream_t s, bool lowrank) {
+pf_status factor_both(pf_ctx *ctx, int prec, cudaStream_t s, bool lowrank, bool cl_inverse = false) {
     Workspace &w = ctx->ws;
     const int ninst = lowrank ? 1 : ctx->dc.ninst;
     const bool dep = ctx->tune.factor == 1 || (ctx->tune.factor == 0 && ninst < ctx->num_sms / 2);
+    // the cluster engine's top inverse of a matrix follows that matrix's
+    // factorisation on its own stream, so the shorter chain's inverse runs
+    // while the longer chain is still factorising
+    auto inverse = [&](int which, cudaStream_t st) -> pf_status {
+        if (!cl_inverse) return PF_OK;
+        cudaError_t e = counted(ctx, PF_K_FACTOR, 1, st, [&] {
+            return launch_cl_inverse(ctx->cl[which], w.F64[which], ctx->clW[which], st);
+        });
+        return e == cudaSuccess ? PF_OK : cuda_fail(ctx, e, "top inverse");
+    };
     if (!dep) {
         TRY(factor_matrix(ctx, PF_MAT_BP, prec, s, 2, ninst));
+        TRY(inverse(PF_MAT_BP, s));
         TRY(factor_matrix(ctx, PF_MAT_BPP, prec, s, 2, ninst));
+        TRY(inverse(PF_MAT_BPP, s));
         return PF_OK;
     }
     if (!w.side) {
@@ -1749,7 +1761,9 @@ pf_status factor_both(pf_ctx *ctx, int prec, cudaStream_t s, bool lowrank) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(w.side, w.fork, 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fork");
     TRY(factor_matrix(ctx, PF_MAT_BPP, prec, w.side, 1, ninst));
+    TRY(inverse(PF_MAT_BPP, w.side));
     TRY(factor_matrix(ctx, PF_MAT_BP, prec, s, 1, ninst));
+    TRY(inverse(PF_MAT_BP, s));
     e = cudaEventRecord(w.join, w.side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join, 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "join");
@@ -2318,7 +2332,7 @@ pf_status issue_fdpf(pf_ctx *ctx, const pf_run_opts *opts, double *vm_dev, doubl
     }
     if (engine == PF_ENGINE_CLUSTER) {
         TRY(ensure_cluster(ctx));
-        TRY(factor_both(ctx, prec, s, false));
+        TRY(factor_both(ctx, prec, s, false, true));
         cudaError_t e = counted(ctx, PF_K_FACTOR, 1, s, [&] {
             return launch_cl_prepare(ctx->cl[0], ctx->cl[1], w.F64[0], w.F64[1], ctx->clW[0], ctx->clW[1], s);
         });

@@ -595,9 +595,12 @@ cudaError_t lane_run(const LaneRun &r, cudaStream_t s);
 int lane_width(int nmax, int prec, size_t smem_optin);
 
 // Single-case engine with the substitutions spread over a cluster
-// (gbpf_cluster.cu): the tail inverses and packed values of both matrices
-// after a factorisation (W0/W1: nt^2 doubles of scratch each), and the
-// iteration kernel (smem: dynamic shared memory of one CTA).
+// (gbpf_cluster.cu): the top set's inverse of one matrix after its
+// factorisation (W: nt^2 doubles of scratch, launched on that matrix's
+// stream), the groups' inverses and packed values of both matrices once
+// both inverses are done, and the iteration kernel (smem: dynamic shared
+// memory of one CTA).
+cudaError_t launch_cl_inverse(const ClMat &m, const double *F, double *W, cudaStream_t s);
 cudaError_t launch_cl_prepare(const ClMat &m0, const ClMat &m1, const double *F0, const double *F1,
                               double *W0, double *W1, cudaStream_t s);
 cudaError_t launch_fdpf_cl(const DevNet &dn, const DevCases &dc, const ClMat &m0, const ClMat &m1,
