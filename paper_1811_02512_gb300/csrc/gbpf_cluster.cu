@@ -323,7 +323,8 @@ __device__ double cl_mismatch(const ClRun &a, int rank, int which, const uint32_
     const int *rhsref = a.m[which].rhsref;
     const bool wantP = full || which == 0, wantQ = full || which == 1;
     unsigned long long mx = 0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    for (int q = i0 + threadIdx.x; q < i1; q += blockDim.x) {
+        const int i = C == kClCtas ? dn.mis_ord_cl[q] : q;  // a warp's rows of one length
         double ir, ii;
         bus_current(dn, i, -1, e, f, ir, ii);
         const int t = dn.btype[i];

@@ -88,7 +88,8 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
     double *xg = a.xg + (long long)c * 3 * nbus;
     const bool wantP = full || which == 0, wantQ = full || which == 1;
     unsigned long long mx = 0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    for (int q = i0 + threadIdx.x; q < i1; q += blockDim.x) {
+        const int i = C == 1 ? dn.mis_ord[q] : q;  // a warp's rows of one length
         double ir, ii;
         bus_current(dn, i, outage, e, f, ir, ii);
         const int t = dn.btype[i];

@@ -1471,6 +1471,8 @@ pf_status ensure_device(pf_ctx *ctx) {
         dn.noff = int(ctx->yoff.size());
         if ((st = upload(ctx, &dn.yoff, ctx->yoff.data(), ctx->yoff.size()))) break;
         if ((st = upload(ctx, &dn.yoff_br, ctx->yoff_br.data(), ctx->yoff_br.size()))) break;
+        if ((st = upload(ctx, &dn.mis_ord, ctx->mis_ord.data(), ctx->mis_ord.size()))) break;
+        if ((st = upload(ctx, &dn.mis_ord_cl, ctx->mis_ord_cl.data(), ctx->mis_ord_cl.size()))) break;
         if ((st = dalloc(ctx, &dn.G, dn.nnz))) break;
         if ((st = dalloc(ctx, &dn.B, dn.nnz))) break;
         if ((st = dalloc(ctx, &dn.Bp, dn.nnz))) break;
@@ -2049,6 +2051,22 @@ pf_status pf_create(const pf_bus *bus, int32_t nbus, const pf_branch *branch, in
                 ctx->yoff_br.insert(ctx->yoff_br.end(), at[p].begin(), at[p].end());
                 ctx->yoff.push_back(int4{p, lo, int(ctx->yoff_br.size()), 0});
             }
+    }
+    {   // the mismatch's thread order: buses by row length within a range
+        auto by_len = [&](std::vector<int> &ord, int i0, int i1) {
+            std::stable_sort(ord.begin() + i0, ord.begin() + i1, [&](int x, int y) {
+                return ctx->rowptr[x + 1] - ctx->rowptr[x] < ctx->rowptr[y + 1] - ctx->rowptr[y];
+            });
+        };
+        ctx->mis_ord.resize(nbus);
+        for (int i = 0; i < nbus; i++) ctx->mis_ord[i] = i;
+        ctx->mis_ord_cl = ctx->mis_ord;
+        by_len(ctx->mis_ord, 0, nbus);
+        const int slice = (nbus + kClCtas - 1) / kClCtas;  // the cluster engine's bus slices
+        for (int r = 0; r < kClCtas; r++) {
+            const int i0 = std::min(nbus, r * slice), i1 = std::min(nbus, i0 + slice);
+            by_len(ctx->mis_ord_cl, i0, i1);
+        }
     }
     for (int e = 0; e < nbranch; e++) {
         const int a = branch[e].from, b = branch[e].to;

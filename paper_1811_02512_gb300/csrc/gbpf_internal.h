@@ -300,6 +300,13 @@ struct DevNet {
     int noff = 0;
     int4 *yoff = nullptr;
     int *yoff_br = nullptr;
+    // Thread order of the nodal mismatch: the buses by Ybus row length
+    // (stable), over the whole grid (mis_ord, one CTA per case) and within
+    // each of the kClCtas slices of the cluster engine (mis_ord_cl).  An
+    // FP64 instruction costs a GB300 SM sub-partition the same whatever
+    // number of its warp's lanes is active, so a warp's rows should be of
+    // one length.
+    int *mis_ord = nullptr, *mis_ord_cl = nullptr;
 };
 
 struct DevCases {
@@ -412,6 +419,7 @@ struct pf_ctx {
     bool on_device = false;   // network and symbolic data uploaded
     std::vector<int> ydiag, inc_ptr, inc_br, inc_side, inc_pos, br_pos, yoff_br;
     std::vector<int4> yoff;
+    std::vector<int> mis_ord, mis_ord_cl;
     int device = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
