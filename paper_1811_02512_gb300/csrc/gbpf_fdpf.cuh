@@ -226,7 +226,8 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
             __syncthreads();
             if (k >= a.ir_max) break;
             unsigned long long rk = 0;
-            for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
+            for (int qr = threadIdx.x; qr < m.n; qr += blockDim.x) {
+                const int r = m.Aord[qr];  // a warp's rows of one length
                 const double s = residual_row<T, double>(m, A, xg, x64, r, lr);
                 xv[r] = T(s);
                 const unsigned long long q = abs_key(s);

@@ -758,6 +758,10 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
             }
             H.Ap[r + 1] = int(H.Aj.size());
         }
+        H.Aord.resize(n);
+        for (int r = 0; r < n; r++) H.Aord[r] = r;
+        std::stable_sort(H.Aord.begin(), H.Aord.end(),
+                         [&](int x, int y) { return H.Ap[x + 1] - H.Ap[x] < H.Ap[y + 1] - H.Ap[y]; });
     }
     TRY(make_pieces(H.Fp, true, 12, 12, H.pf, H.nlev));
     TRY(make_pieces(H.Cp, false, 12, 12, H.pb, H.nlev));
@@ -1117,6 +1121,37 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P, int group) {
             }
         };
         auto close = [&]() { maxlen = std::max(maxlen, int(refs.size()) - tasks.back().w); };
+        // the tasks of a step (from tb on) by entry count, each task's own
+        // entries unchanged: a warp's lanes then take tasks of one length
+        // (an FP64 instruction costs its warp the same whatever number of
+        // lanes it serves)
+        auto sort_step = [&](int tb) {
+            const int te = int(tasks.size());
+            if (te - tb < 2) return;
+            auto end_of = [&](int t) { return t + 1 < te ? tasks[t + 1].w : int(refs.size()); };
+            std::vector<int> ord(te - tb);
+            for (int k = 0; k < te - tb; k++) ord[k] = k;
+            std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+                return end_of(tb + x) - tasks[tb + x].w < end_of(tb + y) - tasks[tb + y].w;
+            });
+            const int base = tasks[tb].w;
+            std::vector<int4> nt_(te - tb), ne_;
+            std::vector<int> nr_;
+            std::vector<int> at(te - tb);
+            for (int k = 0; k < te - tb; k++) {
+                const int t = tb + ord[k];
+                nt_[k] = tasks[t];
+                nt_[k].w = base + int(nr_.size());
+                nr_.insert(nr_.end(), refs.begin() + tasks[t].w, refs.begin() + end_of(t));
+                ne_.insert(ne_.end(), esrc.begin() + tasks[t].w, esrc.begin() + end_of(t));
+                at[ord[k]] = tb + k;
+            }
+            std::copy(nt_.begin(), nt_.end(), tasks.begin() + tb);
+            std::copy(nr_.begin(), nr_.end(), refs.begin() + base);
+            std::copy(ne_.begin(), ne_.end(), esrc.begin() + base);
+            for (int &t : dtask)
+                if (t >= tb) t = at[t - tb];
+        };
         // a step over the tasks added since tb; cluster = 1: a cluster barrier follows
         auto step = [&](int tb, int cluster) {
             int G = 1;
@@ -1147,6 +1182,7 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P, int group) {
                 }
                 close();
             }
+            sort_step(tb);
             if (int(tasks.size()) > tb) step(tb, 0);
         }
         step(int(tasks.size()), 1);
@@ -1178,6 +1214,7 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P, int group) {
                     }
                     close();
                 }
+                sort_step(tb);
                 step(tb, 1);
             }
         }
@@ -1203,6 +1240,7 @@ pf_status build_cluster(pf_ctx *ctx, int which, HostCl &P, int group) {
                 }
                 close();
             }
+            sort_step(tb);
             if (int(tasks.size()) > tb) step(tb, 0);
         }
         step(int(tasks.size()), 1);
@@ -1331,6 +1369,7 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
     TRY(upload_padded(ctx, &D.Ap, H.Ap));
     TRY(upload_padded(ctx, &D.Aj, H.Aj));
     TRY(upload_padded(ctx, &D.Apos, H.Apos));
+    TRY(upload_padded(ctx, &D.Aord, H.Aord));
     TRY(upload(ctx, &D.pfJ, H.pfJ.data(), H.pfJ.size()));
     TRY(upload(ctx, &D.pbJ, H.pbJ.data(), H.pbJ.size()));
     TRY(upload_padded(ctx, &D.srcT, H.srcT));

@@ -137,6 +137,7 @@ struct DevMat {
     int tw_ne = 0, tw_depmax = 0;
     int *Ap = nullptr, *Aj = nullptr, *Apos = nullptr;  // off-diagonal A (no fill), by row:
                                                        // column and value slot of each entry
+    int *Aord = nullptr;       // [n] rows by entry count (stable): the residual's thread order
     // Newton-Raphson Jacobian (2 x 2 blocks on the same pattern, B' only)
     int npfJ = 0, npbJ = 0;
     Piece *pfJ = nullptr, *pbJ = nullptr;
@@ -255,6 +256,7 @@ struct HostMat {
     std::vector<int4> gl;
     std::vector<int> csc_of_steppos;  // step-numbered CSC position -> level-order CSC position
     std::vector<int> Ap, Aj, Apos;    // off-diagonal pattern of A by row (both triangles, no fill)
+    std::vector<int> Aord;            // rows by entry count (stable)
     std::vector<Piece> pfJ, pbJ;
     std::vector<int> srcT;
     int jD = 0, jDi = 0, jLc = 0, jUc = 0, jLr = 0, jUr = 0, jstride = 0;
