@@ -217,7 +217,9 @@ struct ClSmem {
 
 // One step of a sweep in this CTA: for each task t of the step,
 // X[out] = (diag ? vals[diag] X[in] : X[in]) - sum_e vals[e] X(addr[e]),
-// with G lanes per task (up to four entries per lane in flight, the lanes'
+// with G lanes per task (up to four entries per lane loaded at once and
+// summed on one chain -- a warp's FP64 instructions do not overlap on
+// GB300, so split chains would only add the combining ones -- the lanes'
 // partial sums shuffle-reduced in lane order: the order of operations is
 // fixed).  Warps without a task skip the step: on GB300 the FP64 pipe
 // (about 1.7 FMA per cycle per SM) is shared by all warps, so idle
@@ -226,22 +228,22 @@ __device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
     const int G = si.z;
     if (G == 1) {
         // one thread per task (most subtree levels): exactly one multiply-add
-        // per entry, in two chains
+        // per entry, on one chain
         for (int t = si.x + int(threadIdx.x); t < si.y; t += kClThreads) {
             const int4 tk = S.tasks[t];
             const int e1 = S.tasks[t + 1].w;
             const double b = S.X[tk.y];
             const double dv = tk.z >= 0 ? S.vals[tk.z] : 1.0;
-            double acc = 0.0, a1 = 0.0;
+            double acc = 0.0;
             int e = tk.w;
             for (; e + 4 <= e1; e += 4) {
                 const uint32_t p0 = S.addr[e], p1 = S.addr[e + 1], p2 = S.addr[e + 2], p3 = S.addr[e + 3];
                 const double v0 = S.vals[e], v1 = S.vals[e + 1], v2 = S.vals[e + 2], v3 = S.vals[e + 3];
                 const double x0 = ld_cl(p0), x1 = ld_cl(p1), x2 = ld_cl(p2), x3 = ld_cl(p3);
                 acc = fma(v0, x0, acc);
-                a1 = fma(v1, x1, a1);
+                acc = fma(v1, x1, acc);
                 acc = fma(v2, x2, acc);
-                a1 = fma(v3, x3, a1);
+                acc = fma(v3, x3, acc);
             }
             const int r = e1 - e;  // 0 to 3 entries left
             if (r > 0) {
@@ -249,10 +251,10 @@ __device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
                 const double v0 = S.vals[e], v1 = S.vals[r > 1 ? e + 1 : e], v2 = S.vals[r > 2 ? e + 2 : e];
                 const double x0 = ld_cl(p0), x1 = ld_cl(p1), x2 = ld_cl(p2);
                 acc = fma(v0, x0, acc);
-                if (r > 1) a1 = fma(v1, x1, a1);
+                if (r > 1) acc = fma(v1, x1, acc);
                 if (r > 2) acc = fma(v2, x2, acc);
             }
-            S.X[tk.x] = fma(dv, b, -(acc + a1));
+            S.X[tk.x] = fma(dv, b, -acc);
         }
         return;
     }
@@ -272,7 +274,6 @@ __device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
             // values, then their words, then the multiply-adds
             b = S.X[tk.y];
             if (tk.z >= 0) dv = S.vals[tk.z];
-            double a1 = 0.0;
             for (int e = tk.w + gl; e < e1; e += 4 * G) {
                 uint32_t p[4];
                 double v[4], x[4];
@@ -285,11 +286,10 @@ __device__ __forceinline__ void cl_step(const ClSmem &S, int4 si) {
 #pragma unroll
                 for (int u = 0; u < 4; u++) x[u] = e + u * G < e1 ? ld_cl(p[u]) : 0.0;
                 acc = fma(v[0], x[0], acc);
-                a1 = fma(v[1], x[1], a1);
-                acc = fma(v[2], x[2], acc);
-                a1 = fma(v[3], x[3], a1);
+                if (e + G < e1) acc = fma(v[1], x[1], acc);
+                if (e + 2 * G < e1) acc = fma(v[2], x[2], acc);
+                if (e + 3 * G < e1) acc = fma(v[3], x[3], acc);
             }
-            acc += a1;
         }
         for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (act && gl == 0) S.X[tk.x] = fma(dv, b, -acc);

@@ -390,8 +390,10 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
     }
     // level table, per-target descriptors and warp tasks of the tail factor,
     // so that its level loop needs no dependent global loads.  Within a level
-    // every target gets the smallest power of two of lanes G that leaves at
-    // most four terms to a lane (at most 32); the level's targets are
+    // every target gets the smallest power of two of lanes G that leaves one
+    // term to a lane (at most 32: a GB300 FP64 instruction costs its warp
+    // the same for one lane as for 32, so a target's instructions are
+    // 2 ceil(terms / G) + log2 G, least near G = terms); the level's targets are
     // reordered by (G, terms) descending and cut into tasks of 32 / G
     // consecutive targets of one G (a warp's work), listed by decreasing
     // cost (terms per lane) so that warps taking tasks round-robin balance.
@@ -414,7 +416,7 @@ pf_status build_tail(pf_ctx *ctx, HostMat &H, MakePieces &make_pieces, RunEnds &
             for (int k = kb; k < ke; k++) {
                 const int cnt = H.tptr[k + 1] - H.tptr[k];
                 int G = 1;
-                while (G < 32 && cnt > 4 * G) G *= 2;
+                while (G < 32 && cnt > G) G *= 2;
                 ord.push_back(Tg{G, cnt, k});
             }
             std::sort(ord.begin(), ord.end(), [](const Tg &a, const Tg &b) {
