@@ -88,8 +88,11 @@ __device__ double cluster_mismatch(const RunArgs &a, int c, int rank, int which,
     double *xg = a.xg + (long long)c * 3 * nbus;
     const bool wantP = full || which == 0, wantQ = full || which == 1;
     unsigned long long mx = 0;
+    // the next bus index is read a round ahead, off the row's chain
+    int inext = i0 + int(threadIdx.x) < i1 ? (C == 1 ? dn.mis_ord[i0 + threadIdx.x] : i0 + int(threadIdx.x)) : 0;
     for (int q = i0 + threadIdx.x; q < i1; q += blockDim.x) {
-        const int i = C == 1 ? dn.mis_ord[q] : q;  // a warp's rows of one length
+        const int i = inext;  // a warp's rows of one length
+        if (q + int(blockDim.x) < i1) inext = C == 1 ? dn.mis_ord[q + blockDim.x] : q + int(blockDim.x);
         double ir, ii;
         bus_current(dn, i, outage, e, f, ir, ii);
         const int t = dn.btype[i];
@@ -226,8 +229,7 @@ __device__ bool rank0_solve(const RunArgs &a, Ring *R, unsigned char *stages, T 
             __syncthreads();
             if (k >= a.ir_max) break;
             unsigned long long rk = 0;
-            for (int qr = threadIdx.x; qr < m.n; qr += blockDim.x) {
-                const int r = m.Aord[qr];  // a warp's rows of one length
+            for (int r = threadIdx.x; r < m.n; r += blockDim.x) {
                 const double s = residual_row<T, double>(m, A, xg, x64, r, lr);
                 xv[r] = T(s);
                 const unsigned long long q = abs_key(s);

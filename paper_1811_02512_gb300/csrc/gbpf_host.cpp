@@ -760,10 +760,6 @@ pf_status build_layout(pf_ctx *ctx, HostMat &H) {
             }
             H.Ap[r + 1] = int(H.Aj.size());
         }
-        H.Aord.resize(n);
-        for (int r = 0; r < n; r++) H.Aord[r] = r;
-        std::stable_sort(H.Aord.begin(), H.Aord.end(),
-                         [&](int x, int y) { return H.Ap[x + 1] - H.Ap[x] < H.Ap[y + 1] - H.Ap[y]; });
     }
     TRY(make_pieces(H.Fp, true, 12, 12, H.pf, H.nlev));
     TRY(make_pieces(H.Cp, false, 12, 12, H.pb, H.nlev));
@@ -1371,7 +1367,6 @@ pf_status upload_matrix(pf_ctx *ctx, const HostMat &H, DevMat &D) {
     TRY(upload_padded(ctx, &D.Ap, H.Ap));
     TRY(upload_padded(ctx, &D.Aj, H.Aj));
     TRY(upload_padded(ctx, &D.Apos, H.Apos));
-    TRY(upload_padded(ctx, &D.Aord, H.Aord));
     TRY(upload(ctx, &D.pfJ, H.pfJ.data(), H.pfJ.size()));
     TRY(upload(ctx, &D.pbJ, H.pbJ.data(), H.pbJ.size()));
     TRY(upload_padded(ctx, &D.srcT, H.srcT));
@@ -2102,7 +2097,9 @@ pf_status pf_create(const pf_bus *bus, int32_t nbus, const pf_branch *branch, in
         ctx->mis_ord.resize(nbus);
         for (int i = 0; i < nbus; i++) ctx->mis_ord[i] = i;
         ctx->mis_ord_cl = ctx->mis_ord;
-        by_len(ctx->mis_ord, 0, nbus);
+        // within windows of 1,024 consecutive buses: a warp's rows of one
+        // length while the block's accesses stay within a window's sectors
+        for (int i0 = 0; i0 < nbus; i0 += 1024) by_len(ctx->mis_ord, i0, std::min(nbus, i0 + 1024));
         const int slice = (nbus + kClCtas - 1) / kClCtas;  // the cluster engine's bus slices
         for (int r = 0; r < kClCtas; r++) {
             const int i0 = std::min(nbus, r * slice), i1 = std::min(nbus, i0 + slice);

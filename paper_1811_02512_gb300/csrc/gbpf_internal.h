@@ -137,7 +137,6 @@ struct DevMat {
     int tw_ne = 0, tw_depmax = 0;
     int *Ap = nullptr, *Aj = nullptr, *Apos = nullptr;  // off-diagonal A (no fill), by row:
                                                        // column and value slot of each entry
-    int *Aord = nullptr;       // [n] rows by entry count (stable): the residual's thread order
     // Newton-Raphson Jacobian (2 x 2 blocks on the same pattern, B' only)
     int npfJ = 0, npbJ = 0;
     Piece *pfJ = nullptr, *pbJ = nullptr;
@@ -256,7 +255,6 @@ struct HostMat {
     std::vector<int4> gl;
     std::vector<int> csc_of_steppos;  // step-numbered CSC position -> level-order CSC position
     std::vector<int> Ap, Aj, Apos;    // off-diagonal pattern of A by row (both triangles, no fill)
-    std::vector<int> Aord;            // rows by entry count (stable)
     std::vector<Piece> pfJ, pbJ;
     std::vector<int> srcT;
     int jD = 0, jDi = 0, jLc = 0, jUc = 0, jLr = 0, jUr = 0, jstride = 0;
@@ -303,8 +301,9 @@ struct DevNet {
     int4 *yoff = nullptr;
     int *yoff_br = nullptr;
     // Thread order of the nodal mismatch: the buses by Ybus row length
-    // (stable), over the whole grid (mis_ord, one CTA per case) and within
-    // each of the kClCtas slices of the cluster engine (mis_ord_cl).  An
+    // (stable), within windows of 1,024 buses (mis_ord, one CTA per case)
+    // and within each of the kClCtas slices of the cluster engine
+    // (mis_ord_cl).  An
     // FP64 instruction costs a GB300 SM sub-partition the same whatever
     // number of its warp's lanes is active, so a warp's rows should be of
     // one length.
