@@ -3134,6 +3134,34 @@ int gbpf_debug_pieces(const pf_ctx *ctx, int which, int list, int *count, int *o
 // Cr (nnz), gp (n + nnz + 1) and gl (4 ints per term) are copied when cap (ints
 // per array) covers them.  Returns 0, or -1 for a bad argument or a matrix
 // that has not been analysed.
+// Test hook (host only, no GPU needed): the admittance assembly's per-entry
+// tables and the mismatch's thread orders.  sizes[3] receives {nbus, nnz,
+// off-diagonal entries, branch references}; when cap (ints per array)
+// covers them, rowptr (nbus + 1), col (nnz), yoff (4 per off-diagonal
+// entry), yoff_br, mis_ord and mis_ord_cl (nbus each) are copied.  Returns
+// 0, or -1 for a bad argument.
+int gbpf_debug_net_tables(const pf_ctx *ctx, long long *sizes, int *rowptr, int *col, int *yoff, int *yoff_br,
+                          int *mis_ord, int *mis_ord_cl, long long cap) {
+    if (!ctx || !sizes) return -1;
+    sizes[0] = ctx->nbus;
+    sizes[1] = (long long)ctx->col.size();
+    sizes[2] = (long long)ctx->yoff.size();
+    sizes[3] = (long long)ctx->yoff_br.size();
+    if (rowptr && cap > ctx->nbus) std::copy(ctx->rowptr.begin(), ctx->rowptr.end(), rowptr);
+    if (col && cap >= sizes[1]) std::copy(ctx->col.begin(), ctx->col.end(), col);
+    if (yoff && cap >= 4 * sizes[2])
+        for (size_t k = 0; k < ctx->yoff.size(); k++) {
+            yoff[4 * k] = ctx->yoff[k].x;
+            yoff[4 * k + 1] = ctx->yoff[k].y;
+            yoff[4 * k + 2] = ctx->yoff[k].z;
+            yoff[4 * k + 3] = ctx->yoff[k].w;
+        }
+    if (yoff_br && cap >= sizes[3]) std::copy(ctx->yoff_br.begin(), ctx->yoff_br.end(), yoff_br);
+    if (mis_ord && cap >= ctx->nbus) std::copy(ctx->mis_ord.begin(), ctx->mis_ord.end(), mis_ord);
+    if (mis_ord_cl && cap >= ctx->nbus) std::copy(ctx->mis_ord_cl.begin(), ctx->mis_ord_cl.end(), mis_ord_cl);
+    return 0;
+}
+
 int gbpf_debug_gather(const pf_ctx *ctx, int which, long long *sizes, int *Cp, int *Cr, int *gp,
                       int *gl, long long cap) {
     if (!ctx || !sizes || which < 0 || which > 1) return -1;

@@ -446,8 +446,8 @@ __device__ __forceinline__ void tail_barrier() {
 // gather target, the level table and, double-buffered, the packed terms,
 // target descriptors and warp tasks of one level.  Level by level the warps
 // take the level's tasks round-robin; a task is 32 / G targets of G lanes
-// each (G chosen per target on the host for about four terms per lane), so
-// a target with many terms gets many lanes whatever the level's width; each
+// each (G chosen per target on the host for one term per lane, at most 32),
+// so a target with many terms gets many lanes whatever the level's width; each
 // target subtracts its terms from tail columns (the level's tables were
 // staged while the previous level was computed).  Within the tail the
 // entries are kept unnormalised, U(i,c) = L(i,c) D(c), so that an update

@@ -418,6 +418,55 @@ def test_sweep_pieces_with_scatter_tail(lib, oracle, cfg):
     g.close()
 
 
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_admittance_tables_and_mismatch_orders(lib, cfg):
+    """The per-entry admittance tables list, for every off-diagonal Ybus entry
+    (i, j) exactly once, the branches between buses i and j in ascending
+    order (out-of-service ones included: the kernel skips them); the
+    mismatch's thread orders are permutations that keep every bus in its
+    window of 1,024 (mis_ord) or its cluster slice (mis_ord_cl) and order
+    each window or slice by Ybus row length, stably."""
+    case = gridgen.config_raw(cfg)
+    g = gbpf.Grid(case)
+    f = lib.gbpf_debug_net_tables
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_void_p] + [C.c_void_p] * 6 + [C.c_longlong]
+    sz = np.zeros(4, np.int64)
+    assert f(g.ctx, sz.ctypes.data, None, None, None, None, None, None, 0) == 0
+    nbus, nnz, noff, nref = (int(v) for v in sz)
+    cap = max(nbus + 1, nnz, 4 * noff, nref)
+    rowptr, col, yoff, ybr, mo, mc = (np.zeros(cap, np.int32) for _ in range(6))
+    assert f(g.ctx, sz.ctypes.data, rowptr.ctypes.data, col.ctypes.data, yoff.ctypes.data, ybr.ctypes.data,
+             mo.ctypes.data, mc.ctypes.data, cap) == 0
+    rowptr, col, ybr, mo, mc = rowptr[:nbus + 1], col[:nnz], ybr[:nref], mo[:nbus], mc[:nbus]
+    yoff = yoff[:4 * noff].reshape(noff, 4)
+    assert noff == nnz - nbus
+    row = np.repeat(np.arange(nbus), np.diff(rowptr))
+    offd = np.nonzero(col != row)[0]
+    assert np.array_equal(np.sort(yoff[:, 0]), offd)
+    between = {}
+    for e, (a, b) in enumerate(zip(case.f, case.t)):
+        between.setdefault((int(a), int(b)), []).append(e)
+        between.setdefault((int(b), int(a)), []).append(e)
+    for p, lo, hi, _ in yoff:
+        assert list(ybr[lo:hi]) == sorted(between.get((int(row[p]), int(col[p])), []))
+    length = np.diff(rowptr)
+    assert np.array_equal(np.sort(mo), np.arange(nbus)) and np.array_equal(np.sort(mc), np.arange(nbus))
+    for i0 in range(0, nbus, 1024):
+        w = mo[i0:i0 + 1024]
+        assert w.min() >= i0 and w.max() < i0 + 1024
+        assert np.all(np.diff(length[w]) >= 0)
+    sl = (nbus + 15) // 16
+    for r in range(16):
+        w = mc[r * sl:(r + 1) * sl]
+        if w.size:
+            assert w.min() >= r * sl and w.max() < (r + 1) * sl
+            assert np.all(np.diff(length[w]) >= 0)
+            eq = np.diff(length[w]) == 0
+            assert np.all(np.diff(w)[eq] > 0)  # stable: equal lengths keep bus order
+    g.close()
+
+
 def _gather(lib, g, which):
     f = lib.gbpf_debug_gather
     f.restype = C.c_int
