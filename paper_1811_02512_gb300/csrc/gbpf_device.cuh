@@ -744,11 +744,14 @@ __device__ bool block_solve(Ring *R, unsigned char *stages, const DevMat &m, con
 // (each step squares the relative error), started from the correctly rounded
 // FP32 reciprocal (relative error below 2^-24): two steps reach the FP64
 // rounding level (within an ulp or two of the quotient; a self-test checks
-// this against CUDA's division).  Outside the FP32 range, or for a zero or
-// non-finite v, the plain division.
+// this against CUDA's division).  Outside [2^-99, 2^99) -- well inside the
+// FP32 range -- or for a zero or non-finite v, the plain division.  The
+// range is read from the exponent field with integer instructions: on GB300
+// every FP64 instruction, a compare included, costs its warp about 64
+// cycles, and this sits on the factorisations' level chain.
 __device__ __forceinline__ double pivot_recip(double v) {
-    const double a = fabs(v);
-    if (!(a >= 1e-30 && a <= 1e30)) return 1.0 / v;
+    const unsigned ex = (unsigned(__double2hiint(v)) >> 20) & 0x7ffu;  // biased exponent
+    if (ex < 1023u - 99u || ex >= 1023u + 99u) return 1.0 / v;
     double r = double(__frcp_rn(float(v)));
     r = fma(r, fma(-v, r, 1.0), r);
     r = fma(r, fma(-v, r, 1.0), r);

@@ -162,7 +162,10 @@ constexpr int kClCtas = 16;
 constexpr int kClGroupMax = 8;     // subtree levels per grouped step (at most)
 constexpr int kClGroupDefault = 3; // subtree levels per step unless the tuning names another
 constexpr int kClTailMax = 2048;   // largest tail whose dense inverse is formed
-constexpr int kTailInvWarps = 16;  // T columns (one per warp) per block of k_tail_inverse
+// T columns (one per warp) per block of k_tail_inverse: one warp per SM
+// sub-partition, so that no two warps' chains of FP64 instructions share an
+// FP64 unit
+constexpr int kTailInvWarps = 4;
 // shared memory of k_tail_inverse for a tail of nt rows with ne entries and
 // paths of at most depth_max nodes (a tail whose need exceeds kTailInvSmem
 // gets no inverse)
